@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark: Kalman-MPC control steps per second on one B300 (or N replicas).
+
+A step is one receding-horizon control step of Algorithm 1 -- ensemble
+initialisation, H predictions through the CNN surrogate and H ensemble Kalman
+analyses, then the plant update with the smoothed control -- on the
+64 x 64 working workload (l = 8, CNN 2-32-32-1, N = 256 members, H = 10),
+noise drawn on the device (Philox).  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (a 256 MB write) between timed steps, outside the
+per-step events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl oic|reference]
+
+Under torchrun each rank runs an independent replica (the problems are
+independent; there is no collective on the data path) and rank 0 prints one
+JSON line with the whole-job throughput.  `--impl reference` times the FP64
+CPU oracle (the only reference this method has) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EnKS control steps/s (N×H CNN steps/s); p50/p99 solve latency vs plain FP32"
+UNIT = "control steps/s"
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        p["source"] = "measured"
+    except (OSError, ValueError):
+        p = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+             "sm_max_mhz": 2032.0, "source": "fallback"}
+    return p
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """FFMA peak: 148 SMs x 128 FP32 lanes x 2 flops x SM clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------- workload math
+def conv_layer_flops(wl, cin, cout):
+    return 2.0 * 9 * wl.n * wl.m * cin * cout
+
+
+def cnn_flops_per_member_step(wl):
+    f = 2.0 * wl.n * wl.l * wl.m                       # B U
+    for cin, cout in zip(wl.channels[:-1], wl.channels[1:]):
+        f += conv_layer_flops(wl, cin, cout)
+    return f
+
+
+def stage_work(wl, stage):
+    """Algorithmic work of ONE launch of `stage` at the working size:
+    (amount, unit, bound)."""
+    N = wl.N
+    if stage == "conv_hidden":
+        c = wl.channels[1]
+        return conv_layer_flops(wl, c, c) * N, "flop", "alu"
+    if stage == "conv_first":
+        return conv_layer_flops(wl, 2, wl.channels[1]) * N, "flop", "alu"
+    if stage == "conv_out":
+        return conv_layer_flops(wl, wl.channels[-2], 1) * N, "flop", "alu"
+    return None
+
+
+def kernel_traffic(stage):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src_files = {"conv_hidden": "cnn_kernels.cu", "conv_first": "cnn_kernels.cu",
+                 "conv_out": "cnn_kernels.cu"}
+    f = src_files.get(stage)
+    if f is None:
+        return None
+    src = os.path.join(ROOT, "paper_2410_09663_b300", "csrc", f)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if parts.get("stage") == stage and parts.get("src_sha") == sha:
+            return float(parts["dram_bytes_per_launch"])
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- the oracle
+def oracle_step_seconds(wl, N_sample, k=0):
+    """Wall time of one control step of the FP64 oracle with N_sample members."""
+    import oracle
+    w = wl.with_(N=N_sample)
+    net = oracle.Net(w.n, w.m, w.l, w.channels, w.weights(), w.B(), w.residual_scale)
+    xr = w.X_ref_all(k + 1)
+    nz = w.noise_all(k + 1)[k:k + 1]
+    t0 = time.perf_counter()
+    oracle.run(net, w.N, w.H, 1, w.X0(), w.U_init(), xr[k:], w.U_ref(), nz)
+    return time.perf_counter() - t0
+
+
+def host_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                             else os.cpu_count())
+
+
+def cpu_baseline(wl, budget_s=30.0):
+    """Oracle as it stands, one control step on a sample of the members,
+    scaled to control steps/s of the full ensemble (its cost is linear in N)."""
+    t2 = oracle_step_seconds(wl, 2)
+    n_s = int(max(2, min(wl.N, (budget_s / 2.0) / max(t2 / 2.0, 1e-3))))
+    t = oracle_step_seconds(wl, n_s) if n_s > 2 else t2
+    value = (n_s / wl.N) / t
+    return {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+            "sample": f"1 control step with {n_s} of {wl.N} members ({t:.1f} s), scaled by "
+                      f"{n_s}/{wl.N} (oracle cost is linear in N)"}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    total = args.steps + args.warmup
+    t2 = oracle_step_seconds(wl, 2)
+    n_s = int(max(2, min(wl.N, 2 * (150.0 / max(total, 1)) / max(t2, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_step_seconds(wl, n_s)
+    times = [oracle_step_seconds(wl, n_s, k=i % wl.S) for i in range(args.steps)]
+    t = sum(times)
+    value = args.steps * (n_s / wl.N) / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps * wl.N / n_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+                             "sample": f"each step: 1 control step with {n_s} of {wl.N} members, "
+                                       f"scaled by {n_s}/{wl.N}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(wl, extra=None):
+    d = {"workload": wl.name, "n": wl.n, "m": wl.m, "l": wl.l, "N": wl.N, "H": wl.H,
+         "cnn": "-".join(str(c) for c in wl.channels), "precision": "fp32",
+         "noise": "philox-4x32-10 on device", "history": "U blocks + current X",
+         "l2": "flushed between timed steps (256 MB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------------- our arm
+def run_oic(args, wl):
+    import torch
+    import torch.distributed as dist
+    import paper_2410_09663_b300 as oic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = wl.with_(seed=wl.seed + rank)                 # independent replica per rank
+    w, b = wl.flat_weights()
+    cfg = oic.config_from_workload(wl, noise_mode=oic.OIC_NOISE_PHILOX)
+    stream = torch.cuda.Stream(device=dev)
+    s = oic.Solver(cfg, w, b, wl.B(), device=dev, stream=stream)
+
+    S_ref = args.steps + args.warmup + 4
+    xr_all = torch.from_numpy(wl.X_ref_all(S_ref)).to(dev)
+    ur = torch.from_numpy(wl.U_ref()).to(dev)
+    X0 = torch.from_numpy(wl.X0()).to(dev)
+    U0 = torch.from_numpy(wl.U_init()).to(dev)
+    u_out = torch.zeros(wl.l, wl.m, device=dev)
+    x_out = torch.zeros(wl.n, wl.m, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    H = wl.H
+
+    def window(k):
+        return xr_all[k:k + H + 1]
+
+    with torch.cuda.stream(stream):
+        s.oic_reset(X0, U0)
+        for k in range(args.warmup):
+            s.oic_step(window(k), ur, None, u_out, x_out)
+        stream.synchronize()
+
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        launches0 = oic.oic_launch_count()
+        s.oic_profile_begin(max_launches=128 * args.steps)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for i in range(args.steps):
+                k = args.warmup + i
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                s.oic_step(window(k), ur, None, u_out, x_out)
+                ev[i][1].record(stream)
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+        prof = s.oic_profile_end()
+        launches = oic.oic_launch_count() - launches0
+        s.oic_sync()
+        per_step = [a.elapsed_time(c) for a, c in ev]
+    t_dev = sum(per_step) / 1e3                         # seconds of device time in steps
+
+    # e2e: the host-pointer entry point, pinned host buffers, copies inside
+    xr_host = torch.from_numpy(wl.X_ref_all(S_ref)).pin_memory()
+    ur_host = torch.from_numpy(wl.U_ref()).pin_memory()
+    ua_host = torch.zeros(wl.l, wl.m).pin_memory()
+    xn_host = torch.zeros(wl.n, wl.m).pin_memory()
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    for k in range(min(3, args.warmup)):
+        s.oic_step_host_ptr(xr_host[k].data_ptr(), ur_host.data_ptr(), None, ua_host.data_ptr(),
+                            xn_host.data_ptr())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        k = args.warmup + i
+        s.oic_step_host_ptr(xr_host[k].data_ptr(), ur_host.data_ptr(), None, ua_host.data_ptr(),
+                            xn_host.data_ptr())
+    torch.cuda.synchronize(dev)
+    t_e2e = time.perf_counter() - t0
+    h2d = (H + 1) * wl.n * wl.m * 4 + wl.l * wl.m * 4
+    d2h = wl.l * wl.m * 4 + wl.n * wl.m * 4
+
+    if world > 1:
+        t = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = float(t[0]), float(t[1])
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = load_peaks()
+    clocks = clk.summary()
+    total_ms = {k: v[0] for k, v in prof.items()}
+    dominant = max(total_ms, key=total_ms.get) if total_ms else None
+    roof = None
+    if dominant is not None:
+        work = stage_work(wl, dominant)
+        ms, n_l = prof[dominant]
+        if work is not None and n_l > 0:
+            amount, unit, bound = work
+            avg_s = ms / 1e3 / n_l
+            if bound == "alu":
+                peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+                roof = {"bound": "alu", "kernel": dominant, "achieved": amount / avg_s / 1e12,
+                        "peak": peak, "unit": "TFLOP/s",
+                        "frac": amount / avg_s / 1e12 / peak,
+                        "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
+                                       % (peaks.get("sm_max_mhz", 2032.0), peaks["source"]),
+                        "traffic": kernel_traffic(dominant),
+                        "algorithmic_per_launch": amount, "launches": n_l,
+                        "avg_launch_ms": avg_s * 1e3}
+    share = {k: round(v / max(sum(total_ms.values()), 1e-12), 4) for k, v in total_ms.items()}
+    steps_total = world * args.steps
+    value = steps_total / t_dev
+    lat = sorted(per_step)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(wl, {
+            "parallelism": "replicas" if world > 1 else "single",
+            "member_steps_per_s": value * wl.N * wl.H,
+            "cnn_tflops": value * wl.N * wl.H * cnn_flops_per_member_step(wl) / 1e12,
+            "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "wall_s_timed_region": wall, "stage_share": share,
+            "stage_ms_per_step": {k: v / args.steps for k, v in total_ms.items()}}),
+        "roofline": roof,
+        "e2e": {"value": steps_total / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["oic", "reference"], default="oic")
+    ap.add_argument("--workload", default="working_64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    from paper_2410_09663_b300 import workloads
+    wl = workloads.WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_oic(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * oic.h -- C ABI of liboic.so: Kalman-MPC (optimal inferential control of a
+ * CNN surrogate by a matrix-variate single-pass ensemble Kalman smoother) on
+ * one B300 GPU (sm_103a).
+ *
+ * Method: Vaziri & Fang, "Optimal Inferential Control of Convolutional Neural
+ * Networks", arXiv 2410.09663.
+ *   CNN surrogate         X_{k+1} = CNN_theta(X_k, U_k), Eq. (1)
+ *   virtual system        Eq. (virtual-system), compact form
+ *                         Eq. (virtual-system-compact): X̄ = [X; U; dU],
+ *                         Ȳ = [X^ref; U^ref], H = [I 0 0; 0 I 0]
+ *   ensemble smoother     Eq. (mathcalX-prediction-sample-mean) ..
+ *                         Eq. (prediction-mean-cov), Algorithm 1 (Kalman-MPC)
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are row-major float32.  X is n x m (field), U is l x m
+ *     (control).  p = n + l observed rows.
+ *   - Unless an entry point says "host", array pointers are DEVICE pointers
+ *     that must stay valid until the work enqueued on the bound stream has
+ *     finished.  Entry points ending in _host take host pointers, copy through
+ *     the workspace, and return only after the stream has drained.
+ *   - Ownership: weights are copied into the handle at oic_create (the caller
+ *     may free its copies afterwards).  The device workspace and the CUDA
+ *     stream are owned by the caller (oic_bind); the library never allocates
+ *     device memory.
+ *   - Errors are returned as oic_status, never thrown and never trapped on
+ *     the device.  Device-side failures (a covariance that is not positive
+ *     definite) are recorded in a status word inside the workspace; the _host
+ *     entry points and oic_sync report it.  On OIC_ENOTSPD the failing update
+ *     is skipped (the ensemble keeps its prior) so no NaN propagates.
+ *   - Device arrays read as whole rows (noise, and E / V of oic_enks_update)
+ *     must be 16-byte aligned; m % 4 == 0 keeps every row aligned after that.
+ *   - Calls on one handle must not overlap from several host threads.
+ */
+#ifndef OIC_H
+#define OIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OIC_MAX_LAYERS 8
+
+typedef struct oic_handle oic_handle;
+
+typedef enum {
+    OIC_OK = 0,
+    OIC_EINVAL = 1,     /* bad size, null pointer, unsupported option        */
+    OIC_ENOMEM = 2,     /* workspace too small or host allocation failed     */
+    OIC_ECUDA = 3,      /* a CUDA runtime call failed                        */
+    OIC_ENOTSPD = 4,    /* Sigma^Y not positive definite in the gain solve   */
+    OIC_ETIMEOUT = 5,   /* a bounded device wait gave up                     */
+    OIC_ESTATE = 6      /* call order violated (e.g. oic_step before reset)  */
+} oic_status;
+
+typedef enum { OIC_PREC_FP32 = 0, OIC_PREC_MIXED = 1 } oic_precision;
+typedef enum { OIC_NOISE_HOST = 0, OIC_NOISE_PHILOX = 1 } oic_noise_mode;
+
+/* Problem description (Algorithm 1, Eq. (1), Eq. (virtual-system)). */
+typedef struct {
+    int n, m;            /* field X is n x m                                  */
+    int l;               /* control U is l x m                                */
+    int N;               /* ensemble members                                  */
+    int H;               /* horizon: updates at t = k+1 .. k+H                */
+    int n_layers;        /* conv layers of CNN_theta (1 .. OIC_MAX_LAYERS)    */
+    int channels[OIC_MAX_LAYERS + 1]; /* channels[0] = 2 (X and B U),
+                                        channels[n_layers] = 1               */
+    float residual_scale;             /* X_{k+1} = X_k + s * CNN output        */
+    double sigma_w, sigma_vx, sigma_vu; /* noise std of W, V_X, V_U; used by
+                                        OIC_NOISE_PHILOX to draw the noise    */
+    int precision;       /* oic_precision                                     */
+    int keep_full_history; /* 1: keep and update every X block k..k+H (X_hat
+                              output available); 0: keep the U blocks and the
+                              current X only (same U_hat, less work)          */
+    int noise_mode;      /* oic_noise_mode                                    */
+    unsigned long long seed; /* OIC_NOISE_PHILOX key                          */
+} oic_config;
+
+/* Noise buffer of one solve (OIC_NOISE_HOST), float32, contiguous:
+ *   W0 [N][l][m]    initial control spread: U_k^i = U_{k-1} + W0^i, dU_k^i = W0^i
+ *   W  [H][N][l][m] process noise of the prediction to t = k+s+1 (row s):
+ *                   U_{t} = U_{t-1} + W, dU_t = W   (Eq. (virtual-system))
+ *   VX [H][N][n][m] pseudo-observation noise of X at t = k+s+1 (Eq. (Ybar-samples))
+ *   VU [H][N][l][m] pseudo-observation noise of U at t = k+s+1
+ * Its length in floats is returned by oic_noise_floats. */
+size_t oic_noise_floats(const oic_config* cfg);
+
+/* Creates a handle.  conv_w: all layers' weights concatenated, layer k as
+ * [channels[k+1]][channels[k]][3][3] (3x3 cross-correlation, zero padding);
+ * conv_b: all biases concatenated; B: n x l.  Host pointers, copied.
+ * Sizes: n, m >= 1, m % 4 == 0, l >= 1, N >= 2, H >= 1, channels in
+ * 1 .. 256.  Returns OIC_EINVAL on bad sizes, OIC_ENOMEM on host allocation
+ * failure. */
+oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* conv_b,
+                      const float* B, oic_handle** out);
+
+/* Device workspace (bytes) the handle needs: ensemble, CNN activations,
+ * statistics, gain, plant state and staging for the _host entry points. */
+size_t oic_workspace_bytes(const oic_handle* h);
+
+/* Binds caller-owned device memory (>= oic_workspace_bytes, 256-byte
+ * aligned) and a CUDA stream (cudaStream_t, NULL = legacy default stream).
+ * Copies the weights into the workspace.  May be called again to rebind. */
+oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda_stream);
+
+/* Sets the device-resident plant state used by oic_step: X0 (n x m) and the
+ * previously applied control U_prev (l x m).  Device pointers. */
+oic_status oic_reset(oic_handle* h, const float* X0, const float* U_prev);
+
+/* One receding-horizon solve (Algorithm 1, lines 4-15) from X_k with the
+ * previously applied control U_prev.
+ *   X_ref  [(H+1)][n][m] references for times k .. k+H (index 0 unused by the
+ *          updates, kept so callers pass a whole window)
+ *   U_ref  [l][m]
+ *   noise  oic_noise_floats floats (OIC_NOISE_HOST); ignored (may be NULL)
+ *          with OIC_NOISE_PHILOX, where the k-th solve draws its noise from
+ *          (seed, solve counter)
+ *   U_hat  [(H+1)][l][m] out: smoothed control means Û_{k|k:k+H} .. Û_{k+H|k:k+H}
+ *   X_hat  [(H+1)][n][m] out, optional (NULL): smoothed field means; requires
+ *          keep_full_history (OIC_EINVAL otherwise); block 0 is X_k.
+ * Device pointers; asynchronous on the bound stream. */
+oic_status oic_solve(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
+                     const float* U_ref, const float* noise, float* U_hat, float* X_hat);
+
+/* One control step (Algorithm 1, lines 4-17) on the device-resident plant:
+ * solve from the plant state, apply U_k = Û_{k|k:k+H} to the plant
+ * X_{k+1} = CNN_theta(X_k, U_k) (the plant is the surrogate itself), and
+ * keep U_k as the next step's U_prev.  U_applied [l][m] and X_next [n][m]
+ * are optional outputs (NULL to skip).  Device pointers; asynchronous. */
+oic_status oic_step(oic_handle* h, const float* X_ref, const float* U_ref, const float* noise,
+                    float* U_applied, float* X_next);
+
+/* Host-pointer forms of oic_solve / oic_step / oic_reset: copy inputs in,
+ * run, copy outputs out, synchronise the stream, and return the device
+ * status (OIC_ENOTSPD if any update of the call failed). */
+oic_status oic_solve_host(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
+                          const float* U_ref, const float* noise, float* U_hat, float* X_hat);
+oic_status oic_step_host(oic_handle* h, const float* X_ref, const float* U_ref, const float* noise,
+                         float* U_applied, float* X_next);
+oic_status oic_reset_host(oic_handle* h, const float* X0, const float* U_prev);
+
+/* X_next[b] = CNN_theta(X[b], U[b]) for b < batch (Eq. (1)); X, X_next
+ * [batch][n][m], U [batch][l][m]; batch <= N.  Device pointers; uses the
+ * workspace's activation buffers, so it must not overlap other calls. */
+oic_status oic_cnn_forward(oic_handle* h, int batch, const float* X, const float* U,
+                           float* X_next);
+
+/* One ensemble Kalman analysis (Eq. (Ybar-samples) .. Eq.
+ * (ensemble-based-Kalman-update)) on a caller-provided ensemble:
+ *   E      [N][R][m] in/out, member i's state rows (R <= the handle's
+ *          maximum active rows, see oic_max_rows)
+ *   obs_rows (host) p_obs row indices of E observed by H (p_obs = n + l)
+ *   V      [N][p_obs][m] observation perturbations
+ *   Ybar   [p_obs][m] pseudo-observation
+ * E^i <- E^i + K (Ybar - (H E^i + V^i)), K = Sigma^{XY} (Sigma^{Y})^{-1}.
+ * Device pointers except obs_rows; asynchronous. */
+oic_status oic_enks_update(oic_handle* h, int R, const int* obs_rows, float* E, const float* V,
+                           const float* Ybar);
+int oic_max_rows(const oic_handle* h);
+
+/* Stage profiler: CUDA events recorded on the bound stream around every
+ * kernel launch of the selected stages (bit s of stage_mask selects stage s),
+ * for up to max_launches launches.  oic_profile_end waits for the stream
+ * and writes, per stage, the summed device milliseconds and the launch count
+ * (arrays of OIC_NUM_STAGES).  Recording costs no device work beyond the
+ * events themselves. */
+typedef enum {
+    OIC_STAGE_NOISE = 0,       /* Philox noise for one solve                    */
+    OIC_STAGE_INIT,            /* Algorithm 1 line 4                            */
+    OIC_STAGE_CNN_INPUT,       /* [X; B U] assembly, Eq. (1)                    */
+    OIC_STAGE_CONV_FIRST,      /* first conv layer (2 input channels), tanh     */
+    OIC_STAGE_CONV_HIDDEN,     /* hidden -> hidden conv layers, tanh            */
+    OIC_STAGE_CONV_OUT,        /* last conv layer + residual                    */
+    OIC_STAGE_U_ADVANCE,       /* U_t = U_{t-1} + W                             */
+    OIC_STAGE_MEANS,           /* ensemble means                                */
+    OIC_STAGE_COV,             /* anomaly products (split-K)                    */
+    OIC_STAGE_COV_REDUCE,      /* split-K reduction                             */
+    OIC_STAGE_GAIN,            /* Cholesky + K = Sigma^XY (Sigma^Y)^-1          */
+    OIC_STAGE_UPDATE,          /* member-wise update                            */
+    OIC_STAGE_BLOCK_MEANS,     /* smoothed output means                         */
+    OIC_NUM_STAGES
+} oic_stage;
+oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launches);
+oic_status oic_profile_end(oic_handle* h, float* ms, int* launches);
+
+/* Number of kernels this library has launched in this process. */
+unsigned long long oic_launch_count(void);
+
+/* Waits for the bound stream and returns (and clears) the device status. */
+oic_status oic_sync(oic_handle* h);
+
+/* Milliseconds of device time of the last oic_solve/oic_step (CUDA events
+ * around the call on the bound stream; valid after oic_sync). */
+float oic_last_ms(oic_handle* h);
+
+void oic_destroy(oic_handle* h);
+const char* oic_status_string(oic_status s);
+const char* oic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OIC_H */

@@ -1,1 +1,250 @@
-"""paper_2410_09663_b300 -- B300-native Kalman-MPC (placeholder, binding added next)."""
+"""paper_2410_09663_b300 -- Kalman-MPC (arXiv 2410.09663) on one B300 GPU.
+
+Thin ctypes binding over ``liboic.so`` (C ABI in ``include/oic.h``).  The
+functions below carry the C names and only marshal arguments: every step of
+the method runs in the library's CUDA kernels.  PyTorch is used for device
+memory and streams (``Solver`` allocates the workspace with torch and binds
+it).  There is no CPU fallback: if the library cannot be loaded every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = ["OIC_OK", "OICError", "oic_config", "load", "Solver", "config_from_workload"]
+
+MAX_LAYERS = 8
+OIC_OK, OIC_EINVAL, OIC_ENOMEM, OIC_ECUDA, OIC_ENOTSPD, OIC_ETIMEOUT, OIC_ESTATE = range(7)
+OIC_PREC_FP32, OIC_PREC_MIXED = 0, 1
+OIC_NOISE_HOST, OIC_NOISE_PHILOX = 0, 1
+STAGES = ["noise", "init", "cnn_input", "conv_first", "conv_hidden", "conv_out", "u_advance",
+          "means", "cov", "cov_reduce", "gain", "update", "block_means"]
+
+
+class OICError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = int(status)
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class oic_config(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int), ("m", ctypes.c_int), ("l", ctypes.c_int), ("N", ctypes.c_int),
+        ("H", ctypes.c_int), ("n_layers", ctypes.c_int),
+        ("channels", ctypes.c_int * (MAX_LAYERS + 1)),
+        ("residual_scale", ctypes.c_float),
+        ("sigma_w", ctypes.c_double), ("sigma_vx", ctypes.c_double), ("sigma_vu", ctypes.c_double),
+        ("precision", ctypes.c_int), ("keep_full_history", ctypes.c_int), ("noise_mode", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+    ]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_FP = ctypes.POINTER(ctypes.c_float)
+
+_SIGS = {
+    "oic_noise_floats": (ctypes.c_size_t, [ctypes.POINTER(oic_config)]),
+    "oic_create": (ctypes.c_int, [ctypes.POINTER(oic_config), _VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "oic_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "oic_max_rows": (ctypes.c_int, [_VP]),
+    "oic_bind": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _VP]),
+    "oic_reset": (ctypes.c_int, [_VP, _VP, _VP]),
+    "oic_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "oic_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "oic_reset_host": (ctypes.c_int, [_VP, _VP, _VP]),
+    "oic_solve_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "oic_step_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "oic_cnn_forward": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "oic_enks_update": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "oic_sync": (ctypes.c_int, [_VP]),
+    "oic_last_ms": (ctypes.c_float, [_VP]),
+    "oic_profile_begin": (ctypes.c_int, [_VP, ctypes.c_uint, ctypes.c_int]),
+    "oic_profile_end": (ctypes.c_int, [_VP, _FP, ctypes.POINTER(ctypes.c_int)]),
+    "oic_launch_count": (ctypes.c_ulonglong, []),
+    "oic_destroy": (None, [_VP]),
+    "oic_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "oic_version": (ctypes.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liboic.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise OSError(f"liboic.so not found at {path}; run python -m paper_2410_09663_b300.build")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype, f.argtypes = res, args
+        _lib = lib
+    return _lib
+
+
+def oic_launch_count() -> int:
+    return int(load().oic_launch_count())
+
+
+def status_string(s) -> str:
+    return load().oic_status_string(int(s)).decode()
+
+
+def _check(s, what):
+    if s != OIC_OK:
+        raise OICError(s, what)
+
+
+def config_from_workload(wl, precision=OIC_PREC_FP32, keep_full_history=False,
+                         noise_mode=OIC_NOISE_HOST, seed=None) -> oic_config:
+    c = oic_config()
+    c.n, c.m, c.l, c.N, c.H = wl.n, wl.m, wl.l, wl.N, wl.H
+    c.n_layers = len(wl.channels) - 1
+    for k, ch in enumerate(wl.channels):
+        c.channels[k] = ch
+    c.residual_scale = wl.residual_scale
+    c.sigma_w, c.sigma_vx, c.sigma_vu = wl.sigma_w, wl.sigma_vx, wl.sigma_vu
+    c.precision = precision
+    c.keep_full_history = int(bool(keep_full_history))
+    c.noise_mode = noise_mode
+    c.seed = wl.seed if seed is None else seed
+    return c
+
+
+def _ptr(t):
+    """Device or host address of a torch tensor (None -> NULL)."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """Owns an oic_handle plus a torch-allocated device workspace.
+
+    Methods mirror the C entry points; tensors are passed by address.
+    """
+
+    def __init__(self, cfg: oic_config, conv_w, conv_b, B, device="cuda", stream=None):
+        import numpy as np
+        import torch
+        lib = load()
+        self._lib = lib
+        self.cfg = cfg
+        w = np.ascontiguousarray(conv_w, dtype=np.float32)
+        b = np.ascontiguousarray(conv_b, dtype=np.float32)
+        Bm = np.ascontiguousarray(B, dtype=np.float32)
+        h = _VP()
+        _check(lib.oic_create(ctypes.byref(cfg), w.ctypes.data, b.ctypes.data, Bm.ctypes.data,
+                              ctypes.byref(h)), "oic_create")
+        self.h = h
+        self.ws_bytes = lib.oic_workspace_bytes(h)
+        self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        _check(lib.oic_bind(h, ctypes.c_void_p(self._ws_ptr), self.ws_bytes,
+                            ctypes.c_void_p(self.stream.cuda_stream)), "oic_bind")
+
+    # -- sizes
+    @property
+    def noise_floats(self):
+        return self._lib.oic_noise_floats(ctypes.byref(self.cfg))
+
+    @property
+    def max_rows(self):
+        return self._lib.oic_max_rows(self.h)
+
+    # -- device-pointer entry points (asynchronous on self.stream)
+    def oic_reset(self, X0, U_prev):
+        _check(self._lib.oic_reset(self.h, _ptr(X0), _ptr(U_prev)), "oic_reset")
+
+    def oic_solve(self, X_k, U_prev, X_ref, U_ref, noise, U_hat, X_hat=None):
+        _check(self._lib.oic_solve(self.h, _ptr(X_k), _ptr(U_prev), _ptr(X_ref), _ptr(U_ref),
+                                   _ptr(noise), _ptr(U_hat), _ptr(X_hat)), "oic_solve")
+
+    def oic_step(self, X_ref, U_ref, noise, U_applied=None, X_next=None):
+        _check(self._lib.oic_step(self.h, _ptr(X_ref), _ptr(U_ref), _ptr(noise), _ptr(U_applied),
+                                  _ptr(X_next)), "oic_step")
+
+    def oic_cnn_forward(self, X, U, X_next):
+        batch = X.shape[0]
+        _check(self._lib.oic_cnn_forward(self.h, batch, _ptr(X), _ptr(U), _ptr(X_next)),
+               "oic_cnn_forward")
+
+    def oic_enks_update(self, E, obs_rows, V, Ybar):
+        import numpy as np
+        rows = np.ascontiguousarray(obs_rows, dtype=np.int32)
+        _check(self._lib.oic_enks_update(self.h, int(E.shape[1]), rows.ctypes.data, _ptr(E), _ptr(V),
+                                         _ptr(Ybar)), "oic_enks_update")
+
+    # -- host-pointer entry points (synchronous); arguments are numpy arrays
+    def oic_reset_host(self, X0, U_prev):
+        import numpy as np
+        X0 = np.ascontiguousarray(X0, np.float32)
+        U_prev = np.ascontiguousarray(U_prev, np.float32)
+        _check(self._lib.oic_reset_host(self.h, X0.ctypes.data, U_prev.ctypes.data), "oic_reset_host")
+
+    def oic_solve_host(self, X_k, U_prev, X_ref, U_ref, noise, U_hat, X_hat=None):
+        import numpy as np
+        a = [np.ascontiguousarray(x, np.float32) for x in (X_k, U_prev, X_ref, U_ref)]
+        nz = None if noise is None else np.ascontiguousarray(noise, np.float32)
+        _check(self._lib.oic_solve_host(self.h, *[x.ctypes.data for x in a],
+                                        None if nz is None else nz.ctypes.data, U_hat.ctypes.data,
+                                        None if X_hat is None else X_hat.ctypes.data),
+               "oic_solve_host")
+
+    def oic_step_host(self, X_ref, U_ref, noise, U_applied=None, X_next=None):
+        import numpy as np
+        xr = np.ascontiguousarray(X_ref, np.float32)
+        ur = np.ascontiguousarray(U_ref, np.float32)
+        nz = None if noise is None else np.ascontiguousarray(noise, np.float32)
+        _check(self._lib.oic_step_host(self.h, xr.ctypes.data, ur.ctypes.data,
+                                       None if nz is None else nz.ctypes.data,
+                                       None if U_applied is None else U_applied.ctypes.data,
+                                       None if X_next is None else X_next.ctypes.data),
+               "oic_step_host")
+
+    def oic_step_host_ptr(self, X_ref_ptr, U_ref_ptr, noise_ptr, U_applied_ptr, X_next_ptr):
+        """oic_step_host with raw host addresses (e.g. pinned torch tensors)."""
+        _check(self._lib.oic_step_host(self.h, X_ref_ptr, U_ref_ptr, noise_ptr, U_applied_ptr,
+                                       X_next_ptr), "oic_step_host")
+
+    def oic_sync(self):
+        _check(self._lib.oic_sync(self.h), "oic_sync")
+
+    def oic_sync_status(self) -> int:
+        return int(self._lib.oic_sync(self.h))
+
+    def oic_last_ms(self) -> float:
+        return float(self._lib.oic_last_ms(self.h))
+
+    def oic_profile_begin(self, stages=None, max_launches=100000):
+        mask = 0
+        for st in (STAGES if stages is None else stages):
+            mask |= 1 << STAGES.index(st)
+        _check(self._lib.oic_profile_begin(self.h, mask, int(max_launches)), "oic_profile_begin")
+
+    def oic_profile_end(self):
+        """Returns {stage: (total_ms, launches)} for the profiled stages."""
+        n = len(STAGES)
+        ms = (ctypes.c_float * n)()
+        cnt = (ctypes.c_int * n)()
+        _check(self._lib.oic_profile_end(self.h, ms, cnt), "oic_profile_end")
+        return {STAGES[i]: (float(ms[i]), int(cnt[i])) for i in range(n) if cnt[i] > 0}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.oic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,615 @@
+// oic_api.cu -- the C ABI of liboic.so (declared in include/oic.h): handle,
+// workspace layout, and the host-side orchestration of Algorithm 1
+// (Kalman-MPC) over the kernels of cnn_kernels.cu, enks_kernels.cu and
+// noise_kernels.cu.  The library never allocates device memory: every buffer
+// below is carved out of the caller's workspace at oic_bind.
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "oic_internal.cuh"
+
+using namespace oic;
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+std::atomic<unsigned long long> g_launches{0};
+
+struct Profiler {
+    bool on = false;
+    unsigned mask = 0;
+    int max = 0, used = 0;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> stage;
+};
+
+struct Layout {
+    size_t w, b, B, E, act0, act1, meanE, meanY, part, C, K, rowtab, status;
+    size_t plantX, plantU, plantTmp;
+    size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
+    size_t total;
+};
+
+}  // namespace
+
+struct oic_handle {
+    oic_config cfg;
+    std::vector<float> w, b, B;
+    int L = 0, q = 0, p = 0, R_mem = 0, R_act_max = 0, Cmax = 2;
+    int Ubase = 0, splits_max = 1;
+    size_t noise_n = 0;
+    Layout lay{};
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t st = nullptr;
+    bool bound = false, plant_ready = false;
+    unsigned long long solve_counter = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<int> obs_host;
+    Profiler prof;
+
+    template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+    bool full() const { return cfg.keep_full_history != 0; }
+    int xrow(int s) const { return full() ? s * cfg.n : (s % 2) * cfg.n; }
+    int urow(int s) const { return Ubase + s * cfg.l; }
+    int R_of(int s) const {
+        return full() ? s * cfg.n + (s + 1) * cfg.l : cfg.n + (s + 1) * cfg.l;
+    }
+    long ms() const { return (long)R_mem * cfg.m; }
+    // device row tables: for s in 1..H, [act rows (R_act_max) | obs rows (p)];
+    // row H+1 holds the identity rows and the caller's obs rows of oic_enks_update
+    int* act_rows(int s) const { return at<int>(lay.rowtab) + (size_t)s * (R_act_max + p); }
+    int* obs_rows(int s) const { return act_rows(s) + R_act_max; }
+};
+
+namespace {
+
+// Runs one kernel launch of stage `stage`, counting it and, when the stage is
+// being profiled, bracketing it with CUDA events on the bound stream.
+template <typename F>
+void run_stage(oic_handle* h, int stage, F&& launch)
+{
+    Profiler& P = h->prof;
+    const bool rec = P.on && ((P.mask >> stage) & 1u) && P.used < P.max;
+    if (rec) cudaEventRecord(P.ev[2 * P.used], h->st);
+    launch();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (rec) {
+        cudaEventRecord(P.ev[2 * P.used + 1], h->st);
+        P.stage[P.used] = stage;
+        ++P.used;
+    }
+}
+
+bool valid_config(const oic_config* c)
+{
+    if (!c) return false;
+    if (c->n < 1 || c->m < 4 || c->m % 4 != 0 || c->l < 1 || c->N < 2 || c->H < 1) return false;
+    if (c->n_layers < 1 || c->n_layers > OIC_MAX_LAYERS) return false;
+    if (c->channels[0] != 2 || c->channels[c->n_layers] != 1) return false;
+    for (int k = 0; k <= c->n_layers; ++k)
+        if (c->channels[k] < 1 || c->channels[k] > 256) return false;
+    if (c->precision != OIC_PREC_FP32 && c->precision != OIC_PREC_MIXED) return false;
+    if (c->noise_mode != OIC_NOISE_HOST && c->noise_mode != OIC_NOISE_PHILOX) return false;
+    const long p = (long)c->n + c->l;
+    if (p > 224) return false;                  // gain factor lives in shared memory
+    if ((long)c->n * c->m > (1L << 26) || (long)c->N * c->m > (1L << 28)) return false;
+    return true;
+}
+
+size_t noise_count(const oic_config* c)
+{
+    const size_t N = c->N, n = c->n, m = c->m, l = c->l, H = c->H;
+    return N * l * m + H * N * (l * m + n * m + l * m);
+}
+
+void compute_layout(oic_handle* h)
+{
+    const oic_config& c = h->cfg;
+    size_t cur = 0;
+    auto take = [&](size_t bytes) {
+        const size_t off = cur;
+        cur += align_up(bytes > 0 ? bytes : 1, 256);
+        return off;
+    };
+    const size_t n = c.n, m = c.m, l = c.l, N = c.N, H = c.H, p = h->p;
+    const size_t Ra = h->R_act_max;
+    Layout& L = h->lay;
+    L.w = take(sizeof(float) * h->w.size());
+    L.b = take(sizeof(float) * h->b.size());
+    L.B = take(sizeof(float) * n * l);
+    L.E = take(sizeof(float) * N * h->R_mem * m);
+    L.act0 = take(sizeof(float) * N * h->Cmax * n * m);
+    L.act1 = take(sizeof(float) * N * h->Cmax * n * m);
+    L.meanE = take(sizeof(float) * Ra * m);
+    L.meanY = take(sizeof(float) * p * m);
+    L.part = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * p);
+    L.C = take(sizeof(double) * (Ra + p) * p);
+    L.K = take(sizeof(float) * Ra * p);
+    L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
+    L.status = take(64);
+    L.plantX = take(sizeof(float) * n * m);
+    L.plantU = take(sizeof(float) * l * m);
+    L.plantTmp = take(sizeof(float) * n * m);
+    L.xk = take(sizeof(float) * n * m);
+    L.uprev = take(sizeof(float) * l * m);
+    L.xref = take(sizeof(float) * (H + 1) * n * m);
+    L.uref = take(sizeof(float) * l * m);
+    L.noise = take(sizeof(float) * h->noise_n);
+    L.uhat = take(sizeof(float) * (H + 1) * l * m);
+    L.xhat = take(sizeof(float) * (H + 1) * n * m);
+    L.uapp = take(sizeof(float) * l * m);
+    L.xnext = take(sizeof(float) * n * m);
+    L.total = cur;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+oic_status last_cuda()
+{
+    return cudaGetLastError() == cudaSuccess ? OIC_OK : OIC_ECUDA;
+}
+
+// X_next[b] = CNN_theta(X[b], U[b]) for b < Nb, member strides x_ms / u_ms / o_ms.
+void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* U, long u_ms,
+                 float* Xout, long o_ms)
+{
+    const oic_config& c = h->cfg;
+    float* a = h->at<float>(h->lay.act0);
+    float* z = h->at<float>(h->lay.act1);
+    run_stage(h, OIC_STAGE_CNN_INPUT, [&] {
+        launch_cnn_input(X, x_ms, U, u_ms, h->at<float>(h->lay.B), a, Nb, c.n, c.m, c.l, h->st);
+    });
+    const float* w = h->at<float>(h->lay.w);
+    const float* b = h->at<float>(h->lay.b);
+    for (int k = 0; k < h->L - 1; ++k) {
+        const int cin = c.channels[k], cout = c.channels[k + 1];
+        run_stage(h, k == 0 ? OIC_STAGE_CONV_FIRST : OIC_STAGE_CONV_HIDDEN, [&] {
+            launch_conv_hidden(a, cin, z, cout, Nb, c.n, c.m, w, b, h->st);
+        });
+        w += (size_t)cin * cout * 9;
+        b += cout;
+        float* t = a; a = z; z = t;
+    }
+    run_stage(h, OIC_STAGE_CONV_OUT, [&] {
+        launch_conv_out_residual(a, c.channels[h->L - 1], X, x_ms, Xout, o_ms, Nb, c.n, c.m, w, b,
+                                 c.residual_scale, h->st);
+    });
+}
+
+// One ensemble Kalman analysis on rows `act` / `obs` of the ensemble E.
+void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
+              const float* Yu, int n_yx)
+{
+    const oic_config& c = h->cfg;
+    float* meanE = h->at<float>(h->lay.meanE);
+    float* meanY = h->at<float>(h->lay.meanY);
+    float* part = h->at<float>(h->lay.part);
+    double* C = h->at<double>(h->lay.C);
+    float* K = h->at<float>(h->lay.K);
+    run_stage(h, OIC_STAGE_MEANS, [&] {
+        launch_means(E, ms, c.N, c.m, act, obs, V, meanE, meanY, h->st);
+    });
+    const int splits = cov_splits(act.count, obs.count, c.N);
+    run_stage(h, OIC_STAGE_COV, [&] {
+        launch_cov_partial(E, ms, c.N, c.m, act, obs, V, meanE, meanY, part, splits, h->st);
+    });
+    run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
+        launch_cov_reduce(part, splits, act.count + obs.count, obs.count, C, h->st);
+    });
+    run_stage(h, OIC_STAGE_GAIN, [&] {
+        launch_gain(C, act.count, obs.count, K, h->at<int>(h->lay.status), h->st);
+    });
+    run_stage(h, OIC_STAGE_UPDATE, [&] {
+        launch_update(E, ms, c.N, c.m, act, obs, V, K, Yx, Yu, n_yx, h->st);
+    });
+}
+
+oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
+                      const float* U_ref, const float* noise, float* U_hat, float* X_hat)
+{
+    const oic_config& c = h->cfg;
+    const size_t N = c.N, n = c.n, m = c.m, l = c.l, H = c.H;
+    if (c.noise_mode == OIC_NOISE_PHILOX) {
+        const size_t e0 = N * l * m, e1 = e0 + H * N * l * m, e2 = e1 + H * N * n * m,
+                     e3 = e2 + H * N * l * m;
+        const size_t ends[4] = {e0, e1, e2, e3};
+        const float sig[4] = {(float)c.sigma_w, (float)c.sigma_w, (float)c.sigma_vx, (float)c.sigma_vu};
+        float* buf = h->at<float>(h->lay.noise);
+        run_stage(h, OIC_STAGE_NOISE, [&] {
+            launch_philox_noise(buf, h->noise_n, c.seed, h->solve_counter, ends, sig, 4, h->st);
+        });
+        noise = buf;
+    }
+    h->solve_counter++;
+    const float* W0 = noise;
+    const float* W = W0 + N * l * m;
+    const float* VX = W + H * N * l * m;
+    const float* VU = VX + H * N * n * m;
+    float* E = h->at<float>(h->lay.E);
+    const long ms = h->ms();
+
+    run_stage(h, OIC_STAGE_INIT, [&] {
+        launch_ensemble_init(E, ms, c.N, c.n, c.m, c.l, h->xrow(0), h->urow(0), X_k, U_prev, W0, h->st);
+    });
+    for (int s = 1; s <= c.H; ++s) {
+        // prediction, Eq. (prediction-samplewise): X̄_t = f_CNN(X̄_{t-1}) + W̄_{t-1}
+        cnn_forward(h, c.N, E + (size_t)h->xrow(s - 1) * m, ms, E + (size_t)h->urow(s - 1) * m, ms,
+                    E + (size_t)h->xrow(s) * m, ms);
+        run_stage(h, OIC_STAGE_U_ADVANCE, [&] {
+            launch_u_advance(E, ms, c.N, c.m, c.l, h->urow(s - 1), h->urow(s), W + (s - 1) * N * l * m,
+                             h->st);
+        });
+        // analysis at t = k + s with Ybar_t = [X_ref[s]; U_ref]
+        RowSet act{h->act_rows(s), h->R_of(s)};
+        RowSet obs{h->obs_rows(s), h->p};
+        ObsNoise V{VX + (s - 1) * N * n * m, VU + (s - 1) * N * l * m, c.n};
+        analysis(h, E, ms, act, obs, V, X_ref + (size_t)s * n * m, U_ref, c.n);
+    }
+    run_stage(h, OIC_STAGE_BLOCK_MEANS, [&] {
+        launch_block_means(E, ms, c.N, c.m, h->urow(0), c.l, c.H + 1, U_hat, h->st);
+    });
+    if (X_hat)
+        run_stage(h, OIC_STAGE_BLOCK_MEANS, [&] {
+            launch_block_means(E, ms, c.N, c.m, 0, c.n, c.H + 1, X_hat, h->st);
+        });
+    return last_cuda();
+}
+
+oic_status step_impl(oic_handle* h, const float* X_ref, const float* U_ref, const float* noise,
+                     float* U_applied, float* X_next)
+{
+    const oic_config& c = h->cfg;
+    const size_t n = c.n, m = c.m, l = c.l;
+    float* uhat = h->at<float>(h->lay.uhat);
+    float* pX = h->at<float>(h->lay.plantX);
+    float* pU = h->at<float>(h->lay.plantU);
+    float* tmp = h->at<float>(h->lay.plantTmp);
+    oic_status s = solve_impl(h, pX, pU, X_ref, U_ref, noise, uhat,
+                              h->full() ? h->at<float>(h->lay.xhat) : nullptr);
+    if (s != OIC_OK) return s;
+    // Algorithm 1, lines 15-17: apply U_k = Û_{k|k:k+H} to the plant
+    cnn_forward(h, 1, pX, 0, uhat, 0, tmp, 0);
+    OIC_CUDA_OK(cudaMemcpyAsync(pX, tmp, sizeof(float) * n * m, cudaMemcpyDeviceToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(pU, uhat, sizeof(float) * l * m, cudaMemcpyDeviceToDevice, h->st));
+    if (U_applied)
+        OIC_CUDA_OK(cudaMemcpyAsync(U_applied, uhat, sizeof(float) * l * m, cudaMemcpyDeviceToDevice,
+                                    h->st));
+    if (X_next)
+        OIC_CUDA_OK(cudaMemcpyAsync(X_next, pX, sizeof(float) * n * m, cudaMemcpyDeviceToDevice, h->st));
+    return last_cuda();
+}
+
+oic_status read_status(oic_handle* h)
+{
+    int dev = 0;
+    OIC_CUDA_OK(cudaMemcpyAsync(&dev, h->at<int>(h->lay.status), sizeof(int), cudaMemcpyDeviceToHost,
+                                h->st));
+    OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    if (dev != DEV_OK) {
+        OIC_CUDA_OK(cudaMemsetAsync(h->at<int>(h->lay.status), 0, sizeof(int), h->st));
+        OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+        return dev == DEV_NOTSPD ? OIC_ENOTSPD : OIC_ETIMEOUT;
+    }
+    return OIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t oic_noise_floats(const oic_config* cfg) { return valid_config(cfg) ? noise_count(cfg) : 0; }
+
+oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* conv_b, const float* B,
+                      oic_handle** out)
+{
+    if (!out) return OIC_EINVAL;
+    *out = nullptr;
+    if (!valid_config(cfg) || !conv_w || !conv_b || !B) return OIC_EINVAL;
+    oic_handle* h = new (std::nothrow) oic_handle();
+    if (!h) return OIC_ENOMEM;
+    h->cfg = *cfg;
+    const oic_config& c = h->cfg;
+    h->L = c.n_layers;
+    size_t nw = 0, nb = 0;
+    for (int k = 0; k < h->L; ++k) {
+        nw += (size_t)c.channels[k] * c.channels[k + 1] * 9;
+        nb += c.channels[k + 1];
+        if (k > 0 && c.channels[k] > h->Cmax) h->Cmax = c.channels[k];
+    }
+    try {
+        h->w.assign(conv_w, conv_w + nw);
+        h->b.assign(conv_b, conv_b + nb);
+        h->B.assign(B, B + (size_t)c.n * c.l);
+    } catch (...) {
+        delete h;
+        return OIC_ENOMEM;
+    }
+    h->q = c.n + 2 * c.l;
+    h->p = c.n + c.l;
+    h->R_mem = h->full() ? (c.H + 1) * (c.n + c.l) : 2 * c.n + (c.H + 1) * c.l;
+    h->Ubase = h->full() ? (c.H + 1) * c.n : 2 * c.n;
+    h->R_act_max = h->R_of(c.H);
+    h->splits_max = cov_splits(1, h->p, c.N);
+    h->noise_n = noise_count(&c);
+    compute_layout(h);
+    *out = h;
+    return OIC_OK;
+}
+
+size_t oic_workspace_bytes(const oic_handle* h) { return h ? h->lay.total : 0; }
+
+int oic_max_rows(const oic_handle* h) { return h ? h->R_act_max : 0; }
+
+oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda_stream)
+{
+    if (!h || !dev_workspace) return OIC_EINVAL;
+    if (bytes < h->lay.total) return OIC_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return OIC_EINVAL;
+    h->ws = static_cast<char*>(dev_workspace);
+    h->ws_bytes = bytes;
+    h->st = static_cast<cudaStream_t>(cuda_stream);
+    const oic_config& c = h->cfg;
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.w), h->w.data(), sizeof(float) * h->w.size(),
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.b), h->b.data(), sizeof(float) * h->b.size(),
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.B), h->B.data(), sizeof(float) * h->B.size(),
+                                cudaMemcpyHostToDevice, h->st));
+    // row tables
+    const int stride = h->R_act_max + h->p;
+    std::vector<int> tab((size_t)(c.H + 2) * stride, 0);
+    for (int s = 1; s <= c.H; ++s) {
+        int* a = tab.data() + (size_t)s * stride;
+        int* o = a + h->R_act_max;
+        int r = 0;
+        if (h->full()) {
+            for (int t = 1; t <= s; ++t)
+                for (int y = 0; y < c.n; ++y) a[r++] = t * c.n + y;
+        } else {
+            for (int y = 0; y < c.n; ++y) a[r++] = h->xrow(s) + y;
+        }
+        for (int t = 0; t <= s; ++t)
+            for (int y = 0; y < c.l; ++y) a[r++] = h->urow(t) + y;
+        for (int y = 0; y < c.n; ++y) o[y] = h->xrow(s) + y;
+        for (int y = 0; y < c.l; ++y) o[c.n + y] = h->urow(s) + y;
+    }
+    int* gen = tab.data() + (size_t)(c.H + 1) * stride;
+    for (int r = 0; r < h->R_act_max; ++r) gen[r] = r;
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<int>(h->lay.rowtab), tab.data(), sizeof(int) * tab.size(),
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemsetAsync(h->at<int>(h->lay.status), 0, 64, h->st));
+    if (!h->ev0) OIC_CUDA_OK(cudaEventCreate(&h->ev0));
+    if (!h->ev1) OIC_CUDA_OK(cudaEventCreate(&h->ev1));
+    OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    h->bound = true;
+    h->plant_ready = false;
+    h->solve_counter = 0;
+    return OIC_OK;
+}
+
+oic_status oic_reset(oic_handle* h, const float* X0, const float* U_prev)
+{
+    if (!h || !X0 || !U_prev) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    const size_t n = h->cfg.n, m = h->cfg.m, l = h->cfg.l;
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantX), X0, sizeof(float) * n * m,
+                                cudaMemcpyDeviceToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantU), U_prev, sizeof(float) * l * m,
+                                cudaMemcpyDeviceToDevice, h->st));
+    h->plant_ready = true;
+    h->solve_counter = 0;
+    return OIC_OK;
+}
+
+oic_status oic_solve(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
+                     const float* U_ref, const float* noise, float* U_hat, float* X_hat)
+{
+    if (!h || !X_k || !U_prev || !X_ref || !U_ref || !U_hat) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    if (h->cfg.noise_mode == OIC_NOISE_HOST && (!noise || !aligned16(noise))) return OIC_EINVAL;
+    if (X_hat && !h->full()) return OIC_EINVAL;
+    OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
+    oic_status s = solve_impl(h, X_k, U_prev, X_ref, U_ref, noise, U_hat, X_hat);
+    OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
+    return s;
+}
+
+oic_status oic_step(oic_handle* h, const float* X_ref, const float* U_ref, const float* noise,
+                    float* U_applied, float* X_next)
+{
+    if (!h || !X_ref || !U_ref) return OIC_EINVAL;
+    if (!h->bound || !h->plant_ready) return OIC_ESTATE;
+    if (h->cfg.noise_mode == OIC_NOISE_HOST && (!noise || !aligned16(noise))) return OIC_EINVAL;
+    OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
+    oic_status s = step_impl(h, X_ref, U_ref, noise, U_applied, X_next);
+    OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
+    return s;
+}
+
+oic_status oic_reset_host(oic_handle* h, const float* X0, const float* U_prev)
+{
+    if (!h || !X0 || !U_prev) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    const size_t n = h->cfg.n, m = h->cfg.m, l = h->cfg.l;
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantX), X0, sizeof(float) * n * m,
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantU), U_prev, sizeof(float) * l * m,
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    h->plant_ready = true;
+    h->solve_counter = 0;
+    return OIC_OK;
+}
+
+oic_status oic_solve_host(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
+                          const float* U_ref, const float* noise, float* U_hat, float* X_hat)
+{
+    if (!h || !X_k || !U_prev || !X_ref || !U_ref || !U_hat) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    const oic_config& c = h->cfg;
+    if (c.noise_mode == OIC_NOISE_HOST && !noise) return OIC_EINVAL;
+    if (X_hat && !h->full()) return OIC_EINVAL;
+    const size_t n = c.n, m = c.m, l = c.l, H = c.H;
+    const Layout& L = h->lay;
+    OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.xk), X_k, sizeof(float) * n * m, cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.uprev), U_prev, sizeof(float) * l * m, cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.xref), X_ref, sizeof(float) * (H + 1) * n * m,
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.uref), U_ref, sizeof(float) * l * m, cudaMemcpyHostToDevice, h->st));
+    if (c.noise_mode == OIC_NOISE_HOST)
+        OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.noise), noise, sizeof(float) * h->noise_n,
+                                    cudaMemcpyHostToDevice, h->st));
+    oic_status s = solve_impl(h, h->at<float>(L.xk), h->at<float>(L.uprev), h->at<float>(L.xref),
+                              h->at<float>(L.uref), h->at<float>(L.noise), h->at<float>(L.uhat),
+                              X_hat ? h->at<float>(L.xhat) : nullptr);
+    if (s != OIC_OK) return s;
+    OIC_CUDA_OK(cudaMemcpyAsync(U_hat, h->at<float>(L.uhat), sizeof(float) * (H + 1) * l * m,
+                                cudaMemcpyDeviceToHost, h->st));
+    if (X_hat)
+        OIC_CUDA_OK(cudaMemcpyAsync(X_hat, h->at<float>(L.xhat), sizeof(float) * (H + 1) * n * m,
+                                    cudaMemcpyDeviceToHost, h->st));
+    OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
+    return read_status(h);
+}
+
+oic_status oic_step_host(oic_handle* h, const float* X_ref, const float* U_ref, const float* noise,
+                         float* U_applied, float* X_next)
+{
+    if (!h || !X_ref || !U_ref) return OIC_EINVAL;
+    if (!h->bound || !h->plant_ready) return OIC_ESTATE;
+    const oic_config& c = h->cfg;
+    if (c.noise_mode == OIC_NOISE_HOST && !noise) return OIC_EINVAL;
+    const size_t n = c.n, m = c.m, l = c.l, H = c.H;
+    const Layout& L = h->lay;
+    OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.xref), X_ref, sizeof(float) * (H + 1) * n * m,
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.uref), U_ref, sizeof(float) * l * m, cudaMemcpyHostToDevice, h->st));
+    if (c.noise_mode == OIC_NOISE_HOST)
+        OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.noise), noise, sizeof(float) * h->noise_n,
+                                    cudaMemcpyHostToDevice, h->st));
+    oic_status s = step_impl(h, h->at<float>(L.xref), h->at<float>(L.uref), h->at<float>(L.noise),
+                             h->at<float>(L.uapp), h->at<float>(L.xnext));
+    if (s != OIC_OK) return s;
+    if (U_applied)
+        OIC_CUDA_OK(cudaMemcpyAsync(U_applied, h->at<float>(L.uapp), sizeof(float) * l * m,
+                                    cudaMemcpyDeviceToHost, h->st));
+    if (X_next)
+        OIC_CUDA_OK(cudaMemcpyAsync(X_next, h->at<float>(L.xnext), sizeof(float) * n * m,
+                                    cudaMemcpyDeviceToHost, h->st));
+    OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
+    return read_status(h);
+}
+
+oic_status oic_cnn_forward(oic_handle* h, int batch, const float* X, const float* U, float* X_next)
+{
+    if (!h || !X || !U || !X_next || batch < 1 || batch > h->cfg.N) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    const long nx = (long)h->cfg.n * h->cfg.m, nu = (long)h->cfg.l * h->cfg.m;
+    cnn_forward(h, batch, X, nx, U, nu, X_next, nx);
+    return last_cuda();
+}
+
+oic_status oic_enks_update(oic_handle* h, int R, const int* obs_rows, float* E, const float* V,
+                           const float* Ybar)
+{
+    if (!h || !obs_rows || !E || !V || !Ybar) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    if (R < 1 || R > h->R_act_max) return OIC_EINVAL;
+    if (!aligned16(E) || !aligned16(V)) return OIC_EINVAL;
+    const int p = h->p;
+    for (int c = 0; c < p; ++c)
+        if (obs_rows[c] < 0 || obs_rows[c] >= R) return OIC_EINVAL;
+    int* gen = h->act_rows(h->cfg.H + 1);
+    int* gobs = gen + h->R_act_max;
+    OIC_CUDA_OK(cudaMemcpyAsync(gobs, obs_rows, sizeof(int) * p, cudaMemcpyHostToDevice, h->st));
+    RowSet act{gen, R};
+    RowSet obs{gobs, p};
+    ObsNoise Vn{V, V, p};
+    analysis(h, E, (long)R * h->cfg.m, act, obs, Vn, Ybar, Ybar, p);
+    return last_cuda();
+}
+
+oic_status oic_sync(oic_handle* h)
+{
+    if (!h) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    return read_status(h);
+}
+
+float oic_last_ms(oic_handle* h)
+{
+    if (!h || !h->ev0 || !h->ev1) return -1.f;
+    float ms = -1.f;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) != cudaSuccess) return -1.f;
+    return ms;
+}
+
+oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launches)
+{
+    if (!h || max_launches < 1) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    Profiler& P = h->prof;
+    if ((int)P.ev.size() < 2 * max_launches) {
+        for (cudaEvent_t e : P.ev) cudaEventDestroy(e);
+        P.ev.assign(2 * (size_t)max_launches, nullptr);
+        for (auto& e : P.ev) OIC_CUDA_OK(cudaEventCreate(&e));
+        P.stage.assign(max_launches, 0);
+    }
+    P.max = max_launches;
+    P.mask = stage_mask;
+    P.used = 0;
+    P.on = true;
+    return OIC_OK;
+}
+
+oic_status oic_profile_end(oic_handle* h, float* ms, int* launches)
+{
+    if (!h || !ms || !launches) return OIC_EINVAL;
+    Profiler& P = h->prof;
+    for (int s = 0; s < OIC_NUM_STAGES; ++s) { ms[s] = 0.f; launches[s] = 0; }
+    if (!P.on) return OIC_ESTATE;
+    P.on = false;
+    OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    for (int u = 0; u < P.used; ++u) {
+        float t = 0.f;
+        OIC_CUDA_OK(cudaEventElapsedTime(&t, P.ev[2 * u], P.ev[2 * u + 1]));
+        ms[P.stage[u]] += t;
+        launches[P.stage[u]] += 1;
+    }
+    return OIC_OK;
+}
+
+unsigned long long oic_launch_count(void) { return g_launches.load(); }
+
+void oic_destroy(oic_handle* h)
+{
+    if (!h) return;
+    for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+const char* oic_status_string(oic_status s)
+{
+    switch (s) {
+    case OIC_OK: return "ok";
+    case OIC_EINVAL: return "invalid argument";
+    case OIC_ENOMEM: return "out of memory (workspace too small or host allocation failed)";
+    case OIC_ECUDA: return "CUDA runtime error";
+    case OIC_ENOTSPD: return "pseudo-observation covariance not positive definite";
+    case OIC_ETIMEOUT: return "bounded device wait timed out";
+    case OIC_ESTATE: return "call order violated (bind / reset first)";
+    }
+    return "unknown status";
+}
+
+const char* oic_version(void) { return "oic-b300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// oic_internal.cuh -- declarations shared by the library's CUDA sources.
+//
+// Ensemble layout in the workspace (member-major, one contiguous block per
+// member, row-major rows of m floats):
+//   U-history mode  rows = [X slot 0 (n) | X slot 1 (n) | U_0 .. U_H (l each)]
+//   full history    rows = [X_0 .. X_H (n each)        | U_0 .. U_H (l each)]
+// Only these rows are ever touched by an update: the dU rows of the
+// augmented state [X; U; dU] (Eq. (virtual-system-compact)) feed neither the
+// prediction nor the pseudo-observation, and every row's update depends only
+// on its own anomalies (Eq. (ensemble-based-Kalman-update-samplewise)), so
+// dropping them leaves every kept row's arithmetic unchanged.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "oic.h"
+
+namespace oic {
+
+// Values of the device status word.
+enum : int { DEV_OK = 0, DEV_NOTSPD = 1, DEV_TIMEOUT = 2 };
+
+// Where member i's row r lives: E + i * member_stride + row_off[r] * m.
+struct RowSet {
+    const int* rows;   // device: row offsets (in rows) inside a member block
+    int count;
+};
+
+// Observation perturbation V^i (p rows): rows c < pa come from Va (member
+// stride pa*m), rows c >= pa from Vb (member stride (p-pa)*m).  Va == nullptr
+// means V = 0.
+struct ObsNoise {
+    const float* Va;
+    const float* Vb;
+    int pa;
+};
+
+// ---------------------------------------------------------------- CNN
+// act0[b] = [X^b ; B U^b]  (two planes of n x m), b < Nb.
+void launch_cnn_input(const float* X, long x_ms, const float* U, long u_ms, const float* B,
+                      float* act0, int Nb, int n, int m, int l, cudaStream_t st);
+// One hidden 3x3 layer with tanh: out[b] = tanh(conv(in[b]) + bias).
+void launch_conv_hidden(const float* in, int Cin, float* out, int Cout, int Nb, int n, int m,
+                        const float* w, const float* bias, cudaStream_t st);
+// Last layer (one output channel) fused with the residual:
+// Xout[b] = Xin[b] + rs * (conv(in[b]) + bias).
+void launch_conv_out_residual(const float* in, int Cin, const float* Xin, long xin_ms, float* Xout,
+                              long xout_ms, int Nb, int n, int m, const float* w,
+                              const float* bias, float rs, cudaStream_t st);
+
+// ---------------------------------------------------------------- EnKS
+// Algorithm 1 line 4: E[i][x_row0 ..] = X_k, E[i][u_row0 ..] = U_prev + W0^i.
+void launch_ensemble_init(float* E, long ms, int N, int n, int m, int l, int x_row0, int u_row0,
+                          const float* X_k, const float* U_prev, const float* W0, cudaStream_t st);
+// E[i][u_to rows] = E[i][u_from rows] + W^i (l x m per member).
+void launch_u_advance(float* E, long ms, int N, int m, int l, int u_from, int u_to,
+                      const float* W, cudaStream_t st);
+// Ensemble means of the active rows and of the perturbed observations.
+void launch_means(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
+                  float* meanE, float* meanY, cudaStream_t st);
+// Split-K anomaly products: part[s][a][c] = sum over members of split s and
+// columns j of L_a * A_Y,c, with L = [active-row anomalies; A_Y].
+int cov_splits(int R, int p, int N);
+void launch_cov_partial(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
+                        const float* meanE, const float* meanY, float* part, int splits,
+                        cudaStream_t st);
+void launch_cov_reduce(const float* part, int splits, int rows, int p, double* C, cudaStream_t st);
+// K = Cxy Cyy^{-1}; C is [(R + p) x p] with Cxy on top and Cyy below.
+size_t gain_smem_bytes(int p);
+void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st);
+// E^i[act rows] += K (Ybar - (H E^i + V^i)); Ybar rows c < n from Yx, else Yu.
+void launch_update(float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
+                   const float* K, const float* Yx, const float* Yu, int n_yx, cudaStream_t st);
+// out[b][r][j] = mean_i E[i][row0 + b*rows_per_block + r][j] for blocks b.
+void launch_block_means(const float* E, long ms, int N, int m, int row0, int rows_per_block,
+                        int n_blocks, float* out, cudaStream_t st);
+
+// Philox-4x32-10 normal noise (Salmon et al., SC'11) for one solve.
+void launch_philox_noise(float* out, size_t count_total, unsigned long long seed,
+                         unsigned long long counter_hi, const size_t* seg_end, const float* seg_sigma,
+                         int n_seg, cudaStream_t st);
+
+}  // namespace oic
+
+#define OIC_CUDA_OK(expr)                                   \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return OIC_ECUDA;           \
+    } while (0)

@@ -183,3 +183,61 @@ def large_128():
 
 
 WORKLOADS = {"small_16": small_16, "working_64": working_64, "large_128": large_128}
+
+
+# ------------------------------------------------------------------ Philox
+# Counter-based generator Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+# written from its published definition; the CUDA library implements the same
+# definition independently for its on-device noise mode.  Element e of a
+# solve's noise buffer takes word e % 4 of the block for counter
+# (e // 4 low, e // 4 high, solve low, solve high) under key (seed low, seed
+# high); words become uniforms ((w >> 8) + 1/2) 2^-24 and pairs of uniforms
+# become normals by Box-Muller.
+_M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+_W0, _W1 = 0x9E3779B9, 0xBB67AE85
+_MASK = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(ctr, key):
+    """ctr: uint32 array (..., 4); key: (k0, k1) ints.  Returns uint32 (..., 4)."""
+    c0, c1, c2, c3 = (ctr[..., i].astype(np.uint64) for i in range(4))
+    k0, k1 = int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF
+    for _ in range(10):
+        p0 = _M0 * c0
+        p1 = _M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK
+        c0, c1, c2, c3 = hi1 ^ c1 ^ np.uint64(k0), lo1, hi0 ^ c3 ^ np.uint64(k1), lo0
+        k0 = (k0 + _W0) & 0xFFFFFFFF
+        k1 = (k1 + _W1) & 0xFFFFFFFF
+    return np.stack([c0, c1, c2, c3], axis=-1).astype(np.uint32)
+
+
+def philox_normals(count: int, seed: int, solve: int):
+    q = np.arange((count + 3) // 4, dtype=np.uint64)
+    ctr = np.stack([q & _MASK, q >> np.uint64(32),
+                    np.full_like(q, solve & 0xFFFFFFFF), np.full_like(q, (solve >> 32) & 0xFFFFFFFF)],
+                   axis=-1).astype(np.uint32)
+    w = philox4x32_10(ctr, (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF))
+    u = ((w >> 8).astype(np.float64) + 0.5) * (1.0 / 16777216.0)
+    r0 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    r1 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    z = np.stack([r0 * np.cos(2 * np.pi * u[:, 1]), r0 * np.sin(2 * np.pi * u[:, 1]),
+                  r1 * np.cos(2 * np.pi * u[:, 3]), r1 * np.sin(2 * np.pi * u[:, 3])], axis=-1)
+    return z.reshape(-1)[:count]
+
+
+def philox_noise(wl: Workload, solve: int, seed: int | None = None):
+    """The noise buffer the device draws for solve number `solve` (counted from
+    the last reset) in Philox mode, same layout as Workload.noise."""
+    seed = wl.seed if seed is None else seed
+    n, m, l, N, H = wl.n, wl.m, wl.l, wl.N, wl.H
+    z = philox_normals(wl.noise_floats(), seed, solve)
+    e0 = N * l * m
+    e1 = e0 + H * N * l * m
+    e2 = e1 + H * N * n * m
+    sig = np.empty_like(z)
+    sig[:e1] = np.float32(wl.sigma_w)
+    sig[e1:e2] = np.float32(wl.sigma_vx)
+    sig[e2:] = np.float32(wl.sigma_vu)
+    return (sig.astype(np.float32) * z.astype(np.float32)).astype(np.float32)

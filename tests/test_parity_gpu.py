@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerance: relative L2 error <= 1e-4 on ensemble means and controls for the
+FP32 path (the bar the method's FP32 configuration is held to); the CNN alone
+is held to 1e-5 per element relative to the field's scale (a few FP32 ulps
+through K = 9 * C_in term dot products).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2410_09663_b300 as oic
+from paper_2410_09663_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def onet(wl):
+    return oracle.Net(wl.n, wl.m, wl.l, wl.channels, wl.weights(), wl.B(), wl.residual_scale)
+
+
+def solver(wl, **kw):
+    w, b = wl.flat_weights()
+    return oic.Solver(oic.config_from_workload(wl, **kw), w, b, wl.B())
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+RAGGED = W.Workload("ragged_20x24", n=20, m=24, l=3, channels=[2, 6, 1], N=19, H=3, S=4, ref="blobs",
+                    blob_sigma=3.0)
+MID = W.Workload("mid_32x48", n=32, m=48, l=4, channels=[2, 16, 16, 1], N=64, H=4, S=3, ref="blobs",
+                 blob_sigma=4.0)
+CASES = {"small_16": W.small_16(), "ragged": RAGGED, "mid": MID}
+
+
+@pytest.mark.parametrize("name", ["small_16", "ragged", "mid", "working_64"])
+def test_cnn_forward_matches_oracle(cuda_ok, name):
+    wl = CASES[name] if name in CASES else W.working_64()
+    batch = min(wl.N, 6)
+    rng = np.random.default_rng(5)
+    X = (wl.X0()[None] + 0.3 * rng.standard_normal((batch, wl.n, wl.m))).astype(np.float32)
+    U = (0.5 * rng.standard_normal((batch, wl.l, wl.m))).astype(np.float32)
+    s = solver(wl)
+    Xd, Ud = dev(X), dev(U)
+    out = dev(np.zeros_like(X))
+    s.oic_cnn_forward(Xd, Ud, out)
+    s.oic_sync()
+    got = out.cpu().numpy()
+    want = oracle.cnn_step(onet(wl), X, U)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name", ["small_16", "ragged", "mid"])
+@pytest.mark.parametrize("full", [False, True])
+def test_solve_matches_oracle(cuda_ok, name, full):
+    wl = CASES[name]
+    s = solver(wl, keep_full_history=full)
+    k = 2
+    Xk = wl.X0()
+    Up = (0.01 * np.random.default_rng(7).standard_normal((wl.l, wl.m))).astype(np.float32)
+    xr, ur, nz = wl.X_ref_window(k), wl.U_ref(), wl.noise(k)
+    U_hat = np.zeros((wl.H + 1, wl.l, wl.m), np.float32)
+    X_hat = np.zeros((wl.H + 1, wl.n, wl.m), np.float32) if full else None
+    s.oic_solve_host(Xk, Up, xr, ur, nz, U_hat, X_hat)
+    xh = oracle.enks_solve(onet(wl), wl.N, wl.H, Xk, Up, xr, ur, nz)
+    assert rel(U_hat, xh[:, wl.n:wl.n + wl.l]) <= TOL
+    if full:
+        assert rel(X_hat, xh[:, :wl.n]) <= TOL
+
+
+def test_device_and_host_entry_points_agree(cuda_ok):
+    wl = MID
+    s = solver(wl)
+    Xk, Up = wl.X0(), wl.U_init()
+    xr, ur, nz = wl.X_ref_window(0), wl.U_ref(), wl.noise(0)
+    U_host = np.zeros((wl.H + 1, wl.l, wl.m), np.float32)
+    s.oic_solve_host(Xk, Up, xr, ur, nz, U_host)
+    U_dev = dev(np.zeros_like(U_host))
+    s.oic_solve(dev(Xk), dev(Up), dev(xr), dev(ur), dev(nz), U_dev)
+    s.oic_sync()
+    np.testing.assert_array_equal(U_dev.cpu().numpy(), U_host)
+
+
+@pytest.mark.parametrize("name", ["small_16", "ragged"])
+def test_closed_loop_matches_oracle(cuda_ok, name):
+    wl = CASES[name]
+    S = wl.S
+    s = solver(wl)
+    xr_all = wl.X_ref_all(S)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    Ut = np.zeros((S, wl.l, wl.m), np.float32)
+    Xt = np.zeros((S + 1, wl.n, wl.m), np.float32)
+    Xt[0] = wl.X0()
+    for k in range(S):
+        s.oic_step_host(xr_all[k:k + wl.H + 1], wl.U_ref(), wl.noise(k), Ut[k], Xt[k + 1])
+    Xo, Uo, _ = oracle.run(onet(wl), wl.N, wl.H, S, wl.X0(), wl.U_init(), xr_all, wl.U_ref(),
+                           wl.noise_all(S))
+    assert rel(Ut, Uo) <= TOL
+    assert rel(Xt, Xo) <= TOL
+    jg = oracle.closed_loop_cost(Xt, Ut, xr_all, wl.U_ref(), wl.U_init(), wl.sigma_vx, wl.sigma_vu,
+                                 wl.sigma_w)
+    jo = oracle.closed_loop_cost(Xo, Uo, xr_all, wl.U_ref(), wl.U_init(), wl.sigma_vx, wl.sigma_vu,
+                                 wl.sigma_w)
+    assert abs(jg - jo) <= 1e-4 * abs(jo)
+
+
+def test_philox_mode_matches_oracle_fed_host_philox(cuda_ok):
+    wl = W.small_16()
+    s = solver(wl, noise_mode=oic.OIC_NOISE_PHILOX, seed=1234)
+    net = onet(wl)
+    xr_all = wl.X_ref_all(3)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    X = wl.X0().astype(np.float64)
+    Up = wl.U_init().astype(np.float64)
+    for k in range(3):
+        Ua = np.zeros((wl.l, wl.m), np.float32)
+        Xn = np.zeros((wl.n, wl.m), np.float32)
+        s.oic_step_host(xr_all[k:k + wl.H + 1], wl.U_ref(), None, Ua, Xn)
+        nz = W.philox_noise(wl, solve=k, seed=1234)
+        xh = oracle.enks_solve(net, wl.N, wl.H, X, Up, xr_all[k:k + wl.H + 1], wl.U_ref(), nz)
+        Uo = xh[0, wl.n:wl.n + wl.l]
+        assert rel(Ua, Uo) <= TOL
+        X = oracle.cnn_step(net, X, Uo)
+        Up = Uo
+        assert rel(Xn, X) <= TOL
+
+
+def test_enks_update_matches_oracle(cuda_ok):
+    wl = MID
+    s = solver(wl)
+    rng = np.random.default_rng(9)
+    R = 45
+    p = wl.p
+    assert p < R <= s.max_rows
+    E = (1.0 + 0.05 * rng.standard_normal((wl.N, R, wl.m))).astype(np.float32)
+    obs = np.sort(rng.choice(R, size=p, replace=False))
+    V = (0.02 * rng.standard_normal((wl.N, p, wl.m))).astype(np.float32)
+    Ybar = (1.2 + 0.1 * rng.standard_normal((p, wl.m))).astype(np.float32)
+    Ed = dev(E)
+    s.oic_enks_update(Ed, obs, dev(V), dev(Ybar))
+    s.oic_sync()
+    got = Ed.cpu().numpy()
+    want = oracle.enks_analysis(E, E[:, obs, :] + V, Ybar)
+    assert rel(got - E, want - E) <= TOL
+    assert rel(got.mean(0), want.mean(0)) <= TOL
+
+
+def test_not_positive_definite_is_reported_and_skipped(cuda_ok):
+    wl = MID
+    s = solver(wl)
+    R = wl.p
+    E = np.ones((wl.N, R, wl.m), np.float32)        # identical members, V = 0: Sigma^Y = 0
+    V = np.zeros((wl.N, wl.p, wl.m), np.float32)
+    Ed = dev(E)
+    s.oic_enks_update(Ed, np.arange(wl.p), dev(V), dev(np.zeros((wl.p, wl.m), np.float32)))
+    assert s.oic_sync_status() == oic.OIC_ENOTSPD
+    np.testing.assert_array_equal(Ed.cpu().numpy(), E)
+    assert s.oic_sync_status() == oic.OIC_OK       # status is cleared once read
+
+
+@pytest.mark.slow
+def test_working_size_one_control_step(cuda_ok):
+    """Full-size bench workload (64 x 64, N = 256, H = 10, CNN 2-32-32-1), one
+    control step through the same entry point the benchmark times."""
+    wl = W.working_64()
+    s = solver(wl)
+    xr_all = wl.X_ref_all(1)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    Ua = np.zeros((wl.l, wl.m), np.float32)
+    Xn = np.zeros((wl.n, wl.m), np.float32)
+    s.oic_step_host(xr_all[:wl.H + 1], wl.U_ref(), wl.noise(0), Ua, Xn)
+    Xo, Uo, _ = oracle.run(onet(wl), wl.N, wl.H, 1, wl.X0(), wl.U_init(), xr_all, wl.U_ref(),
+                           wl.noise_all(1))
+    assert rel(Ua, Uo[0]) <= TOL
+    assert rel(Xn, Xo[1]) <= TOL
+
+
+def test_large_128_cnn_sampled_members(cuda_ok):
+    """128 x 128 field, CNN 2-64-64-64-1 at full size: run all N = 1024 members
+    through the rollout kernels and check a sample of members one by one."""
+    import torch
+    wl = W.large_128()
+    s = solver(wl)
+    rng = np.random.default_rng(3)
+    X = torch.from_numpy(wl.X0()).cuda()[None].repeat(wl.N, 1, 1)
+    X += 0.05 * torch.randn_like(X)
+    U = 0.3 * torch.randn(wl.N, wl.l, wl.m, device="cuda")
+    out = torch.zeros_like(X)
+    s.oic_cnn_forward(X, U, out)
+    s.oic_sync()
+    idx = rng.choice(wl.N, size=3, replace=False)
+    want = oracle.cnn_step(onet(wl), X[idx].cpu().numpy(), U[idx].cpu().numpy())
+    got = out[idx].cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()

@@ -31,3 +31,23 @@ def test_reference_blobs_move_with_period_50():
     np.testing.assert_allclose(r0, r25, atol=1e-5)
     assert 0.9 < r0.max() <= 1.05
     assert not np.allclose(r0, wl.X_ref(12))
+
+
+def test_philox_known_answers():
+    import json, os
+    kat = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")))
+    for v in kat["vectors"]:
+        ctr = np.array([[int(x, 16) for x in v["ctr"]]], np.uint32)
+        key = [int(x, 16) for x in v["key"]]
+        out = W.philox4x32_10(ctr, key)[0]
+        assert [int(x) for x in out] == [int(x, 16) for x in v["out"]]
+
+
+def test_philox_noise_layout_and_scale():
+    wl = W.small_16().with_(sigma_vx=0.02)
+    z = W.philox_noise(wl, solve=0)
+    assert z.size == wl.noise_floats() and z.dtype == np.float32
+    e1 = wl.N * wl.l * wl.m + wl.H * wl.N * wl.l * wl.m
+    e2 = e1 + wl.H * wl.N * wl.n * wl.m
+    assert abs(z[:e1].std() - 0.01) < 1e-3 and abs(z[e1:e2].std() - 0.02) < 1e-3
+    assert not np.array_equal(W.philox_noise(wl, 0), W.philox_noise(wl, 1))
