@@ -181,9 +181,11 @@ def host_threads():
 def cpu_baseline(wl, budget_s=30.0):
     """Oracle as it stands, one control step on a sample of the members,
     scaled to control steps/s of the full ensemble (its cost is linear in N)."""
-    t2 = oracle_step_seconds(wl, 2)
-    n_s = int(max(2, min(wl.N, (budget_s / 2.0) / max(t2 / 2.0, 1e-3))))
-    t = oracle_step_seconds(wl, n_s) if n_s > 2 else t2
+    # the sample covariance needs (N - 1) m >= n + l samples to be definite
+    n0 = max(8, -(-(wl.n + wl.l) // wl.m) + 2)
+    t0 = oracle_step_seconds(wl, n0)
+    n_s = int(max(n0, min(wl.N, budget_s / max(t0 / n0, 1e-4))))
+    t = oracle_step_seconds(wl, n_s) if n_s > n0 else t0
     value = (n_s / wl.N) / t
     return {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
             "sample": f"1 control step with {n_s} of {wl.N} members ({t:.1f} s), scaled by "
@@ -195,8 +197,9 @@ def run_reference(args, wl):
     if rank != 0:
         return 0
     total = args.steps + args.warmup
-    t2 = oracle_step_seconds(wl, 2)
-    n_s = int(max(2, min(wl.N, 2 * (150.0 / max(total, 1)) / max(t2, 1e-3))))
+    n0 = max(8, -(-(wl.n + wl.l) // wl.m) + 2)
+    t0 = oracle_step_seconds(wl, n0)
+    n_s = int(max(n0, min(wl.N, n0 * (150.0 / max(total, 1)) / max(t0, 1e-3))))
     for _ in range(args.warmup):
         oracle_step_seconds(wl, n_s)
     times = [oracle_step_seconds(wl, n_s, k=i % wl.S) for i in range(args.steps)]
@@ -361,7 +364,11 @@ def run_oic(args, wl):
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
+        try:
+            line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
+        except Exception as e:                          # the GPU line must still print
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": host_threads(),
+                                    "kind": "oracle", "sample": f"failed: {e!r}"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
