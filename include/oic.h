@@ -188,6 +188,14 @@ oic_status oic_profile_end(oic_handle* h, float* ms, int* launches);
 /* Number of kernels this library has launched in this process. */
 unsigned long long oic_launch_count(void);
 
+/* Known-answer check of the tensor-core path on the bound device: a
+ * 128 x 64 x 32 fp16 product with FP32 accumulation in tensor memory,
+ * compared element by element with CUDA-core results.  result[5] (host):
+ * mismatches, then the first mismatch (row, column, got, want).  Returns
+ * OIC_OK, OIC_ECUDA on a mismatch, OIC_ETIMEOUT if the product never
+ * completed.  Synchronous. */
+oic_status oic_selftest(oic_handle* h, int* result);
+
 /* Waits for the bound stream and returns (and clears) the device status. */
 oic_status oic_sync(oic_handle* h);
 

@@ -65,6 +65,7 @@ _SIGS = {
     "oic_profile_begin": (ctypes.c_int, [_VP, ctypes.c_uint, ctypes.c_int]),
     "oic_profile_end": (ctypes.c_int, [_VP, _FP, ctypes.POINTER(ctypes.c_int)]),
     "oic_launch_count": (ctypes.c_ulonglong, []),
+    "oic_selftest": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "oic_destroy": (None, [_VP]),
     "oic_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "oic_version": (ctypes.c_char_p, []),
@@ -214,6 +215,12 @@ class Solver:
         """oic_step_host with raw host addresses (e.g. pinned torch tensors)."""
         _check(self._lib.oic_step_host(self.h, X_ref_ptr, U_ref_ptr, noise_ptr, U_applied_ptr,
                                        X_next_ptr), "oic_step_host")
+
+    def oic_selftest(self):
+        """Returns (status, [mismatches, row, col, got, want])."""
+        res = (ctypes.c_int * 5)()
+        st = self._lib.oic_selftest(self.h, res)
+        return int(st), list(res)
 
     def oic_sync(self):
         _check(self._lib.oic_sync(self.h), "oic_sync")

@@ -27,7 +27,7 @@ struct Profiler {
 };
 
 struct Layout {
-    size_t w, b, B, E, act0, act1, meanE, meanY, part, C, K, rowtab, status;
+    size_t w, b, B, wtc, E, act0, act1, meanE, meanY, part, C, K, rowtab, status, selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -39,7 +39,8 @@ struct oic_handle {
     oic_config cfg;
     std::vector<float> w, b, B;
     int L = 0, q = 0, p = 0, R_mem = 0, R_act_max = 0, Cmax = 2;
-    int Ubase = 0, splits_max = 1;
+    int Ubase = 0, splits_max = 1, n_sm = 148;
+    std::vector<size_t> wtc_off;      // per layer: offset of packed tensor-core weights (or SIZE_MAX)
     size_t noise_n = 0;
     Layout lay{};
     char* ws = nullptr;
@@ -121,6 +122,16 @@ void compute_layout(oic_handle* h)
     L.w = take(sizeof(float) * h->w.size());
     L.b = take(sizeof(float) * h->b.size());
     L.B = take(sizeof(float) * n * l);
+    {
+        size_t tc_bytes = 0;
+        h->wtc_off.assign(h->L, SIZE_MAX);
+        for (int k = 1; k + 1 < h->L; ++k)
+            if (conv_tc_supported(c.channels[k], c.channels[k + 1], c.m)) {
+                h->wtc_off[k] = tc_bytes;
+                tc_bytes += align_up(conv_tc_packed_bytes(c.channels[k]), 256);
+            }
+        L.wtc = take(tc_bytes);
+    }
     L.E = take(sizeof(float) * N * h->R_mem * m);
     L.act0 = take(sizeof(float) * N * h->Cmax * n * m);
     L.act1 = take(sizeof(float) * N * h->Cmax * n * m);
@@ -131,6 +142,7 @@ void compute_layout(oic_handle* h)
     L.K = take(sizeof(float) * Ra * p);
     L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
     L.status = take(64);
+    L.selftest = take(64);
     L.plantX = take(sizeof(float) * n * m);
     L.plantU = take(sizeof(float) * l * m);
     L.plantTmp = take(sizeof(float) * n * m);
@@ -167,8 +179,13 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
     const float* b = h->at<float>(h->lay.b);
     for (int k = 0; k < h->L - 1; ++k) {
         const int cin = c.channels[k], cout = c.channels[k + 1];
+        const size_t toff = h->wtc_off[k];
         run_stage(h, k == 0 ? OIC_STAGE_CONV_FIRST : OIC_STAGE_CONV_HIDDEN, [&] {
-            launch_conv_hidden(a, cin, z, cout, Nb, c.n, c.m, w, b, h->st);
+            if (toff != SIZE_MAX)
+                launch_conv_tc(a, z, h->at<char>(h->lay.wtc) + toff, b, cout, Nb, c.n, c.m, h->n_sm,
+                               h->at<int>(h->lay.status), h->st);
+            else
+                launch_conv_hidden(a, cin, z, cout, Nb, c.n, c.m, w, b, h->st);
         });
         w += (size_t)cin * cout * 9;
         b += cout;
@@ -359,6 +376,23 @@ oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda
                                 cudaMemcpyHostToDevice, h->st));
     OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.B), h->B.data(), sizeof(float) * h->B.size(),
                                 cudaMemcpyHostToDevice, h->st));
+    {
+        int dev = 0;
+        OIC_CUDA_OK(cudaGetDevice(&dev));
+        OIC_CUDA_OK(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
+        if (conv_tc_configure() != 0) return OIC_ECUDA;
+        const float* wl = h->w.data();
+        for (int k = 0; k < h->L; ++k) {
+            const int cin = c.channels[k], cout = c.channels[k + 1];
+            if (h->wtc_off[k] != SIZE_MAX) {
+                std::vector<unsigned char> pk(conv_tc_packed_bytes(cout));
+                conv_tc_pack_weights(wl, cout, pk.data());
+                OIC_CUDA_OK(cudaMemcpy(h->at<char>(h->lay.wtc) + h->wtc_off[k], pk.data(), pk.size(),
+                                       cudaMemcpyHostToDevice));
+            }
+            wl += (size_t)cin * cout * 9;
+        }
+    }
     // row tables
     const int stride = h->R_act_max + h->p;
     std::vector<int> tab((size_t)(c.H + 2) * stride, 0);
@@ -586,6 +620,21 @@ oic_status oic_profile_end(oic_handle* h, float* ms, int* launches)
 }
 
 unsigned long long oic_launch_count(void) { return g_launches.load(); }
+
+oic_status oic_selftest(oic_handle* h, int* result)
+{
+    if (!h || !result) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    int* d = h->at<int>(h->lay.selftest);
+    OIC_CUDA_OK(cudaMemsetAsync(d, 0, 64, h->st));
+    launch_tc_selftest(d, h->st);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    OIC_CUDA_OK(cudaGetLastError());
+    OIC_CUDA_OK(cudaMemcpyAsync(result, d, 5 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    if (result[0] == -1) return OIC_ETIMEOUT;
+    return result[0] == 0 ? OIC_OK : OIC_ECUDA;
+}
 
 void oic_destroy(oic_handle* h)
 {

@@ -75,6 +75,16 @@ void launch_update(float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsN
 void launch_block_means(const float* E, long ms, int N, int m, int row0, int rows_per_block,
                         int n_blocks, float* out, cudaStream_t st);
 
+// Hidden C -> C conv layer on the tensor cores (FP32-accurate fp16 split).
+bool conv_tc_supported(int cin, int cout, int m);
+size_t conv_tc_packed_bytes(int C);
+void conv_tc_pack_weights(const float* w, int C, void* dst_host);
+int conv_tc_configure();
+void launch_conv_tc(const float* in, float* out, const void* wpk, const float* bias, int C, int Nb, int n,
+                    int m, int n_sm, int* err, cudaStream_t st);
+// Known-answer check of the tcgen05 path: res[0] = mismatches (-1 timeout).
+void launch_tc_selftest(int* res, cudaStream_t st);
+
 // Philox-4x32-10 normal noise (Salmon et al., SC'11) for one solve.
 void launch_philox_noise(float* out, size_t count_total, unsigned long long seed,
                          unsigned long long counter_hi, const size_t* seg_end, const float* seg_sigma,

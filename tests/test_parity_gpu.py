@@ -40,10 +40,20 @@ RAGGED = W.Workload("ragged_20x24", n=20, m=24, l=3, channels=[2, 6, 1], N=19, H
                     blob_sigma=3.0)
 MID = W.Workload("mid_32x48", n=32, m=48, l=4, channels=[2, 16, 16, 1], N=64, H=4, S=3, ref="blobs",
                  blob_sigma=4.0)
-CASES = {"small_16": W.small_16(), "ragged": RAGGED, "mid": MID}
+# hidden 32 -> 32 layer on the tensor cores; m = 32 puts 4 members in a
+# 128-pixel tile and N = 13 leaves the last tile with one member
+TC_RAGGED = W.Workload("tc_24x32", n=24, m=32, l=4, channels=[2, 32, 32, 1], N=13, H=3, S=3,
+                       ref="blobs", blob_sigma=4.0)
+CASES = {"small_16": W.small_16(), "ragged": RAGGED, "mid": MID, "tc_ragged": TC_RAGGED}
 
 
-@pytest.mark.parametrize("name", ["small_16", "ragged", "mid", "working_64"])
+def test_tensor_core_selftest(cuda_ok):
+    s = solver(W.small_16())
+    st, res = s.oic_selftest()
+    assert st == oic.OIC_OK and res[0] == 0, res
+
+
+@pytest.mark.parametrize("name", ["small_16", "ragged", "mid", "tc_ragged", "working_64"])
 def test_cnn_forward_matches_oracle(cuda_ok, name):
     wl = CASES[name] if name in CASES else W.working_64()
     batch = min(wl.N, 6)
@@ -60,7 +70,7 @@ def test_cnn_forward_matches_oracle(cuda_ok, name):
     assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("name", ["small_16", "ragged", "mid"])
+@pytest.mark.parametrize("name", ["small_16", "ragged", "mid", "tc_ragged"])
 @pytest.mark.parametrize("full", [False, True])
 def test_solve_matches_oracle(cuda_ok, name, full):
     wl = CASES[name]
