@@ -78,6 +78,10 @@ def stage_work(wl, stage):
         return conv_layer_flops(wl, 2, wl.channels[1]) * N, "flop", "alu"
     if stage == "conv_out":
         return conv_layer_flops(wl, wl.channels[-2], 1) * N, "flop", "alu"
+    if stage == "cnn_fused":
+        # whole CNN step; the hidden layer (the bulk of the flops) runs on the
+        # fp16 tensor pipe as three products per FP32 product
+        return cnn_flops_per_member_step(wl) * N, "flop", "tensor"
     return None
 
 
@@ -87,8 +91,8 @@ def kernel_traffic(stage):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    src_files = {"conv_hidden": "cnn_kernels.cu", "conv_first": "cnn_kernels.cu",
-                 "conv_out": "cnn_kernels.cu"}
+    src_files = {"conv_hidden": "conv_tc.cu", "conv_first": "cnn_kernels.cu",
+                 "conv_out": "cnn_kernels.cu", "cnn_fused": "cnn_fused_tc.cu"}
     f = src_files.get(stage)
     if f is None:
         return None
@@ -332,7 +336,19 @@ def run_oic(args, wl):
         if work is not None and n_l > 0:
             amount, unit, bound = work
             avg_s = ms / 1e3 / n_l
-            if bound == "alu":
+            if bound == "tensor":
+                peak = peaks.get("bf16_tflops_sustained", 1351.5)
+                ach = amount / avg_s / 1e12
+                roof = {"bound": "tensor", "kernel": dominant, "achieved": ach, "peak": peak,
+                        "unit": "TFLOP/s", "frac": ach / peak,
+                        "peak_source": "%s bf16 dense sustained (fp16 runs at the bf16 rate)"
+                                       % peaks["source"],
+                        "traffic": kernel_traffic(dominant),
+                        "algorithmic_per_launch": amount, "launches": n_l,
+                        "avg_launch_ms": avg_s * 1e3,
+                        "fp32_ffma_equiv_frac": ach / fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0)),
+                        "note": "algorithmic FP32 flops; the tensor pipe executes 3 fp16 products each"}
+            elif bound == "alu":
                 peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
                 roof = {"bound": "alu", "kernel": dominant, "achieved": amount / avg_s / 1e12,
                         "peak": peak, "unit": "TFLOP/s",

@@ -180,6 +180,7 @@ typedef enum {
     OIC_STAGE_GAIN,            /* Cholesky + K = Sigma^XY (Sigma^Y)^-1          */
     OIC_STAGE_UPDATE,          /* member-wise update                            */
     OIC_STAGE_BLOCK_MEANS,     /* smoothed output means                         */
+    OIC_STAGE_CNN_FUSED,       /* whole CNN step in one kernel (all layers)     */
     OIC_NUM_STAGES
 } oic_stage;
 oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launches);

@@ -4,6 +4,7 @@
 // noise_kernels.cu.  The library never allocates device memory: every buffer
 // below is carved out of the caller's workspace at oic_bind.
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -46,7 +47,7 @@ struct oic_handle {
     char* ws = nullptr;
     size_t ws_bytes = 0;
     cudaStream_t st = nullptr;
-    bool bound = false, plant_ready = false;
+    bool bound = false, plant_ready = false, fused = false;
     unsigned long long solve_counter = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int> obs_host;
@@ -170,6 +171,22 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
                  float* Xout, long o_ms)
 {
     const oic_config& c = h->cfg;
+    if (h->fused) {
+        const float* w = h->at<float>(h->lay.w);
+        const float* b = h->at<float>(h->lay.b);
+        const int C = c.channels[1];
+        const float* w1 = w;
+        const float* w3 = w + (size_t)2 * C * 9 + (size_t)C * C * 9;
+        const float* b1 = b;
+        const float* b2 = b + C;
+        const float* b3 = b + 2 * C;
+        run_stage(h, OIC_STAGE_CNN_FUSED, [&] {
+            launch_cnn_fused(X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l, w1, b1,
+                             h->at<char>(h->lay.wtc) + h->wtc_off[1], b2, w3, b3, c.residual_scale, h->n_sm,
+                             h->at<int>(h->lay.status), h->st);
+        });
+        return;
+    }
     float* a = h->at<float>(h->lay.act0);
     float* z = h->at<float>(h->lay.act1);
     run_stage(h, OIC_STAGE_CNN_INPUT, [&] {
@@ -352,6 +369,8 @@ oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* c
     h->R_act_max = h->R_of(c.H);
     h->splits_max = cov_splits(1, h->p, c.N);
     h->noise_n = noise_count(&c);
+    h->fused = cnn_fused_supported(c.n_layers, c.channels, c.n, c.m, c.l) &&
+               getenv("OIC_NO_FUSED_CNN") == nullptr;
     compute_layout(h);
     *out = h;
     return OIC_OK;

@@ -212,3 +212,21 @@ def test_large_128_cnn_sampled_members(cuda_ok):
     want = oracle.cnn_step(onet(wl), X[idx].cpu().numpy(), U[idx].cpu().numpy())
     got = out[idx].cpu().numpy()
     assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name", ["tc_ragged", "working_64"])
+def test_cnn_per_layer_tensor_path_matches_oracle(cuda_ok, name, monkeypatch):
+    """The per-layer tensor-core path (used for hidden stacks other than one
+    32 -> 32 layer) stays exact when the fused kernel is switched off."""
+    monkeypatch.setenv("OIC_NO_FUSED_CNN", "1")
+    wl = CASES[name] if name in CASES else W.working_64()
+    batch = min(wl.N, 6)
+    rng = np.random.default_rng(6)
+    X = (wl.X0()[None] + 0.3 * rng.standard_normal((batch, wl.n, wl.m))).astype(np.float32)
+    U = (0.5 * rng.standard_normal((batch, wl.l, wl.m))).astype(np.float32)
+    s = solver(wl)
+    out = dev(np.zeros_like(X))
+    s.oic_cnn_forward(dev(X), dev(U), out)
+    s.oic_sync()
+    want = oracle.cnn_step(onet(wl), X, U)
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-5 * np.abs(want).max()
