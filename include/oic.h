@@ -90,8 +90,8 @@ size_t oic_noise_floats(const oic_config* cfg);
 /* Creates a handle.  conv_w: all layers' weights concatenated, layer k as
  * [channels[k+1]][channels[k]][3][3] (3x3 cross-correlation, zero padding);
  * conv_b: all biases concatenated; B: n x l.  Host pointers, copied.
- * Sizes: n, m >= 1, m % 4 == 0, l >= 1, N >= 2, H >= 1, channels in
- * 1 .. 256.  Returns OIC_EINVAL on bad sizes, OIC_ENOMEM on host allocation
+ * Sizes: n >= 1, 4 <= m <= 128, m % 4 == 0, l >= 1, n + l <= 144, N >= 2,
+ * H >= 1, channels in 1 .. 256.  Returns OIC_EINVAL on bad sizes, OIC_ENOMEM on host allocation
  * failure. */
 oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* conv_b,
                       const float* B, oic_handle** out);
@@ -174,9 +174,9 @@ typedef enum {
     OIC_STAGE_CONV_HIDDEN,     /* hidden -> hidden conv layers, tanh            */
     OIC_STAGE_CONV_OUT,        /* last conv layer + residual                    */
     OIC_STAGE_U_ADVANCE,       /* U_t = U_{t-1} + W                             */
-    OIC_STAGE_MEANS,           /* ensemble means                                */
-    OIC_STAGE_COV,             /* anomaly products (split-K)                    */
-    OIC_STAGE_COV_REDUCE,      /* split-K reduction                             */
+    OIC_STAGE_MEANS,           /* reduction of the anomaly column sums          */
+    OIC_STAGE_COV,             /* anomaly products (split-K) and innovations    */
+    OIC_STAGE_COV_REDUCE,      /* covariance finalisation                       */
     OIC_STAGE_GAIN,            /* Cholesky + K = Sigma^XY (Sigma^Y)^-1          */
     OIC_STAGE_UPDATE,          /* member-wise update                            */
     OIC_STAGE_BLOCK_MEANS,     /* smoothed output means                         */

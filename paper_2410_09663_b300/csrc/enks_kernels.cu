@@ -16,14 +16,6 @@
 namespace oic {
 namespace {
 
-__device__ __forceinline__ float obs_noise(const ObsNoise& V, int i, int c, int p, int m, int j)
-{
-    if (V.Va == nullptr) return 0.f;
-    if (c < V.pa) return V.Va[((long)i * V.pa + c) * m + j];
-    const int pb = p - V.pa;
-    return V.Vb[((long)i * pb + (c - V.pa)) * m + j];
-}
-
 __device__ __forceinline__ float4 obs_noise4(const ObsNoise& V, int i, int c, int p, int m, int j)
 {
     if (V.Va == nullptr) return make_float4(0.f, 0.f, 0.f, 0.f);
@@ -58,294 +50,380 @@ __global__ void u_advance_kernel(float* __restrict__ E, long ms, int m, int l, i
         Ei[(long)u_to * m + e] = Ei[(long)u_from * m + e] + W[(long)i * l * m + e];
 }
 
-// ----------------------------------------------------------------- means
-__global__ void means_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs,
-                             ObsNoise V, float* __restrict__ meanE, float* __restrict__ meanY)
+// ----------------------------------------------------------------- stats
+// Anomaly products without a separate means pass.  With l_i the value of a
+// left row (active state rows a < R, then the p perturbed-observation rows)
+// and y_i that of an observation row, both shifted by member 0's value at
+// the same (row, column):
+//   S1[a][j] = sum_i (l_i - l_0)[a][j]
+//   S2[a][c] = sum_i sum_j (l_i - l_0)[a][j] (y_i - y_0)[c][j]
+// and  sum_i sum_j (l_i - lbar)(y_i - ybar)^T = S2 - (1/N) sum_j S1[a][j] S1y[c][j]
+// exactly.  The shifted values are of the ensemble-spread scale, so the FP32
+// accumulation never subtracts two large means (the correction term is of
+// the same size as S2).  Split-K over members; CTAs of the first row tile
+// also write the innovations D^i = Ybar - Y^i (prior values) for the update.
+constexpr int SBM = 64, SBN = 96, SPAD = 4;
+
+__device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+__device__ __forceinline__ float4 load_left4(const float* Ei, long ms, int m, int a, int R, const RowSet& act,
+                                             const RowSet& obs, const ObsNoise& V, int i, int p, int j)
 {
-    const int R = act.count, p = obs.count;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (R + p) * m) return;
-    const int a = idx / m, j = idx - a * m;
-    const bool is_obs = a >= R;
+    if (a < R) return *reinterpret_cast<const float4*>(Ei + (long)act.rows[a] * m + j);
     const int c = a - R;
-    const long off = (long)(is_obs ? obs.rows[c] : act.rows[a]) * m + j;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int i = 0;
-    for (; i + 4 <= N; i += 4) {
-        float v0 = E[(long)i * ms + off], v1 = E[(long)(i + 1) * ms + off];
-        float v2 = E[(long)(i + 2) * ms + off], v3 = E[(long)(i + 3) * ms + off];
-        if (is_obs) {
-            v0 += obs_noise(V, i, c, p, m, j);
-            v1 += obs_noise(V, i + 1, c, p, m, j);
-            v2 += obs_noise(V, i + 2, c, p, m, j);
-            v3 += obs_noise(V, i + 3, c, p, m, j);
-        }
-        s0 += v0; s1 += v1; s2 += v2; s3 += v3;
-    }
-    for (; i < N; ++i) {
-        float v = E[(long)i * ms + off];
-        if (is_obs) v += obs_noise(V, i, c, p, m, j);
-        s0 += v;
-    }
-    const float mean = ((s0 + s1) + (s2 + s3)) / (float)N;
-    if (is_obs) meanY[c * m + j] = mean;
-    else meanE[a * m + j] = mean;
+    return f4add(*reinterpret_cast<const float4*>(Ei + (long)obs.rows[c] * m + j), obs_noise4(V, i, c, p, m, j));
 }
 
-// ------------------------------------------------------------ covariance
-constexpr int CBM = 64, CBN = 64, CKC = 16;
-
-// part[s][a][c] = sum_{i in split s} sum_j L[a](i,j) * A_Y[c](i,j), where
-// L = [anomalies of the active rows (a < R); anomalies of Y (a >= R)].
-__global__ void __launch_bounds__(256)
-cov_partial_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                   const float* __restrict__ meanE, const float* __restrict__ meanY,
-                   float* __restrict__ part, int splits)
+template <int NT>
+__global__ void __launch_bounds__(NT)
+stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
+             const float* __restrict__ Yx, const float* __restrict__ Yu, int n_yx, float* __restrict__ part1,
+             float* __restrict__ part2, float* __restrict__ Dbuf, int splits)
 {
-    __shared__ __align__(16) float As[CKC][CBM];
-    __shared__ __align__(16) float Bs[CKC][CBN];
+    // output tile SBM x SBN: thread (ty, tx) owns rows 4 ty .. +3 and CPT
+    // consecutive columns from CPT tx
+    constexpr int TXN = NT / 16, CPT = SBN / TXN;
+    constexpr int QA = 4, QB = 6;                 // loader chunks per thread (m <= 64 / 128 with NT)
+    extern __shared__ __align__(16) float sm[];
     const int R = act.count, p = obs.count, M = R + p;
-    const int bm0 = blockIdx.x * CBM, bn0 = blockIdx.y * CBN, s = blockIdx.z;
-    const int i0 = (int)((long)s * N / splits), i1 = (int)((long)(s + 1) * N / splits);
-    const int t = threadIdx.x, tx = t % 16, ty = t / 16;
-    const int lr = t / 4, lc = (t % 4) * 4;       // loader: row, first column of 4
+    const int ld = m + 4;
+    float* As = sm;                               // [SBM][ld]  (k contiguous)
+    float* Bs = As + SBM * ld;                    // [SBN][ld]
+    const int bm0 = blockIdx.x * SBM, bn0 = blockIdx.y * SBN, sidx = blockIdx.z;
+    const int i0 = (int)((long)sidx * N / splits), i1 = (int)((long)(sidx + 1) * N / splits);
+    const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
+    const int m4 = m / 4;
+    const bool do_s1 = blockIdx.y == 0, do_d = blockIdx.x == 0;
 
-    // loader rows
-    const int a = bm0 + lr;
-    const bool a_ok = a < M;
-    const bool a_obs = a >= R;
-    const long a_off = a_ok ? (long)(a_obs ? obs.rows[a - R] : act.rows[a]) * m : 0;
-    const float* a_mean = a_ok ? (a_obs ? meanY + (long)(a - R) * m : meanE + (long)a * m) : nullptr;
-    const int cb = bn0 + lr;
-    const bool c_ok = cb < p;
-    const long c_off = c_ok ? (long)obs.rows[cb] * m : 0;
-    const float* c_mean = c_ok ? meanY + (long)cb * m : nullptr;
-
-    float acc[4][4];
+    // loader chunks: consecutive threads take consecutive 16-byte pieces of a row
+    int ar[QA], aj[QA], br[QB], bj[QB];
+    float4 refa[QA], refb[QB], pa[QA], pb[QB], s1[QA];
+    const float4 Z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < QA; ++q) {
+        const int e = tid + NT * q;
+        ar[q] = e < SBM * m4 ? e / m4 : -1;
+        aj[q] = 4 * (e % m4);
+        const int a = bm0 + ar[q];
+        refa[q] = (ar[q] >= 0 && a < M) ? load_left4(E, ms, m, a, R, act, obs, V, 0, p, aj[q]) : Z;
+        s1[q] = Z;
+    }
+#pragma unroll
+    for (int q = 0; q < QB; ++q) {
+        const int e = tid + NT * q;
+        br[q] = e < SBN * m4 ? e / m4 : -1;
+        bj[q] = 4 * (e % m4);
+        const int c = bn0 + br[q];
+        refb[q] = (br[q] >= 0 && c < p) ? load_left4(E, ms, m, R + c, R, act, obs, V, 0, p, bj[q]) : Z;
+    }
+    auto fetch = [&](int i) {
+        const float* Ei = E + (long)i * ms;
+#pragma unroll
+        for (int q = 0; q < QA; ++q) {
+            const int a = bm0 + ar[q];
+            pa[q] = (ar[q] >= 0 && a < M) ? f4sub(load_left4(Ei, ms, m, a, R, act, obs, V, i, p, aj[q]), refa[q]) : Z;
+        }
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+            const int c = bn0 + br[q];
+            pb[q] = (br[q] >= 0 && c < p) ? f4sub(load_left4(Ei, ms, m, R + c, R, act, obs, V, i, p, bj[q]), refb[q]) : Z;
+        }
+    };
+    float acc[4][CPT];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        for (int v = 0; v < CPT; ++v) acc[u][v] = 0.f;
 
+    if (i0 < i1) fetch(i0);
     for (int i = i0; i < i1; ++i) {
-        const float* Ei = E + (long)i * ms;
-        for (int j0 = 0; j0 < m; j0 += CKC) {
-            const int j = j0 + lc;
-            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
-            if (j < m) {
-                if (a_ok) {
-                    float4 x = *reinterpret_cast<const float4*>(Ei + a_off + j);
-                    const float4 mu = *reinterpret_cast<const float4*>(a_mean + j);
-                    if (a_obs) {
-                        const float4 z = obs_noise4(V, i, a - R, p, m, j);
-                        x.x += z.x; x.y += z.y; x.z += z.z; x.w += z.w;
-                    }
-                    va = make_float4(x.x - mu.x, x.y - mu.y, x.z - mu.z, x.w - mu.w);
-                }
-                if (c_ok) {
-                    float4 y = *reinterpret_cast<const float4*>(Ei + c_off + j);
-                    const float4 z = obs_noise4(V, i, cb, p, m, j);
-                    const float4 mu = *reinterpret_cast<const float4*>(c_mean + j);
-                    vb = make_float4(y.x + z.x - mu.x, y.y + z.y - mu.y, y.z + z.z - mu.z,
-                                     y.w + z.w - mu.w);
+#pragma unroll
+        for (int q = 0; q < QA; ++q)
+            if (ar[q] >= 0) {
+                *reinterpret_cast<float4*>(As + ar[q] * ld + aj[q]) = pa[q];
+                s1[q] = f4add(s1[q], pa[q]);
+            }
+#pragma unroll
+        for (int q = 0; q < QB; ++q)
+            if (br[q] >= 0) {
+                *reinterpret_cast<float4*>(Bs + br[q] * ld + bj[q]) = pb[q];
+                const int c = bn0 + br[q];
+                if (do_d && c < p) {
+                    const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
+                    const float4 y = f4add(pb[q], refb[q]);
+                    *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + bj[q]) =
+                        f4sub(*reinterpret_cast<const float4*>(yb + bj[q]), y);
                 }
             }
-            As[lc + 0][lr] = va.x; As[lc + 1][lr] = va.y; As[lc + 2][lr] = va.z; As[lc + 3][lr] = va.w;
-            Bs[lc + 0][lr] = vb.x; Bs[lc + 1][lr] = vb.y; Bs[lc + 2][lr] = vb.z; Bs[lc + 3][lr] = vb.w;
-            __syncthreads();
+        __syncthreads();
+        if (i + 1 < i1) fetch(i + 1);            // next member's loads overlap the products
+#pragma unroll 2
+        for (int k = 0; k < m; k += 4) {
+            float4 av[4], bv[CPT];
 #pragma unroll
-            for (int kk = 0; kk < CKC; ++kk) {
-                const float4 x = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-                const float4 y = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-                const float xa[4] = {x.x, x.y, x.z, x.w}, yb[4] = {y.x, y.y, y.z, y.w};
+            for (int u = 0; u < 4; ++u) av[u] = *reinterpret_cast<const float4*>(As + (4 * ty + u) * ld + k);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+            for (int v = 0; v < CPT; ++v) bv[v] = *reinterpret_cast<const float4*>(Bs + (CPT * tx + v) * ld + k);
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xa[u], yb[v], acc[u][v]);
-            }
-            __syncthreads();
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < CPT; ++v) {
+                    acc[u][v] = fmaf(av[u].x, bv[v].x, acc[u][v]);
+                    acc[u][v] = fmaf(av[u].y, bv[v].y, acc[u][v]);
+                    acc[u][v] = fmaf(av[u].z, bv[v].z, acc[u][v]);
+                    acc[u][v] = fmaf(av[u].w, bv[v].w, acc[u][v]);
+                }
         }
+        __syncthreads();
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int ar = bm0 + ty * 4 + u;
-        if (ar >= M) continue;
+        const int a = bm0 + 4 * ty + u;
+        if (a >= M) continue;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int cc = bn0 + tx * 4 + v;
-            if (cc < p) part[((long)s * M + ar) * p + cc] = acc[u][v];
+        for (int v = 0; v < CPT; ++v) {
+            const int c = bn0 + CPT * tx + v;
+            if (c < p) part2[((long)sidx * M + a) * p + c] = acc[u][v];
+        }
+    }
+    if (do_s1) {
+#pragma unroll
+        for (int q = 0; q < QA; ++q) {
+            const int a = bm0 + ar[q];
+            if (ar[q] >= 0 && a < M)
+                *reinterpret_cast<float4*>(part1 + ((long)sidx * M + a) * m + aj[q]) = s1[q];
         }
     }
 }
 
-__global__ void cov_reduce_kernel(const float* __restrict__ part, int splits, int rows, int p,
-                                  double* __restrict__ C)
+// Sum over split-K partials, 32 consecutive outputs per CTA: warp w adds the
+// splits w, w + 8, ... (coalesced), then the 8 partial sums are combined.
+__device__ __forceinline__ float split_sum(const float* __restrict__ part, long stride, int splits, int idx,
+                                           bool ok, float (*red)[33])
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows * p) return;
-    double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += (double)part[(long)k * rows * p + idx];
-    C[idx] = s;
+    const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+    float s = 0.f;
+    if (ok)
+        for (int k = w; k < splits; k += 8) s += part[(long)k * stride + idx];
+    red[w][ln] = s;
+    __syncthreads();
+    float t = 0.f;
+    if (w == 0)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][ln];
+    return t;
+}
+
+// S1[a][j] = sum over splits of part1.
+__global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict__ part1, int splits, int M, int m,
+                                                        float* __restrict__ S1)
+{
+    __shared__ float red[8][33];
+    const int idx = blockIdx.x * 32 + threadIdx.x % 32;
+    const bool ok = idx < M * m;
+    const float t = split_sum(part1, (long)M * m, splits, idx, ok, red);
+    if (threadIdx.x < 32 && ok) S1[idx] = t;
+}
+
+// C[a][c] = sum over splits of part2 - (1/N) sum_j S1[a][j] S1[R + c][j].
+__global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restrict__ part2,
+                                                           const float* __restrict__ S1, int splits, int R, int p,
+                                                           int m, int N, double* __restrict__ C)
+{
+    __shared__ float red[8][33];
+    const int M = R + p;
+    const int idx = blockIdx.x * 32 + threadIdx.x % 32;
+    const bool ok = idx < M * p;
+    const float t = split_sum(part2, (long)M * p, splits, idx, ok, red);
+    if (threadIdx.x < 32 && ok) {
+        const int a = idx / p, c = idx % p;
+        const float* x = S1 + (long)a * m;
+        const float* y = S1 + (long)(R + c) * m;
+        float d0 = 0.f, d1 = 0.f;
+        for (int j = 0; j < m; j += 2) {
+            d0 = fmaf(x[j], y[j], d0);
+            d1 = fmaf(x[j + 1], y[j + 1], d1);
+        }
+        C[idx] = (double)(t - (d0 + d1) / (float)N);
+    }
 }
 
 // ------------------------------------------------------------------ gain
+// K = Cxy Cyy^{-1}, written transposed (Kt = K^T, [p][R]).  Every CTA factors
+// Cyy = L L^T (FP32 Cholesky, lower triangle in shared memory, odd row stride)
+// and then each warp solves L L^T k = c for its rows c of Cxy.
+//
+// Cholesky, right-looking, one barrier per step: step j subtracts the outer
+// product of the UNSCALED column j divided by the pivot, A[i][k] -= A[i][j]
+// A[k][j] / A[j][j] for j < k <= i; column j itself is scaled by 1/sqrt of
+// the pivot one step later (nobody reads it after step j).  Threads tile the
+// trailing triangle as a 16 x 16 grid of (row, column) strides.
+//
+// Solves: lane t owns entries r = t + 32 q; the pivot value is broadcast by
+// shuffle, forward L z = c walks the columns of L, back L^T k = z its rows.
 constexpr int G_THREADS = 256;
-constexpr int G_ROWS_PER_WARP = 2;
-constexpr int G_ROWS_PER_CTA = (G_THREADS / 32) * G_ROWS_PER_WARP;
-constexpr int G_KMAX = 8;                       // p <= 256
+constexpr int G_WARPS = G_THREADS / 32;
+constexpr int G_MAXP = 144;
+constexpr int G_KQ = (G_MAXP + 31) / 32;
 
-// Every CTA factors Cyy = L L^T in shared memory (FP32, right-looking, odd
-// row stride so column walks are bank-conflict free), then each warp solves
-// L L^T k = c for its rows c of Cxy: lane owns entries r = lane + 32 k, the
-// pivot value is broadcast by shuffle.
 __global__ void __launch_bounds__(G_THREADS)
-gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ K, int* __restrict__ status)
+gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
 {
-    extern __shared__ float A[];                 // p x ps
+    extern __shared__ float Ls[];                 // [p][ps]
+    __shared__ float rdiag[G_MAXP];               // 1 / L_jj
     __shared__ int bad;
     const int ps = p | 1;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const double* Cyy = C + (long)R * p;
-    for (int e = tid; e < p * p; e += G_THREADS) A[(e / p) * ps + (e % p)] = (float)Cyy[e];
+    for (int e = tid; e < p * p; e += G_THREADS) {
+        const int i = e / p, k = e % p;
+        if (k <= i) Ls[i * ps + k] = (float)Cyy[e];
+    }
     if (tid == 0) bad = 0;
+    __syncthreads();
     for (int j = 0; j < p; ++j) {
-        __syncthreads();
-        const float d = A[j * ps + j];
-        if (!(d > 0.f)) {
+        const float d = Ls[j * ps + j];
+        if (!(d > 0.f)) {                          // same value in every thread
             if (tid == 0) bad = 1;
             break;
         }
-        const float ljj = sqrtf(d);
-        const float inv = 1.f / ljj;
-        __syncthreads();
-        for (int i = j + 1 + tid; i < p; i += G_THREADS) A[i * ps + j] *= inv;
-        if (tid == 0) A[j * ps + j] = ljj;
-        __syncthreads();
-        const int cnt = p - j - 1;
-        for (int e = tid; e < cnt * cnt; e += G_THREADS) {
-            const int ii = j + 1 + e / cnt, kk = j + 1 + e % cnt;
-            if (kk <= ii) A[ii * ps + kk] = fmaf(-A[ii * ps + j], A[kk * ps + j], A[ii * ps + kk]);
+        const float dinv = 1.f / d;
+        for (int i = j + 1 + ty; i < p; i += 16) {
+            const float f = Ls[i * ps + j] * dinv;
+            float* Li = Ls + i * ps;
+            for (int k = j + 1 + tx; k <= i; k += 16) Li[k] = fmaf(-f, Ls[k * ps + j], Li[k]);
         }
+        __syncthreads();
+        // column j is final now: L[i][j] = A[i][j] / sqrt(d)
+        const float rs = rsqrtf(d);
+        for (int i = j + tid; i < p; i += G_THREADS) Ls[i * ps + j] = i == j ? d * rs : Ls[i * ps + j] * rs;
+        if (tid == 0) rdiag[j] = 1.f / (d * rs);
+        // the next step reads column j + 1 only, which this scaling does not touch
     }
     __syncthreads();
     const int warp = tid / 32, lane = tid % 32;
     if (bad) {
         if (blockIdx.x == 0 && tid == 0) atomicExch(status, DEV_NOTSPD);
-        for (int rr = 0; rr < G_ROWS_PER_WARP; ++rr) {
-            const int a = blockIdx.x * G_ROWS_PER_CTA + warp * G_ROWS_PER_WARP + rr;
-            if (a < R)
-                for (int r = lane; r < p; r += 32) K[(long)a * p + r] = 0.f;
-        }
+        const int a = blockIdx.x * G_WARPS + warp;
+        if (a < R)
+            for (int r = lane; r < p; r += 32) Kt[(long)r * R + a] = 0.f;
         return;
     }
-    for (int rr = 0; rr < G_ROWS_PER_WARP; ++rr) {
-        const int a = blockIdx.x * G_ROWS_PER_CTA + warp * G_ROWS_PER_WARP + rr;
-        if (a >= R) break;                       // warp-uniform
-        float v[G_KMAX];
+    const int a = blockIdx.x * G_WARPS + warp;
+    if (a >= R) return;
+    float v[G_KQ];
 #pragma unroll
-        for (int k = 0; k < G_KMAX; ++k) {
-            const int r = lane + 32 * k;
-            v[k] = (r < p) ? (float)C[(long)a * p + r] : 0.f;
-        }
-        // forward: L z = c
+    for (int q = 0; q < G_KQ; ++q) {
+        const int r = lane + 32 * q;
+        v[q] = r < p ? (float)C[(long)a * p + r] : 0.f;
+    }
+    // forward: L z = c
 #pragma unroll
-        for (int kb = 0; kb < G_KMAX; ++kb) {
-            if (kb * 32 >= p) break;
-            for (int il = 0; il < 32; ++il) {
-                const int i = kb * 32 + il;
-                if (i >= p) break;
-                const float zi = __shfl_sync(0xffffffffu, v[kb], il) / A[i * ps + i];
-                if (lane == il) v[kb] = zi;
+    for (int qb = 0; qb < G_KQ; ++qb) {
+        if (32 * qb >= p) break;
+        for (int il = 0; il < 32; ++il) {
+            const int i = 32 * qb + il;
+            if (i >= p) break;
+            const float zi = __shfl_sync(0xffffffffu, v[qb], il) * rdiag[i];
+            if (lane == il) v[qb] = zi;
 #pragma unroll
-                for (int k = 0; k < G_KMAX; ++k) {
-                    if (k < kb) continue;
-                    const int r = lane + 32 * k;
-                    if (r > i && r < p) v[k] = fmaf(-A[r * ps + i], zi, v[k]);
-                }
+            for (int q = 0; q < G_KQ; ++q) {
+                if (q < qb) continue;
+                const int r = lane + 32 * q;
+                if (r > i && r < p) v[q] = fmaf(-Ls[r * ps + i], zi, v[q]);
             }
         }
-        // backward: L^T k = z
+    }
+    // back: L^T k = z
 #pragma unroll
-        for (int kb = G_KMAX - 1; kb >= 0; --kb) {
-            if (kb * 32 >= p) continue;
-            for (int il = 31; il >= 0; --il) {
-                const int i = kb * 32 + il;
-                if (i >= p) continue;
-                const float ki = __shfl_sync(0xffffffffu, v[kb], il) / A[i * ps + i];
-                if (lane == il) v[kb] = ki;
+    for (int qb = G_KQ - 1; qb >= 0; --qb) {
+        if (32 * qb >= p) continue;
+        for (int il = 31; il >= 0; --il) {
+            const int i = 32 * qb + il;
+            if (i >= p) continue;
+            const float ki = __shfl_sync(0xffffffffu, v[qb], il) * rdiag[i];
+            if (lane == il) v[qb] = ki;
 #pragma unroll
-                for (int k = 0; k < G_KMAX; ++k) {
-                    if (k > kb) continue;
-                    const int r = lane + 32 * k;
-                    if (r < i) v[k] = fmaf(-A[i * ps + r], ki, v[k]);
-                }
+            for (int q = 0; q < G_KQ; ++q) {
+                if (q > qb) continue;
+                const int r = lane + 32 * q;
+                if (r < i) v[q] = fmaf(-Ls[i * ps + r], ki, v[q]);
             }
         }
+    }
 #pragma unroll
-        for (int k = 0; k < G_KMAX; ++k) {
-            const int r = lane + 32 * k;
-            if (r < p) K[(long)a * p + r] = v[k];
-        }
+    for (int q = 0; q < G_KQ; ++q) {
+        const int r = lane + 32 * q;
+        if (r < p) Kt[(long)r * R + a] = v[q];
     }
 }
 
 // ---------------------------------------------------------------- update
-constexpr int U_CT = 64;     // columns per CTA
-constexpr int U_RCH = 32;    // rows per K chunk
+// E^i[act rows] += K D^i for every member: a GEMM tile of 64 rows x 64
+// columns of one member; K is read transposed (Kt[c][a], row length R) and
+// D from the buffer the stats pass filled from the prior ensemble.
+constexpr int UBM = 64, UBN = 64, UT = 256;
 
-__global__ void __launch_bounds__(256)
-update_kernel(float* __restrict__ E, long ms, int m, RowSet act, RowSet obs, ObsNoise V,
-              const float* __restrict__ K, const float* __restrict__ Yx, const float* __restrict__ Yu,
-              int n_yx)
+__global__ void __launch_bounds__(UT)
+update_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float* __restrict__ Kt, int p,
+              const float* __restrict__ Dbuf)
 {
     extern __shared__ __align__(16) float sm[];
-    const int R = act.count, p = obs.count;
-    float* D = sm;                               // [p][U_CT]
-    float* Kt = sm + p * U_CT;                   // [p][U_RCH]
-    const int i = blockIdx.x;
-    const int j0 = blockIdx.y * U_CT;
-    const int tid = threadIdx.x;
-    float* Ei = E + (long)i * ms;
-
-    // innovation D^i = Ybar - (H E^i + V^i), taken from the prior before any write
-    for (int e = tid; e < p * U_CT; e += blockDim.x) {
-        const int c = e / U_CT, jj = e - c * U_CT, j = j0 + jj;
-        float d = 0.f;
-        if (j < m) {
-            const float yb = c < n_yx ? Yx[(long)c * m + j] : Yu[(long)(c - n_yx) * m + j];
-            d = yb - (Ei[(long)obs.rows[c] * m + j] + obs_noise(V, i, c, p, m, j));
+    const int R = act.count;
+    const int ld = UBM + SPAD;
+    float* Ks = sm;                               // [p][ld]
+    float* Ds = sm + p * ld;                      // [p][ld]
+    const int a0 = blockIdx.x * UBM;
+    const int ctiles = (m + UBN - 1) / UBN;
+    const int i = blockIdx.y / ctiles, j0 = (blockIdx.y % ctiles) * UBN;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    for (int e = tid; e < p * (UBM / 4); e += UT) {
+        const int c = e / (UBM / 4), r4 = (e % (UBM / 4)) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int a = a0 + r4;
+        if ((R & 3) == 0 && a + 3 < R) v = *reinterpret_cast<const float4*>(Kt + (long)c * R + a);
+        else {
+            float t[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int u = 0; u < 4; ++u) if (a + u < R) t[u] = Kt[(long)c * R + a + u];
+            v = make_float4(t[0], t[1], t[2], t[3]);
         }
-        D[c * U_CT + jj] = d;
+        *reinterpret_cast<float4*>(Ks + c * ld + r4) = v;
     }
-    const int jj = tid % U_CT, rg = tid / U_CT;  // rg in 0..3, rows rg*8 .. rg*8+7 of a chunk
-    const int j = j0 + jj;
-    for (int a0 = 0; a0 < R; a0 += U_RCH) {
-        __syncthreads();                         // D ready / previous chunk consumed
-        for (int e = tid; e < p * U_RCH; e += blockDim.x) {
-            const int c = e / U_RCH, rr = e - c * U_RCH;
-            const int a = a0 + rr;
-            Kt[c * U_RCH + rr] = a < R ? K[(long)a * p + c] : 0.f;
-        }
-        __syncthreads();
-        float acc[8];
+    const float* Di = Dbuf + (long)i * p * m;
+    for (int e = tid; e < p * (UBN / 4); e += UT) {
+        const int c = e / (UBN / 4), j4 = (e % (UBN / 4)) * 4, j = j0 + j4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < m) v = *reinterpret_cast<const float4*>(Di + (long)c * m + j);
+        *reinterpret_cast<float4*>(Ds + c * ld + j4) = v;
+    }
+    __syncthreads();
+    float acc[4][4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-        for (int c = 0; c < p; ++c) {
-            const float d = D[c * U_CT + jj];
-            const float4 k0 = *reinterpret_cast<const float4*>(&Kt[c * U_RCH + rg * 8]);
-            const float4 k1 = *reinterpret_cast<const float4*>(&Kt[c * U_RCH + rg * 8 + 4]);
-            acc[0] = fmaf(k0.x, d, acc[0]); acc[1] = fmaf(k0.y, d, acc[1]);
-            acc[2] = fmaf(k0.z, d, acc[2]); acc[3] = fmaf(k0.w, d, acc[3]);
-            acc[4] = fmaf(k1.x, d, acc[4]); acc[5] = fmaf(k1.y, d, acc[5]);
-            acc[6] = fmaf(k1.z, d, acc[6]); acc[7] = fmaf(k1.w, d, acc[7]);
-        }
-        if (j < m) {
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int a = a0 + rg * 8 + q;
-                if (a < R) Ei[(long)act.rows[a] * m + j] += acc[q];
-            }
-        }
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+    for (int c = 0; c < p; ++c) {
+        const float4 k4 = *reinterpret_cast<const float4*>(Ks + c * ld + ty * 4);
+        const float4 d4 = *reinterpret_cast<const float4*>(Ds + c * ld + tx * 4);
+        const float kv[4] = {k4.x, k4.y, k4.z, k4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(kv[u], dv[v], acc[u][v]);
+    }
+    const int j = j0 + tx * 4;
+    if (j >= m) return;
+    float* Ei = E + (long)i * ms;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int a = a0 + ty * 4 + u;
+        if (a >= R) continue;
+        float4* dst = reinterpret_cast<float4*>(Ei + (long)act.rows[a] * m + j);
+        float4 e4 = *dst;
+        e4.x += acc[u][0]; e4.y += acc[u][1]; e4.z += acc[u][2]; e4.w += acc[u][3];
+        *dst = e4;
     }
 }
 
@@ -383,63 +461,68 @@ void launch_u_advance(float* E, long ms, int N, int m, int l, int u_from, int u_
     u_advance_kernel<<<grid, 256, 0, st>>>(E, ms, m, l, u_from, u_to, W);
 }
 
-void launch_means(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                  float* meanE, float* meanY, cudaStream_t st)
+int stats_splits(int R, int p, int N)
 {
-    const int total = (act.count + obs.count) * m;
-    means_kernel<<<(total + 255) / 256, 256, 0, st>>>(E, ms, N, m, act, obs, V, meanE, meanY);
-}
-
-int cov_splits(int R, int p, int N)
-{
-    const int tiles = ((R + p + CBM - 1) / CBM) * ((p + CBN - 1) / CBN);
-    int s = (2 * 148 + tiles - 1) / tiles;
+    const int tiles = ((R + p + SBM - 1) / SBM) * ((p + SBN - 1) / SBN);
+    int s = 148 / tiles;                          // one wave: at most one CTA per SM
     if (s > N) s = N;
     if (s < 1) s = 1;
     return s;
 }
 
-void launch_cov_partial(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                        const float* meanE, const float* meanY, float* part, int splits,
-                        cudaStream_t st)
+size_t stats_smem_bytes(int m) { return sizeof(float) * (size_t)(SBM + SBN) * (m + 4); }
+
+void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
+                  const float* Yu, int n_yx, float* part1, float* part2, float* Dbuf, int splits, cudaStream_t st)
 {
     const int M = act.count + obs.count, p = obs.count;
-    dim3 grid((M + CBM - 1) / CBM, (p + CBN - 1) / CBN, splits);
-    cov_partial_kernel<<<grid, 256, 0, st>>>(E, ms, N, m, act, obs, V, meanE, meanY, part, splits);
+    dim3 grid((M + SBM - 1) / SBM, (p + SBN - 1) / SBN, splits);
+    if (m <= 64)
+        stats_kernel<256><<<grid, 256, stats_smem_bytes(m), st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1,
+                                                                  part2, Dbuf, splits);
+    else
+        stats_kernel<512><<<grid, 512, stats_smem_bytes(m), st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1,
+                                                                  part2, Dbuf, splits);
 }
 
-void launch_cov_reduce(const float* part, int splits, int rows, int p, double* C, cudaStream_t st)
+void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st)
 {
-    const int total = rows * p;
-    cov_reduce_kernel<<<(total + 255) / 256, 256, 0, st>>>(part, splits, rows, p, C);
+    s1_reduce_kernel<<<(M * m + 31) / 32, 256, 0, st>>>(part1, splits, M, m, S1);
 }
 
-size_t gain_smem_bytes(int p) { return sizeof(float) * (size_t)p * (size_t)(p | 1); }
+void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
+                         cudaStream_t st)
+{
+    const int total = (R + p) * p;
+    cov_finalize_kernel<<<(total + 31) / 32, 256, 0, st>>>(part2, S1, splits, R, p, m, N, C);
+}
+
+size_t gain_smem_bytes(int p) { return p <= G_MAXP ? 0 : (size_t)-1; }
+int gain_max_p() { return G_MAXP; }
 
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
 {
-    const size_t smem = gain_smem_bytes(p);
+    const size_t smem = sizeof(float) * (size_t)p * (p | 1);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(gain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(gain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
         attr_set = true;
     }
-    const int grid = (R + G_ROWS_PER_CTA - 1) / G_ROWS_PER_CTA;
+    const int grid = (R + G_WARPS - 1) / G_WARPS;
     gain_kernel<<<grid > 0 ? grid : 1, G_THREADS, smem, st>>>(C, R, p, K, status);
 }
 
-void launch_update(float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                   const float* K, const float* Yx, const float* Yu, int n_yx, cudaStream_t st)
+void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
+                   cudaStream_t st)
 {
-    const int p = obs.count;
-    const size_t smem = sizeof(float) * (size_t)p * (U_CT + U_RCH);
+    const size_t smem = sizeof(float) * 2 * (size_t)p * (UBM + SPAD);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    dim3 grid(N, (m + U_CT - 1) / U_CT);
-    update_kernel<<<grid, 256, smem, st>>>(E, ms, m, act, obs, V, K, Yx, Yu, n_yx);
+    dim3 grid((act.count + UBM - 1) / UBM, N * ((m + UBN - 1) / UBN));
+    update_kernel<<<grid, UT, smem, st>>>(E, ms, m, act, Kt, p, Dbuf);
 }
 
 void launch_block_means(const float* E, long ms, int N, int m, int row0, int rows_per_block,

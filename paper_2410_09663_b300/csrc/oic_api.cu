@@ -28,7 +28,7 @@ struct Profiler {
 };
 
 struct Layout {
-    size_t w, b, B, wtc, E, act0, act1, meanE, meanY, part, C, K, rowtab, status, selftest;
+    size_t w, b, B, wtc, E, act0, act1, part1, part2, S1, D, C, K, rowtab, status, selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -97,8 +97,9 @@ bool valid_config(const oic_config* c)
     if (c->precision != OIC_PREC_FP32 && c->precision != OIC_PREC_MIXED) return false;
     if (c->noise_mode != OIC_NOISE_HOST && c->noise_mode != OIC_NOISE_PHILOX) return false;
     const long p = (long)c->n + c->l;
-    if (p > 224) return false;                  // gain factor lives in shared memory
+    if (p > 144) return false;                  // the gain's elimination lives in registers
     if ((long)c->n * c->m > (1L << 26) || (long)c->N * c->m > (1L << 28)) return false;
+    if (c->m > 128) return false;                // analysis tiles hold one member row of <= 128 columns
     return true;
 }
 
@@ -136,9 +137,10 @@ void compute_layout(oic_handle* h)
     L.E = take(sizeof(float) * N * h->R_mem * m);
     L.act0 = take(sizeof(float) * N * h->Cmax * n * m);
     L.act1 = take(sizeof(float) * N * h->Cmax * n * m);
-    L.meanE = take(sizeof(float) * Ra * m);
-    L.meanY = take(sizeof(float) * p * m);
-    L.part = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * p);
+    L.part1 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * m);
+    L.part2 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * p);
+    L.S1 = take(sizeof(float) * (Ra + p) * m);
+    L.D = take(sizeof(float) * N * p * m);
     L.C = take(sizeof(double) * (Ra + p) * p);
     L.K = take(sizeof(float) * Ra * p);
     L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
@@ -219,27 +221,23 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
               const float* Yu, int n_yx)
 {
     const oic_config& c = h->cfg;
-    float* meanE = h->at<float>(h->lay.meanE);
-    float* meanY = h->at<float>(h->lay.meanY);
-    float* part = h->at<float>(h->lay.part);
+    float* part1 = h->at<float>(h->lay.part1);
+    float* part2 = h->at<float>(h->lay.part2);
+    float* S1 = h->at<float>(h->lay.S1);
+    float* D = h->at<float>(h->lay.D);
     double* C = h->at<double>(h->lay.C);
-    float* K = h->at<float>(h->lay.K);
-    run_stage(h, OIC_STAGE_MEANS, [&] {
-        launch_means(E, ms, c.N, c.m, act, obs, V, meanE, meanY, h->st);
-    });
-    const int splits = cov_splits(act.count, obs.count, c.N);
+    float* Kt = h->at<float>(h->lay.K);
+    const int R = act.count, p = obs.count, M = R + p;
+    const int splits = stats_splits(R, p, c.N);
     run_stage(h, OIC_STAGE_COV, [&] {
-        launch_cov_partial(E, ms, c.N, c.m, act, obs, V, meanE, meanY, part, splits, h->st);
+        launch_stats(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, part1, part2, D, splits, h->st);
     });
+    run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
     run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
-        launch_cov_reduce(part, splits, act.count + obs.count, obs.count, C, h->st);
+        launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st);
     });
-    run_stage(h, OIC_STAGE_GAIN, [&] {
-        launch_gain(C, act.count, obs.count, K, h->at<int>(h->lay.status), h->st);
-    });
-    run_stage(h, OIC_STAGE_UPDATE, [&] {
-        launch_update(E, ms, c.N, c.m, act, obs, V, K, Yx, Yu, n_yx, h->st);
-    });
+    run_stage(h, OIC_STAGE_GAIN, [&] { launch_gain(C, R, p, Kt, h->at<int>(h->lay.status), h->st); });
+    run_stage(h, OIC_STAGE_UPDATE, [&] { launch_update(E, ms, c.N, c.m, act, Kt, p, D, h->st); });
 }
 
 oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
@@ -367,7 +365,7 @@ oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* c
     h->R_mem = h->full() ? (c.H + 1) * (c.n + c.l) : 2 * c.n + (c.H + 1) * c.l;
     h->Ubase = h->full() ? (c.H + 1) * c.n : 2 * c.n;
     h->R_act_max = h->R_of(c.H);
-    h->splits_max = cov_splits(1, h->p, c.N);
+    h->splits_max = stats_splits(1, h->p, c.N);
     h->noise_n = noise_count(&c);
     h->fused = cnn_fused_supported(c.n_layers, c.channels, c.n, c.m, c.l) &&
                getenv("OIC_NO_FUSED_CNN") == nullptr;

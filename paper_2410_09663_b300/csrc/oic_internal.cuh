@@ -55,22 +55,25 @@ void launch_ensemble_init(float* E, long ms, int N, int n, int m, int l, int x_r
 // E[i][u_to rows] = E[i][u_from rows] + W^i (l x m per member).
 void launch_u_advance(float* E, long ms, int N, int m, int l, int u_from, int u_to,
                       const float* W, cudaStream_t st);
-// Ensemble means of the active rows and of the perturbed observations.
-void launch_means(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                  float* meanE, float* meanY, cudaStream_t st);
-// Split-K anomaly products: part[s][a][c] = sum over members of split s and
-// columns j of L_a * A_Y,c, with L = [active-row anomalies; A_Y].
-int cov_splits(int R, int p, int N);
-void launch_cov_partial(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                        const float* meanE, const float* meanY, float* part, int splits,
-                        cudaStream_t st);
-void launch_cov_reduce(const float* part, int splits, int rows, int p, double* C, cudaStream_t st);
-// K = Cxy Cyy^{-1}; C is [(R + p) x p] with Cxy on top and Cyy below.
+// Shifted anomaly sums (split-K over members): part1[s][a][j] (first column
+// tile only) and part2[s][a][c]; the first row tile also writes the
+// innovations Dbuf[i][c][j] = Ybar[c][j] - Y^i[c][j].  Rows a < R are active
+// state rows, a >= R the perturbed observations; Ybar rows c < n_yx come from
+// Yx, the rest from Yu.  m <= 128.
+int stats_splits(int R, int p, int N);
+size_t stats_smem_bytes(int m);
+void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
+                  const float* Yu, int n_yx, float* part1, float* part2, float* Dbuf, int splits, cudaStream_t st);
+void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st);
+// C = sum_s part2 - S1 S1_Y^T / N  ([(R + p) x p], Cxy on top, Cyy below).
+void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
+                         cudaStream_t st);
+// Kt = (Cxy Cyy^{-1})^T, [p][R].
 size_t gain_smem_bytes(int p);
-void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st);
-// E^i[act rows] += K (Ybar - (H E^i + V^i)); Ybar rows c < n from Yx, else Yu.
-void launch_update(float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                   const float* K, const float* Yx, const float* Yu, int n_yx, cudaStream_t st);
+void launch_gain(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st);
+// E^i[act rows] += K D^i for every member.
+void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
+                   cudaStream_t st);
 // out[b][r][j] = mean_i E[i][row0 + b*rows_per_block + r][j] for blocks b.
 void launch_block_means(const float* E, long ms, int N, int m, int row0, int rows_per_block,
                         int n_blocks, float* out, cudaStream_t st);
