@@ -27,7 +27,7 @@
 namespace oic {
 namespace {
 
-constexpr int FT = 256;                                 // threads
+constexpr int FT = 512;                                 // threads (16 warps)
 constexpr int FM = 128;                                 // tile rows (pixels)
 constexpr long long F_WAIT = 4000000000LL;
 
@@ -42,21 +42,29 @@ struct FS {
     static constexpr int BTILE = 2 * (2 * C) * 16;
     static constexpr int BBYTES = 9 * KS * BTILE;
     static constexpr int SP = NPOS | 1;                 // odd FP32 row stride (bank spread)
-    static constexpr int NXB = 5;                       // ring of [X; B U] rows
+    static constexpr int NXB = 6;                       // ring of [X; B U] rows
     static constexpr int OFF_SLOT = 0;
     static constexpr int OFF_B = OFF_SLOT + 3 * SLOT;
     static constexpr int OFF_H2 = OFF_B + BBYTES;                      // [C][SP] fp32
     static constexpr int OFF_XB = OFF_H2 + al16(C * SP * 4);           // [NXB][2][SP] fp32
-    static constexpr int OFF_W1 = OFF_XB + al16(NXB * 2 * SP * 4);     // [C][2][9]
+    static constexpr int OFF_W1 = OFF_XB + al16(NXB * 2 * SP * 4);     // [C/8][2][9][8]
     static constexpr int OFF_B1 = OFF_W1 + al16(C * 2 * 9 * 4);
-    static constexpr int OFF_W3 = OFF_B1 + al16(C * 4);                // [C][9]
-    static constexpr int OFF_B2 = OFF_W3 + al16(C * 9 * 4);
+    static constexpr int OFF_W3 = OFF_B1 + al16(C * 4);                // [C/4][4][12] (9 used)
+    static constexpr int OFF_B2 = OFF_W3 + al16(C * 12 * 4);
     static constexpr int OFF_MISC = OFF_B2 + al16(C * 4);              // b3, mbar, tmem
     static constexpr int OFF_DYN = OFF_MISC + 64;                      // U group, B matrix
     static constexpr int TMEM_COLS = 4 * C;
 };
 
 __device__ __forceinline__ int mod_pos(int r, int k) { return ((r % k) + k) % k; }
+
+// tanh(x) = 1 - 2 / (1 + e^{2x}): saturates correctly at both ends; absolute
+// error a few 1e-7 (the exponential and the quotient are each within a few
+// ulps), which is below the FP32 rounding of the layer's inputs.
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    return 1.f - __fdividef(2.f, 1.f + __expf(2.f * x));
+}
 
 template <int C, int G>
 __device__ __forceinline__ void issue_hidden_mmas(uint32_t s0, uint32_t acc, int r)
@@ -85,6 +93,18 @@ __device__ __forceinline__ void issue_hidden_mmas(uint32_t s0, uint32_t acc, int
     }
 }
 
+// 8 x 32-bit TMEM columns for the warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int C, int G>
 __global__ void __launch_bounds__(FT, 1)
 cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
@@ -94,6 +114,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                  float rs, int* __restrict__ err)
 {
     using S = FS<C, G>;
+    static_assert(C == 32, "one 16-byte chunk of 8 channels per producer thread");
     constexpr int m = FM / G;
     extern __shared__ __align__(1024) unsigned char smem[];
     float* h2 = reinterpret_cast<float*>(smem + S::OFF_H2);
@@ -117,8 +138,17 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
         reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk2)[e];
     for (int e = tid; e < C * S::SP; e += FT) h2[e] = 0.f;
     for (int e = tid; e < S::NXB * 2 * S::SP; e += FT) xb[e] = 0.f;
-    for (int e = tid; e < C * 18; e += FT) sw1[e] = w1[e];
-    for (int e = tid; e < C * 9; e += FT) sw3[e] = w3[e];
+    for (int e = tid; e < C * 18; e += FT) {     // [co][ch][tap] -> [co/8][ch][tap][co%8]
+        const int co = e / 18, r = e % 18;
+        sw1[((co / 8) * 18 + r) * 8 + (co % 8)] = w1[e];
+    }
+    // last-layer weights as [j][quarter][12]: channel ci = quarter * C/4 + j, so
+    // the four channel quarters read by one warp fall in different banks
+    for (int e = tid; e < C * 12; e += FT) {
+        const int slot = e / 12, k = e % 12;
+        const int j = slot / 4, qq = slot % 4, ci = qq * (C / 4) + j;
+        sw3[e] = k < 9 ? w3[ci * 9 + k] : 0.f;
+    }
     for (int e = tid; e < C; e += FT) { sb1[e] = b1[e]; sb2[e] = b2[e]; }
     for (int e = tid; e < n * l; e += FT) sB[e] = Bmat[e];
     if (tid == 0) {
@@ -142,10 +172,10 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     int par = 0;
     bool failed = false;
 
-    // roles
-    const int pp = tid % FM;                            // producer pixel (interleaved index)
-    const int cg = tid / FM;                            // producer channel half
-    const int lp = tid >> 1, lh = tid & 1;              // last layer: pixel, channel half
+    // roles: producer = (pixel pp, 8-channel chunk cq); last layer = (pixel
+    // lp, 8-channel quarter lq); epilogue = (TMEM lane quarter, channel group)
+    const int pp = tid % FM, cq = tid / FM;
+    const int lp = tid >> 2, lq = tid & 3;
 
     for (long t = t0; t < t1 && !failed;) {
         const int g = (int)(t / n);
@@ -156,7 +186,6 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
         const int r_lo = ys > 0 ? ys - 1 : 0;
         const int r_hi = ye < n ? ye : n - 1;
 
-        // U of the group
         for (int e = tid; e < G * l * m; e += FT) {
             const int b = e / (l * m), rr = e % (l * m);
             const int mb = g * G + b;
@@ -166,8 +195,8 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
 
         // [X; B U] row r into its ring slot (zero outside the image / group)
         auto load_xb = [&](int r) {
-            float* d = xb + mod_pos(r, S::NXB) * 2 * S::SP;
             if (tid < FM) {
+                float* d = xb + mod_pos(r, S::NXB) * 2 * S::SP;
                 const int b = tid / m, x = tid % m;     // coalesced over x
                 const int mb = g * G + b;
                 const int q = G + G * x + b;
@@ -181,57 +210,56 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                 d[S::SP + q] = bu;
             }
         };
-        // first layer row r (C channels for this thread's pixel half cg) -> hi/lo fp16
-        auto first_layer = [&](int r, uint4 (&hv)[2], uint4 (&lv)[2]) {
-            float acc[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = sb1[cg * 16 + j];
+        // first layer row r, this thread's 8 channels of pixel pp -> hi/lo fp16
+        auto first_layer = [&](int r, uint4& hv, uint4& lv) {
             if (r >= 0 && r < n) {
+                float acc[8];
+                const float4 bA = *reinterpret_cast<const float4*>(sb1 + 8 * cq);
+                const float4 bB = *reinterpret_cast<const float4*>(sb1 + 8 * cq + 4);
+                acc[0] = bA.x; acc[1] = bA.y; acc[2] = bA.z; acc[3] = bA.w;
+                acc[4] = bB.x; acc[5] = bB.y; acc[6] = bB.z; acc[7] = bB.w;
                 const int q = G + pp;
+                const float* wq = sw1 + cq * 18 * 8;
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy) {
                     const float* row = xb + mod_pos(r + dy - 1, S::NXB) * 2 * S::SP;
 #pragma unroll
                     for (int ch = 0; ch < 2; ++ch) {
-                        const float v0 = row[ch * S::SP + q - G];
-                        const float v1 = row[ch * S::SP + q];
-                        const float v2 = row[ch * S::SP + q + G];
+                        const float v3[3] = {row[ch * S::SP + q - G], row[ch * S::SP + q], row[ch * S::SP + q + G]};
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float* w = sw1 + ((cg * 16 + j) * 2 + ch) * 9 + dy * 3;
-                            acc[j] = fmaf(w[0], v0, fmaf(w[1], v1, fmaf(w[2], v2, acc[j])));
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const float* w = wq + (ch * 9 + dy * 3 + dx) * 8;
+                            const float4 wa = *reinterpret_cast<const float4*>(w);
+                            const float4 wb = *reinterpret_cast<const float4*>(w + 4);
+                            const float v = v3[dx];
+                            acc[0] = fmaf(wa.x, v, acc[0]); acc[1] = fmaf(wa.y, v, acc[1]);
+                            acc[2] = fmaf(wa.z, v, acc[2]); acc[3] = fmaf(wa.w, v, acc[3]);
+                            acc[4] = fmaf(wb.x, v, acc[4]); acc[5] = fmaf(wb.y, v, acc[5]);
+                            acc[6] = fmaf(wb.z, v, acc[6]); acc[7] = fmaf(wb.w, v, acc[7]);
                         }
                     }
                 }
+                __align__(16) __half hi[8], lo[8];
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    __align__(16) __half hi[8], lo[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) tc::split_f16(tanhf(acc[8 * k + e]), hi[e], lo[e]);
-                    hv[k] = *reinterpret_cast<const uint4*>(hi);
-                    lv[k] = *reinterpret_cast<const uint4*>(lo);
-                }
+                for (int e = 0; e < 8; ++e) tc::split_f16(tanh_fast(acc[e]), hi[e], lo[e]);
+                hv = *reinterpret_cast<const uint4*>(hi);
+                lv = *reinterpret_cast<const uint4*>(lo);
             } else {
-#pragma unroll
-                for (int k = 0; k < 2; ++k) hv[k] = lv[k] = make_uint4(0u, 0u, 0u, 0u);
+                hv = lv = make_uint4(0u, 0u, 0u, 0u);
             }
         };
-        auto store_h1 = [&](int r, const uint4 (&hv)[2], const uint4 (&lv)[2]) {
+        auto store_h1 = [&](int r, const uint4& hv, const uint4& lv) {
             unsigned char* slot = smem + S::OFF_SLOT + mod_pos(r, 3) * S::SLOT;
             const int q = G + pp;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int kc = cg * 2 + k;
-                *reinterpret_cast<uint4*>(slot + kc * S::PLANE + q * 16) = hv[k];
-                *reinterpret_cast<uint4*>(slot + (S::KC + kc) * S::PLANE + q * 16) = lv[k];
-            }
+            *reinterpret_cast<uint4*>(slot + cq * S::PLANE + q * 16) = hv;
+            *reinterpret_cast<uint4*>(slot + (S::KC + cq) * S::PLANE + q * 16) = lv;
         };
 
-        // prologue: [X; B U] rows r_lo-2 .. r_lo+2, first-layer rows r_lo-1 .. r_lo+1
-        for (int r = r_lo - 2; r <= r_lo + 2; ++r) load_xb(r);
+        // prologue: [X; B U] rows r_lo-2 .. r_lo+3, first-layer rows r_lo-1 .. r_lo+1
+        for (int r = r_lo - 2; r <= r_lo + 3; ++r) load_xb(r);
         __syncthreads();
         for (int r = r_lo - 1; r <= r_lo + 1; ++r) {
-            uint4 hv[2], lv[2];
+            uint4 hv, lv;
             first_layer(r, hv, lv);
             store_h1(r, hv, lv);
         }
@@ -245,12 +273,8 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;            // outputs of rows r-1, r, r+1
         for (int r = r_lo; r <= r_hi; ++r) {
             const bool more = r + 1 <= r_hi;
-            uint4 hv[2], lv[2];
-            if (more) {
-                load_xb(r + 3);
-                __syncthreads();
-                first_layer(r + 2, hv, lv);            // overlaps hidden row r on the tensor core
-            }
+            uint4 hv, lv;
+            if (more) first_layer(r + 2, hv, lv);      // overlaps hidden row r on the tensor core
             const bool ok = tc::mbar_wait_bounded(mbar, phase, F_WAIT);
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -261,26 +285,31 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
             if (more) {
                 store_h1(r + 2, hv, lv);
                 tc::fence_proxy_async_smem();
+                tc::fence_before_sync();
                 __syncthreads();
                 if (tid == 0) {
                     tc::fence_after_sync();
                     issue_hidden_mmas<C, G>(s0, tmem + (par ^ 1) * 2 * C, r + 1);
                     tc::mma_commit(mbar);
                 }
+                load_xb(r + 4);                          // slot of row r - 2, no longer read
+            } else {
+                tc::fence_before_sync();
+                __syncthreads();                        // previous row's last layer is done with h2
             }
             // hidden row r: tanh(main + corr 2^-11 + b2) -> h2[co][G + lane]
             {
-                const int q4 = warp & 3, hh = warp >> 2;
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + par * 2 * C + hh * (C / 2);
-                float mv[16], cv[16];
-                tc::tmem_ld16(taddr, mv);
-                tc::tmem_ld16(taddr + C, cv);
+                const int q4 = warp & 3, cg = warp >> 2;  // lane quarter, 8-channel group
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + par * 2 * C + cg * 8;
+                float mv[8], cv[8];
+                tmem_ld8(taddr, mv);
+                tmem_ld8(taddr + C, cv);
                 tc::tmem_ld_wait();
                 const int pos = G + 32 * q4 + lane;
 #pragma unroll
-                for (int j = 0; j < C / 2; ++j) {
-                    const int co = hh * (C / 2) + j;
-                    h2[co * S::SP + pos] = tanhf(fmaf(cv[j], tc::SPLIT_INV, mv[j]) + sb2[co]);
+                for (int j = 0; j < 8; ++j) {
+                    const int co = cg * 8 + j;
+                    h2[co * S::SP + pos] = tanh_fast(fmaf(cv[j], tc::SPLIT_INV, mv[j]) + sb2[co]);
                 }
             }
             __syncthreads();
@@ -288,24 +317,30 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
             {
                 const int q = G + lp;
                 float p0 = 0.f, p1 = 0.f, p2 = 0.f;
-#pragma unroll 4
-                for (int j = 0; j < C / 2; ++j) {
-                    const int ci = lh * (C / 2) + j;
+#pragma unroll
+                for (int j = 0; j < C / 4; ++j) {
+                    const int ci = lq * (C / 4) + j;
                     const float* hrow = h2 + ci * S::SP;
                     const float v0 = hrow[q - G], v1 = hrow[q], v2 = hrow[q + G];
-                    const float* w = sw3 + ci * 9;
-                    p0 = fmaf(w[0], v0, fmaf(w[1], v1, fmaf(w[2], v2, p0)));
-                    p1 = fmaf(w[3], v0, fmaf(w[4], v1, fmaf(w[5], v2, p1)));
-                    p2 = fmaf(w[6], v0, fmaf(w[7], v1, fmaf(w[8], v2, p2)));
+                    const float* wr = sw3 + (j * 4 + lq) * 12;
+                    const float4 wA = *reinterpret_cast<const float4*>(wr);
+                    const float4 wB = *reinterpret_cast<const float4*>(wr + 4);
+                    const float w8 = wr[8];
+                    p0 = fmaf(wA.x, v0, fmaf(wA.y, v1, fmaf(wA.z, v2, p0)));
+                    p1 = fmaf(wA.w, v0, fmaf(wB.x, v1, fmaf(wB.y, v2, p1)));
+                    p2 = fmaf(wB.z, v0, fmaf(wB.w, v1, fmaf(w8, v2, p2)));
                 }
                 p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
                 p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
                 p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
+                p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+                p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+                p2 += __shfl_xor_sync(0xffffffffu, p2, 2);
                 a0 += p2;                               // kernel row 2 of hidden row r -> output r-1
                 a1 += p1;
                 a2 += p0;
                 const int ro = r - 1;
-                if (lh == 0 && ro >= ys && ro < ye) {
+                if (lq == 0 && ro >= ys && ro < ye) {
                     const int b = lp % G, x = lp / G, mb = g * G + b;
                     if (mb < Nb) {
                         const float xv = xb[mod_pos(ro, S::NXB) * 2 * S::SP + q];
@@ -314,11 +349,9 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                 }
                 a0 = a1; a1 = a2; a2 = 0.f;
             }
-            tc::fence_before_sync();
-            __syncthreads();
             par ^= 1;
         }
-        if (!failed && ye == n && n - 1 >= ys && lh == 0) {
+        if (!failed && ye == n && n - 1 >= ys && lq == 0) {
             // bottom row: the hidden row below the image is zero
             const int b = lp % G, x = lp / G, mb = g * G + b;
             if (mb < Nb) {

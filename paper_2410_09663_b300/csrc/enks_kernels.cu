@@ -16,14 +16,6 @@
 namespace oic {
 namespace {
 
-__device__ __forceinline__ float4 obs_noise4(const ObsNoise& V, int i, int c, int p, int m, int j)
-{
-    if (V.Va == nullptr) return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c < V.pa) return *reinterpret_cast<const float4*>(V.Va + ((long)i * V.pa + c) * m + j);
-    const int pb = p - V.pa;
-    return *reinterpret_cast<const float4*>(V.Vb + ((long)i * pb + (c - V.pa)) * m + j);
-}
-
 // ------------------------------------------------------------------ init
 __global__ void init_kernel(float* __restrict__ E, long ms, int n, int m, int l, int x_row0, int u_row0,
                             const float* __restrict__ X_k, const float* __restrict__ U_prev,
@@ -67,14 +59,6 @@ constexpr int SBM = 64, SBN = 96, SPAD = 4;
 __device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
-__device__ __forceinline__ float4 load_left4(const float* Ei, long ms, int m, int a, int R, const RowSet& act,
-                                             const RowSet& obs, const ObsNoise& V, int i, int p, int j)
-{
-    if (a < R) return *reinterpret_cast<const float4*>(Ei + (long)act.rows[a] * m + j);
-    const int c = a - R;
-    return f4add(*reinterpret_cast<const float4*>(Ei + (long)obs.rows[c] * m + j), obs_noise4(V, i, c, p, m, j));
-}
-
 template <int NT>
 __global__ void __launch_bounds__(NT)
 stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
@@ -96,17 +80,33 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
     const int m4 = m / 4;
     const bool do_s1 = blockIdx.y == 0, do_d = blockIdx.x == 0;
 
-    // loader chunks: consecutive threads take consecutive 16-byte pieces of a row
-    int ar[QA], aj[QA], br[QB], bj[QB];
+    // loader chunks: consecutive threads take consecutive 16-byte pieces of a
+    // row.  Row offsets and the noise source are resolved once: off < 0 marks
+    // an empty chunk, vsel 0 no noise, 1 Va, 2 Vb.
+    long aoff[QA], boff[QB];
+    int aj[QA], bj[QB], avs[QA], bvs[QB], ar[QA], br[QB];
+    long avo[QA], bvo[QB];
     float4 refa[QA], refb[QB], pa[QA], pb[QB], s1[QA];
     const float4 Z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int pb_rows = p - V.pa;
+    auto resolve = [&](int a, long& off, int& vs, long& vo) {
+        vs = 0; vo = 0;
+        if (a < R) { off = (long)act.rows[a] * m; return; }
+        const int c = a - R;
+        off = (long)obs.rows[c] * m;
+        if (V.Va == nullptr) return;
+        if (c < V.pa) { vs = 1; vo = (long)c * m; }
+        else { vs = 2; vo = (long)(c - V.pa) * m; }
+    };
 #pragma unroll
     for (int q = 0; q < QA; ++q) {
         const int e = tid + NT * q;
         ar[q] = e < SBM * m4 ? e / m4 : -1;
         aj[q] = 4 * (e % m4);
         const int a = bm0 + ar[q];
-        refa[q] = (ar[q] >= 0 && a < M) ? load_left4(E, ms, m, a, R, act, obs, V, 0, p, aj[q]) : Z;
+        aoff[q] = -1;
+        avs[q] = 0; avo[q] = 0;
+        if (ar[q] >= 0 && a < M) resolve(a, aoff[q], avs[q], avo[q]);
         s1[q] = Z;
     }
 #pragma unroll
@@ -115,20 +115,25 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
         br[q] = e < SBN * m4 ? e / m4 : -1;
         bj[q] = 4 * (e % m4);
         const int c = bn0 + br[q];
-        refb[q] = (br[q] >= 0 && c < p) ? load_left4(E, ms, m, R + c, R, act, obs, V, 0, p, bj[q]) : Z;
+        boff[q] = -1;
+        bvs[q] = 0; bvo[q] = 0;
+        if (br[q] >= 0 && c < p) resolve(R + c, boff[q], bvs[q], bvo[q]);
     }
+    auto value = [&](int i, long off, int vs, long vo, int j) {
+        float4 x = *reinterpret_cast<const float4*>(E + (long)i * ms + off + j);
+        if (vs == 1) x = f4add(x, *reinterpret_cast<const float4*>(V.Va + (long)i * V.pa * m + vo + j));
+        else if (vs == 2) x = f4add(x, *reinterpret_cast<const float4*>(V.Vb + (long)i * pb_rows * m + vo + j));
+        return x;
+    };
+#pragma unroll
+    for (int q = 0; q < QA; ++q) refa[q] = aoff[q] >= 0 ? value(0, aoff[q], avs[q], avo[q], aj[q]) : Z;
+#pragma unroll
+    for (int q = 0; q < QB; ++q) refb[q] = boff[q] >= 0 ? value(0, boff[q], bvs[q], bvo[q], bj[q]) : Z;
     auto fetch = [&](int i) {
-        const float* Ei = E + (long)i * ms;
 #pragma unroll
-        for (int q = 0; q < QA; ++q) {
-            const int a = bm0 + ar[q];
-            pa[q] = (ar[q] >= 0 && a < M) ? f4sub(load_left4(Ei, ms, m, a, R, act, obs, V, i, p, aj[q]), refa[q]) : Z;
-        }
+        for (int q = 0; q < QA; ++q) pa[q] = aoff[q] >= 0 ? f4sub(value(i, aoff[q], avs[q], avo[q], aj[q]), refa[q]) : Z;
 #pragma unroll
-        for (int q = 0; q < QB; ++q) {
-            const int c = bn0 + br[q];
-            pb[q] = (br[q] >= 0 && c < p) ? f4sub(load_left4(Ei, ms, m, R + c, R, act, obs, V, i, p, bj[q]), refb[q]) : Z;
-        }
+        for (int q = 0; q < QB; ++q) pb[q] = boff[q] >= 0 ? f4sub(value(i, boff[q], bvs[q], bvo[q], bj[q]), refb[q]) : Z;
     };
     float acc[4][CPT];
 #pragma unroll
@@ -270,15 +275,22 @@ constexpr int G_KQ = (G_MAXP + 31) / 32;
 __global__ void __launch_bounds__(G_THREADS)
 gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
 {
-    extern __shared__ float Ls[];                 // [p][ps]
+    extern __shared__ float Ls[];                 // [p][ps], then the triangle table
     __shared__ float rdiag[G_MAXP];               // 1 / L_jj
     __shared__ int bad;
     const int ps = p | 1;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    uint32_t* tri = reinterpret_cast<uint32_t*>(Ls + p * ps);   // e -> (r << 16 | c), c <= r
+    const int tid = threadIdx.x;
     const double* Cyy = C + (long)R * p;
     for (int e = tid; e < p * p; e += G_THREADS) {
         const int i = e / p, k = e % p;
         if (k <= i) Ls[i * ps + k] = (float)Cyy[e];
+    }
+    // enumerate the triangle {(r, c): 0 <= c <= r} row by row; the trailing
+    // block of step j is the first (p-1-j)(p-j)/2 entries shifted by j + 1
+    for (int r = tid; r < p - 1; r += G_THREADS) {
+        const int base = r * (r + 1) / 2;
+        for (int c = 0; c <= r; ++c) tri[base + c] = ((uint32_t)r << 16) | (uint32_t)c;
     }
     if (tid == 0) bad = 0;
     __syncthreads();
@@ -289,17 +301,36 @@ gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, 
             break;
         }
         const float dinv = 1.f / d;
-        for (int i = j + 1 + ty; i < p; i += 16) {
-            const float f = Ls[i * ps + j] * dinv;
-            float* Li = Ls + i * ps;
-            for (int k = j + 1 + tx; k <= i; k += 16) Li[k] = fmaf(-f, Ls[k * ps + j], Li[k]);
+        const int tj = (p - 1 - j) * (p - j) / 2;   // trailing entries (i, k), j < k <= i
+        const int o = j + 1;
+        for (int e0 = tid; e0 < tj; e0 += 4 * G_THREADS) {
+            // four independent entries per batch: loads first, then the updates
+            int ii[4], kk[4];
+            float aij[4], akj[4], aik[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = e0 + q * G_THREADS;
+                const uint32_t rc = e < tj ? tri[e] : 0u;
+                ii[q] = o + (int)(rc >> 16);
+                kk[q] = o + (int)(rc & 0xffffu);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool ok = e0 + q * G_THREADS < tj;
+                aij[q] = ok ? Ls[ii[q] * ps + j] : 0.f;
+                akj[q] = ok ? Ls[kk[q] * ps + j] : 0.f;
+                aik[q] = ok ? Ls[ii[q] * ps + kk[q]] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (e0 + q * G_THREADS < tj) Ls[ii[q] * ps + kk[q]] = fmaf(-aij[q] * dinv, akj[q], aik[q]);
         }
         __syncthreads();
-        // column j is final now: L[i][j] = A[i][j] / sqrt(d)
+        // column j is final now: L[i][j] = A[i][j] / sqrt(d); the next step
+        // reads column j + 1 only
         const float rs = rsqrtf(d);
         for (int i = j + tid; i < p; i += G_THREADS) Ls[i * ps + j] = i == j ? d * rs : Ls[i * ps + j] * rs;
         if (tid == 0) rdiag[j] = 1.f / (d * rs);
-        // the next step reads column j + 1 only, which this scaling does not touch
     }
     __syncthreads();
     const int warp = tid / 32, lane = tid % 32;
@@ -502,7 +533,7 @@ int gain_max_p() { return G_MAXP; }
 
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * (size_t)p * (p | 1);
+    const size_t smem = sizeof(float) * (size_t)p * (p | 1) + sizeof(uint32_t) * (size_t)p * (p - 1) / 2;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(gain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
