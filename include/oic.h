@@ -197,6 +197,48 @@ unsigned long long oic_launch_count(void);
  * completed.  Synchronous. */
 oic_status oic_selftest(oic_handle* h, int* result);
 
+/* Size of the fixed device scratch behind oic_enks_update_static. */
+#define OIC_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* oic_enks_update for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a deployment variant of the same
+ * ensemble Kalman analysis.
+ *
+ * Who needs it: code that may not call cudaMalloc at all -- work issued
+ * inside a CUDA graph capture, a real-time loop that must never reach the
+ * allocator after start-up, a plug-in whose host application owns all GPU
+ * memory, or an embedding with a fixed memory map.  Such a caller cannot
+ * provide the workspace oic_bind needs, so this entry point takes no handle
+ * and keeps every intermediate (split-K partials, innovations, covariances,
+ * gain, row tables, status) in one device array of OIC_STATIC_SCRATCH_BYTES
+ * that the library's CUDA module carries.  Every GPU that loads the library
+ * holds that array until the process exits.
+ *
+ * Arguments (device pointers unless noted; E and V 16-byte aligned):
+ *   N, R, m, p   members, state rows, columns, observed rows
+ *                (N >= 2, 4 <= m <= 128 with m % 4 == 0, 1 <= p <= 144)
+ *   obs_rows     HOST array of p row indices of E (each < R), read during the
+ *                call only
+ *   E            [N][R][m] in/out: E^i <- E^i + K (Ybar - (E^i[obs_rows] + V^i))
+ *   V            [N][p][m] observation perturbations
+ *   Ybar         [p][m] pseudo-observation
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
+ * Returns OIC_OK, OIC_ENOTSPD (the update was skipped; E unchanged),
+ * OIC_EINVAL on bad arguments, or OIC_ENOMEM when these sizes need more than
+ * OIC_STATIC_SCRATCH_BYTES, which is about
+ *   4 (N p m + s (R + p)(m + p) + (R + p) m + p R) + 8 (R + p) p bytes,
+ * s = split count (<= 148 / ceil((R + p) / 64)).  It allocates nothing and
+ * synchronises the stream before returning (it reads the status word).
+ *
+ * The first call on each device looks up the scratch's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind
+ * (the status word is cleared at the start of each call): calls that overlap
+ * on the GPU -- from several host threads or several streams -- race on it
+ * and must be serialised by the caller. */
+oic_status oic_enks_update_static(int N, int R, int m, int p, const int* obs_rows, float* E,
+                                  const float* V, const float* Ybar, void* cuda_stream);
+
 /* Waits for the bound stream and returns (and clears) the device status. */
 oic_status oic_sync(oic_handle* h);
 

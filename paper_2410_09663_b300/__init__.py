@@ -66,6 +66,8 @@ _SIGS = {
     "oic_profile_end": (ctypes.c_int, [_VP, _FP, ctypes.POINTER(ctypes.c_int)]),
     "oic_launch_count": (ctypes.c_ulonglong, []),
     "oic_selftest": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "oic_enks_update_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                                              _VP, _VP, _VP]),
     "oic_destroy": (None, [_VP]),
     "oic_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "oic_version": (ctypes.c_char_p, []),
