@@ -213,7 +213,9 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / args.steps * wl.N / n_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(wl),
+            "config": config_dict(wl, {"precision": "fp64", "noise": "host generator (numpy PCG64)",
+                                       "history": "full smoothed history [X; U; dU] blocks k..k+H",
+                                       "l2": "n/a (CPU)"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
                              "sample": f"each step: 1 control step with {n_s} of {wl.N} members, "
                                        f"scaled by {n_s}/{wl.N}"},
