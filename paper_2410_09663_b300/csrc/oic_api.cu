@@ -28,7 +28,7 @@ struct Profiler {
 };
 
 struct Layout {
-    size_t w, b, B, wtc, E, act0, act1, part1, part2, S1, D, C, K, rowtab, status, selftest;
+    size_t w, b, B, wtc, wfused, E, act0, act1, part1, part2, S1, D, C, K, rowtab, status, selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -133,6 +133,7 @@ void compute_layout(oic_handle* h)
                 tc_bytes += align_up(conv_tc_packed_bytes(c.channels[k]), 256);
             }
         L.wtc = take(tc_bytes);
+        L.wfused = take(h->fused ? cnn_fused_packed_bytes() : 0);
     }
     L.E = take(sizeof(float) * N * h->R_mem * m);
     L.act0 = take(sizeof(float) * N * h->Cmax * n * m);
@@ -174,18 +175,12 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
 {
     const oic_config& c = h->cfg;
     if (h->fused) {
-        const float* w = h->at<float>(h->lay.w);
         const float* b = h->at<float>(h->lay.b);
         const int C = c.channels[1];
-        const float* w1 = w;
-        const float* w3 = w + (size_t)2 * C * 9 + (size_t)C * C * 9;
-        const float* b1 = b;
-        const float* b2 = b + C;
-        const float* b3 = b + 2 * C;
         run_stage(h, OIC_STAGE_CNN_FUSED, [&] {
-            launch_cnn_fused(X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l, w1, b1,
-                             h->at<char>(h->lay.wtc) + h->wtc_off[1], b2, w3, b3, c.residual_scale, h->n_sm,
-                             h->at<int>(h->lay.status), h->st);
+            launch_cnn_fused(X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l, b,
+                             h->at<char>(h->lay.wtc) + h->wtc_off[1], b + C, h->at<char>(h->lay.wfused),
+                             b + 2 * C, c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st);
         });
         return;
     }
@@ -408,6 +403,14 @@ oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda
                                        cudaMemcpyHostToDevice));
             }
             wl += (size_t)cin * cout * 9;
+        }
+        if (h->fused) {
+            const int C = c.channels[1];
+            const float* w1 = h->w.data();
+            const float* w3 = w1 + (size_t)2 * C * 9 + (size_t)C * C * 9;
+            std::vector<unsigned char> pk(cnn_fused_packed_bytes());
+            cnn_fused_pack_weights(w1, w3, pk.data());
+            OIC_CUDA_OK(cudaMemcpy(h->at<char>(h->lay.wfused), pk.data(), pk.size(), cudaMemcpyHostToDevice));
         }
     }
     // row tables
