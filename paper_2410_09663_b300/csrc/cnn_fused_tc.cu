@@ -31,8 +31,10 @@
 namespace oic {
 namespace {
 
-constexpr int FT = 512;                                 // threads (16 warps)
+constexpr int FT = 544;                                 // 16 drain warps + 1 MMA-issuing warp
+constexpr int ND = 512;                                 // drain threads
 constexpr int FM = 128;                                 // tile rows (pixels)
+constexpr int BAR_DRAIN = 1;                            // named barrier of the drain warps
 constexpr long long F_WAIT = 4000000000LL;
 
 __host__ __device__ constexpr int al16(int x) { return (x + 15) / 16 * 16; }
@@ -49,10 +51,11 @@ struct FS {
     static constexpr int B1BYTES = 3 * 2 * 64 * 16;     // first layer: 3 taps x (2 x 64 x 8)
     static constexpr int B3TILE = 2 * 16 * 16;          // last layer tile: 2 x 16 x 8
     static constexpr int B3BYTES = 3 * KS * 2 * B3TILE;
-    static constexpr int NH1 = 4, NXB = 8;
+    static constexpr int NH1 = 4, NXB = 10;
     static constexpr int SP = NPOS | 1;                 // odd FP32 row stride
     static constexpr int OFF_H1 = 0;
-    static constexpr int OFF_H2 = OFF_H1 + NH1 * SLOT;
+    static constexpr int OFF_Z = OFF_H1 + NH1 * SLOT;   // permanently zero activation row
+    static constexpr int OFF_H2 = OFF_Z + SLOT;
     static constexpr int OFF_F = OFF_H2 + 2 * SLOT;
     static constexpr int OFF_B = OFF_F + 2 * FBUF;
     static constexpr int OFF_B1 = OFF_B + BBYTES;
@@ -60,7 +63,7 @@ struct FS {
     static constexpr int OFF_XB = OFF_B3 + B3BYTES;                    // [NXB][2][SP] fp32
     static constexpr int OFF_BIAS = OFF_XB + al16(NXB * 2 * SP * 4);   // b1[C], b2[C], b3
     static constexpr int OFF_MISC = OFF_BIAS + al16((2 * C + 4) * 4);  // mbarriers, TMEM base
-    static constexpr int OFF_DYN = OFF_MISC + 64;                      // U group, B matrix
+    static constexpr int OFF_DYN = OFF_MISC + 128;                     // U group, B matrix
     static constexpr int ZERO_BYTES = OFF_B;                           // operand buffers incl. pads
     // tensor memory: first-layer, hidden and last-layer accumulators, double buffered
     static constexpr int T_F = 0, T_H = 4 * C, T_L = 8 * C;
@@ -103,8 +106,10 @@ __device__ __forceinline__ void issue_first(uint32_t s0, uint32_t acc, int r1)
     }
 }
 
+// Hidden row r from first-layer rows r-1, r, r+1; rows outside the image read
+// the zero slot.
 template <int C, int G>
-__device__ __forceinline__ void issue_hidden(uint32_t s0, uint32_t acc, int r)
+__device__ __forceinline__ void issue_hidden(uint32_t s0, uint32_t acc, int r, int n)
 {
     using S = FS<C, G>;
     constexpr uint32_t id1 = tc::idesc_f16(FM, 2 * C);
@@ -112,7 +117,8 @@ __device__ __forceinline__ void issue_hidden(uint32_t s0, uint32_t acc, int r)
     uint32_t accumulate = 0;
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
-        const uint32_t slot = s0 + S::OFF_H1 + mod_pos(r + dy - 1, S::NH1) * S::SLOT;
+        const int j = r + dy - 1;
+        const uint32_t slot = s0 + ((j < 0 || j >= n) ? S::OFF_Z : S::OFF_H1 + mod_pos(j, S::NH1) * S::SLOT);
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
@@ -150,6 +156,18 @@ __device__ __forceinline__ void issue_last(uint32_t s0, uint32_t acc, int h)
     }
 }
 
+// mbarriers in the MISC region (8 bytes each)
+enum : int {
+    MB_F = 0,          // first layer done (tensor core -> drain warps)
+    MB_H = 1,          // [2] hidden layer done, by row parity
+    MB_L = 3,          // [2] last layer done, by row parity
+    MB_RH1 = 5,        // first-layer row drained into its operand slot (16 warps)
+    MB_RF = 6,         // [2] first-layer operand built, by row parity (4 warps)
+    MB_RH2 = 8,        // [2] hidden row drained into its operand buffer (16 warps)
+    MB_FIN = 10,       // every MMA of the kernel done
+    MB_COUNT = 11
+};
+
 template <int C, int G>
 __global__ void __launch_bounds__(FT, 1)
 cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
@@ -158,20 +176,21 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                  const __half* __restrict__ wpk13, const float* __restrict__ b3, float rs, int* __restrict__ err)
 {
     using S = FS<C, G>;
-    static_assert(C == 32, "16 warps = 4 lane quarters x 4 groups of 8 channels");
+    static_assert(C == 32, "16 drain warps = 4 lane quarters x 4 groups of 8 channels");
+    static_assert(MB_COUNT * 8 + 4 <= 128, "MISC region");
     constexpr int m = FM / G;
     extern __shared__ __align__(1024) unsigned char smem[];
     float* xb = reinterpret_cast<float*>(smem + S::OFF_XB);
     float* sbias = reinterpret_cast<float*>(smem + S::OFF_BIAS);   // b1 | b2 | b3
-    uint64_t* mbarF = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
-    uint64_t* mbarM = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC + 8);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + 16);
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + MB_COUNT * 8);
     float* su = reinterpret_cast<float*>(smem + S::OFF_DYN);                 // [G][l][m]
     float* sB = su + G * l * m;                                              // [n][l]
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const uint32_t s0 = tc::smem_u32(smem);
 
-    // ---- one-time set-up: zero the operand buffers (pads stay zero), copy weights
+    // ---- one-time set-up: zero the operand buffers (pads and the zero slot
+    // stay zero), copy weights
     for (int e = tid; e < S::ZERO_BYTES / 16; e += FT)
         reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
     for (int e = tid; e < S::BBYTES / 16; e += FT)
@@ -183,8 +202,11 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     for (int e = tid; e < n * l; e += FT) sB[e] = Bmat[e];
     if (tid == 0) {
         sbias[2 * C] = b3[0];
-        tc::mbar_init(mbarF, 1);
-        tc::mbar_init(mbarM, 1);
+        for (int i = 0; i < MB_COUNT; ++i) {
+            const int cnt = (i == MB_RH1 || i == MB_RH2 || i == MB_RH2 + 1) ? 16
+                          : (i == MB_RF || i == MB_RF + 1) ? 4 : 1;
+            tc::mbar_init(mb + i, cnt);
+        }
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -200,49 +222,93 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n;
     const long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
-    uint32_t phF = 0, phM = 0;
+    uint32_t ph = 0;                                    // this thread's phase bit per mbarrier
     bool failed = false;
-    const int q4 = warp & 3, cg = warp >> 2;            // epilogue: lane quarter, channel group
-    const int ep = 32 * q4 + lane;                      // epilogue pixel (TMEM lane)
+    auto wait = [&](int i) {
+        if (!tc::mbar_wait_bounded(mb + i, (ph >> i) & 1u, F_WAIT)) {
+            failed = true;
+            atomicExch(err, DEV_TIMEOUT);
+        }
+        ph ^= 1u << i;
+        tc::fence_after_sync();
+    };
+    const int q4 = warp & 3, cg = (warp >> 2) & 3;     // drain: lane quarter, channel group
+    const int ep = 32 * q4 + lane;                      // drain pixel (TMEM lane)
     const uint32_t tlane = (uint32_t)(32 * q4) << 16;
 
-    for (long t = t0; t < t1 && !failed;) {
+    for (long t = t0; t < t1;) {
         const int g = (int)(t / n);
         const int ys = (int)(t % n);
         const long rem = t1 - t;
         const int ye = (long)(n - ys) < rem ? n : (int)(ys + rem);
         t += ye - ys;
+        // output rows ys .. ye-1 need hidden rows r_lo .. r_hi and first-layer
+        // rows r_lo-1 .. r_hi+1 (those inside the image are computed)
         const int r_lo = ys > 0 ? ys - 1 : 0;
         const int r_hi = ye < n ? ye : n - 1;
+        const int f_lo = r_lo - 1 > 0 ? r_lo - 1 : 0;
+        const int f_hi = r_hi + 1 < n - 1 ? r_hi + 1 : n - 1;
+        auto Fvalid = [&](int f) { return f >= f_lo && f <= f_hi; };
 
-        for (int e = tid; e < G * l * m; e += FT) {
-            const int b = e / (l * m), rr = e % (l * m);
-            const int mb = g * G + b;
-            su[e] = mb < Nb ? U[(long)mb * u_ms + rr] : 0.f;
-        }
-        __syncthreads();
-
-        // [X; B U] row r into its ring slot (zero outside the image / group)
-        auto load_xb = [&](int r) {
-            if (tid < FM) {
-                float* d = xb + mod_pos(r, S::NXB) * 2 * S::SP;
-                const int b = tid / m, x = tid % m;     // coalesced over x
-                const int mb = g * G + b;
-                const int q = G + G * x + b;
-                float xv = 0.f, bu = 0.f;
-                if (r >= 0 && r < n && mb < Nb) {
-                    xv = X[(long)mb * x_ms + (long)r * m + x];
-                    const float* ub = su + b * l * m + x;
-                    for (int c = 0; c < l; ++c) bu = fmaf(sB[r * l + c], ub[c * m], bu);
+        if (warp == ND / 32) {
+            // ================= MMA-issuing warp (one thread) =================
+            // iteration k: first-layer row k+3, hidden row k+1, last layer of row k
+            if (lane == 0) {
+                for (int k = r_lo - 4; k <= r_hi && !failed; ++k) {
+                    if (Fvalid(k + 2)) wait(MB_RH1);                // rows k .. k+2 in their slots
+                    const bool f3 = Fvalid(k + 3);
+                    if (f3) wait(MB_RF + ((k + 3) & 1));           // operand of first-layer row k+3
+                    if (f3) {
+                        issue_first<C, G>(s0, tmem + S::T_F + ((k + 3) & 1) * 64, k + 3);
+                        tc::mma_commit(mb + MB_F);
+                    }
+                    if (k + 1 >= r_lo && k + 1 <= r_hi) {
+                        issue_hidden<C, G>(s0, tmem + S::T_H + ((k + 1) & 1) * 64, k + 1, n);
+                        tc::mma_commit(mb + MB_H + ((k + 1) & 1));
+                    }
+                    if (k >= r_lo) {
+                        wait(MB_RH2 + (k & 1));                     // hidden row k in its buffer
+                        issue_last<C, G>(s0, tmem + S::T_L + (k & 1) * 16, k);
+                        tc::mma_commit(mb + MB_L + (k & 1));
+                    }
                 }
-                d[q] = xv;
-                d[S::SP + q] = bu;
             }
-        };
-        // first-layer operand of row r1: [X, BU] of rows r1-1 .. r1+1, hi | lo
-        auto build_f = [&](int r1) {
-            if (tid < FM) {
-                const int q = G + tid;
+            __syncwarp();
+        } else {
+            // ================= 16 drain warps =================
+            for (int e = tid; e < G * l * m; e += ND) {
+                const int b = e / (l * m), rr = e % (l * m);
+                const int mbr = g * G + b;
+                su[e] = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
+            }
+            tc::named_bar(BAR_DRAIN, ND);
+
+            // [X; B U] row r into its ring slot (zero outside the image / group);
+            // warps 8-11, the X row fetched one row ahead
+            const bool xb_role = tid >= 2 * FM && tid < 3 * FM;
+            const int xt = tid - 2 * FM;
+            const int xb_b = xb_role ? xt / m : 0, xb_x = xb_role ? xt % m : 0;
+            const int xb_mb = g * G + xb_b;
+            auto fetch_x = [&](int r) -> float {
+                return (xb_role && r >= 0 && r < n && xb_mb < Nb) ? X[(long)xb_mb * x_ms + (long)r * m + xb_x] : 0.f;
+            };
+            auto store_xb = [&](int r, float xv) {
+                if (xb_role) {
+                    float* d = xb + mod_pos(r, S::NXB) * 2 * S::SP;
+                    const int q = G + G * xb_x + xb_b;
+                    float bu = 0.f;
+                    if (r >= 0 && r < n && xb_mb < Nb) {
+                        const float* ub = su + xb_b * l * m + xb_x;
+                        for (int c = 0; c < l; ++c) bu = fmaf(sB[r * l + c], ub[c * m], bu);
+                    }
+                    d[q] = xv;
+                    d[S::SP + q] = bu;
+                }
+            };
+            // first-layer operand of row r1: [X, BU] of rows r1-1 .. r1+1, hi | lo (warps 4-7)
+            const bool f_role = tid >= FM && tid < 2 * FM;
+            auto build_f = [&](int r1) {
+                const int q = G + (tid - FM);
                 __align__(16) __half hi[8], lo[8];
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy) {
@@ -254,12 +320,9 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                 unsigned char* f = smem + S::OFF_F + (r1 & 1) * S::FBUF + q * 16;
                 *reinterpret_cast<uint4*>(f) = *reinterpret_cast<const uint4*>(hi);
                 *reinterpret_cast<uint4*>(f + S::PLANE) = *reinterpret_cast<const uint4*>(lo);
-            }
-        };
-        // tanh(main + corr 2^-11 + bias) of this warp's 8 channels -> hi/lo operand row
-        auto drain = [&](uint32_t acc, const float* bias, unsigned char* dst, bool zero) {
-            uint4 H = make_uint4(0u, 0u, 0u, 0u), L = H;
-            if (!zero) {
+            };
+            // tanh(main + corr 2^-11 + bias) of this warp's 8 channels -> hi/lo operand row
+            auto drain = [&](uint32_t acc, const float* bias, unsigned char* dst) {
                 float mv[8], cv[8];
                 tmem_ld8(tmem + tlane + acc + cg * 8, mv);
                 tmem_ld8(tmem + tlane + acc + C + cg * 8, cv);
@@ -268,110 +331,88 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     tc::split_f16(tanh_fast(fmaf(cv[j], tc::SPLIT_INV, mv[j]) + bias[cg * 8 + j]), hi[j], lo[j]);
-                H = *reinterpret_cast<const uint4*>(hi);
-                L = *reinterpret_cast<const uint4*>(lo);
-            }
-            const int q = G + ep;
-            *reinterpret_cast<uint4*>(dst + cg * S::PLANE + q * 16) = H;
-            *reinterpret_cast<uint4*>(dst + (S::KC + cg) * S::PLANE + q * 16) = L;
-        };
-        auto wait = [&](uint64_t* mb, uint32_t& ph) {
-            if (!tc::mbar_wait_bounded(mb, ph, F_WAIT)) failed = true;
-            ph ^= 1u;
-            tc::fence_after_sync();
-        };
-
-        // prologue: [X; B U] rows r_lo-2 .. r_lo+4; first-layer rows r_lo-1 .. r_lo+1
-        for (int r = r_lo - 2; r <= r_lo + 4; ++r) load_xb(r);
-        __syncthreads();
-        for (int r1 = r_lo - 1; r1 <= r_lo + 1; ++r1) {
-            unsigned char* dst = smem + S::OFF_H1 + mod_pos(r1, S::NH1) * S::SLOT;
-            const bool inside = r1 >= 0 && r1 < n;
-            if (inside) {
-                build_f(r1);
+                const int q = G + ep;
+                *reinterpret_cast<uint4*>(dst + cg * S::PLANE + q * 16) = *reinterpret_cast<const uint4*>(hi);
+                *reinterpret_cast<uint4*>(dst + (S::KC + cg) * S::PLANE + q * 16) = *reinterpret_cast<const uint4*>(lo);
+            };
+            // this warp's operand writes (and TMEM reads) are done: one arrival
+            auto arrive = [&](int i) {
                 tc::fence_proxy_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::fence_after_sync();
-                    issue_first<C, G>(s0, tmem + S::T_F + (r1 & 1) * 64, r1);
-                    tc::mma_commit(mbarF);
-                }
-                wait(mbarF, phF);
-            }
-            drain(S::T_F + (r1 & 1) * 64, sbias, dst, !inside);
-            tc::fence_before_sync();
-            __syncthreads();
-        }
-        if (r_lo + 2 <= r_hi + 1 && r_lo + 2 < n) build_f(r_lo + 2);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;            // outputs of rows h-1, h, h+1 (epilogue warps 0-3)
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + i);
+            };
 
-        for (int r = r_lo; r <= r_hi + 1; ++r) {
-            const bool needF = r + 2 <= r_hi + 1;      // first-layer row r+2 is an input of hidden r+1
-            const bool doF = needF && r + 2 < n;
-            const bool doH = r <= r_hi;
-            const bool doL = r - 1 >= r_lo;
-            tc::fence_proxy_async_smem();
-            tc::fence_before_sync();
-            if (__syncthreads_or(failed)) { failed = true; break; }
-            tc::fence_after_sync();
-            if (tid == 0) {
-                if (doF) {
-                    issue_first<C, G>(s0, tmem + S::T_F + ((r + 2) & 1) * 64, r + 2);
-                    tc::mma_commit(mbarF);
+            for (int r = r_lo - 2; r <= r_lo; ++r) store_xb(r, fetch_x(r));
+            float xpf = fetch_x(r_lo + 1);               // next [X; B U] row, in flight
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;          // outputs of rows h-1, h, h+1 (warps 0-3)
+
+            // iteration k: drain first-layer row k+2 and hidden row k, finish the
+            // last layer of row k-1 (output row k-2), build first-layer row k+4
+            for (int k = r_lo - 5; k <= r_hi + 1; ++k) {
+                if (tc::named_bar_or(BAR_DRAIN, ND, failed)) { failed = true; break; }
+                tc::fence_after_sync();
+                if (Fvalid(k + 2)) {
+                    // its slot held row k-2, last read by hidden row k-1 (done)
+                    wait(MB_F);
+                    drain(S::T_F + ((k + 2) & 1) * 64, sbias, smem + S::OFF_H1 + mod_pos(k + 2, S::NH1) * S::SLOT);
+                    arrive(MB_RH1);
                 }
-                if (doH) issue_hidden<C, G>(s0, tmem + S::T_H + (r & 1) * 64, r);
-                if (doL) issue_last<C, G>(s0, tmem + S::T_L + ((r - 1) & 1) * 16, r - 1);
-                tc::mma_commit(mbarM);
-            }
-            // first-layer row r+2 -> operand slot (the slot of row r-2, free)
-            if (needF) {
-                if (doF) wait(mbarF, phF);
-                drain(S::T_F + ((r + 2) & 1) * 64, sbias, smem + S::OFF_H1 + mod_pos(r + 2, S::NH1) * S::SLOT, !doF);
-            }
-            wait(mbarM, phM);
-            // hidden row r -> last-layer operand
-            if (doH) drain(S::T_H + (r & 1) * 64, sbias + C, smem + S::OFF_H2 + (r & 1) * S::SLOT, false);
-            // last layer of hidden row h = r-1: contributions to output rows h+1, h, h-1
-            if (doL && warp < 4) {
-                float v[8];
-                tmem_ld8(tmem + tlane + S::T_L + ((r - 1) & 1) * 16, v);
-                tc::tmem_ld_wait();
-                const float p0 = fmaf(v[3], tc::SPLIT_INV, v[0]);
-                const float p1 = fmaf(v[4], tc::SPLIT_INV, v[1]);
-                const float p2 = fmaf(v[5], tc::SPLIT_INV, v[2]);
-                a0 += p2;
-                a1 += p1;
-                a2 += p0;
-                const int ro = r - 2;
-                if (ro >= ys && ro < ye) {
-                    const int b = ep % G, x = ep / G, mb = g * G + b;
-                    if (mb < Nb) {
-                        const float xv = xb[mod_pos(ro, S::NXB) * 2 * S::SP + G + ep];
-                        Xout[(long)mb * o_ms + (long)ro * m + x] = fmaf(rs, a0 + sbias[2 * C], xv);
+                if (k >= r_lo && k <= r_hi) {
+                    // its buffer held row k-2, read by last(k-2) (done: waited by
+                    // warps 0-3 before the barrier above)
+                    wait(MB_H + (k & 1));
+                    drain(S::T_H + (k & 1) * 64, sbias + C, smem + S::OFF_H2 + (k & 1) * S::SLOT);
+                    arrive(MB_RH2 + (k & 1));
+                }
+                // last layer of hidden row h = k-1: contributions to output rows h+1, h, h-1
+                if (warp < 4 && k - 1 >= r_lo && k - 1 <= r_hi) {
+                    wait(MB_L + ((k - 1) & 1));
+                    float v[8];
+                    tmem_ld8(tmem + tlane + S::T_L + ((k - 1) & 1) * 16, v);
+                    tc::tmem_ld_wait();
+                    const float p0 = fmaf(v[3], tc::SPLIT_INV, v[0]);
+                    const float p1 = fmaf(v[4], tc::SPLIT_INV, v[1]);
+                    const float p2 = fmaf(v[5], tc::SPLIT_INV, v[2]);
+                    a0 += p2;
+                    a1 += p1;
+                    a2 += p0;
+                    const int ro = k - 2;
+                    if (ro >= ys && ro < ye) {
+                        const int b = ep % G, x = ep / G, mbr = g * G + b;
+                        if (mbr < Nb) {
+                            const float xv = xb[mod_pos(ro, S::NXB) * 2 * S::SP + G + ep];
+                            Xout[(long)mbr * o_ms + (long)ro * m + x] = fmaf(rs, a0 + sbias[2 * C], xv);
+                        }
                     }
+                    a0 = a1; a1 = a2; a2 = 0.f;
                 }
-                a0 = a1; a1 = a2; a2 = 0.f;
+                // operand of first-layer row k+4 (its buffer held row k+2, whose
+                // MMA was waited for above), [X; B U] row k+6
+                if (f_role && Fvalid(k + 4)) {
+                    build_f(k + 4);
+                    arrive(MB_RF + ((k + 4) & 1));
+                }
+                store_xb(k + 6, xpf);
+                xpf = fetch_x(k + 7);
             }
-            // operands for the next rows: first-layer input of row r+3, [X; B U] row r+5
-            if (r + 3 <= r_hi + 1 && r + 3 < n) build_f(r + 3);
-            load_xb(r + 5);
-        }
-        if (!failed && ye == n && n - 1 >= ys && warp < 4) {
-            // bottom row: the hidden row below the image is zero
-            const int b = ep % G, x = ep / G, mb = g * G + b;
-            if (mb < Nb) {
-                const float xv = xb[mod_pos(n - 1, S::NXB) * 2 * S::SP + G + ep];
-                Xout[(long)mb * o_ms + (long)(n - 1) * m + x] = fmaf(rs, a0 + sbias[2 * C], xv);
+            if (!failed && ye == n && warp < 4) {
+                // bottom row: the hidden row below the image is zero
+                const int b = ep % G, x = ep / G, mbr = g * G + b;
+                if (mbr < Nb) {
+                    const float xv = xb[mod_pos(n - 1, S::NXB) * 2 * S::SP + G + ep];
+                    Xout[(long)mbr * o_ms + (long)(n - 1) * m + x] = fmaf(rs, a0 + sbias[2 * C], xv);
+                }
             }
         }
         tc::fence_before_sync();
-        __syncthreads();
+        if (__syncthreads_or(failed)) { failed = true; break; }
+        tc::fence_after_sync();
     }
-    if (failed) {
-        if (tid == 0) atomicExch(err, DEV_TIMEOUT);
-        // give MMAs still in flight a last bounded chance to land
-        tc::mbar_wait_bounded(mbarF, phF, F_WAIT);
-        tc::mbar_wait_bounded(mbarM, phM, F_WAIT);
+    // every MMA issued has landed before the tensor memory is released
+    if (warp == ND / 32 && lane == 0) {
+        tc::mma_commit(mb + MB_FIN);
+        if (!tc::mbar_wait_bounded(mb + MB_FIN, 0u, F_WAIT)) atomicExch(err, DEV_TIMEOUT);
     }
     tc::fence_before_sync();
     __syncthreads();

@@ -84,6 +84,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity)
     return ok != 0;
 }
 
+// One arrival on `mbar` (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Named barrier `id` over the first `nthreads` threads that reach it (a
+// multiple of 32), with an OR-reduction of `v` over those threads.
+__device__ __forceinline__ bool named_bar_or(int id, int nthreads, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void named_bar(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Bounded wait for phase `parity` of `mbar`: gives up after `max_cycles`
 // SM clock cycles and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, long long max_cycles)
