@@ -1,28 +1,38 @@
 // cnn_fused_tc.cu -- the whole surrogate X_{t+1} = X_t + s * CNN_theta(X_t, U_t)
 // of Eq. (1), structure [X; B U] -> C (tanh) -> C (tanh) -> 1, in ONE kernel,
-// every layer on the tcgen05 tensor cores at FP32 accuracy:
+// every layer on the tcgen05 tensor cores at FP32 accuracy.
 //
-//   operands are split x = hi + lo * 2^-11 (hi, lo fp16) and each layer
-//   accumulates main = A_hi B_hi and corr = A_hi B_lo + A_lo B_hi in tensor
-//   memory (out = main + corr * 2^-11, error ~2^-21 per product);
+// Precision: operands are split x = hi + lo * 2^-11 (hi, lo fp16) and each
+// layer accumulates main = A_hi B_hi and corr = A_hi B_lo + A_lo B_hi in
+// tensor memory (out = main + corr * 2^-11, error ~2^-21 per product).
+//
+// Layout: a CTA owns a group of G = 128/m members; an M = 128 tile is one
+// image row of the group with the members INTERLEAVED pixel by pixel
+// (position G + G x + b for member b, pixel x, zero pads at both ends), so a
+// horizontal stencil tap is a shift of the operand start by G positions.
+//
+// One MMA costs at least ~50 cycles whatever its N up to 64, and runs at the
+// full tensor rate only from N = 128 up, so each layer is cast into few wide
+// MMAs:
 //   first layer (2 -> C)   K = 16 per horizontal tap holds [X, B U] of the
-//                          three stencil rows, hi in one half and lo in the
-//                          other; one N = 2C MMA per tap gives main and corr
-//   hidden layer (C -> C)  K = C per tap; [B_hi; B_lo] stacked as N = 2C, then
-//                          A_lo B_hi with N = C
-//   last layer (C -> 1)    N = 16 columns hold main and corr of the three
-//                          stencil rows; the CUDA cores turn them into rolling
-//                          per-pixel sums over output rows r+1, r, r-1
+//                          three stencil rows, hi and lo; N = 2C (main, corr)
+//   hidden layer (C -> C)  the three VERTICAL taps are stacked along N: one
+//                          first-layer row j, read once per (horizontal tap,
+//                          16-channel step), feeds hidden rows j+1, j, j-1 at
+//                          once (N = 6C).  Hidden-row accumulators live in a
+//                          ring of 4 TMEM slots whose window of three is
+//                          contiguous except at the ring's end (then split)
+//   last layer (C -> 1)    all nine taps are stacked along N (main and corr
+//                          of each, N = 32) on the UNshifted row; the CUDA
+//                          cores add the horizontal neighbours (+-G lanes,
+//                          through shared memory) and keep rolling sums over
+//                          output rows h+1, h, h-1
 //
-// Only X, U and the weights are read and X_next written.  A CTA owns a group
-// of G = 128/m members; an M = 128 tile is one image row of the group with
-// the members INTERLEAVED pixel by pixel (position G + G x + b for member b,
-// pixel x, zero pads at both ends), so a horizontal stencil tap is a shift of
-// the operand start by G positions = 16 G bytes and one copy of each row
-// serves all three taps.  Per hidden row r the tensor core runs first-layer
-// row r+2, hidden row r and last layer of row r-1 while the CUDA cores drain
-// the previous results (tanh, split, stores).  The grid is persistent over
-// contiguous (group, row) ranges.
+// Roles: one thread issues every MMA and waits only on "operand ready"
+// mbarriers; 16 drain warps turn accumulators into the next layer's operands
+// (tanh, split, stores), arrive on those barriers and wait on the MMA commit
+// barriers.  Only X, U and the weights are read and X_next written.  The grid
+// is persistent over contiguous (group, row) ranges.
 #include <cuda_fp16.h>
 
 #include "oic_internal.cuh"
@@ -35,6 +45,8 @@ constexpr int FT = 544;                                 // 16 drain warps + 1 MM
 constexpr int ND = 512;                                 // drain threads
 constexpr int FM = 128;                                 // tile rows (pixels)
 constexpr int BAR_DRAIN = 1;                            // named barrier of the drain warps
+constexpr int BAR_E3 = 2;                               // named barrier of the last-layer warps
+constexpr int E3_WARP0 = 12;                            // warps 12-15 finish the last layer
 constexpr long long F_WAIT = 4000000000LL;
 
 __host__ __device__ constexpr int al16(int x) { return (x + 15) / 16 * 16; }
@@ -46,28 +58,33 @@ struct FS {
     static constexpr int PLANE = NPOS * 16;             // one (part, 8-channel) plane
     static constexpr int SLOT = 2 * KC * PLANE;         // hi and lo of one activation row
     static constexpr int FBUF = 2 * PLANE;              // first-layer operand: hi | lo
-    static constexpr int BTILE = 2 * (2 * C) * 16;      // hidden (tap, K-step) tile
-    static constexpr int BBYTES = 9 * KS * BTILE;
+    static constexpr int HROWS = 6 * C;                 // hidden B tile rows: 3 x [B_hi; B_lo]
+    static constexpr int HTILE = 2 * HROWS * 16;        // one (tap, K-step, part) tile, 2 K chunks
+    static constexpr int BBYTES = 3 * KS * 2 * HTILE;   // [dx][ks][hi | lo]
     static constexpr int B1BYTES = 3 * 2 * 64 * 16;     // first layer: 3 taps x (2 x 64 x 8)
-    static constexpr int B3TILE = 2 * 16 * 16;          // last layer tile: 2 x 16 x 8
-    static constexpr int B3BYTES = 3 * KS * 2 * B3TILE;
-    static constexpr int NH1 = 4, NXB = 10;
+    static constexpr int B3TILE = 2 * 32 * 16;          // last layer tile: 2 K chunks x 32 rows
+    static constexpr int B3BYTES = KS * 2 * B3TILE;     // [ks][hi | lo]
+    static constexpr int NXB = 10;
     static constexpr int SP = NPOS | 1;                 // odd FP32 row stride
-    static constexpr int OFF_H1 = 0;
-    static constexpr int OFF_Z = OFF_H1 + NH1 * SLOT;   // permanently zero activation row
-    static constexpr int OFF_H2 = OFF_Z + SLOT;
-    static constexpr int OFF_F = OFF_H2 + 2 * SLOT;
-    static constexpr int OFF_B = OFF_F + 2 * FBUF;
+    static constexpr int OFF_H1 = 0;                    // first-layer rows, 2 slots
+    static constexpr int OFF_H2 = OFF_H1 + 2 * SLOT;    // hidden rows, 2 slots
+    static constexpr int OFF_F = OFF_H2 + 2 * SLOT;     // first-layer operands, 2 buffers
+    static constexpr int OFF_EX = OFF_F + 2 * FBUF;     // last-layer neighbour exchange [2][6][NPOS] fp32
+    static constexpr int EXBYTES = al16(2 * 6 * NPOS * 4);
+    static constexpr int ZERO_BYTES = OFF_EX + EXBYTES; // operand buffers incl. pads
+    static constexpr int OFF_B = ZERO_BYTES;
     static constexpr int OFF_B1 = OFF_B + BBYTES;
     static constexpr int OFF_B3 = OFF_B1 + B1BYTES;
+    static constexpr int PACKED = BBYTES + B1BYTES + B3BYTES;
     static constexpr int OFF_XB = OFF_B3 + B3BYTES;                    // [NXB][2][SP] fp32
     static constexpr int OFF_BIAS = OFF_XB + al16(NXB * 2 * SP * 4);   // b1[C], b2[C], b3
     static constexpr int OFF_MISC = OFF_BIAS + al16((2 * C + 4) * 4);  // mbarriers, TMEM base
     static constexpr int OFF_DYN = OFF_MISC + 128;                     // U group, B matrix
-    static constexpr int ZERO_BYTES = OFF_B;                           // operand buffers incl. pads
-    // tensor memory: first-layer, hidden and last-layer accumulators, double buffered
-    static constexpr int T_F = 0, T_H = 4 * C, T_L = 8 * C;
+    // tensor memory: hidden ring (4 x [main | corr]), first layer (2 x [main | corr]),
+    // last layer (2 x 32)
+    static constexpr int T_H = 0, T_F = 8 * C, T_L = 12 * C;
     static constexpr int TMEM_COLS = 512;
+    static_assert(T_L + 64 <= TMEM_COLS, "tensor memory");
 };
 
 __device__ __forceinline__ int mod_pos(int r, int k) { return ((r % k) + k) % k; }
@@ -92,88 +109,169 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int C, int G>
-__device__ __forceinline__ void issue_first(uint32_t s0, uint32_t acc, int r1)
+// Shared-memory operand descriptors are handled as their low 32-bit word
+// (address >> 4 in bits [0,14), leading byte offset >> 4 in bits [16,30));
+// the high word is the same for every operand here (stride byte offset 128,
+// descriptor version 1).  Every shared address is below 256 KB, so adding a
+// byte offset >> 4 to the low word never carries out of the address field.
+constexpr uint32_t DESC_HI = (128u >> 4) | (1u << 14);
+__host__ __device__ constexpr uint32_t desc_lo(uint32_t saddr, uint32_t lbo)
 {
-    using S = FS<C, G>;
-    constexpr uint32_t id = tc::idesc_f16(FM, 64);
-    const uint32_t f = s0 + S::OFF_F + (r1 & 1) * S::FBUF;
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-        const uint64_t da = tc::desc_kmajor(f + dx * G * 16, S::PLANE, 128);
-        const uint64_t db = tc::desc_kmajor(s0 + S::OFF_B1 + dx * 2048, 64 * 16, 128);
-        tc::mma_f16(acc, da, db, id, dx > 0 ? 1u : 0u);
-    }
+    return ((saddr & 0x3FFFFu) >> 4) | (((lbo >> 4) & 0x3FFFu) << 16);
 }
 
-// Hidden row r from first-layer rows r-1, r, r+1; rows outside the image read
-// the zero slot.
+// One MMA from descriptor low words (see tc::mma_f16).
+__device__ __forceinline__ void mma_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .b64 da, db;\n\t.reg .pred p;\n\t"
+        "mov.b64 da, {%1, %5};\n\t"
+        "mov.b64 db, {%2, %5};\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_lo), "r"(b_lo), "r"(idesc), "r"(acc), "r"(DESC_HI)
+        : "memory");
+}
+
+// First layer of row r1: a = descriptor of its operand buffer, b = of the tiles.
 template <int C, int G>
-__device__ __forceinline__ void issue_hidden(uint32_t s0, uint32_t acc, int r, int n)
+__device__ __forceinline__ void issue_first(uint32_t acc, uint32_t a, uint32_t b)
+{
+    constexpr uint32_t id = tc::idesc_f16(FM, 64);
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) mma_lo(acc, a + dx * G, b + dx * (2048 >> 4), id, dx > 0 ? 1u : 0u);
+}
+
+// MMA over the vertical-tap blocks [B0, B1) of one hidden B tile into TMEM
+// from column COL (blocks are 2C columns wide: main | corr).  The lo part
+// writes only the corr halves: N = 2C (B1 - B0) - C from column COL + C.
+template <int C, int B0, int B1, int COL, bool LO>
+__device__ __forceinline__ void hid_piece(uint32_t tmem, uint32_t a, uint32_t b, uint32_t acc)
+{
+    constexpr int NN = LO ? 2 * C * (B1 - B0) - C : 2 * C * (B1 - B0);
+    constexpr uint32_t id = tc::idesc_f16(FM, NN);
+    constexpr uint32_t brow = 2 * C * B0 + (LO ? C : 0);
+    mma_lo(tmem + COL + (LO ? C : 0), a, b + brow, id, acc);
+}
+
+// All hidden-layer MMAs of first-layer row j.  Blocks b = 0, 1, 2 hold
+// vertical taps dy = b, i.e. hidden rows j+1, j, j-1, whose ring slots are
+// SR, SR+1, SR+2 (mod 4) with SR = (-j-1) mod 4.  The first MMA starts hidden
+// row j+1 (accumulate = 0 on its block); with INIT_ALL it starts every block.
+// a = descriptor of the row's operand slot, b = of the hidden tiles.
+template <int C, int G, int SR, bool INIT_ALL>
+__device__ __forceinline__ void issue_hidden_s(uint32_t tmem, uint32_t a, uint32_t b)
 {
     using S = FS<C, G>;
-    constexpr uint32_t id1 = tc::idesc_f16(FM, 2 * C);
-    constexpr uint32_t id2 = tc::idesc_f16(FM, C);
-    uint32_t accumulate = 0;
+    constexpr int W = 2 * C;                            // ring slot width in columns
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-        const int j = r + dy - 1;
-        const uint32_t slot = s0 + ((j < 0 || j >= n) ? S::OFF_Z : S::OFF_H1 + mod_pos(j, S::NH1) * S::SLOT);
+    for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
+        for (int ks = 0; ks < S::KS; ++ks) {
 #pragma unroll
-            for (int ks = 0; ks < S::KS; ++ks) {
-                const uint32_t a_hi = slot + (2 * ks) * S::PLANE + dx * G * 16;
-                const uint32_t a_lo = slot + (S::KC + 2 * ks) * S::PLANE + dx * G * 16;
-                const uint32_t b = s0 + S::OFF_B + ((dy * 3 + dx) * S::KS + ks) * S::BTILE;
-                const uint64_t db = tc::desc_kmajor(b, 2 * C * 16, 128);
-                tc::mma_f16(acc, tc::desc_kmajor(a_hi, S::PLANE, 128), db, id1, accumulate);
-                tc::mma_f16(acc + C, tc::desc_kmajor(a_lo, S::PLANE, 128), db, id2, 1u);
-                accumulate = 1;
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t aa = a + (((part ? S::KC : 0) + 2 * ks) * S::PLANE) / 16 + dx * G;
+                const uint32_t bb = b + (((dx * S::KS + ks) * 2 + part) * S::HTILE) / 16;
+                const bool first = dx == 0 && ks == 0 && part == 0;
+                if (part == 0) {
+                    if (first && !INIT_ALL) {
+                        // block 0 alone with accumulate = 0, blocks 1-2 accumulate
+                        hid_piece<C, 0, 1, S::T_H + W * SR, false>(tmem, aa, bb, 0u);
+                        if constexpr (SR == 2) {
+                            hid_piece<C, 1, 2, S::T_H + W * 3, false>(tmem, aa, bb, 1u);
+                            hid_piece<C, 2, 3, S::T_H, false>(tmem, aa, bb, 1u);
+                        } else if constexpr (SR == 3) {
+                            hid_piece<C, 1, 3, S::T_H, false>(tmem, aa, bb, 1u);
+                        } else {
+                            hid_piece<C, 1, 3, S::T_H + W * (SR + 1), false>(tmem, aa, bb, 1u);
+                        }
+                        continue;
+                    }
+                }
+                const uint32_t acc = first ? 0u : 1u;
+                if (part == 0) {
+                    if constexpr (SR <= 1) {
+                        hid_piece<C, 0, 3, S::T_H + W * SR, false>(tmem, aa, bb, acc);
+                    } else if constexpr (SR == 2) {
+                        hid_piece<C, 0, 2, S::T_H + W * 2, false>(tmem, aa, bb, acc);
+                        hid_piece<C, 2, 3, S::T_H, false>(tmem, aa, bb, acc);
+                    } else {
+                        hid_piece<C, 0, 1, S::T_H + W * 3, false>(tmem, aa, bb, acc);
+                        hid_piece<C, 1, 3, S::T_H, false>(tmem, aa, bb, acc);
+                    }
+                } else {
+                    if constexpr (SR <= 1) {
+                        hid_piece<C, 0, 3, S::T_H + W * SR, true>(tmem, aa, bb, 1u);
+                    } else if constexpr (SR == 2) {
+                        hid_piece<C, 0, 2, S::T_H + W * 2, true>(tmem, aa, bb, 1u);
+                        hid_piece<C, 2, 3, S::T_H, true>(tmem, aa, bb, 1u);
+                    } else {
+                        hid_piece<C, 0, 1, S::T_H + W * 3, true>(tmem, aa, bb, 1u);
+                        hid_piece<C, 1, 3, S::T_H, true>(tmem, aa, bb, 1u);
+                    }
+                }
             }
         }
     }
 }
 
+// Dispatch on the ring position once per row, so that the MMA sequence itself
+// is straight-line code.
 template <int C, int G>
-__device__ __forceinline__ void issue_last(uint32_t s0, uint32_t acc, int h)
+__device__ __forceinline__ void issue_hidden(uint32_t tmem, int j, bool init_all, uint32_t a, uint32_t b)
 {
-    using S = FS<C, G>;
-    constexpr uint32_t id = tc::idesc_f16(FM, 16);
-    const uint32_t buf = s0 + S::OFF_H2 + (h & 1) * S::SLOT;
-    uint32_t accumulate = 0;
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-#pragma unroll
-        for (int ks = 0; ks < S::KS; ++ks) {
-            const uint32_t a_hi = buf + (2 * ks) * S::PLANE + dx * G * 16;
-            const uint32_t a_lo = buf + (S::KC + 2 * ks) * S::PLANE + dx * G * 16;
-            const uint32_t b = s0 + S::OFF_B3 + (dx * S::KS + ks) * 2 * S::B3TILE;
-            tc::mma_f16(acc, tc::desc_kmajor(a_hi, S::PLANE, 128), tc::desc_kmajor(b, 16 * 16, 128), id, accumulate);
-            tc::mma_f16(acc, tc::desc_kmajor(a_lo, S::PLANE, 128), tc::desc_kmajor(b + S::B3TILE, 16 * 16, 128), id, 1u);
-            accumulate = 1;
+    const int s = (-j - 1) & 3;
+    if (init_all) {
+        switch (s) {
+        case 0: issue_hidden_s<C, G, 0, true>(tmem, a, b); break;
+        case 1: issue_hidden_s<C, G, 1, true>(tmem, a, b); break;
+        case 2: issue_hidden_s<C, G, 2, true>(tmem, a, b); break;
+        default: issue_hidden_s<C, G, 3, true>(tmem, a, b); break;
+        }
+    } else {
+        switch (s) {
+        case 0: issue_hidden_s<C, G, 0, false>(tmem, a, b); break;
+        case 1: issue_hidden_s<C, G, 1, false>(tmem, a, b); break;
+        case 2: issue_hidden_s<C, G, 2, false>(tmem, a, b); break;
+        default: issue_hidden_s<C, G, 3, false>(tmem, a, b); break;
         }
     }
 }
 
-// mbarriers in the MISC region (8 bytes each)
+// Last layer of hidden row h, all nine taps along N, on the unshifted row:
+// a = descriptor of the row's operand buffer (centre tap), b = of the tiles.
+template <int C, int G>
+__device__ __forceinline__ void issue_last(uint32_t acc, uint32_t a, uint32_t b)
+{
+    using S = FS<C, G>;
+    constexpr uint32_t id = tc::idesc_f16(FM, 32);
+#pragma unroll
+    for (int ks = 0; ks < S::KS; ++ks) {
+#pragma unroll
+        for (int part = 0; part < 2; ++part)
+            mma_lo(acc, a + (((part ? S::KC : 0) + 2 * ks) * S::PLANE) / 16, b + ((ks * 2 + part) * S::B3TILE) / 16,
+                   id, (ks | part) ? 1u : 0u);
+    }
+}
+
+// mbarriers in the MISC region (8 bytes each); [2] = by row parity
 enum : int {
-    MB_F = 0,          // first layer done (tensor core -> drain warps)
-    MB_H = 1,          // [2] hidden layer done, by row parity
-    MB_L = 3,          // [2] last layer done, by row parity
-    MB_RH1 = 5,        // first-layer row drained into its operand slot (16 warps)
-    MB_RF = 6,         // [2] first-layer operand built, by row parity (4 warps)
-    MB_RH2 = 8,        // [2] hidden row drained into its operand buffer (16 warps)
-    MB_FIN = 10,       // every MMA of the kernel done
-    MB_COUNT = 11
+    MB_F = 0,          // [2] first layer of row f done (tensor core -> drain warps)
+    MB_H = 2,          // [2] hidden MMAs of first-layer row j done
+    MB_L = 4,          // [2] last layer of hidden row h done
+    MB_RH1 = 6,        // [2] first-layer row drained into its operand slot (16 warps)
+    MB_RF = 8,         // [2] first-layer operand built (4 warps)
+    MB_RH2 = 10,       // [2] hidden row drained into its operand buffer (16 warps)
+    MB_FIN = 12,       // every MMA of the kernel done
+    MB_COUNT = 13
 };
 
 template <int C, int G>
 __global__ void __launch_bounds__(FT, 1)
 cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
                  float* __restrict__ Xout, long o_ms, const float* __restrict__ Bmat, int Nb, int n, int l,
-                 const float* __restrict__ b1, const __half* __restrict__ wpk2, const float* __restrict__ b2,
-                 const __half* __restrict__ wpk13, const float* __restrict__ b3, float rs, int* __restrict__ err)
+                 const float* __restrict__ b1, const float* __restrict__ b2, const float* __restrict__ b3,
+                 const __half* __restrict__ wpk, float rs, int* __restrict__ err)
 {
     using S = FS<C, G>;
     static_assert(C == 32, "16 drain warps = 4 lane quarters x 4 groups of 8 channels");
@@ -181,6 +279,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     constexpr int m = FM / G;
     extern __shared__ __align__(1024) unsigned char smem[];
     float* xb = reinterpret_cast<float*>(smem + S::OFF_XB);
+    float* ex = reinterpret_cast<float*>(smem + S::OFF_EX);
     float* sbias = reinterpret_cast<float*>(smem + S::OFF_BIAS);   // b1 | b2 | b3
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + MB_COUNT * 8);
@@ -189,22 +288,19 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const uint32_t s0 = tc::smem_u32(smem);
 
-    // ---- one-time set-up: zero the operand buffers (pads and the zero slot
-    // stay zero), copy weights
+    // ---- one-time set-up: zero the operand buffers (pads stay zero), copy weights
     for (int e = tid; e < S::ZERO_BYTES / 16; e += FT)
         reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
-    for (int e = tid; e < S::BBYTES / 16; e += FT)
-        reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk2)[e];
-    for (int e = tid; e < (S::B1BYTES + S::B3BYTES) / 16; e += FT)
-        reinterpret_cast<uint4*>(smem + S::OFF_B1)[e] = reinterpret_cast<const uint4*>(wpk13)[e];
+    for (int e = tid; e < S::PACKED / 16; e += FT)
+        reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk)[e];
     for (int e = tid; e < S::NXB * 2 * S::SP; e += FT) xb[e] = 0.f;
     for (int e = tid; e < C; e += FT) { sbias[e] = b1[e]; sbias[C + e] = b2[e]; }
     for (int e = tid; e < n * l; e += FT) sB[e] = Bmat[e];
     if (tid == 0) {
         sbias[2 * C] = b3[0];
         for (int i = 0; i < MB_COUNT; ++i) {
-            const int cnt = (i == MB_RH1 || i == MB_RH2 || i == MB_RH2 + 1) ? 16
-                          : (i == MB_RF || i == MB_RF + 1) ? 4 : 1;
+            const int cnt = (i >= MB_RH1 && i < MB_RH1 + 2) || (i >= MB_RH2 && i < MB_RH2 + 2) ? 16
+                          : (i >= MB_RF && i < MB_RF + 2) ? 4 : 1;
             tc::mbar_init(mb + i, cnt);
         }
         tc::fence_mbar_init();
@@ -243,33 +339,42 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
         const int ye = (long)(n - ys) < rem ? n : (int)(ys + rem);
         t += ye - ys;
         // output rows ys .. ye-1 need hidden rows r_lo .. r_hi and first-layer
-        // rows r_lo-1 .. r_hi+1 (those inside the image are computed)
+        // rows f_lo .. f_hi (zero outside the image)
         const int r_lo = ys > 0 ? ys - 1 : 0;
         const int r_hi = ye < n ? ye : n - 1;
         const int f_lo = r_lo - 1 > 0 ? r_lo - 1 : 0;
         const int f_hi = r_hi + 1 < n - 1 ? r_hi + 1 : n - 1;
-        auto Fvalid = [&](int f) { return f >= f_lo && f <= f_hi; };
+        auto Fv = [&](int f) { return f >= f_lo && f <= f_hi; };
+        auto Hv = [&](int h) { return h >= r_lo && h <= r_hi; };
 
         if (warp == ND / 32) {
             // ================= MMA-issuing warp (one thread) =================
-            // iteration k: first-layer row k+3, hidden row k+1, last layer of row k
+            // iteration k: hidden MMAs of first-layer row k, first layer of row
+            // k+2, last layer of hidden row k-2
             if (lane == 0) {
-                for (int k = r_lo - 4; k <= r_hi && !failed; ++k) {
-                    if (Fvalid(k + 2)) wait(MB_RH1);                // rows k .. k+2 in their slots
-                    const bool f3 = Fvalid(k + 3);
-                    if (f3) wait(MB_RF + ((k + 3) & 1));           // operand of first-layer row k+3
-                    if (f3) {
-                        issue_first<C, G>(s0, tmem + S::T_F + ((k + 3) & 1) * 64, k + 3);
-                        tc::mma_commit(mb + MB_F);
+                const uint32_t dH1 = desc_lo(s0 + S::OFF_H1, S::PLANE);           // first-layer rows (A)
+                const uint32_t dHB = desc_lo(s0 + S::OFF_B, S::HROWS * 16);       // hidden tiles (B)
+                const uint32_t dF = desc_lo(s0 + S::OFF_F, S::PLANE);             // first-layer operands (A)
+                const uint32_t dB1 = desc_lo(s0 + S::OFF_B1, 64 * 16);            // first-layer tiles (B)
+                const uint32_t dH2 = desc_lo(s0 + S::OFF_H2 + G * 16, S::PLANE);  // hidden rows, centre (A)
+                const uint32_t dB3 = desc_lo(s0 + S::OFF_B3, 32 * 16);            // last-layer tiles (B)
+                for (int k = f_lo - 2; k <= r_hi + 2 && !failed; ++k) {
+                    if (Fv(k)) {
+                        wait(MB_RH1 + (k & 1));                     // first-layer row k in its slot
+                        issue_hidden<C, G>(tmem, k, k == f_lo, dH1 + (k & 1) * (S::SLOT / 16), dHB);
+                        tc::mma_commit(mb + MB_H + (k & 1));
                     }
-                    if (k + 1 >= r_lo && k + 1 <= r_hi) {
-                        issue_hidden<C, G>(s0, tmem + S::T_H + ((k + 1) & 1) * 64, k + 1, n);
-                        tc::mma_commit(mb + MB_H + ((k + 1) & 1));
+                    if (Fv(k + 2)) {
+                        wait(MB_RF + ((k + 2) & 1));                // operand of first-layer row k+2
+                        issue_first<C, G>(tmem + S::T_F + ((k + 2) & 1) * 2 * C,
+                                          dF + ((k + 2) & 1) * (S::FBUF / 16), dB1);
+                        tc::mma_commit(mb + MB_F + ((k + 2) & 1));
                     }
-                    if (k >= r_lo) {
-                        wait(MB_RH2 + (k & 1));                     // hidden row k in its buffer
-                        issue_last<C, G>(s0, tmem + S::T_L + (k & 1) * 16, k);
-                        tc::mma_commit(mb + MB_L + (k & 1));
+                    if (Hv(k - 2)) {
+                        wait(MB_RH2 + ((k - 2) & 1));               // hidden row k-2 in its buffer
+                        issue_last<C, G>(tmem + S::T_L + ((k - 2) & 1) * 32, dH2 + ((k - 2) & 1) * (S::SLOT / 16),
+                                         dB3);
+                        tc::mma_commit(mb + MB_L + ((k - 2) & 1));
                     }
                 }
             }
@@ -343,41 +448,65 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                 if (lane == 0) tc::mbar_arrive(mb + i);
             };
 
-            for (int r = r_lo - 2; r <= r_lo; ++r) store_xb(r, fetch_x(r));
-            float xpf = fetch_x(r_lo + 1);               // next [X; B U] row, in flight
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;          // outputs of rows h-1, h, h+1 (warps 0-3)
+            for (int r = f_lo - 1; r <= f_lo + 1; ++r) store_xb(r, fetch_x(r));
+            float xpf = fetch_x(f_lo + 2);               // next [X; B U] row, in flight
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;          // outputs of rows h-1, h, h+1 (warps 12-15)
 
-            // iteration k: drain first-layer row k+2 and hidden row k, finish the
-            // last layer of row k-1 (output row k-2), build first-layer row k+4
-            for (int k = r_lo - 5; k <= r_hi + 1; ++k) {
+            // iteration k: drain first-layer row k+1 and hidden row k-1, finish
+            // the last layer of hidden row k-2 (output row k-3), build the
+            // first-layer operand of row k+3
+            for (int k = f_lo - 3; k <= r_hi + 2; ++k) {
                 if (tc::named_bar_or(BAR_DRAIN, ND, failed)) { failed = true; break; }
                 tc::fence_after_sync();
-                if (Fvalid(k + 2)) {
-                    // its slot held row k-2, last read by hidden row k-1 (done)
-                    wait(MB_F);
-                    drain(S::T_F + ((k + 2) & 1) * 64, sbias, smem + S::OFF_H1 + mod_pos(k + 2, S::NH1) * S::SLOT);
-                    arrive(MB_RH1);
+                if (Fv(k + 1)) {
+                    // its slot held first-layer row k-1, whose hidden MMAs were
+                    // waited for in the previous iteration
+                    wait(MB_F + ((k + 1) & 1));
+                    drain(S::T_F + ((k + 1) & 1) * 2 * C, sbias, smem + S::OFF_H1 + ((k + 1) & 1) * S::SLOT);
+                    arrive(MB_RH1 + ((k + 1) & 1));
                 }
-                if (k >= r_lo && k <= r_hi) {
-                    // its buffer held row k-2, read by last(k-2) (done: waited by
-                    // warps 0-3 before the barrier above)
-                    wait(MB_H + (k & 1));
-                    drain(S::T_H + (k & 1) * 64, sbias + C, smem + S::OFF_H2 + (k & 1) * S::SLOT);
-                    arrive(MB_RH2 + (k & 1));
+                if (Fv(k)) wait(MB_H + (k & 1));                 // hidden MMAs of first-layer row k
+                if (Hv(k - 1)) {
+                    // hidden row k-1 is complete; its buffer held row k-3, read by
+                    // last(k-3) (waited for by warps 12-15 before the barrier above)
+                    drain(S::T_H + ((-(k - 1)) & 3) * 2 * C, sbias + C, smem + S::OFF_H2 + ((k - 1) & 1) * S::SLOT);
+                    arrive(MB_RH2 + ((k - 1) & 1));
                 }
-                // last layer of hidden row h = k-1: contributions to output rows h+1, h, h-1
-                if (warp < 4 && k - 1 >= r_lo && k - 1 <= r_hi) {
-                    wait(MB_L + ((k - 1) & 1));
-                    float v[8];
-                    tmem_ld8(tmem + tlane + S::T_L + ((k - 1) & 1) * 16, v);
+                // last layer of hidden row h = k-2: contributions to output rows h+1, h, h-1
+                if (warp >= E3_WARP0 && Hv(k - 2)) {
+                    const int h = k - 2;
+                    wait(MB_L + (h & 1));
+                    float v[8], w[8], z[8];
+                    const uint32_t ta = tmem + tlane + S::T_L + (h & 1) * 32;
+                    tmem_ld8(ta, v);          // main of taps 0-7
+                    tmem_ld8(ta + 8, w);      // main of tap 8, corr of taps 0-6
+                    tmem_ld8(ta + 16, z);     // corr of taps 7-8
                     tc::tmem_ld_wait();
-                    const float p0 = fmaf(v[3], tc::SPLIT_INV, v[0]);
-                    const float p1 = fmaf(v[4], tc::SPLIT_INV, v[1]);
-                    const float p2 = fmaf(v[5], tc::SPLIT_INV, v[2]);
-                    a0 += p2;
-                    a1 += p1;
-                    a2 += p0;
-                    const int ro = k - 2;
+                    // tap t = 3 dy + dx: main in column t, corr in column 9 + t
+                    float P[9];
+#pragma unroll
+                    for (int tp = 0; tp < 9; ++tp) {
+                        const float mn = tp < 8 ? v[tp] : w[0];
+                        const float cr = tp < 7 ? w[1 + tp] : z[tp - 7];
+                        P[tp] = fmaf(cr, tc::SPLIT_INV, mn);
+                    }
+                    // horizontal neighbours: output pixel x takes tap dx from
+                    // hidden pixel x + dx - 1, i.e. lane ep + (dx - 1) G
+                    float* e0 = ex + (h & 1) * 6 * S::NPOS;
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        e0[(2 * dy) * S::NPOS + G + ep] = P[3 * dy];
+                        e0[(2 * dy + 1) * S::NPOS + G + ep] = P[3 * dy + 2];
+                    }
+                    tc::named_bar(BAR_E3, 4 * 32);
+                    float c3[3];
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+                        c3[dy] = P[3 * dy + 1] + e0[(2 * dy) * S::NPOS + ep] + e0[(2 * dy + 1) * S::NPOS + 2 * G + ep];
+                    a0 += c3[2];
+                    a1 += c3[1];
+                    a2 += c3[0];
+                    const int ro = h - 1;
                     if (ro >= ys && ro < ye) {
                         const int b = ep % G, x = ep / G, mbr = g * G + b;
                         if (mbr < Nb) {
@@ -387,16 +516,16 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                     }
                     a0 = a1; a1 = a2; a2 = 0.f;
                 }
-                // operand of first-layer row k+4 (its buffer held row k+2, whose
-                // MMA was waited for above), [X; B U] row k+6
-                if (f_role && Fvalid(k + 4)) {
-                    build_f(k + 4);
-                    arrive(MB_RF + ((k + 4) & 1));
+                // operand of first-layer row k+3 (its buffer held row k+1, whose
+                // MMA was waited for above), [X; B U] row k+5
+                if (f_role && Fv(k + 3)) {
+                    build_f(k + 3);
+                    arrive(MB_RF + ((k + 3) & 1));
                 }
-                store_xb(k + 6, xpf);
-                xpf = fetch_x(k + 7);
+                store_xb(k + 5, xpf);
+                xpf = fetch_x(k + 6);
             }
-            if (!failed && ye == n && warp < 4) {
+            if (!failed && ye == n && warp >= E3_WARP0) {
                 // bottom row: the hidden row below the image is zero
                 const int b = ep % G, x = ep / G, mbr = g * G + b;
                 if (mbr < Nb) {
@@ -428,8 +557,8 @@ size_t fused_smem(int n, int l)
 
 template <int C, int G>
 int fused_launch(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
-                 const float* Bmat, int Nb, int n, int l, const float* b1, const void* wpk2, const float* b2,
-                 const void* wpk13, const float* b3, float rs, int n_sm, int* err, cudaStream_t st)
+                 const float* Bmat, int Nb, int n, int l, const float* b1, const float* b2, const float* b3,
+                 const void* wpk, float rs, int n_sm, int* err, cudaStream_t st)
 {
     const size_t smem = fused_smem<C, G>(n, l);
     if (smem > 227 * 1024) return 1;
@@ -442,9 +571,8 @@ int fused_launch(const float* X, long x_ms, const float* U, long u_ms, float* Xo
     }
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
-    cnn_fused_kernel<C, G><<<grid, FT, smem, st>>>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1,
-                                                  static_cast<const __half*>(wpk2), b2,
-                                                  static_cast<const __half*>(wpk13), b3, rs, err);
+    cnn_fused_kernel<C, G><<<grid, FT, smem, st>>>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3,
+                                                  static_cast<const __half*>(wpk), rs, err);
     return 0;
 }
 
@@ -459,61 +587,87 @@ bool cnn_fused_supported(int n_layers, const int* channels, int n, int m, int l)
     return (size_t)FS<32, 8>::OFF_DYN + dyn + 16 <= 227 * 1024;
 }
 
-size_t cnn_fused_packed_bytes() { return (size_t)FS<32, 1>::B1BYTES + FS<32, 1>::B3BYTES; }
+size_t cnn_fused_packed_bytes() { return (size_t)FS<32, 1>::PACKED; }
 
-// First-layer tiles (3 taps): [kc][64 rows][8]; rows 0..31 main = [w_hi(6), 0, 0 | 0],
-// rows 32..63 corr = [w_lo(6), 0, 0 | w_hi(6), 0, 0], with K index e = 2 dy + ch.
-// Last-layer tiles (3 taps x 2 K-steps x {B1, B2}): [kc][16 rows][8]; B1 rows
-// 0..2 = w_hi of stencil rows 0..2, rows 3..5 = w_lo; B2 rows 3..5 = w_hi.
-void cnn_fused_pack_weights(const float* w1, const float* w3, void* dst_host)
+// Packed operand tiles, K-major (8-element core rows of 16 bytes), each
+// weight split w = hi + lo 2^-11:
+//   hidden [dx][ks][part] tiles of 2 K chunks x 6C rows; row 2C dy + r:
+//     part hi: r < C -> w_hi(co = r), else w_lo(co = r - C); part lo: r < C
+//     -> 0, else w_hi(co = r - C)
+//   first layer [dx] tiles of 2 K chunks x 64 rows; rows 0..31 main =
+//     [w_hi(6), 0, 0 | 0], rows 32..63 corr = [w_lo(6), 0, 0 | w_hi(6), 0, 0]
+//     with K index e = 2 dy + ch
+//   last layer [ks][part] tiles of 2 K chunks x 32 rows; tap t = 3 dy + dx:
+//     part hi: row t -> w_hi, row 9 + t -> w_lo; part lo: row 9 + t -> w_hi
+void cnn_fused_pack_weights(const float* w1, const float* w2, const float* w3, void* dst_host)
 {
-    constexpr int C = 32;
+    constexpr int C = 32, KS = C / 16;
+    using S = FS<C, 1>;
     __half* out = static_cast<__half*>(dst_host);
-    const size_t n1 = FS<C, 1>::B1BYTES / 2, n3 = FS<C, 1>::B3BYTES / 2;
-    for (size_t i = 0; i < n1 + n3; ++i) out[i] = __float2half(0.f);
+    for (size_t i = 0; i < (size_t)S::PACKED / 2; ++i) out[i] = __float2half(0.f);
     auto split = [](float v, __half& hi, __half& lo) {
         hi = __float2half_rn(v);
         lo = __float2half_rn((v - __half2float(hi)) * tc::SPLIT_SCALE);
     };
+    // hidden
+    for (int dx = 0; dx < 3; ++dx)
+        for (int ks = 0; ks < KS; ++ks)
+            for (int kc = 0; kc < 2; ++kc)
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int co = 0; co < C; ++co)
+                        for (int e = 0; e < 8; ++e) {
+                            const int ci = ks * 16 + kc * 8 + e;
+                            __half hi, lo;
+                            split(w2[((co * C + ci) * 3 + dy) * 3 + dx], hi, lo);
+                            __half* th = out + (size_t)((dx * KS + ks) * 2 + 0) * (S::HTILE / 2);
+                            __half* tl = out + (size_t)((dx * KS + ks) * 2 + 1) * (S::HTILE / 2);
+                            const int r_main = 2 * C * dy + co, r_corr = 2 * C * dy + C + co;
+                            th[((size_t)kc * S::HROWS + r_main) * 8 + e] = hi;
+                            th[((size_t)kc * S::HROWS + r_corr) * 8 + e] = lo;
+                            tl[((size_t)kc * S::HROWS + r_corr) * 8 + e] = hi;
+                        }
+    // first layer
+    __half* f1 = out + S::BBYTES / 2;
     for (int dx = 0; dx < 3; ++dx)
         for (int co = 0; co < C; ++co)
             for (int e = 0; e < 6; ++e) {
                 const int dy = e / 2, ch = e % 2;
                 __half hi, lo;
                 split(w1[((co * 2 + ch) * 3 + dy) * 3 + dx], hi, lo);
-                __half* t = out + (size_t)dx * 2 * 64 * 8;
+                __half* t = f1 + (size_t)dx * 2 * 64 * 8;
                 t[(0 * 64 + co) * 8 + e] = hi;              // main: kc 0
                 t[(0 * 64 + 32 + co) * 8 + e] = lo;         // corr: kc 0 lo
                 t[(1 * 64 + 32 + co) * 8 + e] = hi;         // corr: kc 1 hi
             }
-    __half* l3 = out + n1;
-    for (int dx = 0; dx < 3; ++dx)
-        for (int ks = 0; ks < C / 16; ++ks)
-            for (int kc = 0; kc < 2; ++kc)
-                for (int e = 0; e < 8; ++e) {
-                    const int ci = ks * 16 + kc * 8 + e;
-                    for (int d = 0; d < 3; ++d) {
+    // last layer
+    __half* l3 = f1 + S::B1BYTES / 2;
+    for (int ks = 0; ks < KS; ++ks)
+        for (int kc = 0; kc < 2; ++kc)
+            for (int e = 0; e < 8; ++e) {
+                const int ci = ks * 16 + kc * 8 + e;
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int tp = 3 * dy + dx;
                         __half hi, lo;
-                        split(w3[(ci * 3 + d) * 3 + dx], hi, lo);
-                        __half* b1 = l3 + (size_t)((dx * (C / 16) + ks) * 2 + 0) * (2 * 16 * 8);
-                        __half* b2 = l3 + (size_t)((dx * (C / 16) + ks) * 2 + 1) * (2 * 16 * 8);
-                        b1[(kc * 16 + d) * 8 + e] = hi;
-                        b1[(kc * 16 + 3 + d) * 8 + e] = lo;
-                        b2[(kc * 16 + 3 + d) * 8 + e] = hi;
+                        split(w3[(ci * 3 + dy) * 3 + dx], hi, lo);
+                        __half* th = l3 + (size_t)(ks * 2 + 0) * (S::B3TILE / 2);
+                        __half* tl = l3 + (size_t)(ks * 2 + 1) * (S::B3TILE / 2);
+                        th[(kc * 32 + tp) * 8 + e] = hi;
+                        th[(kc * 32 + 9 + tp) * 8 + e] = lo;
+                        tl[(kc * 32 + 9 + tp) * 8 + e] = hi;
                     }
-                }
+            }
 }
 
 int launch_cnn_fused(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
-                     const float* Bmat, int Nb, int n, int m, int l, const float* b1, const void* wpk2,
-                     const float* b2, const void* wpk13, const float* b3, float rs, int n_sm, int* err,
-                     cudaStream_t st)
+                     const float* Bmat, int Nb, int n, int m, int l, const float* b1, const float* b2,
+                     const float* b3, const void* wpk, float rs, int n_sm, int* err, cudaStream_t st)
 {
     switch (m) {
-    case 128: return fused_launch<32, 1>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, wpk2, b2, wpk13, b3, rs, n_sm, err, st);
-    case 64: return fused_launch<32, 2>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, wpk2, b2, wpk13, b3, rs, n_sm, err, st);
-    case 32: return fused_launch<32, 4>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, wpk2, b2, wpk13, b3, rs, n_sm, err, st);
-    case 16: return fused_launch<32, 8>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, wpk2, b2, wpk13, b3, rs, n_sm, err, st);
+    case 128: return fused_launch<32, 1>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
+    case 64: return fused_launch<32, 2>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
+    case 32: return fused_launch<32, 4>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
+    case 16: return fused_launch<32, 8>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
     }
     return 1;
 }

@@ -179,8 +179,8 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
         const int C = c.channels[1];
         run_stage(h, OIC_STAGE_CNN_FUSED, [&] {
             launch_cnn_fused(X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l, b,
-                             h->at<char>(h->lay.wtc) + h->wtc_off[1], b + C, h->at<char>(h->lay.wfused),
-                             b + 2 * C, c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st);
+                             b + C, b + 2 * C, h->at<char>(h->lay.wfused), c.residual_scale, h->n_sm,
+                             h->at<int>(h->lay.status), h->st);
         });
         return;
     }
@@ -407,9 +407,10 @@ oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda
         if (h->fused) {
             const int C = c.channels[1];
             const float* w1 = h->w.data();
-            const float* w3 = w1 + (size_t)2 * C * 9 + (size_t)C * C * 9;
+            const float* w2 = w1 + (size_t)2 * C * 9;
+            const float* w3 = w2 + (size_t)C * C * 9;
             std::vector<unsigned char> pk(cnn_fused_packed_bytes());
-            cnn_fused_pack_weights(w1, w3, pk.data());
+            cnn_fused_pack_weights(w1, w2, w3, pk.data());
             OIC_CUDA_OK(cudaMemcpy(h->at<char>(h->lay.wfused), pk.data(), pk.size(), cudaMemcpyHostToDevice));
         }
     }

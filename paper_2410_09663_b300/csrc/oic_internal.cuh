@@ -86,16 +86,15 @@ int conv_tc_configure();
 void launch_conv_tc(const float* in, float* out, const void* wpk, const float* bias, int C, int Nb, int n,
                     int m, int n_sm, int* err, cudaStream_t st);
 // Whole [X; B U] -> 32 -> 32 -> 1 surrogate in one kernel, every layer on the
-// tensor cores.  wpk2: hidden-layer tiles (conv_tc_pack_weights); wpk13:
-// first- and last-layer tiles (cnn_fused_pack_weights).  Returns non-zero if
-// the shape is not supported.
+// tensor cores.  wpk: all three layers' operand tiles (cnn_fused_pack_weights
+// from the OIHW weights w1 [32][2][3][3], w2 [32][32][3][3], w3 [1][32][3][3]).
+// Returns non-zero if the shape is not supported.
 bool cnn_fused_supported(int n_layers, const int* channels, int n, int m, int l);
 size_t cnn_fused_packed_bytes();
-void cnn_fused_pack_weights(const float* w1, const float* w3, void* dst_host);
+void cnn_fused_pack_weights(const float* w1, const float* w2, const float* w3, void* dst_host);
 int launch_cnn_fused(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
-                     const float* Bmat, int Nb, int n, int m, int l, const float* b1, const void* wpk2,
-                     const float* b2, const void* wpk13, const float* b3, float rs, int n_sm, int* err,
-                     cudaStream_t st);
+                     const float* Bmat, int Nb, int n, int m, int l, const float* b1, const float* b2,
+                     const float* b3, const void* wpk, float rs, int n_sm, int* err, cudaStream_t st);
 // Known-answer check of the tcgen05 path: res[0] = mismatches (-1 timeout).
 void launch_tc_selftest(int* res, cudaStream_t st);
 
