@@ -142,8 +142,9 @@ oic_status oic_step_host(oic_handle* h, const float* X_ref, const float* U_ref, 
 oic_status oic_reset_host(oic_handle* h, const float* X0, const float* U_prev);
 
 /* X_next[b] = CNN_theta(X[b], U[b]) for b < batch (Eq. (1)); X, X_next
- * [batch][n][m], U [batch][l][m]; batch <= N.  Device pointers; uses the
- * workspace's activation buffers, so it must not overlap other calls. */
+ * [batch][n][m], U [batch][l][m]; batch <= N.  Device pointers; X_next must
+ * not overlap X (OIC_EINVAL otherwise).  Uses the workspace's activation
+ * buffers, so it must not overlap other calls. */
 oic_status oic_cnn_forward(oic_handle* h, int batch, const float* X, const float* U,
                            float* X_next);
 

@@ -28,11 +28,13 @@
 //                          through shared memory) and keep rolling sums over
 //                          output rows h+1, h, h-1
 //
-// Roles: one thread issues every MMA and waits only on "operand ready"
-// mbarriers; 16 drain warps turn accumulators into the next layer's operands
-// (tanh, split, stores), arrive on those barriers and wait on the MMA commit
-// barriers.  Only X, U and the weights are read and X_next written.  The grid
-// is persistent over contiguous (group, row) ranges.
+// Roles: one thread issues every MMA and waits only on "operand ready" /
+// "accumulator drained" mbarriers; 16 drain warps turn accumulators into the
+// next layer's operands (tanh, split, stores); 4 warps finish the last layer
+// (neighbour sums, residual, X_next).  Both wait on the MMA commit barriers.
+// Only X, U and the weights are read and X_next written (X_next must not
+// overlap X: neighbouring CTAs read halo rows of X).  The grid is persistent
+// over contiguous (group, row) ranges.
 #include <cuda_fp16.h>
 
 #include "oic_internal.cuh"
@@ -41,12 +43,13 @@
 namespace oic {
 namespace {
 
-constexpr int FT = 544;                                 // 16 drain warps + 1 MMA-issuing warp
-constexpr int ND = 512;                                 // drain threads
+constexpr int FT = 672;                                 // 16 drain + 4 last-layer + 1 MMA-issuing warp
+constexpr int ND = 512;                                 // drain threads (warps 0-15)
 constexpr int FM = 128;                                 // tile rows (pixels)
-constexpr int BAR_DRAIN = 1;                            // named barrier of the drain warps
+constexpr int BAR_DRAIN = 1;                            // named barrier of the drain warps (segment start)
 constexpr int BAR_E3 = 2;                               // named barrier of the last-layer warps
-constexpr int E3_WARP0 = 12;                            // warps 12-15 finish the last layer
+constexpr int E3_WARP0 = 16;                            // warps 16-19 finish the last layer
+constexpr int ISSUE_WARP = 20;
 constexpr long long F_WAIT = 4000000000LL;
 
 __host__ __device__ constexpr int al16(int x) { return (x + 15) / 16 * 16; }
@@ -64,8 +67,6 @@ struct FS {
     static constexpr int B1BYTES = 3 * 2 * 64 * 16;     // first layer: 3 taps x (2 x 64 x 8)
     static constexpr int B3TILE = 2 * 32 * 16;          // last layer tile: 2 K chunks x 32 rows
     static constexpr int B3BYTES = KS * 2 * B3TILE;     // [ks][hi | lo]
-    static constexpr int NXB = 10;
-    static constexpr int SP = NPOS | 1;                 // odd FP32 row stride
     static constexpr int OFF_H1 = 0;                    // first-layer rows, 2 slots
     static constexpr int OFF_H2 = OFF_H1 + 2 * SLOT;    // hidden rows, 2 slots
     static constexpr int OFF_F = OFF_H2 + 2 * SLOT;     // first-layer operands, 2 buffers
@@ -76,8 +77,7 @@ struct FS {
     static constexpr int OFF_B1 = OFF_B + BBYTES;
     static constexpr int OFF_B3 = OFF_B1 + B1BYTES;
     static constexpr int PACKED = BBYTES + B1BYTES + B3BYTES;
-    static constexpr int OFF_XB = OFF_B3 + B3BYTES;                    // [NXB][2][SP] fp32
-    static constexpr int OFF_BIAS = OFF_XB + al16(NXB * 2 * SP * 4);   // b1[C], b2[C], b3
+    static constexpr int OFF_BIAS = OFF_B3 + B3BYTES;                  // b1[C], b2[C], b3
     static constexpr int OFF_MISC = OFF_BIAS + al16((2 * C + 4) * 4);  // mbarriers, TMEM base
     static constexpr int OFF_DYN = OFF_MISC + 128;                     // U group, B matrix
     // tensor memory: hidden ring (4 x [main | corr]), first layer (2 x [main | corr]),
@@ -87,14 +87,23 @@ struct FS {
     static_assert(T_L + 64 <= TMEM_COLS, "tensor memory");
 };
 
-__device__ __forceinline__ int mod_pos(int r, int k) { return ((r % k) + k) % k; }
-
 // tanh(x) = 1 - 2 / (1 + e^{2x}): saturates correctly at both ends; absolute
 // error a few 1e-7 (the exponential and the quotient are each within a few
 // ulps), which is below the FP32 rounding of the layer's inputs.
 __device__ __forceinline__ float tanh_fast(float x)
 {
     return 1.f - __fdividef(2.f, 1.f + __expf(2.f * x));
+}
+
+// Two values split at once: hi = fp16 rounding of (y0, y1), lo = fp16 of the
+// residuals scaled by 2^11 (packed conversions).
+__device__ __forceinline__ void split2(float y0, float y1, uint32_t& hi, uint32_t& lo)
+{
+    const __half2 h = __floats2half2_rn(y0, y1);
+    const float2 b = __half22float2(h);
+    const __half2 l = __floats2half2_rn((y0 - b.x) * tc::SPLIT_SCALE, (y1 - b.y) * tc::SPLIT_SCALE);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // 8 x 32-bit TMEM columns for the warp's 32 lanes.
@@ -259,13 +268,18 @@ enum : int {
     MB_F = 0,          // [2] first layer of row f done (tensor core -> drain warps)
     MB_H = 2,          // [2] hidden MMAs of first-layer row j done
     MB_L = 4,          // [2] last layer of hidden row h done
-    MB_RH1 = 6,        // [2] first-layer row drained into its operand slot (16 warps)
-    MB_RF = 8,         // [2] first-layer operand built (4 warps)
-    MB_RH2 = 10,       // [2] hidden row drained into its operand buffer (16 warps)
-    MB_FIN = 12,       // every MMA of the kernel done
-    MB_COUNT = 13
+    MB_W1 = 6,         // [2] drain pass k-1 done: first-layer row k in its slot, operand
+                       //     of first-layer row k+2 built (16 drain warps)
+    MB_W2 = 8,         // [2] hidden row h in its buffer (16 drain warps)
+    MB_FIN = 10,       // every MMA of the kernel done
+    MB_COUNT = 11
 };
 
+// Ordering used below: tcgen05.commit signals completion of ALL earlier MMAs
+// of the committing thread.  The first- and hidden-layer MMAs come from one
+// thread in the order first(k+2), hidden(k), so the wait for hidden(k) also
+// covers first(k+1).  The last-layer MMAs come from lane 0 of the first
+// last-layer warp, which issues last(h) once hidden row h is in its buffer.
 template <int C, int G>
 __global__ void __launch_bounds__(FT, 1)
 cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
@@ -276,14 +290,14 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     using S = FS<C, G>;
     static_assert(C == 32, "16 drain warps = 4 lane quarters x 4 groups of 8 channels");
     static_assert(MB_COUNT * 8 + 4 <= 128, "MISC region");
+    static_assert(FT == 32 * (ISSUE_WARP + 1) && E3_WARP0 * 32 == ND, "warp roles");
     constexpr int m = FM / G;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float* xb = reinterpret_cast<float*>(smem + S::OFF_XB);
     float* ex = reinterpret_cast<float*>(smem + S::OFF_EX);
     float* sbias = reinterpret_cast<float*>(smem + S::OFF_BIAS);   // b1 | b2 | b3
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + MB_COUNT * 8);
-    float* su = reinterpret_cast<float*>(smem + S::OFF_DYN);                 // [G][l][m]
+    float* su = reinterpret_cast<float*>(smem + S::OFF_DYN);                 // [G][m][l]
     float* sB = su + G * l * m;                                              // [n][l]
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const uint32_t s0 = tc::smem_u32(smem);
@@ -293,14 +307,12 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
         reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
     for (int e = tid; e < S::PACKED / 16; e += FT)
         reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk)[e];
-    for (int e = tid; e < S::NXB * 2 * S::SP; e += FT) xb[e] = 0.f;
     for (int e = tid; e < C; e += FT) { sbias[e] = b1[e]; sbias[C + e] = b2[e]; }
     for (int e = tid; e < n * l; e += FT) sB[e] = Bmat[e];
     if (tid == 0) {
         sbias[2 * C] = b3[0];
         for (int i = 0; i < MB_COUNT; ++i) {
-            const int cnt = (i >= MB_RH1 && i < MB_RH1 + 2) || (i >= MB_RH2 && i < MB_RH2 + 2) ? 16
-                          : (i >= MB_RF && i < MB_RF + 2) ? 4 : 1;
+            const int cnt = (i >= MB_W1 && i < MB_W2 + 2) ? 16 : 1;
             tc::mbar_init(mb + i, cnt);
         }
         tc::fence_mbar_init();
@@ -328,6 +340,14 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
         ph ^= 1u << i;
         tc::fence_after_sync();
     };
+    // the same by all 32 lanes of a warp, which then agree on the outcome
+    // (every later warp-wide step is taken by all lanes or by none)
+    auto wait_w = [&](int i) {
+        wait(i);
+        failed = __any_sync(0xffffffffu, failed);
+    };
+    // a phase this thread knows to be complete without waiting for it
+    auto passed = [&](int i) { ph ^= 1u << i; };
     const int q4 = warp & 3, cg = (warp >> 2) & 3;     // drain: lane quarter, channel group
     const int ep = 32 * q4 + lane;                      // drain pixel (TMEM lane)
     const uint32_t tlane = (uint32_t)(32 * q4) << 16;
@@ -347,84 +367,135 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
         auto Fv = [&](int f) { return f >= f_lo && f <= f_hi; };
         auto Hv = [&](int h) { return h >= r_lo && h <= r_hi; };
 
-        if (warp == ND / 32) {
+        if (warp == ISSUE_WARP) {
             // ================= MMA-issuing warp (one thread) =================
-            // iteration k: hidden MMAs of first-layer row k, first layer of row
-            // k+2, last layer of hidden row k-2
             if (lane == 0) {
                 const uint32_t dH1 = desc_lo(s0 + S::OFF_H1, S::PLANE);           // first-layer rows (A)
                 const uint32_t dHB = desc_lo(s0 + S::OFF_B, S::HROWS * 16);       // hidden tiles (B)
                 const uint32_t dF = desc_lo(s0 + S::OFF_F, S::PLANE);             // first-layer operands (A)
                 const uint32_t dB1 = desc_lo(s0 + S::OFF_B1, 64 * 16);            // first-layer tiles (B)
-                const uint32_t dH2 = desc_lo(s0 + S::OFF_H2 + G * 16, S::PLANE);  // hidden rows, centre (A)
-                const uint32_t dB3 = desc_lo(s0 + S::OFF_B3, 32 * 16);            // last-layer tiles (B)
-                for (int k = f_lo - 2; k <= r_hi + 2 && !failed; ++k) {
-                    if (Fv(k)) {
-                        wait(MB_RH1 + (k & 1));                     // first-layer row k in its slot
-                        issue_hidden<C, G>(tmem, k, k == f_lo, dH1 + (k & 1) * (S::SLOT / 16), dHB);
-                        tc::mma_commit(mb + MB_H + (k & 1));
-                    }
+                for (int k = f_lo - 2; k <= r_hi + 1 && !failed; ++k) {
+                    wait(MB_W1 + (k & 1));                          // drain pass k-1
                     if (Fv(k + 2)) {
-                        wait(MB_RF + ((k + 2) & 1));                // operand of first-layer row k+2
                         issue_first<C, G>(tmem + S::T_F + ((k + 2) & 1) * 2 * C,
                                           dF + ((k + 2) & 1) * (S::FBUF / 16), dB1);
                         tc::mma_commit(mb + MB_F + ((k + 2) & 1));
                     }
-                    if (Hv(k - 2)) {
-                        wait(MB_RH2 + ((k - 2) & 1));               // hidden row k-2 in its buffer
-                        issue_last<C, G>(tmem + S::T_L + ((k - 2) & 1) * 32, dH2 + ((k - 2) & 1) * (S::SLOT / 16),
-                                         dB3);
-                        tc::mma_commit(mb + MB_L + ((k - 2) & 1));
+                    if (Fv(k)) {
+                        issue_hidden<C, G>(tmem, k, k == f_lo, dH1 + (k & 1) * (S::SLOT / 16), dHB);
+                        tc::mma_commit(mb + MB_H + (k & 1));
                     }
                 }
             }
             __syncwarp();
+        } else if (warp >= E3_WARP0) {
+            // ================= 4 last-layer warps =================
+            // hidden row h: its nine tap products at every pixel -> contributions
+            // to output rows h+1, h, h-1; output row h-1 is then complete
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;          // outputs of rows h-1, h, h+1
+            const int b = ep % G, x = ep / G, mbr = g * G + b;
+            const uint32_t dH2 = desc_lo(s0 + S::OFF_H2 + G * 16, S::PLANE);      // hidden rows, centre (A)
+            const uint32_t dB3 = desc_lo(s0 + S::OFF_B3, 32 * 16);                // last-layer tiles (B)
+            for (int h = r_lo; h <= r_hi; ++h) {
+                if (warp == E3_WARP0 && lane == 0) {
+                    // hidden row h in its buffer; its accumulator buffer was read
+                    // out for row h-2 by all four warps before the last barrier
+                    wait(MB_W2 + (h & 1));
+                    issue_last<C, G>(tmem + S::T_L + (h & 1) * 32, dH2 + (h & 1) * (S::SLOT / 16), dB3);
+                    tc::mma_commit(mb + MB_L + (h & 1));
+                }
+                wait_w(MB_L + (h & 1));
+                float v[8], w[8], z[8];
+                const uint32_t ta = tmem + tlane + S::T_L + (h & 1) * 32;
+                tmem_ld8(ta, v);          // main of taps 0-7
+                tmem_ld8(ta + 8, w);      // main of tap 8, corr of taps 0-6
+                tmem_ld8(ta + 16, z);     // corr of taps 7-8
+                tc::tmem_ld_wait();
+                tc::fence_before_sync();
+                // tap t = 3 dy + dx: main in column t, corr in column 9 + t
+                float P[9];
+#pragma unroll
+                for (int tp = 0; tp < 9; ++tp) {
+                    const float mn = tp < 8 ? v[tp] : w[0];
+                    const float cr = tp < 7 ? w[1 + tp] : z[tp - 7];
+                    P[tp] = fmaf(cr, tc::SPLIT_INV, mn);
+                }
+                // horizontal neighbours: output pixel x takes tap dx from
+                // hidden pixel x + dx - 1, i.e. lane ep + (dx - 1) G
+                float* e0 = ex + (h & 1) * 6 * S::NPOS;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    e0[(2 * dy) * S::NPOS + G + ep] = P[3 * dy];
+                    e0[(2 * dy + 1) * S::NPOS + G + ep] = P[3 * dy + 2];
+                }
+                if (tc::named_bar_or(BAR_E3, 4 * 32, failed)) { failed = true; break; }
+                tc::fence_after_sync();
+                float c3[3];
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+                    c3[dy] = P[3 * dy + 1] + e0[(2 * dy) * S::NPOS + ep] + e0[(2 * dy + 1) * S::NPOS + 2 * G + ep];
+                a0 += c3[2];
+                a1 += c3[1];
+                a2 += c3[0];
+                const int ro = h - 1;
+                if (ro >= ys && ro < ye && mbr < Nb)
+                    Xout[(long)mbr * o_ms + (long)ro * m + x] =
+                        fmaf(rs, a0 + sbias[2 * C], X[(long)mbr * x_ms + (long)ro * m + x]);
+                a0 = a1; a1 = a2; a2 = 0.f;
+            }
+            if (!failed && ye == n && mbr < Nb) {
+                // bottom row: the hidden row below the image is zero
+                Xout[(long)mbr * o_ms + (long)(n - 1) * m + x] =
+                    fmaf(rs, a0 + sbias[2 * C], X[(long)mbr * x_ms + (long)(n - 1) * m + x]);
+            }
         } else {
             // ================= 16 drain warps =================
+            // U of the group, transposed to [member][pixel][control] so that one
+            // pixel's l controls are contiguous
             for (int e = tid; e < G * l * m; e += ND) {
-                const int b = e / (l * m), rr = e % (l * m);
+                const int b = e / (l * m), rr = e % (l * m), c = rr / m, xx = rr % m;
                 const int mbr = g * G + b;
-                su[e] = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
+                su[(b * m + xx) * l + c] = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
             }
             tc::named_bar(BAR_DRAIN, ND);
 
-            // [X; B U] row r into its ring slot (zero outside the image / group);
-            // warps 8-11, the X row fetched one row ahead
-            const bool xb_role = tid >= 2 * FM && tid < 3 * FM;
-            const int xt = tid - 2 * FM;
-            const int xb_b = xb_role ? xt / m : 0, xb_x = xb_role ? xt % m : 0;
-            const int xb_mb = g * G + xb_b;
-            auto fetch_x = [&](int r) -> float {
-                return (xb_role && r >= 0 && r < n && xb_mb < Nb) ? X[(long)xb_mb * x_ms + (long)r * m + xb_x] : 0.f;
-            };
-            auto store_xb = [&](int r, float xv) {
-                if (xb_role) {
-                    float* d = xb + mod_pos(r, S::NXB) * 2 * S::SP;
-                    const int q = G + G * xb_x + xb_b;
-                    float bu = 0.f;
-                    if (r >= 0 && r < n && xb_mb < Nb) {
-                        const float* ub = su + xb_b * l * m + xb_x;
-                        for (int c = 0; c < l; ++c) bu = fmaf(sB[r * l + c], ub[c * m], bu);
-                    }
-                    d[q] = xv;
-                    d[S::SP + q] = bu;
-                }
-            };
-            // first-layer operand of row r1: [X, BU] of rows r1-1 .. r1+1, hi | lo (warps 4-7)
+            // warps 4-7 build the first-layer operands: thread p owns position
+            // G + p (member p % G, pixel p / G) and keeps [X, B U] of the three
+            // rows it needs in registers
             const bool f_role = tid >= FM && tid < 2 * FM;
-            auto build_f = [&](int r1) {
-                const int q = G + (tid - FM);
-                __align__(16) __half hi[8], lo[8];
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy) {
-                    const float* row = xb + mod_pos(r1 - 1 + dy, S::NXB) * 2 * S::SP;
-#pragma unroll
-                    for (int ch = 0; ch < 2; ++ch) tc::split_f16(row[ch * S::SP + q], hi[2 * dy + ch], lo[2 * dy + ch]);
+            const int fp = f_role ? tid - FM : 0;
+            const int f_b = fp % G, f_x = fp / G, f_mb = g * G + f_b;
+            auto fetch_x = [&](int r) -> float {
+                return (f_role && r >= 0 && r < n && f_mb < Nb) ? X[(long)f_mb * x_ms + (long)r * m + f_x] : 0.f;
+            };
+            auto bu_of = [&](int r) -> float {
+                float bu = 0.f;
+                if (f_role && r >= 0 && r < n && f_mb < Nb) {
+                    const float* ub = su + (f_b * m + f_x) * l;
+                    const float* bb = sB + r * l;
+                    if ((l & 3) == 0) {
+                        for (int c = 0; c < l; c += 4) {
+                            const float4 u4 = *reinterpret_cast<const float4*>(ub + c);
+                            const float4 b4 = *reinterpret_cast<const float4*>(bb + c);
+                            bu = fmaf(b4.x, u4.x, fmaf(b4.y, u4.y, fmaf(b4.z, u4.z, fmaf(b4.w, u4.w, bu))));
+                        }
+                    } else {
+                        for (int c = 0; c < l; ++c) bu = fmaf(bb[c], ub[c], bu);
+                    }
                 }
-                hi[6] = hi[7] = lo[6] = lo[7] = __float2half(0.f);
-                unsigned char* f = smem + S::OFF_F + (r1 & 1) * S::FBUF + q * 16;
-                *reinterpret_cast<uint4*>(f) = *reinterpret_cast<const uint4*>(hi);
-                *reinterpret_cast<uint4*>(f + S::PLANE) = *reinterpret_cast<const uint4*>(lo);
+                return bu;
+            };
+            float xr[3], br[3];                           // rows k+2 .. k+4 at pass k
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { xr[i] = fetch_x(f_lo - 1 + i); br[i] = bu_of(f_lo - 1 + i); }
+            float xpf = fetch_x(f_lo + 2);                // row k+5, in flight
+            auto build_f = [&](int r1) {
+                uint32_t hi[3], lo[3];
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) split2(xr[dy], br[dy], hi[dy], lo[dy]);
+                unsigned char* f = smem + S::OFF_F + (r1 & 1) * S::FBUF + (G + fp) * 16;
+                *reinterpret_cast<uint4*>(f) = make_uint4(hi[0], hi[1], hi[2], 0u);
+                *reinterpret_cast<uint4*>(f + S::PLANE) = make_uint4(lo[0], lo[1], lo[2], 0u);
             };
             // tanh(main + corr 2^-11 + bias) of this warp's 8 channels -> hi/lo operand row
             auto drain = [&](uint32_t acc, const float* bias, unsigned char* dst) {
@@ -432,13 +503,16 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                 tmem_ld8(tmem + tlane + acc + cg * 8, mv);
                 tmem_ld8(tmem + tlane + acc + C + cg * 8, cv);
                 tc::tmem_ld_wait();
-                __align__(16) __half hi[8], lo[8];
+                uint32_t hi[4], lo[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    tc::split_f16(tanh_fast(fmaf(cv[j], tc::SPLIT_INV, mv[j]) + bias[cg * 8 + j]), hi[j], lo[j]);
+                for (int j = 0; j < 4; ++j) {
+                    const float y0 = tanh_fast(fmaf(cv[2 * j], tc::SPLIT_INV, mv[2 * j]) + bias[cg * 8 + 2 * j]);
+                    const float y1 = tanh_fast(fmaf(cv[2 * j + 1], tc::SPLIT_INV, mv[2 * j + 1]) + bias[cg * 8 + 2 * j + 1]);
+                    split2(y0, y1, hi[j], lo[j]);
+                }
                 const int q = G + ep;
-                *reinterpret_cast<uint4*>(dst + cg * S::PLANE + q * 16) = *reinterpret_cast<const uint4*>(hi);
-                *reinterpret_cast<uint4*>(dst + (S::KC + cg) * S::PLANE + q * 16) = *reinterpret_cast<const uint4*>(lo);
+                *reinterpret_cast<uint4*>(dst + cg * S::PLANE + q * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4*>(dst + (S::KC + cg) * S::PLANE + q * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
             };
             // this warp's operand writes (and TMEM reads) are done: one arrival
             auto arrive = [&](int i) {
@@ -448,98 +522,45 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                 if (lane == 0) tc::mbar_arrive(mb + i);
             };
 
-            for (int r = f_lo - 1; r <= f_lo + 1; ++r) store_xb(r, fetch_x(r));
-            float xpf = fetch_x(f_lo + 2);               // next [X; B U] row, in flight
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;          // outputs of rows h-1, h, h+1 (warps 12-15)
-
-            // iteration k: drain first-layer row k+1 and hidden row k-1, finish
-            // the last layer of hidden row k-2 (output row k-3), build the
-            // first-layer operand of row k+3
-            for (int k = f_lo - 3; k <= r_hi + 2; ++k) {
-                if (tc::named_bar_or(BAR_DRAIN, ND, failed)) { failed = true; break; }
-                tc::fence_after_sync();
+            // pass k: drain first-layer row k+1, build the operand of first-layer
+            // row k+3, then drain hidden row k-1
+            for (int k = f_lo - 3; k <= r_hi + 2 && !failed; ++k) {
                 if (Fv(k + 1)) {
-                    // its slot held first-layer row k-1, whose hidden MMAs were
-                    // waited for in the previous iteration
-                    wait(MB_F + ((k + 1) & 1));
+                    // first(k+1) precedes hidden(k-1), waited for in pass k-1
+                    if (Fv(k - 1)) passed(MB_F + ((k + 1) & 1));
+                    else wait_w(MB_F + ((k + 1) & 1));
+                    // the slot held first-layer row k-1 (hidden(k-1) done)
                     drain(S::T_F + ((k + 1) & 1) * 2 * C, sbias, smem + S::OFF_H1 + ((k + 1) & 1) * S::SLOT);
-                    arrive(MB_RH1 + ((k + 1) & 1));
                 }
-                if (Fv(k)) wait(MB_H + (k & 1));                 // hidden MMAs of first-layer row k
+                // its buffer held row k+1, read by first(k+1) (done, see above)
+                if (f_role && Fv(k + 3)) build_f(k + 3);
+                if (k <= r_hi) arrive(MB_W1 + ((k + 1) & 1));   // consumed by issue pass k+1
+                if (f_role) {
+                    xr[0] = xr[1]; xr[1] = xr[2]; xr[2] = xpf;
+                    br[0] = br[1]; br[1] = br[2]; br[2] = bu_of(k + 5);
+                    xpf = fetch_x(k + 6);
+                }
+                if (Fv(k)) wait_w(MB_H + (k & 1));               // hidden MMAs of first-layer row k
                 if (Hv(k - 1)) {
                     // hidden row k-1 is complete; its buffer held row k-3, read by
-                    // last(k-3) (waited for by warps 12-15 before the barrier above)
+                    // last(k-3)
+                    if (Hv(k - 3)) wait_w(MB_L + ((k - 3) & 1));
                     drain(S::T_H + ((-(k - 1)) & 3) * 2 * C, sbias + C, smem + S::OFF_H2 + ((k - 1) & 1) * S::SLOT);
-                    arrive(MB_RH2 + ((k - 1) & 1));
-                }
-                // last layer of hidden row h = k-2: contributions to output rows h+1, h, h-1
-                if (warp >= E3_WARP0 && Hv(k - 2)) {
-                    const int h = k - 2;
-                    wait(MB_L + (h & 1));
-                    float v[8], w[8], z[8];
-                    const uint32_t ta = tmem + tlane + S::T_L + (h & 1) * 32;
-                    tmem_ld8(ta, v);          // main of taps 0-7
-                    tmem_ld8(ta + 8, w);      // main of tap 8, corr of taps 0-6
-                    tmem_ld8(ta + 16, z);     // corr of taps 7-8
-                    tc::tmem_ld_wait();
-                    // tap t = 3 dy + dx: main in column t, corr in column 9 + t
-                    float P[9];
-#pragma unroll
-                    for (int tp = 0; tp < 9; ++tp) {
-                        const float mn = tp < 8 ? v[tp] : w[0];
-                        const float cr = tp < 7 ? w[1 + tp] : z[tp - 7];
-                        P[tp] = fmaf(cr, tc::SPLIT_INV, mn);
-                    }
-                    // horizontal neighbours: output pixel x takes tap dx from
-                    // hidden pixel x + dx - 1, i.e. lane ep + (dx - 1) G
-                    float* e0 = ex + (h & 1) * 6 * S::NPOS;
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy) {
-                        e0[(2 * dy) * S::NPOS + G + ep] = P[3 * dy];
-                        e0[(2 * dy + 1) * S::NPOS + G + ep] = P[3 * dy + 2];
-                    }
-                    tc::named_bar(BAR_E3, 4 * 32);
-                    float c3[3];
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
-                        c3[dy] = P[3 * dy + 1] + e0[(2 * dy) * S::NPOS + ep] + e0[(2 * dy + 1) * S::NPOS + 2 * G + ep];
-                    a0 += c3[2];
-                    a1 += c3[1];
-                    a2 += c3[0];
-                    const int ro = h - 1;
-                    if (ro >= ys && ro < ye) {
-                        const int b = ep % G, x = ep / G, mbr = g * G + b;
-                        if (mbr < Nb) {
-                            const float xv = xb[mod_pos(ro, S::NXB) * 2 * S::SP + G + ep];
-                            Xout[(long)mbr * o_ms + (long)ro * m + x] = fmaf(rs, a0 + sbias[2 * C], xv);
-                        }
-                    }
-                    a0 = a1; a1 = a2; a2 = 0.f;
-                }
-                // operand of first-layer row k+3 (its buffer held row k+1, whose
-                // MMA was waited for above), [X; B U] row k+5
-                if (f_role && Fv(k + 3)) {
-                    build_f(k + 3);
-                    arrive(MB_RF + ((k + 3) & 1));
-                }
-                store_xb(k + 5, xpf);
-                xpf = fetch_x(k + 6);
-            }
-            if (!failed && ye == n && warp >= E3_WARP0) {
-                // bottom row: the hidden row below the image is zero
-                const int b = ep % G, x = ep / G, mbr = g * G + b;
-                if (mbr < Nb) {
-                    const float xv = xb[mod_pos(n - 1, S::NXB) * 2 * S::SP + G + ep];
-                    Xout[(long)mbr * o_ms + (long)(n - 1) * m + x] = fmaf(rs, a0 + sbias[2 * C], xv);
+                    arrive(MB_W2 + ((k - 1) & 1));
                 }
             }
+            // phases of the last two rows' last-layer MMAs (waited for by the
+            // last-layer warps before the barrier below)
+            // (the drain warps wait for last(h) only when reusing its buffer)
+            for (int h = r_hi - 1; h <= r_hi; ++h)
+                if (Hv(h)) passed(MB_L + (h & 1));
         }
         tc::fence_before_sync();
         if (__syncthreads_or(failed)) { failed = true; break; }
         tc::fence_after_sync();
     }
     // every MMA issued has landed before the tensor memory is released
-    if (warp == ND / 32 && lane == 0) {
+    if (warp == ISSUE_WARP && lane == 0) {
         tc::mma_commit(mb + MB_FIN);
         if (!tc::mbar_wait_bounded(mb + MB_FIN, 0u, F_WAIT)) atomicExch(err, DEV_TIMEOUT);
     }

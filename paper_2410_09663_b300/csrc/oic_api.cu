@@ -566,6 +566,11 @@ oic_status oic_cnn_forward(oic_handle* h, int batch, const float* X, const float
     if (!h || !X || !U || !X_next || batch < 1 || batch > h->cfg.N) return OIC_EINVAL;
     if (!h->bound) return OIC_ESTATE;
     const long nx = (long)h->cfg.n * h->cfg.m, nu = (long)h->cfg.l * h->cfg.m;
+    // X_next must not overlap X: tiles of neighbouring rows read X rows that
+    // another tile writes
+    const float* xe = X + (size_t)batch * nx;
+    const float* ye = X_next + (size_t)batch * nx;
+    if (X_next < xe && X < ye) return OIC_EINVAL;
     cnn_forward(h, batch, X, nx, U, nu, X_next, nx);
     return last_cuda();
 }

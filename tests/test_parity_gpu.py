@@ -70,6 +70,22 @@ def test_cnn_forward_matches_oracle(cuda_ok, name):
     assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
 
 
+def test_cnn_forward_rejects_overlapping_output(cuda_ok):
+    """X_next overlapping X is refused before any launch (halo rows of X are
+    read by neighbouring tiles while others write X_next)."""
+    wl = CASES["small_16"]
+    s = solver(wl)
+    X = dev(np.zeros((2, wl.n, wl.m), np.float32))
+    U = dev(np.zeros((2, wl.l, wl.m), np.float32))
+    with pytest.raises(oic.OICError) as e:
+        s.oic_cnn_forward(X, U, X)
+    assert e.value.status == oic.OIC_EINVAL
+    with pytest.raises(oic.OICError) as e:
+        shifted = X.view(-1)[wl.m: wl.m + wl.n * wl.m].view(1, wl.n, wl.m)   # one image row into X[0]
+        s.oic_cnn_forward(X[:1], U[:1], shifted)
+    assert e.value.status == oic.OIC_EINVAL
+
+
 @pytest.mark.parametrize("name", ["small_16", "ragged", "mid", "tc_ragged"])
 @pytest.mark.parametrize("full", [False, True])
 def test_solve_matches_oracle(cuda_ok, name, full):
