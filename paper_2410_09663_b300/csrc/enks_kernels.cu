@@ -255,138 +255,124 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
 }
 
 // ------------------------------------------------------------------ gain
-// K = Cxy Cyy^{-1}, written transposed (Kt = K^T, [p][R]).  Every CTA factors
-// Cyy = L L^T (FP32 Cholesky, lower triangle in shared memory, odd row stride)
-// and then each warp solves L L^T k = c for its rows c of Cxy.
+// K = Cxy Cyy^{-1}, written transposed: Kt = K^T = Cyy^{-1} Cxy^T, [p][R].
 //
-// Cholesky, right-looking, one barrier per step: step j subtracts the outer
-// product of the UNSCALED column j divided by the pivot, A[i][k] -= A[i][j]
-// A[k][j] / A[j][j] for j < k <= i; column j itself is scaled by 1/sqrt of
-// the pivot one step later (nobody reads it after step j).  Threads tile the
-// trailing triangle as a 16 x 16 grid of (row, column) strides.
+// Gauss-Jordan elimination on [Cyy | Cxy^T] without pivoting, FP32, the
+// matrix held in registers.  Cyy is symmetric positive definite, so the
+// pivots are the Schur complements (the squares of the Cholesky diagonal; no
+// growth, no pivoting needed) and a pivot <= 0 means "not positive definite".
+// Rows are never normalised: step j subtracts A[i][j] / A[j][j] times row j
+// from every row i != j.  At the end the left block is diagonal and
+// Kt[c][a] = A[c][p + a] / A[c][c].
 //
-// Solves: lane t owns entries r = t + 32 q; the pivot value is broadcast by
-// shuffle, forward L z = c walks the columns of L, back L^T k = z its rows.
-constexpr int G_THREADS = 256;
-constexpr int G_WARPS = G_THREADS / 32;
-constexpr int G_MAXP = 144;
-constexpr int G_KQ = (G_MAXP + 31) / 32;
-
-__global__ void __launch_bounds__(G_THREADS)
-gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
+// Warp w owns rows w + RG k (k < RPT), lane t owns columns t + 32 q (q < CPT);
+// per step only pivot column j and pivot row j go through shared memory
+// (double-buffered, so one barrier per step).  CTA b takes the right-hand
+// sides a in [b RC, (b+1) RC), RC = 32 CPT - p, and eliminates Cyy itself.
+// Owners of column j / row j write them to the shared pivot buffers.  Row j
+// lives in row slot KS = j / RG of warp j % RG; column j in column slot
+// (KS RG) / 32 of lane j % 32 (RG divides 32, so both are compile-time for a
+// given KS).
+template <int RPT, int CPT, int RG, int KS>
+__device__ __forceinline__ void gain_publish(const float (&A)[RPT][CPT], int j, float* col, float* row, int w, int t)
 {
-    extern __shared__ float Ls[];                 // [p][ps], then the triangle table
-    __shared__ float rdiag[G_MAXP];               // 1 / L_jj
-    __shared__ int bad;
-    const int ps = p | 1;
-    uint32_t* tri = reinterpret_cast<uint32_t*>(Ls + p * ps);   // e -> (r << 16 | c), c <= r
-    const int tid = threadIdx.x;
-    const double* Cyy = C + (long)R * p;
-    for (int e = tid; e < p * p; e += G_THREADS) {
-        const int i = e / p, k = e % p;
-        if (k <= i) Ls[i * ps + k] = (float)Cyy[e];
+    constexpr int QS = (KS * RG) / 32;
+    if ((j & 31) == t) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) col[w + RG * k] = A[k][QS];
     }
-    // enumerate the triangle {(r, c): 0 <= c <= r} row by row; the trailing
-    // block of step j is the first (p-1-j)(p-j)/2 entries shifted by j + 1
-    for (int r = tid; r < p - 1; r += G_THREADS) {
-        const int base = r * (r + 1) / 2;
-        for (int c = 0; c <= r; ++c) tri[base + c] = ((uint32_t)r << 16) | (uint32_t)c;
+    if (j % RG == w) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) row[t + 32 * q] = A[KS][q];
     }
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    for (int j = 0; j < p; ++j) {
-        const float d = Ls[j * ps + j];
-        if (!(d > 0.f)) {                          // same value in every thread
-            if (tid == 0) bad = 1;
-            break;
+}
+
+// Elimination steps j = KS RG .. KS RG + RG - 1 (row slot KS), then the next
+// slot.  Returns false if a pivot was not positive.
+template <int RPT, int CPT, int RG, int KS>
+__device__ __forceinline__ bool gain_steps(float (&A)[RPT][CPT], int p, float (*colbuf)[RPT * RG],
+                                           float (*rowbuf)[32 * CPT], int w, int t)
+{
+    for (int w0 = 0; w0 < RG; ++w0) {
+        const int j = KS * RG + w0;
+        if (j >= p) return true;
+        const int buf = j & 1;
+        const float piv = rowbuf[buf][j];
+        if (!(piv > 0.f)) return false;           // same value in every thread
+        const float ipiv = __frcp_rn(piv);
+        float rj[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) rj[q] = rowbuf[buf][t + 32 * q];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int i = w + RG * k;
+            const float f = (i == j) ? 0.f : colbuf[buf][i] * ipiv;
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) A[k][q] = fmaf(-f, rj[q], A[k][q]);
         }
-        const float dinv = 1.f / d;
-        const int tj = (p - 1 - j) * (p - j) / 2;   // trailing entries (i, k), j < k <= i
-        const int o = j + 1;
-        for (int e0 = tid; e0 < tj; e0 += 4 * G_THREADS) {
-            // four independent entries per batch: loads first, then the updates
-            int ii[4], kk[4];
-            float aij[4], akj[4], aik[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = e0 + q * G_THREADS;
-                const uint32_t rc = e < tj ? tri[e] : 0u;
-                ii[q] = o + (int)(rc >> 16);
-                kk[q] = o + (int)(rc & 0xffffu);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool ok = e0 + q * G_THREADS < tj;
-                aij[q] = ok ? Ls[ii[q] * ps + j] : 0.f;
-                akj[q] = ok ? Ls[kk[q] * ps + j] : 0.f;
-                aik[q] = ok ? Ls[ii[q] * ps + kk[q]] : 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (e0 + q * G_THREADS < tj) Ls[ii[q] * ps + kk[q]] = fmaf(-aij[q] * dinv, akj[q], aik[q]);
+        if (j + 1 < p) {
+            if (w0 + 1 < RG) gain_publish<RPT, CPT, RG, KS>(A, j + 1, colbuf[buf ^ 1], rowbuf[buf ^ 1], w, t);
+            else if constexpr (KS + 1 < RPT)
+                gain_publish<RPT, CPT, RG, KS + 1>(A, j + 1, colbuf[buf ^ 1], rowbuf[buf ^ 1], w, t);
         }
         __syncthreads();
-        // column j is final now: L[i][j] = A[i][j] / sqrt(d); the next step
-        // reads column j + 1 only
-        const float rs = rsqrtf(d);
-        for (int i = j + tid; i < p; i += G_THREADS) Ls[i * ps + j] = i == j ? d * rs : Ls[i * ps + j] * rs;
-        if (tid == 0) rdiag[j] = 1.f / (d * rs);
     }
+    if constexpr (KS + 1 < RPT) return gain_steps<RPT, CPT, RG, KS + 1>(A, p, colbuf, rowbuf, w, t);
+    return true;
+}
+
+template <int RPT, int CPT, int RG>
+__global__ void __launch_bounds__(32 * RG, 1)
+gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
+{
+    static_assert(32 % RG == 0, "row groups divide the warp");
+    constexpr int NT = 32 * RG, NCOL = 32 * CPT;
+    __shared__ float colbuf[2][RPT * RG];         // pivot column (all rows)
+    __shared__ float rowbuf[2][NCOL];             // pivot row (all columns)
+    __shared__ float diag[RPT * RG];
+    const int RC = NCOL - p;
+    const int a0 = blockIdx.x * RC;
+    const int nr = R - a0 < RC ? R - a0 : RC;
+    const int W = p + nr;
+    const int tid = threadIdx.x, w = tid / 32, t = tid % 32;
+    const double* Cyy = C + (long)R * p;
+    float A[RPT][CPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int i = w + RG * k;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = t + 32 * q;
+            float v = 0.f;
+            if (i < p) {
+                if (c < p) v = (float)Cyy[(long)i * p + c];
+                else if (c < W) v = (float)C[(long)(a0 + c - p) * p + i];
+            }
+            A[k][q] = v;
+        }
+    }
+    gain_publish<RPT, CPT, RG, 0>(A, 0, colbuf[0], rowbuf[0], w, t);
     __syncthreads();
-    const int warp = tid / 32, lane = tid % 32;
-    if (bad) {
-        if (blockIdx.x == 0 && tid == 0) atomicExch(status, DEV_NOTSPD);
-        const int a = blockIdx.x * G_WARPS + warp;
-        if (a < R)
-            for (int r = lane; r < p; r += 32) Kt[(long)r * R + a] = 0.f;
+    if (!gain_steps<RPT, CPT, RG, 0>(A, p, colbuf, rowbuf, w, t)) {
+        if (tid == 0) atomicExch(status, DEV_NOTSPD);
+        for (int e = tid; e < nr * p; e += NT) Kt[(long)(e / nr) * R + a0 + e % nr] = 0.f;
         return;
     }
-    const int a = blockIdx.x * G_WARPS + warp;
-    if (a >= R) return;
-    float v[G_KQ];
+    // diagonal of the eliminated block, then Kt[i][a0 + c - p] = A[i][c] / A[i][i]
 #pragma unroll
-    for (int q = 0; q < G_KQ; ++q) {
-        const int r = lane + 32 * q;
-        v[q] = r < p ? (float)C[(long)a * p + r] : 0.f;
-    }
-    // forward: L z = c
+    for (int k = 0; k < RPT; ++k)
 #pragma unroll
-    for (int qb = 0; qb < G_KQ; ++qb) {
-        if (32 * qb >= p) break;
-        for (int il = 0; il < 32; ++il) {
-            const int i = 32 * qb + il;
-            if (i >= p) break;
-            const float zi = __shfl_sync(0xffffffffu, v[qb], il) * rdiag[i];
-            if (lane == il) v[qb] = zi;
+        for (int q = 0; q < CPT; ++q)
+            if (w + RG * k == t + 32 * q) diag[w + RG * k] = A[k][q];
+    __syncthreads();
 #pragma unroll
-            for (int q = 0; q < G_KQ; ++q) {
-                if (q < qb) continue;
-                const int r = lane + 32 * q;
-                if (r > i && r < p) v[q] = fmaf(-Ls[r * ps + i], zi, v[q]);
-            }
+    for (int k = 0; k < RPT; ++k) {
+        const int i = w + RG * k;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int c = t + 32 * q;
+            if (i < p && c >= p && c < W) Kt[(long)i * R + a0 + c - p] = A[k][q] / diag[i];
         }
-    }
-    // back: L^T k = z
-#pragma unroll
-    for (int qb = G_KQ - 1; qb >= 0; --qb) {
-        if (32 * qb >= p) continue;
-        for (int il = 31; il >= 0; --il) {
-            const int i = 32 * qb + il;
-            if (i >= p) continue;
-            const float ki = __shfl_sync(0xffffffffu, v[qb], il) * rdiag[i];
-            if (lane == il) v[qb] = ki;
-#pragma unroll
-            for (int q = 0; q < G_KQ; ++q) {
-                if (q > qb) continue;
-                const int r = lane + 32 * q;
-                if (r < i) v[q] = fmaf(-Ls[i * ps + r], ki, v[q]);
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < G_KQ; ++q) {
-        const int r = lane + 32 * q;
-        if (r < p) Kt[(long)r * R + a] = v[q];
     }
 }
 
@@ -528,19 +514,20 @@ void launch_cov_finalize(const float* part2, const float* S1, int splits, int R,
     cov_finalize_kernel<<<(total + 31) / 32, 256, 0, st>>>(part2, S1, splits, R, p, m, N, C);
 }
 
-size_t gain_smem_bytes(int p) { return p <= G_MAXP ? 0 : (size_t)-1; }
-int gain_max_p() { return G_MAXP; }
+size_t gain_smem_bytes(int p) { return p <= 144 ? 0 : (size_t)-1; }
+int gain_max_p() { return 144; }
 
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * (size_t)p * (p | 1) + sizeof(uint32_t) * (size_t)p * (p - 1) / 2;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(gain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_set = true;
+    // rows = 8 warps x 9 (p <= 72, 128 columns) or 16 warps x 9 (p <= 144,
+    // 256 columns); the columns beyond p carry right-hand sides
+    if (p <= 72) {
+        const int RC = 128 - p, grid = (R + RC - 1) / RC;
+        gain_kernel<9, 4, 8><<<grid > 0 ? grid : 1, 256, 0, st>>>(C, R, p, K, status);
+    } else {
+        const int RC = 256 - p, grid = (R + RC - 1) / RC;
+        gain_kernel<9, 8, 16><<<grid > 0 ? grid : 1, 512, 0, st>>>(C, R, p, K, status);
     }
-    const int grid = (R + G_WARPS - 1) / G_WARPS;
-    gain_kernel<<<grid > 0 ? grid : 1, G_THREADS, smem, st>>>(C, R, p, K, status);
 }
 
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
