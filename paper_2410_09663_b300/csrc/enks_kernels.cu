@@ -269,37 +269,71 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
 // per step only pivot column j and pivot row j go through shared memory
 // (double-buffered, so one barrier per step).  CTA b takes the right-hand
 // sides a in [b RC, (b+1) RC), RC = 32 CPT - p, and eliminates Cyy itself.
-// Owners of column j / row j write them to the shared pivot buffers.  Row j
-// lives in row slot KS = j / RG of warp j % RG; column j in column slot
-// (KS RG) / 32 of lane j % 32 (RG divides 32, so both are compile-time for a
-// given KS).
-template <int RPT, int CPT, int RG, int KS>
-__device__ __forceinline__ void gain_publish(const float (&A)[RPT][CPT], int j, float* col, float* row, int w, int t)
+// Register slots picked by the runtime step go through select chains, so
+// the loop body exists once (the kernel is bound by instruction issue).
+template <int N>
+__device__ __forceinline__ float gsel(const float (&v)[N], int q)
 {
-    constexpr int QS = (KS * RG) / 32;
-    if ((j & 31) == t) {
+    float r = v[0];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) col[w + RG * k] = A[k][QS];
-    }
-    if (j % RG == w) {
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) row[t + 32 * q] = A[KS][q];
-    }
+    for (int i = 1; i < N; ++i) r = q == i ? v[i] : r;
+    return r;
 }
 
-// Elimination steps j = KS RG .. KS RG + RG - 1 (row slot KS), then the next
-// slot.  Returns false if a pivot was not positive.
-template <int RPT, int CPT, int RG, int KS>
-__device__ __forceinline__ bool gain_steps(float (&A)[RPT][CPT], int p, float (*colbuf)[RPT * RG],
-                                           float (*rowbuf)[32 * CPT], int w, int t)
+template <int RPT, int CPT, int RG>
+__global__ void __launch_bounds__(32 * RG, 1)
+gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
 {
-    for (int w0 = 0; w0 < RG; ++w0) {
-        const int j = KS * RG + w0;
-        if (j >= p) return true;
+    constexpr int NT = 32 * RG, NCOL = 32 * CPT, NROW = RPT * RG;
+    extern __shared__ __align__(16) float gsm[];
+    float* stage = gsm;                           // [NROW][NCOL]: [Cyy | Cxy^T slice] as FP32
+    float (*colbuf)[NROW] = reinterpret_cast<float (*)[NROW]>(gsm + NROW * NCOL);
+    float (*rowbuf)[NCOL] = reinterpret_cast<float (*)[NCOL]>(gsm + NROW * NCOL + 2 * NROW);
+    float* diag = gsm + NROW * NCOL + 2 * NROW + 2 * NCOL;
+    const int RC = NCOL - p;
+    const int a0 = blockIdx.x * RC;
+    const int nr = R - a0 < RC ? R - a0 : RC;
+    const int W = p + nr;
+    const int tid = threadIdx.x, w = tid / 32, t = tid % 32;
+    const double* Cyy = C + (long)R * p;
+    // coalesced reads: Cyy row by row, the Cxy rows of this slice row by row
+    // (stored transposed); everything else zero
+    for (int e = tid; e < NROW * NCOL; e += NT) stage[e] = 0.f;
+    __syncthreads();
+    for (int e = tid; e < p * p; e += NT) stage[(e / p) * NCOL + e % p] = (float)Cyy[e];
+    for (int e = tid; e < nr * p; e += NT) stage[(e % p) * NCOL + p + e / p] = (float)C[(long)a0 * p + e];
+    __syncthreads();
+    float A[RPT][CPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) A[k][q] = stage[(w + RG * k) * NCOL + t + 32 * q];
+    // owners of column j / row j publish them
+    auto publish = [&](int j, int buf) {
+        if ((j & 31) == t) {
+            const int qs = j / 32;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) colbuf[buf][w + RG * k] = gsel<CPT>(A[k], qs);
+        }
+        if (j % RG == w) {
+            const int ks = j / RG;
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                float v = A[0][q];
+#pragma unroll
+                for (int k = 1; k < RPT; ++k) v = ks == k ? A[k][q] : v;
+                rowbuf[buf][t + 32 * q] = v;
+            }
+        }
+    };
+    publish(0, 0);
+    __syncthreads();
+    bool bad = false;
+    for (int j = 0; j < p; ++j) {
         const int buf = j & 1;
         const float piv = rowbuf[buf][j];
-        if (!(piv > 0.f)) return false;           // same value in every thread
-        const float ipiv = __frcp_rn(piv);
+        if (!(piv > 0.f)) { bad = true; break; }   // same value in every thread
+        const float ipiv = __fdividef(1.f, piv);
         float rj[CPT];
 #pragma unroll
         for (int q = 0; q < CPT; ++q) rj[q] = rowbuf[buf][t + 32 * q];
@@ -310,50 +344,10 @@ __device__ __forceinline__ bool gain_steps(float (&A)[RPT][CPT], int p, float (*
 #pragma unroll
             for (int q = 0; q < CPT; ++q) A[k][q] = fmaf(-f, rj[q], A[k][q]);
         }
-        if (j + 1 < p) {
-            if (w0 + 1 < RG) gain_publish<RPT, CPT, RG, KS>(A, j + 1, colbuf[buf ^ 1], rowbuf[buf ^ 1], w, t);
-            else if constexpr (KS + 1 < RPT)
-                gain_publish<RPT, CPT, RG, KS + 1>(A, j + 1, colbuf[buf ^ 1], rowbuf[buf ^ 1], w, t);
-        }
+        if (j + 1 < p) publish(j + 1, buf ^ 1);
         __syncthreads();
     }
-    if constexpr (KS + 1 < RPT) return gain_steps<RPT, CPT, RG, KS + 1>(A, p, colbuf, rowbuf, w, t);
-    return true;
-}
-
-template <int RPT, int CPT, int RG>
-__global__ void __launch_bounds__(32 * RG, 1)
-gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
-{
-    static_assert(32 % RG == 0, "row groups divide the warp");
-    constexpr int NT = 32 * RG, NCOL = 32 * CPT;
-    __shared__ float colbuf[2][RPT * RG];         // pivot column (all rows)
-    __shared__ float rowbuf[2][NCOL];             // pivot row (all columns)
-    __shared__ float diag[RPT * RG];
-    const int RC = NCOL - p;
-    const int a0 = blockIdx.x * RC;
-    const int nr = R - a0 < RC ? R - a0 : RC;
-    const int W = p + nr;
-    const int tid = threadIdx.x, w = tid / 32, t = tid % 32;
-    const double* Cyy = C + (long)R * p;
-    float A[RPT][CPT];
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int i = w + RG * k;
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int c = t + 32 * q;
-            float v = 0.f;
-            if (i < p) {
-                if (c < p) v = (float)Cyy[(long)i * p + c];
-                else if (c < W) v = (float)C[(long)(a0 + c - p) * p + i];
-            }
-            A[k][q] = v;
-        }
-    }
-    gain_publish<RPT, CPT, RG, 0>(A, 0, colbuf[0], rowbuf[0], w, t);
-    __syncthreads();
-    if (!gain_steps<RPT, CPT, RG, 0>(A, p, colbuf, rowbuf, w, t)) {
+    if (bad) {
         if (tid == 0) atomicExch(status, DEV_NOTSPD);
         for (int e = tid; e < nr * p; e += NT) Kt[(long)(e / nr) * R + a0 + e % nr] = 0.f;
         return;
@@ -374,6 +368,20 @@ gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, 
             if (i < p && c >= p && c < W) Kt[(long)i * R + a0 + c - p] = A[k][q] / diag[i];
         }
     }
+}
+
+template <int RPT, int CPT, int RG>
+void gain_launch(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
+{
+    constexpr int NCOL = 32 * CPT, NROW = RPT * RG;
+    const size_t smem = sizeof(float) * ((size_t)NROW * NCOL + 3 * NROW + 2 * NCOL);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(gain_kernel<RPT, CPT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    const int RC = NCOL - p, grid = (R + RC - 1) / RC;
+    gain_kernel<RPT, CPT, RG><<<grid > 0 ? grid : 1, 32 * RG, smem, st>>>(C, R, p, K, status);
 }
 
 // ---------------------------------------------------------------- update
@@ -519,15 +527,10 @@ int gain_max_p() { return 144; }
 
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
 {
-    // rows = 8 warps x 9 (p <= 72, 128 columns) or 16 warps x 9 (p <= 144,
+    // rows = 16 warps x 5 (p <= 80, 128 columns) or 16 warps x 9 (p <= 144,
     // 256 columns); the columns beyond p carry right-hand sides
-    if (p <= 72) {
-        const int RC = 128 - p, grid = (R + RC - 1) / RC;
-        gain_kernel<9, 4, 8><<<grid > 0 ? grid : 1, 256, 0, st>>>(C, R, p, K, status);
-    } else {
-        const int RC = 256 - p, grid = (R + RC - 1) / RC;
-        gain_kernel<9, 8, 16><<<grid > 0 ? grid : 1, 512, 0, st>>>(C, R, p, K, status);
-    }
+    if (p <= 80) gain_launch<5, 4, 16>(C, R, p, K, status, st);
+    else gain_launch<9, 8, 16>(C, R, p, K, status, st);
 }
 
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
