@@ -54,29 +54,35 @@ __global__ void u_advance_kernel(float* __restrict__ E, long ms, int m, int l, i
 // accumulation never subtracts two large means (the correction term is of
 // the same size as S2).  Split-K over members; CTAs of the first row tile
 // also write the innovations D^i = Ybar - Y^i (prior values) for the update.
-constexpr int SBM = 64, SBN = 96, SPAD = 4;
+constexpr int SBM = 64, SBN = 72, SPAD = 4;
+constexpr int S_TX = 18, S_TY = 16, S_NT = S_TX * S_TY;   // 4 rows x 4 columns per thread
 
 __device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 
-template <int NT>
-__global__ void __launch_bounds__(NT)
+// Output tile SBM x SBN: thread (ty, tx) owns rows 4 ty .. 4 ty + 3 and the
+// columns tx + S_TX v (v < 4).  Strided columns keep the 16-byte shared reads
+// of B conflict-free (8 consecutive lanes read 8 consecutive rows; the row
+// stride m + 4 places them in distinct 16-byte bank groups).  Tiles are
+// stored k-contiguous ([row][m + 4]); member 0's values (the shift) sit in
+// shared memory next to them.  QA / QB: 16-byte loader chunks per thread.
+template <int QA, int QB>
+__global__ void __launch_bounds__(S_NT)
 stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
              const float* __restrict__ Yx, const float* __restrict__ Yu, int n_yx, float* __restrict__ part1,
              float* __restrict__ part2, float* __restrict__ Dbuf, int splits)
 {
-    // output tile SBM x SBN: thread (ty, tx) owns rows 4 ty .. +3 and CPT
-    // consecutive columns from CPT tx
-    constexpr int TXN = NT / 16, CPT = SBN / TXN;
-    constexpr int QA = 4, QB = 6;                 // loader chunks per thread (m <= 64 / 128 with NT)
+    constexpr int NT = S_NT;
     extern __shared__ __align__(16) float sm[];
     const int R = act.count, p = obs.count, M = R + p;
-    const int ld = m + 4;
+    const int ld = m + SPAD;
     float* As = sm;                               // [SBM][ld]  (k contiguous)
     float* Bs = As + SBM * ld;                    // [SBN][ld]
+    float* A0 = Bs + SBN * ld;                    // member 0, same layout
+    float* B0 = A0 + SBM * ld;
     const int bm0 = blockIdx.x * SBM, bn0 = blockIdx.y * SBN, sidx = blockIdx.z;
     const int i0 = (int)((long)sidx * N / splits), i1 = (int)((long)(sidx + 1) * N / splits);
-    const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
+    const int tid = threadIdx.x, tx = tid % S_TX, ty = tid / S_TX;
     const int m4 = m / 4;
     const bool do_s1 = blockIdx.y == 0, do_d = blockIdx.x == 0;
 
@@ -86,7 +92,7 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
     long aoff[QA], boff[QB];
     int aj[QA], bj[QB], avs[QA], bvs[QB], ar[QA], br[QB];
     long avo[QA], bvo[QB];
-    float4 refa[QA], refb[QB], pa[QA], pb[QB], s1[QA];
+    float4 pa[QA], pb[QB], s1[QA];
     const float4 Z = make_float4(0.f, 0.f, 0.f, 0.f);
     const int pb_rows = p - V.pa;
     auto resolve = [&](int a, long& off, int& vs, long& vo) {
@@ -125,55 +131,60 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
         else if (vs == 2) x = f4add(x, *reinterpret_cast<const float4*>(V.Vb + (long)i * pb_rows * m + vo + j));
         return x;
     };
+    // member 0 (the shift) into shared memory
 #pragma unroll
-    for (int q = 0; q < QA; ++q) refa[q] = aoff[q] >= 0 ? value(0, aoff[q], avs[q], avo[q], aj[q]) : Z;
+    for (int q = 0; q < QA; ++q)
+        if (ar[q] >= 0) *reinterpret_cast<float4*>(A0 + ar[q] * ld + aj[q]) = aoff[q] >= 0 ? value(0, aoff[q], avs[q], avo[q], aj[q]) : Z;
 #pragma unroll
-    for (int q = 0; q < QB; ++q) refb[q] = boff[q] >= 0 ? value(0, boff[q], bvs[q], bvo[q], bj[q]) : Z;
+    for (int q = 0; q < QB; ++q)
+        if (br[q] >= 0) *reinterpret_cast<float4*>(B0 + br[q] * ld + bj[q]) = boff[q] >= 0 ? value(0, boff[q], bvs[q], bvo[q], bj[q]) : Z;
     auto fetch = [&](int i) {
 #pragma unroll
-        for (int q = 0; q < QA; ++q) pa[q] = aoff[q] >= 0 ? f4sub(value(i, aoff[q], avs[q], avo[q], aj[q]), refa[q]) : Z;
+        for (int q = 0; q < QA; ++q) pa[q] = aoff[q] >= 0 ? value(i, aoff[q], avs[q], avo[q], aj[q]) : Z;
 #pragma unroll
-        for (int q = 0; q < QB; ++q) pb[q] = boff[q] >= 0 ? f4sub(value(i, boff[q], bvs[q], bvo[q], bj[q]), refb[q]) : Z;
+        for (int q = 0; q < QB; ++q) pb[q] = boff[q] >= 0 ? value(i, boff[q], bvs[q], bvo[q], bj[q]) : Z;
     };
-    float acc[4][CPT];
+    float acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < CPT; ++v) acc[u][v] = 0.f;
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
 
     if (i0 < i1) fetch(i0);
     for (int i = i0; i < i1; ++i) {
+        // shift by member 0 (each thread reads back only what it wrote)
 #pragma unroll
         for (int q = 0; q < QA; ++q)
             if (ar[q] >= 0) {
-                *reinterpret_cast<float4*>(As + ar[q] * ld + aj[q]) = pa[q];
-                s1[q] = f4add(s1[q], pa[q]);
+                const float4 d = f4sub(pa[q], *reinterpret_cast<const float4*>(A0 + ar[q] * ld + aj[q]));
+                *reinterpret_cast<float4*>(As + ar[q] * ld + aj[q]) = d;
+                s1[q] = f4add(s1[q], d);
             }
 #pragma unroll
         for (int q = 0; q < QB; ++q)
             if (br[q] >= 0) {
-                *reinterpret_cast<float4*>(Bs + br[q] * ld + bj[q]) = pb[q];
+                const float4 d = f4sub(pb[q], *reinterpret_cast<const float4*>(B0 + br[q] * ld + bj[q]));
+                *reinterpret_cast<float4*>(Bs + br[q] * ld + bj[q]) = d;
                 const int c = bn0 + br[q];
                 if (do_d && c < p) {
                     const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
-                    const float4 y = f4add(pb[q], refb[q]);
                     *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + bj[q]) =
-                        f4sub(*reinterpret_cast<const float4*>(yb + bj[q]), y);
+                        f4sub(*reinterpret_cast<const float4*>(yb + bj[q]), pb[q]);
                 }
             }
         __syncthreads();
         if (i + 1 < i1) fetch(i + 1);            // next member's loads overlap the products
 #pragma unroll 2
         for (int k = 0; k < m; k += 4) {
-            float4 av[4], bv[CPT];
+            float4 av[4], bv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) av[u] = *reinterpret_cast<const float4*>(As + (4 * ty + u) * ld + k);
 #pragma unroll
-            for (int v = 0; v < CPT; ++v) bv[v] = *reinterpret_cast<const float4*>(Bs + (CPT * tx + v) * ld + k);
+            for (int v = 0; v < 4; ++v) bv[v] = *reinterpret_cast<const float4*>(Bs + (tx + S_TX * v) * ld + k);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < CPT; ++v) {
+                for (int v = 0; v < 4; ++v) {
                     acc[u][v] = fmaf(av[u].x, bv[v].x, acc[u][v]);
                     acc[u][v] = fmaf(av[u].y, bv[v].y, acc[u][v]);
                     acc[u][v] = fmaf(av[u].z, bv[v].z, acc[u][v]);
@@ -187,8 +198,8 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
         const int a = bm0 + 4 * ty + u;
         if (a >= M) continue;
 #pragma unroll
-        for (int v = 0; v < CPT; ++v) {
-            const int c = bn0 + CPT * tx + v;
+        for (int v = 0; v < 4; ++v) {
+            const int c = bn0 + tx + S_TX * v;
             if (c < p) part2[((long)sidx * M + a) * p + c] = acc[u][v];
         }
     }
@@ -495,19 +506,27 @@ int stats_splits(int R, int p, int N)
     return s;
 }
 
-size_t stats_smem_bytes(int m) { return sizeof(float) * (size_t)(SBM + SBN) * (m + 4); }
+size_t stats_smem_bytes(int m) { return sizeof(float) * 2 * (size_t)(SBM + SBN) * (m + SPAD); }
 
 void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
                   const float* Yu, int n_yx, float* part1, float* part2, float* Dbuf, int splits, cudaStream_t st)
 {
     const int M = act.count + obs.count, p = obs.count;
     dim3 grid((M + SBM - 1) / SBM, (p + SBN - 1) / SBN, splits);
+    const size_t smem = stats_smem_bytes(m);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(stats_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(stats_kernel<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    // loader chunks: SBM m / 4 and SBN m / 4 pieces over S_NT threads
     if (m <= 64)
-        stats_kernel<256><<<grid, 256, stats_smem_bytes(m), st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1,
-                                                                  part2, Dbuf, splits);
+        stats_kernel<4, 4><<<grid, S_NT, smem, st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1, part2, Dbuf,
+                                                     splits);
     else
-        stats_kernel<512><<<grid, 512, stats_smem_bytes(m), st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1,
-                                                                  part2, Dbuf, splits);
+        stats_kernel<8, 8><<<grid, S_NT, smem, st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1, part2, Dbuf,
+                                                     splits);
 }
 
 void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st)
