@@ -182,6 +182,7 @@ typedef enum {
     OIC_STAGE_UPDATE,          /* member-wise update                            */
     OIC_STAGE_BLOCK_MEANS,     /* smoothed output means                         */
     OIC_STAGE_CNN_FUSED,       /* whole CNN step in one kernel (all layers)     */
+    OIC_STAGE_CNN_BF16,        /* CNN step in BF16, one kernel per layer        */
     OIC_NUM_STAGES
 } oic_stage;
 oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launches);

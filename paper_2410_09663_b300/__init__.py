@@ -21,7 +21,7 @@ OIC_OK, OIC_EINVAL, OIC_ENOMEM, OIC_ECUDA, OIC_ENOTSPD, OIC_ETIMEOUT, OIC_ESTATE
 OIC_PREC_FP32, OIC_PREC_MIXED = 0, 1
 OIC_NOISE_HOST, OIC_NOISE_PHILOX = 0, 1
 STAGES = ["noise", "init", "cnn_input", "conv_first", "conv_hidden", "conv_out", "u_advance",
-          "means", "cov", "cov_reduce", "gain", "update", "block_means", "cnn_fused"]
+          "means", "cov", "cov_reduce", "gain", "update", "block_means", "cnn_fused", "cnn_bf16"]
 
 
 class OICError(RuntimeError):

@@ -1,0 +1,482 @@
+// conv_bf16_tc.cu -- the CNN of Eq. (1) in the mixed-precision mode: every 3x3
+// "same" convolution runs on the tcgen05 tensor cores with BF16 operands and
+// FP32 accumulation in tensor memory; bias + tanh are applied in FP32 and the
+// activations stored as BF16; the residual X_{t+1} = X_t + s out stays FP32.
+//
+// Activation rows in global memory are already in the tensor core's operand
+// layout: a row of one member group is [C/8 planes][NPOS positions][8
+// channels] BF16, where position G + G x + b holds pixel x of member b of the
+// group (G = 128/m members interleaved, zero pads of G positions at both
+// ends).  One 1-D bulk copy moves a whole row into shared memory, and a
+// horizontal stencil tap is a shift of the operand start by G positions.
+//
+// One kernel per layer: conv_bf16_kernel<CI, CO, MODE, G>.
+//   MODE_HIDDEN  CO channels, tanh, BF16 rows out
+//   MODE_LAST    CO = 16 columns of which channel 0 is the output; X_next =
+//                X + s (out + b) in FP32
+// Like the FP32 kernel, the three VERTICAL taps are stacked along N: each
+// input row j is read once per (horizontal tap, 16-channel step) and feeds
+// output rows j+1, j, j-1 (N = 3 CO) into a ring of 4 TMEM slots of CO
+// columns.  Roles: one thread loads input rows (bulk copies), one thread
+// issues the MMAs, NDW warps drain finished output rows.
+#include <cuda_bf16.h>
+
+#include "oic_internal.cuh"
+#include "tc_sm103.cuh"
+
+namespace oic {
+namespace {
+
+constexpr int BM = 128;                                 // tile rows (positions)
+constexpr int NIN = 4;                                  // input row slots
+constexpr long long B_WAIT = 4000000000LL;
+enum { MODE_HIDDEN = 0, MODE_LAST = 1 };
+
+template <int CI, int CO, int MODE, int G>
+struct BS {
+    static constexpr int NPOS = BM + 2 * G;
+    static constexpr int PLANE = NPOS * 16;             // one 8-channel plane of a row
+    static constexpr int INROW = (CI / 8) * PLANE;      // one input row
+    static constexpr int KS = CI / 16;
+    static constexpr int NB = 3 * CO;                   // B rows: vertical taps stacked
+    static constexpr int BTILE = 2 * NB * 16;           // one (dx, ks) tile, 2 K chunks
+    static constexpr int BBYTES = 3 * KS * BTILE;
+    static constexpr int NDW = MODE == MODE_LAST ? 4 : 16;   // drain warps
+    static constexpr int LOAD_WARP = NDW, ISSUE_WARP = NDW + 1;
+    static constexpr int NT = 32 * (NDW + 2);
+    static constexpr int OFF_IN = 0;
+    static constexpr int OFF_B = OFF_IN + NIN * INROW;
+    static constexpr int OFF_BIAS = OFF_B + BBYTES;
+    static constexpr int OFF_MISC = OFF_BIAS + (CO * 4 + 15) / 16 * 16;
+    static constexpr int SMEM = OFF_MISC + 256;
+    static constexpr int TMEM_COLS = 4 * CO <= 32 ? 32 : 4 * CO <= 64 ? 64 : 4 * CO <= 128 ? 128 : 256;
+    static_assert(CI % 16 == 0 && (CO == 16 || CO == 32 || CO == 64), "shapes");
+    static_assert(MODE != MODE_LAST || CO == 16, "last layer: 16 columns, channel 0 used");
+};
+
+// mbarriers (8 bytes each)
+enum : int {
+    BB_FULL = 0,       // [NIN] input row landed (bulk copy)
+    BB_FREE = 4,       // [NIN] MMAs of the input row in the slot done
+    BB_HDONE = 8,      // [2]   MMAs of input row j done (parity of j)
+    BB_PASS = 10,      // [4]   drain pass k done (k mod 4)
+    BB_FIN = 14,
+    BB_COUNT = 15
+};
+
+constexpr uint32_t DESC_HI = (128u >> 4) | (1u << 14);
+__host__ __device__ constexpr uint32_t desc_lo(uint32_t saddr, uint32_t lbo)
+{
+    return ((saddr & 0x3FFFFu) >> 4) | (((lbo >> 4) & 0x3FFFu) << 16);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .b64 da, db;\n\t.reg .pred p;\n\t"
+        "mov.b64 da, {%1, %5};\n\t"
+        "mov.b64 db, {%2, %5};\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_lo), "r"(b_lo), "r"(idesc), "r"(acc), "r"(DESC_HI)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on `mbar` (both
+// addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <int N>
+__device__ __forceinline__ void tmem_ldn(uint32_t taddr, float (&v)[N])
+{
+    static_assert(N == 8 || N == 16, "width");
+    if constexpr (N == 16) {
+        tc::tmem_ld16(taddr, v);
+    } else {
+        uint32_t r[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(taddr)
+                     : "memory");
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+    }
+}
+
+// MMA over vertical-tap blocks [B0, B1) of one B tile into TMEM from column COL.
+template <int CO, int B0, int B1, int COL>
+__device__ __forceinline__ void piece(uint32_t tmem, uint32_t a, uint32_t b, uint32_t acc)
+{
+    constexpr uint32_t id = tc::idesc_f16(BM, CO * (B1 - B0), true);
+    mma_bf16(tmem + COL, a, b + (CO * B0 * 16) / 16, id, acc);
+}
+
+// All MMAs of input row j (ring position SR = (-j-1) mod 4: blocks b = 0, 1,
+// 2 = output rows j+1, j, j-1 in slots SR, SR+1, SR+2 mod 4).  The first MMA
+// starts output row j+1 (accumulate 0 on its block); INIT_ALL starts all.
+template <int CI, int CO, int MODE, int G, int SR, bool INIT_ALL>
+__device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t b)
+{
+    using S = BS<CI, CO, MODE, G>;
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+        for (int ks = 0; ks < S::KS; ++ks) {
+            const uint32_t aa = a + (2 * ks * S::PLANE) / 16 + dx * G;
+            const uint32_t bb = b + ((dx * S::KS + ks) * S::BTILE) / 16;
+            const bool first = dx == 0 && ks == 0;
+            if (first && !INIT_ALL) {
+                piece<CO, 0, 1, CO * SR>(tmem, aa, bb, 0u);
+                if constexpr (SR == 2) {
+                    piece<CO, 1, 2, CO * 3>(tmem, aa, bb, 1u);
+                    piece<CO, 2, 3, 0>(tmem, aa, bb, 1u);
+                } else if constexpr (SR == 3) {
+                    piece<CO, 1, 3, 0>(tmem, aa, bb, 1u);
+                } else {
+                    piece<CO, 1, 3, CO * (SR + 1)>(tmem, aa, bb, 1u);
+                }
+            } else {
+                const uint32_t acc = first ? 0u : 1u;
+                if constexpr (SR <= 1) {
+                    piece<CO, 0, 3, CO * SR>(tmem, aa, bb, acc);
+                } else if constexpr (SR == 2) {
+                    piece<CO, 0, 2, CO * 2>(tmem, aa, bb, acc);
+                    piece<CO, 2, 3, 0>(tmem, aa, bb, acc);
+                } else {
+                    piece<CO, 0, 1, CO * 3>(tmem, aa, bb, acc);
+                    piece<CO, 1, 3, 0>(tmem, aa, bb, acc);
+                }
+            }
+        }
+    }
+}
+
+template <int CI, int CO, int MODE, int G>
+__device__ __forceinline__ void issue_row(uint32_t tmem, int j, bool init_all, uint32_t a, uint32_t b)
+{
+    const int s = (-j - 1) & 3;
+    if (init_all) {
+        switch (s) {
+        case 0: issue_row_s<CI, CO, MODE, G, 0, true>(tmem, a, b); break;
+        case 1: issue_row_s<CI, CO, MODE, G, 1, true>(tmem, a, b); break;
+        case 2: issue_row_s<CI, CO, MODE, G, 2, true>(tmem, a, b); break;
+        default: issue_row_s<CI, CO, MODE, G, 3, true>(tmem, a, b); break;
+        }
+    } else {
+        switch (s) {
+        case 0: issue_row_s<CI, CO, MODE, G, 0, false>(tmem, a, b); break;
+        case 1: issue_row_s<CI, CO, MODE, G, 1, false>(tmem, a, b); break;
+        case 2: issue_row_s<CI, CO, MODE, G, 2, false>(tmem, a, b); break;
+        default: issue_row_s<CI, CO, MODE, G, 3, false>(tmem, a, b); break;
+        }
+    }
+}
+
+// in: activation rows [groups][n][CI/8][NPOS][8] BF16.  MODE_HIDDEN: out the
+// same layout with CO channels.  MODE_LAST: X_next[member][row][x] = X +
+// rs (out + bias) for member < Nb.
+template <int CI, int CO, int MODE, int G>
+__global__ void __launch_bounds__(BS<CI, CO, MODE, G>::NT, 1)
+conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out, const float* __restrict__ X,
+                 long x_ms, float* __restrict__ Xout, long o_ms, const __nv_bfloat16* __restrict__ wpk,
+                 const float* __restrict__ bias, int Nb, int n, float rs, int* __restrict__ err)
+{
+    using S = BS<CI, CO, MODE, G>;
+    constexpr int m = BM / G;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + BB_COUNT * 8);
+    float* sbias = reinterpret_cast<float*>(smem + S::OFF_BIAS);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const uint32_t s0 = tc::smem_u32(smem);
+
+    for (int e = tid; e < S::BBYTES / 16; e += S::NT)
+        reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk)[e];
+    for (int e = tid; e < CO; e += S::NT) sbias[e] = bias[e];
+    if (tid == 0) {
+        for (int i = 0; i < BB_COUNT; ++i) tc::mbar_init(mb + i, (i >= BB_PASS && i < BB_PASS + 4) ? S::NDW : 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_holder, S::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+
+    const int groups = (Nb + G - 1) / G;
+    const long total = (long)groups * n;
+    const long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+    uint32_t ph = 0;
+    bool failed = false;
+    auto wait = [&](int i) {
+        if (!tc::mbar_wait_bounded(mb + i, (ph >> i) & 1u, B_WAIT)) {
+            failed = true;
+            atomicExch(err, DEV_TIMEOUT);
+        }
+        ph ^= 1u << i;
+        tc::fence_after_sync();
+    };
+    auto wait_w = [&](int i) {
+        wait(i);
+        failed = __any_sync(0xffffffffu, failed);
+    };
+    const int q4 = warp & 3, cg = warp >> 2;            // drain: lane quarter, channel group
+    const int ep = 32 * q4 + lane;
+    const uint32_t tlane = (uint32_t)(32 * q4) << 16;
+
+    for (long t = t0; t < t1;) {
+        const int g = (int)(t / n);
+        const int ys = (int)(t % n);
+        const long rem = t1 - t;
+        const int ye = (long)(n - ys) < rem ? n : (int)(ys + rem);
+        t += ye - ys;
+        // output rows ys .. ye-1 need input rows f_lo .. f_hi (zero outside the image)
+        const int f_lo = ys > 0 ? ys - 1 : 0;
+        const int f_hi = ye < n ? ye : n - 1;
+        auto Fv = [&](int f) { return f >= f_lo && f <= f_hi; };
+        auto Ov = [&](int h) { return h >= ys && h < ye; };
+        const __nv_bfloat16* in_g = in + (size_t)g * n * (S::INROW / 2);
+
+        if (warp == S::LOAD_WARP) {
+            // ============ loads: input row j into slot j % NIN ============
+            if (lane == 0) {
+                for (int j = f_lo; j <= f_hi && !failed; ++j) {
+                    const int sl = j % NIN;
+                    if (j - NIN >= f_lo) wait(BB_FREE + sl);       // MMAs of row j - NIN done
+                    mbar_expect_tx(mb + BB_FULL + sl, S::INROW);
+                    bulk_g2s(smem + S::OFF_IN + sl * S::INROW, in_g + (size_t)j * (S::INROW / 2), S::INROW,
+                             mb + BB_FULL + sl);
+                }
+                // the last slots' MMAs, before the next segment reuses them
+                for (int j = f_hi - NIN + 1; j <= f_hi && !failed; ++j)
+                    if (j >= f_lo) wait(BB_FREE + j % NIN);
+            }
+            __syncwarp();
+        } else if (warp == S::ISSUE_WARP) {
+            // ============ MMAs: input row j ============
+            if (lane == 0) {
+                const uint32_t dIn = desc_lo(s0 + S::OFF_IN, S::PLANE);
+                const uint32_t dB = desc_lo(s0 + S::OFF_B, S::NB * 16);
+                for (int j = f_lo; j <= f_hi && !failed; ++j) {
+                    // output row j+1 takes the ring slot of row j-3, drained in pass j-2
+                    if (j - 2 >= f_lo) wait(BB_PASS + ((j - 2) & 3));
+                    wait(BB_FULL + j % NIN);
+                    issue_row<CI, CO, MODE, G>(tmem, j, j == f_lo, dIn + (j % NIN) * (S::INROW / 16), dB);
+                    tc::mma_commit(mb + BB_FREE + j % NIN);
+                    tc::mma_commit(mb + BB_HDONE + (j & 1));
+                }
+                // the remaining drain passes
+                for (int k = f_hi - 1; k <= f_hi + 1 && !failed; ++k)
+                    if (k >= f_lo && k <= (ye < n ? ye : n)) wait(BB_PASS + (k & 3));
+            }
+            __syncwarp();
+        } else {
+            // ============ drain: pass k finishes output row k-1 ============
+            const int last_pass = ye < n ? ye : n;              // = f_hi + 1 at the image bottom
+            for (int k = f_lo; k <= last_pass && !failed; ++k) {
+                if (Fv(k)) wait_w(BB_HDONE + (k & 1));
+                const int h = k - 1;
+                if (Ov(h)) {
+                    const uint32_t col = (uint32_t)(CO * ((-h) & 3));
+                    if constexpr (MODE == MODE_HIDDEN) {
+                        constexpr int CPW = CO / 4;             // channels per warp
+                        float v[CPW];
+                        tmem_ldn<CPW>(tmem + tlane + col + cg * CPW, v);
+                        tc::tmem_ld_wait();
+                        uint32_t pk[CPW / 2];
+#pragma unroll
+                        for (int i = 0; i < CPW / 2; ++i) {
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(
+                                tanh_approx(v[2 * i] + sbias[cg * CPW + 2 * i]),
+                                tanh_approx(v[2 * i + 1] + sbias[cg * CPW + 2 * i + 1]));
+                            pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+                        }
+                        __nv_bfloat16* orow = out + ((size_t)g * n + h) * (CO / 8) * S::NPOS * 8;
+#pragma unroll
+                        for (int pl = 0; pl < CPW / 8; ++pl)
+                            *reinterpret_cast<uint4*>(orow + ((size_t)(cg * CPW / 8 + pl) * S::NPOS + G + ep) * 8) =
+                                make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
+                    } else {
+                        float v[8];
+                        tmem_ldn<8>(tmem + tlane + col, v);
+                        tc::tmem_ld_wait();
+                        const int b = ep % G, x = ep / G, mbr = g * G + b;
+                        if (mbr < Nb)
+                            Xout[(long)mbr * o_ms + (long)h * m + x] =
+                                fmaf(rs, v[0] + sbias[0], X[(long)mbr * x_ms + (long)h * m + x]);
+                    }
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & 3));
+            }
+        }
+        tc::fence_before_sync();
+        if (__syncthreads_or(failed)) { failed = true; break; }
+        tc::fence_after_sync();
+    }
+    if (warp == S::ISSUE_WARP && lane == 0) {
+        tc::mma_commit(mb + BB_FIN);
+        if (!tc::mbar_wait_bounded(mb + BB_FIN, 0u, B_WAIT)) atomicExch(err, DEV_TIMEOUT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
+// [X, B U] of every member row into the first layer's input rows (CI = 16:
+// plane 0 = [X, BU, 0 ...], plane 1 stays zero; pads stay zero).
+template <int G>
+__global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
+                                  const float* __restrict__ Bmat, int Nb, int n, int l,
+                                  __nv_bfloat16* __restrict__ act)
+{
+    constexpr int m = BM / G, NPOS = BM + 2 * G;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int groups = (Nb + G - 1) / G;
+    if (e >= (long)groups * n * BM) return;
+    const int p = (int)(e % BM);
+    const long gr = e / BM;
+    const int r = (int)(gr % n), g = (int)(gr / n);
+    const int b = p % G, x = p / G, mbr = g * G + b;
+    float xv = 0.f, bu = 0.f;
+    if (mbr < Nb) {
+        xv = X[(long)mbr * x_ms + (long)r * m + x];
+        for (int c = 0; c < l; ++c) bu = fmaf(Bmat[r * l + c], U[(long)mbr * u_ms + (long)c * m + x], bu);
+    }
+    const __nv_bfloat162 v = __floats2bfloat162_rn(xv, bu);
+    __nv_bfloat16* row = act + ((size_t)g * n + r) * 2 * NPOS * 8;
+    *reinterpret_cast<uint4*>(row + (size_t)(G + p) * 8) =
+        make_uint4(*reinterpret_cast<const uint32_t*>(&v), 0u, 0u, 0u);
+}
+
+template <int CI, int CO, int MODE, int G>
+int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const float* X, long x_ms, float* Xout, long o_ms,
+               const void* wpk, const float* bias, int Nb, int n, float rs, int n_sm, int* err, cudaStream_t st)
+{
+    using S = BS<CI, CO, MODE, G>;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(conv_bf16_kernel<CI, CO, MODE, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 S::SMEM) != cudaSuccess)
+            return 1;
+        configured = true;
+    }
+    const long tiles = (long)((Nb + G - 1) / G) * n;
+    const int grid = (int)(tiles < n_sm ? tiles : n_sm);
+    conv_bf16_kernel<CI, CO, MODE, G><<<grid, S::NT, S::SMEM, st>>>(
+        in, out, X, x_ms, Xout, o_ms, static_cast<const __nv_bfloat16*>(wpk), bias, Nb, n, rs, err);
+    return 0;
+}
+
+template <int G>
+int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
+                   const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st)
+{
+    const int groups = (Nb + G - 1) / G;
+    const long total = (long)groups * n * BM;
+    bf16_input_kernel<G><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(X, x_ms, U, u_ms, Bmat, Nb, n, l,
+                                                                         static_cast<__nv_bfloat16*>(net.act_in));
+    const int C = net.C;
+    const __nv_bfloat16* cur = static_cast<const __nv_bfloat16*>(net.act_in);
+    __nv_bfloat16* bufs[2] = {static_cast<__nv_bfloat16*>(net.act[0]), static_cast<__nv_bfloat16*>(net.act[1])};
+    int rc = 0;
+    // first layer (input channels padded to 16)
+    if (C == 64)
+        rc |= bf16_layer<16, 64, MODE_HIDDEN, G>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
+                                                 n_sm, err, st);
+    else
+        rc |= bf16_layer<16, 32, MODE_HIDDEN, G>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
+                                                 n_sm, err, st);
+    cur = bufs[0];
+    for (int k = 1; k + 1 < net.n_layers; ++k) {
+        __nv_bfloat16* o = bufs[k & 1];
+        if (C == 64)
+            rc |= bf16_layer<64, 64, MODE_HIDDEN, G>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
+                                                     n_sm, err, st);
+        else
+            rc |= bf16_layer<32, 32, MODE_HIDDEN, G>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
+                                                     n_sm, err, st);
+        cur = o;
+    }
+    const int L = net.n_layers - 1;
+    if (C == 64)
+        rc |= bf16_layer<64, 16, MODE_LAST, G>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
+                                               n_sm, err, st);
+    else
+        rc |= bf16_layer<32, 16, MODE_LAST, G>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
+                                               n_sm, err, st);
+    return rc;
+}
+
+}  // namespace
+
+bool bf16_supported(int n_layers, const int* channels, int m)
+{
+    if (n_layers < 3 || channels[0] != 2 || channels[n_layers] != 1) return false;
+    const int C = channels[1];
+    if (C != 32 && C != 64) return false;
+    for (int k = 1; k < n_layers; ++k)
+        if (channels[k] != C) return false;
+    return m == 16 || m == 32 || m == 64 || m == 128;
+}
+
+size_t bf16_act_bytes(int N, int n, int m, int C)
+{
+    const int G = BM / m, groups = (N + G - 1) / G;
+    return (size_t)groups * n * (C / 8) * (BM + 2 * G) * 16;
+}
+
+// Packed B tiles of one layer: [dx][ks] tiles of 2 K chunks x 3 CO rows; row
+// b CO + co, K index e = ci - 16 ks: w[co][ci][dy = b][dx] as BF16 (zero for
+// co >= cout or ci >= cin).  CI, CO: padded sizes.
+size_t bf16_layer_bytes(int CI, int CO) { return (size_t)3 * (CI / 16) * 2 * 3 * CO * 16; }
+
+void bf16_pack_layer(const float* w, int cin, int cout, int CI, int CO, void* dst_host)
+{
+    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(dst_host);
+    const int KS = CI / 16, NB = 3 * CO;
+    for (int dx = 0; dx < 3; ++dx)
+        for (int ks = 0; ks < KS; ++ks)
+            for (int kc = 0; kc < 2; ++kc)
+                for (int row = 0; row < NB; ++row)
+                    for (int e = 0; e < 8; ++e) {
+                        const int dy = row / CO, co = row % CO, ci = ks * 16 + kc * 8 + e;
+                        const float v = (co < cout && ci < cin) ? w[((co * cin + ci) * 3 + dy) * 3 + dx] : 0.f;
+                        out[((((size_t)(dx * KS + ks) * 2 + kc) * NB) + row) * 8 + e] = __float2bfloat16_rn(v);
+                    }
+}
+
+int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout,
+                        long o_ms, const float* Bmat, int Nb, int n, int m, int l, float rs, int n_sm, int* err,
+                        cudaStream_t st)
+{
+    switch (m) {
+    case 128: return bf16_forward_g<1>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 64: return bf16_forward_g<2>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 32: return bf16_forward_g<4>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 16: return bf16_forward_g<8>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    }
+    return 1;
+}
+
+}  // namespace oic

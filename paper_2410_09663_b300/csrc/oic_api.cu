@@ -28,7 +28,8 @@ struct Profiler {
 };
 
 struct Layout {
-    size_t w, b, B, wtc, wfused, E, act0, act1, part1, part2, S1, D, C, K, rowtab, status, selftest;
+    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, rowtab, status,
+        selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -47,7 +48,8 @@ struct oic_handle {
     char* ws = nullptr;
     size_t ws_bytes = 0;
     cudaStream_t st = nullptr;
-    bool bound = false, plant_ready = false, fused = false;
+    bool bound = false, plant_ready = false, fused = false, bf16 = false;
+    std::vector<size_t> w16_off, b16_off;   // mixed-precision CNN: packed layer tiles, padded biases
     unsigned long long solve_counter = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int> obs_host;
@@ -135,9 +137,31 @@ void compute_layout(oic_handle* h)
         L.wtc = take(tc_bytes);
         L.wfused = take(h->fused ? cnn_fused_packed_bytes() : 0);
     }
+    {
+        // mixed-precision CNN: per layer packed BF16 tiles and biases padded to CO
+        size_t wb = 0, bb = 0;
+        h->w16_off.assign(h->L, 0);
+        h->b16_off.assign(h->L, 0);
+        if (h->bf16) {
+            const int C = c.channels[1];
+            for (int k = 0; k < h->L; ++k) {
+                const int CI = k == 0 ? 16 : C, CO = k + 1 == h->L ? 16 : C;
+                h->w16_off[k] = wb;
+                wb += align_up(bf16_layer_bytes(CI, CO), 256);
+                h->b16_off[k] = bb;
+                bb += align_up(sizeof(float) * CO, 256);
+            }
+        }
+        L.w16 = take(wb);
+        L.b16 = take(bb);
+        L.act16_in = take(h->bf16 ? bf16_act_bytes(c.N, c.n, c.m, 16) : 0);
+    }
     L.E = take(sizeof(float) * N * h->R_mem * m);
-    L.act0 = take(sizeof(float) * N * h->Cmax * n * m);
-    L.act1 = take(sizeof(float) * N * h->Cmax * n * m);
+    // per-layer activations: FP32 [N][C][n][m], or BF16 operand rows in the
+    // mixed-precision mode (smaller)
+    const size_t act_bytes = h->bf16 ? bf16_act_bytes(c.N, c.n, c.m, c.channels[1]) : sizeof(float) * N * h->Cmax * n * m;
+    L.act0 = take(act_bytes);
+    L.act1 = take(act_bytes);
     L.part1 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * m);
     L.part2 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * p);
     L.S1 = take(sizeof(float) * (Ra + p) * m);
@@ -174,6 +198,23 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
                  float* Xout, long o_ms)
 {
     const oic_config& c = h->cfg;
+    if (h->bf16) {
+        Bf16Net net;
+        net.n_layers = h->L;
+        net.C = c.channels[1];
+        for (int k = 0; k < h->L; ++k) {
+            net.w[k] = h->at<char>(h->lay.w16) + h->w16_off[k];
+            net.b[k] = reinterpret_cast<const float*>(h->at<char>(h->lay.b16) + h->b16_off[k]);
+        }
+        net.act_in = h->at<char>(h->lay.act16_in);
+        net.act[0] = h->at<char>(h->lay.act0);
+        net.act[1] = h->at<char>(h->lay.act1);
+        run_stage(h, OIC_STAGE_CNN_BF16, [&] {
+            launch_bf16_forward(net, X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l,
+                                c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st);
+        });
+        return;
+    }
     if (h->fused) {
         const float* b = h->at<float>(h->lay.b);
         const int C = c.channels[1];
@@ -362,7 +403,8 @@ oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* c
     h->R_act_max = h->R_of(c.H);
     h->splits_max = stats_splits(1, h->p, c.N);
     h->noise_n = noise_count(&c);
-    h->fused = cnn_fused_supported(c.n_layers, c.channels, c.n, c.m, c.l) &&
+    h->bf16 = c.precision == OIC_PREC_MIXED && bf16_supported(c.n_layers, c.channels, c.m);
+    h->fused = !h->bf16 && cnn_fused_supported(c.n_layers, c.channels, c.n, c.m, c.l) &&
                getenv("OIC_NO_FUSED_CNN") == nullptr;
     compute_layout(h);
     *out = h;
@@ -412,6 +454,31 @@ oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda
             std::vector<unsigned char> pk(cnn_fused_packed_bytes());
             cnn_fused_pack_weights(w1, w2, w3, pk.data());
             OIC_CUDA_OK(cudaMemcpy(h->at<char>(h->lay.wfused), pk.data(), pk.size(), cudaMemcpyHostToDevice));
+        }
+        if (h->bf16) {
+            const int C = c.channels[1];
+            const float* wl2 = h->w.data();
+            const float* bl = h->b.data();
+            for (int k = 0; k < h->L; ++k) {
+                const int cin = c.channels[k], cout = c.channels[k + 1];
+                const int CI = k == 0 ? 16 : C, CO = k + 1 == h->L ? 16 : C;
+                std::vector<unsigned char> pk(bf16_layer_bytes(CI, CO));
+                bf16_pack_layer(wl2, cin, cout, CI, CO, pk.data());
+                OIC_CUDA_OK(cudaMemcpy(h->at<char>(h->lay.w16) + h->w16_off[k], pk.data(), pk.size(),
+                                       cudaMemcpyHostToDevice));
+                std::vector<float> bp(CO, 0.f);
+                for (int o = 0; o < cout; ++o) bp[o] = bl[o];
+                OIC_CUDA_OK(cudaMemcpy(h->at<char>(h->lay.b16) + h->b16_off[k], bp.data(), sizeof(float) * CO,
+                                       cudaMemcpyHostToDevice));
+                wl2 += (size_t)cin * cout * 9;
+                bl += cout;
+            }
+            // operand rows: the pad positions (and the first layer's zero
+            // channels) are never written, so they must start at zero
+            OIC_CUDA_OK(cudaMemsetAsync(h->at<char>(h->lay.act16_in), 0,
+                                        bf16_act_bytes(c.N, c.n, c.m, 16), h->st));
+            OIC_CUDA_OK(cudaMemsetAsync(h->at<char>(h->lay.act0), 0, bf16_act_bytes(c.N, c.n, c.m, C), h->st));
+            OIC_CUDA_OK(cudaMemsetAsync(h->at<char>(h->lay.act1), 0, bf16_act_bytes(c.N, c.n, c.m, C), h->st));
         }
     }
     // row tables

@@ -95,6 +95,26 @@ void cnn_fused_pack_weights(const float* w1, const float* w2, const float* w3, v
 int launch_cnn_fused(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                      const float* Bmat, int Nb, int n, int m, int l, const float* b1, const float* b2,
                      const float* b3, const void* wpk, float rs, int n_sm, int* err, cudaStream_t st);
+// Mixed-precision CNN (BF16 operands, FP32 accumulation, FP32 residual):
+// one tcgen05 kernel per layer, activations as BF16 rows in the tensor
+// core's operand layout.  w[k]: packed tiles of layer k (bf16_pack_layer
+// with CI = 16 for k = 0, CO = 16 for the last layer); b[k]: biases padded
+// to CO; act_in: first-layer input rows; act[2]: ping-pong activation rows
+// (all three zero-initialised: the pad positions are never written).
+struct Bf16Net {
+    int n_layers = 0, C = 0;
+    const void* w[9] = {};
+    const float* b[9] = {};
+    void* act_in = nullptr;
+    void* act[2] = {nullptr, nullptr};
+};
+bool bf16_supported(int n_layers, const int* channels, int m);
+size_t bf16_act_bytes(int N, int n, int m, int C);
+size_t bf16_layer_bytes(int CI, int CO);
+void bf16_pack_layer(const float* w, int cin, int cout, int CI, int CO, void* dst_host);
+int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout,
+                        long o_ms, const float* Bmat, int Nb, int n, int m, int l, float rs, int n_sm, int* err,
+                        cudaStream_t st);
 // Known-answer check of the tcgen05 path: res[0] = mismatches (-1 timeout).
 void launch_tc_selftest(int* res, cudaStream_t st);
 

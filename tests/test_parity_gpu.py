@@ -246,3 +246,35 @@ def test_cnn_per_layer_tensor_path_matches_oracle(cuda_ok, name, monkeypatch):
     s.oic_sync()
     want = oracle.cnn_step(onet(wl), X, U)
     assert np.abs(out.cpu().numpy() - want).max() <= 1e-5 * np.abs(want).max()
+
+
+MIXED_CASES = {
+    "m16_c32": W.Workload("mixed_16x16_c32", n=16, m=16, l=4, channels=[2, 32, 32, 1], N=40, H=2, S=2, ref="zero"),
+    "m32_c64": W.Workload("mixed_32x32_c64", n=32, m=32, l=4, channels=[2, 64, 64, 64, 1], N=12, H=2, S=2,
+                          ref="zero"),
+    "m64_c64": W.Workload("mixed_64x64_c64", n=64, m=64, l=8, channels=[2, 64, 64, 1], N=6, H=2, S=2, ref="zero"),
+    "m128_c64": W.Workload("mixed_128x128_c64", n=128, m=128, l=16, channels=[2, 64, 64, 64, 1], N=3, H=2, S=2,
+                           ref="zero"),
+}
+
+
+@pytest.mark.parametrize("name", list(MIXED_CASES))
+def test_mixed_precision_cnn_within_bf16_bound(cuda_ok, name):
+    """Mixed mode: BF16 operands, FP32 accumulation and residual.  Every
+    operand is rounded once to 8 significant bits (unit roundoff u = 2^-9), so
+    the CNN increment X_next - X carries a relative error of a few u; the
+    bound is 4u in relative L2 and 8u in max norm of the increment."""
+    wl = MIXED_CASES[name]
+    s = solver(wl, precision=oic.OIC_PREC_MIXED)
+    rng = np.random.default_rng(5)
+    X = (wl.X0()[None] + 0.3 * rng.standard_normal((wl.N, wl.n, wl.m))).astype(np.float32)
+    U = (0.5 * rng.standard_normal((wl.N, wl.l, wl.m))).astype(np.float32)
+    out = dev(np.zeros_like(X))
+    s.oic_cnn_forward(dev(X), dev(U), out)
+    s.oic_sync()
+    got = out.cpu().numpy().astype(np.float64)
+    want = oracle.cnn_step(onet(wl), X, U)
+    inc = want - X
+    u = 2.0 ** -9
+    assert np.linalg.norm(got - want) <= 4 * u * np.linalg.norm(inc)
+    assert np.abs(got - want).max() <= 8 * u * np.abs(inc).max()
