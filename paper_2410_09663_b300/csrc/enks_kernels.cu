@@ -11,6 +11,8 @@
 // Every kernel reads member rows through a row-offset table, so one set of
 // kernels serves the U-history layout, the full-history layout and
 // caller-provided ensembles.
+#include <type_traits>
+
 #include "oic_internal.cuh"
 
 namespace oic {
@@ -243,25 +245,37 @@ __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict_
 }
 
 // C[a][c] = sum over splits of part2 - (1/N) sum_j S1[a][j] S1[R + c][j].
+// F64: the split sum, the mean correction and the subtraction in FP64 (the
+// mixed-precision mode's FP64 anomaly step); else FP32 with an FP64 result.
+template <bool F64>
 __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restrict__ part2,
                                                            const float* __restrict__ S1, int splits, int R, int p,
                                                            int m, int N, double* __restrict__ C)
 {
-    __shared__ float red[8][33];
+    using T = typename std::conditional<F64, double, float>::type;
+    __shared__ T red[8][33];
     const int M = R + p;
     const int idx = blockIdx.x * 32 + threadIdx.x % 32;
     const bool ok = idx < M * p;
-    const float t = split_sum(part2, (long)M * p, splits, idx, ok, red);
+    const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+    T sp = 0;
+    if (ok)
+        for (int k = w; k < splits; k += 8) sp += (T)part2[(long)k * M * p + idx];
+    red[w][ln] = sp;
+    __syncthreads();
     if (threadIdx.x < 32 && ok) {
+        T t = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][ln];
         const int a = idx / p, c = idx % p;
         const float* x = S1 + (long)a * m;
         const float* y = S1 + (long)(R + c) * m;
-        float d0 = 0.f, d1 = 0.f;
+        T d0 = 0, d1 = 0;
         for (int j = 0; j < m; j += 2) {
-            d0 = fmaf(x[j], y[j], d0);
-            d1 = fmaf(x[j + 1], y[j + 1], d1);
+            d0 = fma((T)x[j], (T)y[j], d0);
+            d1 = fma((T)x[j + 1], (T)y[j + 1], d1);
         }
-        C[idx] = (double)(t - (d0 + d1) / (float)N);
+        C[idx] = (double)(t - (d0 + d1) / (T)N);
     }
 }
 
@@ -535,10 +549,108 @@ void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, c
 }
 
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st)
+                         cudaStream_t st, bool f64)
 {
     const int total = (R + p) * p;
-    cov_finalize_kernel<<<(total + 31) / 32, 256, 0, st>>>(part2, S1, splits, R, p, m, N, C);
+    if (f64) cov_finalize_kernel<true><<<(total + 31) / 32, 256, 0, st>>>(part2, S1, splits, R, p, m, N, C);
+    else cov_finalize_kernel<false><<<(total + 31) / 32, 256, 0, st>>>(part2, S1, splits, R, p, m, N, C);
+}
+
+// ------------------------------------------------------------ FP64 gain
+// The mixed-precision mode's gain: Cyy = L L^T by a right-looking FP64
+// Cholesky in one CTA (L in shared memory, two barriers per column), then
+// one warp per row a of Cxy solves L z = Cxy[a]^T and L^T k = z in FP64
+// (lane-parallel dot products, shuffle reductions) and writes Kt[.][a].
+constexpr int G64_T = 1024;
+
+__global__ void __launch_bounds__(G64_T, 1)
+chol64_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ Lg, int* __restrict__ status,
+              int* __restrict__ bad_out)
+{
+    extern __shared__ double Ls[];                // [p][p + 1], lower triangle used
+    __shared__ int bad;
+    const int ld = p + 1, tid = threadIdx.x;
+    const double* Cyy = C + (long)R * p;
+    for (int e = tid; e < p * p; e += G64_T) Ls[(e / p) * ld + e % p] = Cyy[e];
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < p; ++j) {
+        const double d = Ls[j * ld + j];
+        if (!(d > 0.0)) {                         // same value in every thread
+            if (tid == 0) bad = 1;
+            break;
+        }
+        const double rd = 1.0 / sqrt(d);
+        // column j below the diagonal (rows i > j); the trailing update below
+        // reads these scaled values
+        for (int i = j + 1 + tid; i < p; i += G64_T) Ls[i * ld + j] *= rd;
+        __syncthreads();
+        // A[i][k] -= L[i][j] L[k][j] for j < k <= i
+        const int nt = p - 1 - j;
+        for (int e = tid; e < nt * nt; e += G64_T) {
+            const int i = j + 1 + e / nt, k = j + 1 + e % nt;
+            if (k <= i) Ls[i * ld + k] = fma(-Ls[i * ld + j], Ls[k * ld + j], Ls[i * ld + k]);
+        }
+        if (tid == 0) Ls[j * ld + j] = d * rd;
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) { atomicExch(status, DEV_NOTSPD); *bad_out = 1; }
+        return;
+    }
+    if (tid == 0) *bad_out = 0;
+    for (int e = tid; e < p * p; e += G64_T) {
+        const int i = e / p, k = e % p;
+        Lg[e] = k <= i ? Ls[i * ld + k] : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+solve64_kernel(const double* __restrict__ C, int R, int p, const double* __restrict__ Lg,
+               const int* __restrict__ bad_in, float* __restrict__ Kt)
+{
+    extern __shared__ double zs[];                // [8 warps][p]
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int a = blockIdx.x * 8 + w;
+    if (a >= R) return;
+    double* z = zs + (size_t)w * p;
+    if (*bad_in) {
+        for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
+        return;
+    }
+    for (int i = lane; i < p; i += 32) z[i] = C[(long)a * p + i];
+    __syncwarp();
+    // forward: z_i = (c_i - sum_{k < i} L_ik z_k) / L_ii
+    for (int i = 0; i < p; ++i) {
+        double s = 0.0;
+        for (int k = lane; k < i; k += 32) s = fma(Lg[(long)i * p + k], z[k], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) z[i] = (z[i] - s) / Lg[(long)i * p + i];
+        __syncwarp();
+    }
+    // back: k_i = (z_i - sum_{k > i} L_ki k_k) / L_ii
+    for (int i = p - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < p; k += 32) s = fma(Lg[(long)k * p + i], z[k], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) z[i] = (z[i] - s) / Lg[(long)i * p + i];
+        __syncwarp();
+    }
+    for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = (float)z[i];
+}
+
+void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st)
+{
+    const size_t smem = sizeof(double) * (size_t)p * (p + 1);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(chol64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    chol64_kernel<<<1, G64_T, smem, st>>>(C, R, p, L, status, bad);
+    solve64_kernel<<<(R + 7) / 8, 256, sizeof(double) * 8 * (size_t)p, st>>>(C, R, p, L, bad, Kt);
 }
 
 size_t gain_smem_bytes(int p) { return p <= 144 ? 0 : (size_t)-1; }

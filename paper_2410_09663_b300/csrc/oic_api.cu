@@ -28,8 +28,8 @@ struct Profiler {
 };
 
 struct Layout {
-    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, rowtab, status,
-        selftest;
+    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, rowtab,
+        status, selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -168,6 +168,7 @@ void compute_layout(oic_handle* h)
     L.D = take(sizeof(float) * N * p * m);
     L.C = take(sizeof(double) * (Ra + p) * p);
     L.K = take(sizeof(float) * Ra * p);
+    L.L64 = take(c.precision == OIC_PREC_MIXED ? sizeof(double) * p * p : 0);
     L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
     L.status = take(64);
     L.selftest = take(64);
@@ -269,10 +270,17 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
         launch_stats(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, part1, part2, D, splits, h->st);
     });
     run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
+    const bool mixed = c.precision == OIC_PREC_MIXED;
     run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
-        launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st);
+        launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed);
     });
-    run_stage(h, OIC_STAGE_GAIN, [&] { launch_gain(C, R, p, Kt, h->at<int>(h->lay.status), h->st); });
+    run_stage(h, OIC_STAGE_GAIN, [&] {
+        if (mixed)
+            launch_gain64(C, R, p, h->at<double>(h->lay.L64), h->at<int>(h->lay.status) + 1, Kt,
+                          h->at<int>(h->lay.status), h->st);
+        else
+            launch_gain(C, R, p, Kt, h->at<int>(h->lay.status), h->st);
+    });
     run_stage(h, OIC_STAGE_UPDATE, [&] { launch_update(E, ms, c.N, c.m, act, Kt, p, D, h->st); });
 }
 

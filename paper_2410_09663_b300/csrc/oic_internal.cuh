@@ -67,7 +67,10 @@ void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs,
 void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st);
 // C = sum_s part2 - S1 S1_Y^T / N  ([(R + p) x p], Cxy on top, Cyy below).
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st);
+                         cudaStream_t st, bool f64 = false);
+// Mixed-precision gain: FP64 Cholesky of Cyy (one CTA) into L [p][p], then
+// FP64 triangular solves per row of Cxy; bad: device flag (not SPD).
+void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st);
 // Kt = (Cxy Cyy^{-1})^T, [p][R].
 size_t gain_smem_bytes(int p);
 void launch_gain(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st);

@@ -161,9 +161,13 @@ def test_philox_mode_matches_oracle_fed_host_philox(cuda_ok):
         assert rel(Xn, X) <= TOL
 
 
-def test_enks_update_matches_oracle(cuda_ok):
+@pytest.mark.parametrize("precision", [oic.OIC_PREC_FP32, oic.OIC_PREC_MIXED])
+def test_enks_update_matches_oracle(cuda_ok, precision):
+    """FP32 mode: FP32 gain by elimination; mixed mode: FP64 mean correction,
+    FP64 Cholesky gain (the MID CNN has 16 channels, outside the BF16 path,
+    so only the analysis differs)."""
     wl = MID
-    s = solver(wl)
+    s = solver(wl, precision=precision)
     rng = np.random.default_rng(9)
     R = 45
     p = wl.p
@@ -181,9 +185,10 @@ def test_enks_update_matches_oracle(cuda_ok):
     assert rel(got.mean(0), want.mean(0)) <= TOL
 
 
-def test_not_positive_definite_is_reported_and_skipped(cuda_ok):
+@pytest.mark.parametrize("precision", [oic.OIC_PREC_FP32, oic.OIC_PREC_MIXED])
+def test_not_positive_definite_is_reported_and_skipped(cuda_ok, precision):
     wl = MID
-    s = solver(wl)
+    s = solver(wl, precision=precision)
     R = wl.p
     E = np.ones((wl.N, R, wl.m), np.float32)        # identical members, V = 0: Sigma^Y = 0
     V = np.zeros((wl.N, wl.p, wl.m), np.float32)
