@@ -283,3 +283,37 @@ def test_mixed_precision_cnn_within_bf16_bound(cuda_ok, name):
     u = 2.0 ** -9
     assert np.linalg.norm(got - want) <= 4 * u * np.linalg.norm(inc)
     assert np.abs(got - want).max() <= 8 * u * np.abs(inc).max()
+
+
+MIXED_LOOP = {
+    "m16_c32": W.Workload("mixed_loop_16", n=16, m=16, l=4, channels=[2, 32, 32, 1], N=32, H=3, S=6, ref="zero"),
+    "m32_c64": W.Workload("mixed_loop_32", n=32, m=32, l=4, channels=[2, 64, 64, 64, 1], N=32, H=3, S=4,
+                          ref="blobs", blob_sigma=3.0),
+}
+
+
+@pytest.mark.parametrize("name", list(MIXED_LOOP))
+def test_mixed_precision_closed_loop_cost_within_half_percent(cuda_ok, name):
+    """Mixed mode (BF16 CNN, FP32 covariances, FP64 mean correction and
+    gain) against the FP64 oracle fed the same noise: the closed-loop cost J
+    within 0.5%, the applied controls within 4u of BF16 (u = 2^-9) in
+    relative L2, the states within 1e-3."""
+    wl = MIXED_LOOP[name]
+    S = wl.S
+    s = solver(wl, precision=oic.OIC_PREC_MIXED)
+    xr_all = wl.X_ref_all(S)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    Ut = np.zeros((S, wl.l, wl.m), np.float32)
+    Xt = np.zeros((S + 1, wl.n, wl.m), np.float32)
+    Xt[0] = wl.X0()
+    for k in range(S):
+        s.oic_step_host(xr_all[k:k + wl.H + 1], wl.U_ref(), wl.noise(k), Ut[k], Xt[k + 1])
+    Xo, Uo, _ = oracle.run(onet(wl), wl.N, wl.H, S, wl.X0(), wl.U_init(), xr_all, wl.U_ref(),
+                           wl.noise_all(S))
+    jg = oracle.closed_loop_cost(Xt, Ut, xr_all, wl.U_ref(), wl.U_init(), wl.sigma_vx, wl.sigma_vu,
+                                 wl.sigma_w)
+    jo = oracle.closed_loop_cost(Xo, Uo, xr_all, wl.U_ref(), wl.U_init(), wl.sigma_vx, wl.sigma_vu,
+                                 wl.sigma_w)
+    assert abs(jg - jo) <= 5e-3 * abs(jo)
+    assert rel(Ut, Uo) <= 4 * 2.0 ** -9
+    assert rel(Xt, Xo) <= 1e-3
