@@ -82,6 +82,9 @@ def stage_work(wl, stage):
         # whole CNN step; the hidden layer (the bulk of the flops) runs on the
         # fp16 tensor pipe as three products per FP32 product
         return cnn_flops_per_member_step(wl) * N, "flop", "tensor"
+    if stage == "cnn_bf16":
+        # whole CNN step in BF16 (one kernel per layer), one product per product
+        return cnn_flops_per_member_step(wl) * N, "flop", "tensor"
     return None
 
 
@@ -250,7 +253,9 @@ def run_oic(args, wl):
 
     wl = wl.with_(seed=wl.seed + rank)                 # independent replica per rank
     w, b = wl.flat_weights()
-    cfg = oic.config_from_workload(wl, noise_mode=oic.OIC_NOISE_PHILOX)
+    mixed = args.precision == "mixed"
+    cfg = oic.config_from_workload(wl, noise_mode=oic.OIC_NOISE_PHILOX,
+                                   precision=oic.OIC_PREC_MIXED if mixed else oic.OIC_PREC_FP32)
     stream = torch.cuda.Stream(device=dev)
     s = oic.Solver(cfg, w, b, wl.B(), device=dev, stream=stream)
 
@@ -349,7 +354,8 @@ def run_oic(args, wl):
                         "algorithmic_per_launch": amount, "launches": n_l,
                         "avg_launch_ms": avg_s * 1e3,
                         "fp32_ffma_equiv_frac": ach / fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0)),
-                        "note": "algorithmic FP32 flops; the tensor pipe executes 3 fp16 products each"}
+                        "note": ("BF16 operands, FP32 accumulation" if dominant == "cnn_bf16" else
+                                 "algorithmic FP32 flops; the tensor pipe executes 3 fp16 products each")}
             elif bound == "alu":
                 peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
                 roof = {"bound": "alu", "kernel": dominant, "achieved": amount / avg_s / 1e12,
@@ -367,9 +373,10 @@ def run_oic(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64" if mixed else "f32", "data": "synthetic",
         "config": config_dict(wl, {
             "parallelism": "replicas" if world > 1 else "single",
+            "precision": "mixed: BF16 conv, FP32 covariance, FP64 mean correction and gain" if mixed else "fp32",
             "member_steps_per_s": value * wl.N * wl.H,
             "cnn_tflops": value * wl.N * wl.H * cnn_flops_per_member_step(wl) / 1e12,
             "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
@@ -400,6 +407,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["oic", "reference"], default="oic")
     ap.add_argument("--workload", default="working_64")
+    ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args(argv)
