@@ -28,7 +28,6 @@ namespace oic {
 namespace {
 
 constexpr int BM = 128;                                 // tile rows (positions)
-constexpr int NIN = 4;                                  // input row slots
 constexpr long long B_WAIT = 4000000000LL;
 enum { MODE_HIDDEN = 0, MODE_LAST = 1 };
 
@@ -41,6 +40,11 @@ struct BS {
     static constexpr int NB = 3 * CO;                   // B rows: vertical taps stacked
     static constexpr int BTILE = 2 * NB * 16;           // one (dx, ks) tile, 2 K chunks
     static constexpr int BBYTES = 3 * KS * BTILE;
+    // input rows in flight (bulk copies from HBM): as many as fit next to the
+    // weights, up to 12
+    static constexpr int NIN_FIT = (200 * 1024 - BBYTES) / INROW;
+    static constexpr int NIN = NIN_FIT > 12 ? 12 : NIN_FIT;
+    static_assert(NIN >= 4, "input ring");
     static constexpr int NDW = MODE == MODE_LAST ? 4 : 16;   // drain warps
     static constexpr int LOAD_WARP = NDW, ISSUE_WARP = NDW + 1;
     static constexpr int NT = 32 * (NDW + 2);
@@ -48,7 +52,7 @@ struct BS {
     static constexpr int OFF_B = OFF_IN + NIN * INROW;
     static constexpr int OFF_BIAS = OFF_B + BBYTES;
     static constexpr int OFF_MISC = OFF_BIAS + (CO * 4 + 15) / 16 * 16;
-    static constexpr int SMEM = OFF_MISC + 256;
+    static constexpr int SMEM = OFF_MISC + 512;
     static constexpr int TMEM_COLS = 4 * CO <= 32 ? 32 : 4 * CO <= 64 ? 64 : 4 * CO <= 128 ? 128 : 256;
     static_assert(CI % 16 == 0 && (CO == 16 || CO == 32 || CO == 64), "shapes");
     static_assert(MODE != MODE_LAST || CO == 16, "last layer: 16 columns, channel 0 used");
@@ -56,12 +60,12 @@ struct BS {
 
 // mbarriers (8 bytes each)
 enum : int {
-    BB_FULL = 0,       // [NIN] input row landed (bulk copy)
-    BB_FREE = 4,       // [NIN] MMAs of the input row in the slot done
-    BB_HDONE = 8,      // [2]   MMAs of input row j done (parity of j)
-    BB_PASS = 10,      // [4]   drain pass k done (k mod 4)
-    BB_FIN = 14,
-    BB_COUNT = 15
+    BB_FULL = 0,       // [12] input row landed (bulk copy), by slot
+    BB_FREE = 12,      // [12] MMAs of the input row in the slot done
+    BB_HDONE = 24,     // [2]  MMAs of input row j done (parity of j)
+    BB_PASS = 26,      // [4]  drain pass k done (k mod 4)
+    BB_FIN = 30,
+    BB_COUNT = 31
 };
 
 constexpr uint32_t DESC_HI = (128u >> 4) | (1u << 14);
@@ -260,15 +264,15 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
             // ============ loads: input row j into slot j % NIN ============
             if (lane == 0) {
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
-                    const int sl = j % NIN;
-                    if (j - NIN >= f_lo) wait(BB_FREE + sl);       // MMAs of row j - NIN done
+                    const int sl = j % S::NIN;
+                    if (j - S::NIN >= f_lo) wait(BB_FREE + sl);    // MMAs of row j - NIN done
                     mbar_expect_tx(mb + BB_FULL + sl, S::INROW);
                     bulk_g2s(smem + S::OFF_IN + sl * S::INROW, in_g + (size_t)j * (S::INROW / 2), S::INROW,
                              mb + BB_FULL + sl);
                 }
                 // the last slots' MMAs, before the next segment reuses them
-                for (int j = f_hi - NIN + 1; j <= f_hi && !failed; ++j)
-                    if (j >= f_lo) wait(BB_FREE + j % NIN);
+                for (int j = f_hi - S::NIN + 1; j <= f_hi && !failed; ++j)
+                    if (j >= f_lo) wait(BB_FREE + j % S::NIN);
             }
             __syncwarp();
         } else if (warp == S::ISSUE_WARP) {
@@ -279,9 +283,9 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
                     // output row j+1 takes the ring slot of row j-3, drained in pass j-2
                     if (j - 2 >= f_lo) wait(BB_PASS + ((j - 2) & 3));
-                    wait(BB_FULL + j % NIN);
-                    issue_row<CI, CO, MODE, G>(tmem, j, j == f_lo, dIn + (j % NIN) * (S::INROW / 16), dB);
-                    tc::mma_commit(mb + BB_FREE + j % NIN);
+                    wait(BB_FULL + j % S::NIN);
+                    issue_row<CI, CO, MODE, G>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
+                    tc::mma_commit(mb + BB_FREE + j % S::NIN);
                     tc::mma_commit(mb + BB_HDONE + (j & 1));
                 }
                 // the remaining drain passes
@@ -292,7 +296,16 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
         } else {
             // ============ drain: pass k finishes output row k-1 ============
             const int last_pass = ye < n ? ye : n;              // = f_hi + 1 at the image bottom
+            // last layer: X of the output row of the next pass, loaded one pass ahead
+            const int xb = ep % G, xx = ep / G, xmb = g * G + xb;
+            auto fetch_x = [&](int h) -> float {
+                return (MODE == MODE_LAST && h >= ys && h < ye && xmb < Nb) ? X[(long)xmb * x_ms + (long)h * m + xx]
+                                                                           : 0.f;
+            };
+            float xpf = fetch_x(f_lo - 1);
             for (int k = f_lo; k <= last_pass && !failed; ++k) {
+                const float xcur = xpf;
+                xpf = fetch_x(k);
                 if (Fv(k)) wait_w(BB_HDONE + (k & 1));
                 const int h = k - 1;
                 if (Ov(h)) {
@@ -319,10 +332,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                         float v[8];
                         tmem_ldn<8>(tmem + tlane + col, v);
                         tc::tmem_ld_wait();
-                        const int b = ep % G, x = ep / G, mbr = g * G + b;
-                        if (mbr < Nb)
-                            Xout[(long)mbr * o_ms + (long)h * m + x] =
-                                fmaf(rs, v[0] + sbias[0], X[(long)mbr * x_ms + (long)h * m + x]);
+                        if (xmb < Nb) Xout[(long)xmb * o_ms + (long)h * m + xx] = fmaf(rs, v[0] + sbias[0], xcur);
                     }
                 }
                 tc::fence_before_sync();

@@ -585,11 +585,15 @@ chol64_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ L
         // reads these scaled values
         for (int i = j + 1 + tid; i < p; i += G64_T) Ls[i * ld + j] *= rd;
         __syncthreads();
-        // A[i][k] -= L[i][j] L[k][j] for j < k <= i
-        const int nt = p - 1 - j;
-        for (int e = tid; e < nt * nt; e += G64_T) {
-            const int i = j + 1 + e / nt, k = j + 1 + e % nt;
-            if (k <= i) Ls[i * ld + k] = fma(-Ls[i * ld + j], Ls[k * ld + j], Ls[i * ld + k]);
+        // A[i][k] -= L[i][j] L[k][j] for j < k <= i: warp w takes rows
+        // j+1+w, +32, ..., lane t columns j+1+t, +32, ... (consecutive lanes,
+        // consecutive doubles)
+        {
+            const int w = tid / 32, t = tid % 32;
+            for (int i = j + 1 + w; i < p; i += G64_T / 32) {
+                const double lij = Ls[i * ld + j];
+                for (int k = j + 1 + t; k <= i; k += 32) Ls[i * ld + k] = fma(-lij, Ls[k * ld + j], Ls[i * ld + k]);
+            }
         }
         if (tid == 0) Ls[j * ld + j] = d * rd;
         __syncthreads();
@@ -605,40 +609,64 @@ chol64_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ L
     }
 }
 
+// lane t owns z_i for i = t + 32 q (q < 5, p <= 160), in registers
+constexpr int S64_Q = 5;
+
 __global__ void __launch_bounds__(256)
 solve64_kernel(const double* __restrict__ C, int R, int p, const double* __restrict__ Lg,
                const int* __restrict__ bad_in, float* __restrict__ Kt)
 {
-    extern __shared__ double zs[];                // [8 warps][p]
+    extern __shared__ double rinv[];              // 1 / L_ii
     const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) rinv[i] = 1.0 / Lg[(long)i * p + i];
+    __syncthreads();
     const int a = blockIdx.x * 8 + w;
     if (a >= R) return;
-    double* z = zs + (size_t)w * p;
     if (*bad_in) {
         for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
         return;
     }
-    for (int i = lane; i < p; i += 32) z[i] = C[(long)a * p + i];
-    __syncwarp();
-    // forward: z_i = (c_i - sum_{k < i} L_ik z_k) / L_ii
-    for (int i = 0; i < p; ++i) {
-        double s = 0.0;
-        for (int k = lane; k < i; k += 32) s = fma(Lg[(long)i * p + k], z[k], s);
+    double z[S64_Q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) z[i] = (z[i] - s) / Lg[(long)i * p + i];
-        __syncwarp();
+    for (int q = 0; q < S64_Q; ++q) {
+        const int i = lane + 32 * q;
+        z[q] = i < p ? C[(long)a * p + i] : 0.0;
     }
-    // back: k_i = (z_i - sum_{k > i} L_ki k_k) / L_ii
-    for (int i = p - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int k = i + 1 + lane; k < p; k += 32) s = fma(Lg[(long)k * p + i], z[k], s);
+    // forward, column by column: z_j /= L_jj, then z_i -= L_ij z_j for i > j
+    for (int j = 0; j < p; ++j) {
+        const int qj = j / 32, lj = j % 32;
+        double zj = 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) z[i] = (z[i] - s) / Lg[(long)i * p + i];
-        __syncwarp();
+        for (int q = 0; q < S64_Q; ++q)
+            if (q == qj) zj = z[q];
+        zj = __shfl_sync(0xffffffffu, zj, lj) * rinv[j];
+#pragma unroll
+        for (int q = 0; q < S64_Q; ++q) {
+            const int i = lane + 32 * q;
+            if (i == j) z[q] = zj;
+            else if (i > j && i < p) z[q] = fma(-Lg[(long)i * p + j], zj, z[q]);
+        }
     }
-    for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = (float)z[i];
+    // back, row by row of L: k_j = z_j / L_jj, then z_i -= L_ji k_j for i < j
+    for (int j = p - 1; j >= 0; --j) {
+        const int qj = j / 32, lj = j % 32;
+        double kj = 0.0;
+#pragma unroll
+        for (int q = 0; q < S64_Q; ++q)
+            if (q == qj) kj = z[q];
+        kj = __shfl_sync(0xffffffffu, kj, lj) * rinv[j];
+#pragma unroll
+        for (int q = 0; q < S64_Q; ++q) {
+            const int i = lane + 32 * q;
+            if (i == j) z[q] = kj;
+            else if (i < j) z[q] = fma(-Lg[(long)j * p + i], kj, z[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < S64_Q; ++q) {
+        const int i = lane + 32 * q;
+        if (i < p) Kt[(long)i * R + a] = (float)z[q];
+    }
 }
 
 void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st)
@@ -650,7 +678,7 @@ void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt
         attr_set = true;
     }
     chol64_kernel<<<1, G64_T, smem, st>>>(C, R, p, L, status, bad);
-    solve64_kernel<<<(R + 7) / 8, 256, sizeof(double) * 8 * (size_t)p, st>>>(C, R, p, L, bad, Kt);
+    solve64_kernel<<<(R + 7) / 8, 256, sizeof(double) * (size_t)p, st>>>(C, R, p, L, bad, Kt);
 }
 
 size_t gain_smem_bytes(int p) { return p <= 144 ? 0 : (size_t)-1; }
