@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict_
     if (threadIdx.x < 32 && ok) S1[idx] = t;
 }
 
-// C[a][c] = sum over splits of part2 - (1/N) sum_j S1[a][j] S1[R + c][j].
+// C[a][c] = sum over splits of part2 - (1/N) sum_j S1[a][j] S1[R + c][j]
+// (S1 == nullptr: the partials already have the means removed).
 // F64: the split sum, the mean correction and the subtraction in FP64 (the
 // mixed-precision mode's FP64 anomaly step); else FP32 with an FP64 result.
 template <bool F64>
@@ -267,15 +268,19 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
         T t = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) t += red[q][ln];
-        const int a = idx / p, c = idx % p;
-        const float* x = S1 + (long)a * m;
-        const float* y = S1 + (long)(R + c) * m;
-        T d0 = 0, d1 = 0;
-        for (int j = 0; j < m; j += 2) {
-            d0 = fma((T)x[j], (T)y[j], d0);
-            d1 = fma((T)x[j + 1], (T)y[j + 1], d1);
+        T corr = 0;
+        if (S1 != nullptr) {                      // one-pass products: remove the mean term
+            const int a = idx / p, c = idx % p;
+            const float* x = S1 + (long)a * m;
+            const float* y = S1 + (long)(R + c) * m;
+            T d0 = 0, d1 = 0;
+            for (int j = 0; j < m; j += 2) {
+                d0 = fma((T)x[j], (T)y[j], d0);
+                d1 = fma((T)x[j + 1], (T)y[j + 1], d1);
+            }
+            corr = (d0 + d1) / (T)N;
         }
-        C[idx] = (double)(t - (d0 + d1) / (T)N);
+        C[idx] = (double)(t - corr);
     }
 }
 

@@ -28,8 +28,7 @@ struct Profiler {
 };
 
 struct Layout {
-    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, rowtab,
-        status, selftest;
+    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, tB, rowtab, status, selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -169,6 +168,8 @@ void compute_layout(oic_handle* h)
     L.C = take(sizeof(double) * (Ra + p) * p);
     L.K = take(sizeof(float) * Ra * p);
     L.L64 = take(c.precision == OIC_PREC_MIXED ? sizeof(double) * p * p : 0);
+    // tensor-core anomaly products: the pre-split observation tiles
+    L.tB = take(stats_tc_supported(c.m, (int)p) ? stats_tc_bbytes(c.N, (int)p, c.m) : 0);
     L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
     L.status = take(64);
     L.selftest = take(64);
@@ -265,15 +266,27 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
     double* C = h->at<double>(h->lay.C);
     float* Kt = h->at<float>(h->lay.K);
     const int R = act.count, p = obs.count, M = R + p;
-    const int splits = stats_splits(R, p, c.N);
-    run_stage(h, OIC_STAGE_COV, [&] {
-        launch_stats(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, part1, part2, D, splits, h->st);
-    });
-    run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
     const bool mixed = c.precision == OIC_PREC_MIXED;
-    run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
-        launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed);
-    });
+    if (stats_tc_supported(c.m, p)) {
+        const int splits = stats_tc_splits(M, c.N);
+        run_stage(h, OIC_STAGE_COV, [&] {
+            launch_stats_tc(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, h->at<float>(h->lay.tB), part1, part2, D,
+                            splits, h->at<int>(h->lay.status), h->st);
+        });
+        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
+        run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
+            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed);
+        });
+    } else {
+        const int splits = stats_splits(R, p, c.N);
+        run_stage(h, OIC_STAGE_COV, [&] {
+            launch_stats(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, part1, part2, D, splits, h->st);
+        });
+        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
+        run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
+            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed);
+        });
+    }
     run_stage(h, OIC_STAGE_GAIN, [&] {
         if (mixed)
             launch_gain64(C, R, p, h->at<double>(h->lay.L64), h->at<int>(h->lay.status) + 1, Kt,
@@ -410,6 +423,7 @@ oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* c
     h->Ubase = h->full() ? (c.H + 1) * c.n : 2 * c.n;
     h->R_act_max = h->R_of(c.H);
     h->splits_max = stats_splits(1, h->p, c.N);
+    if (stats_tc_splits(1, c.N) > h->splits_max) h->splits_max = stats_tc_splits(1, c.N);
     h->noise_n = noise_count(&c);
     h->bf16 = c.precision == OIC_PREC_MIXED && bf16_supported(c.n_layers, c.channels, c.m);
     h->fused = !h->bf16 && cnn_fused_supported(c.n_layers, c.channels, c.n, c.m, c.l) &&

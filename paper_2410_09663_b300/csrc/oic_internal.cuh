@@ -68,6 +68,15 @@ void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, c
 // C = sum_s part2 - S1 S1_Y^T / N  ([(R + p) x p], Cxy on top, Cyy below).
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
                          cudaStream_t st, bool f64 = false);
+// Anomaly products on the tensor cores (TF32 hi / lo split, one pass over
+// the ensemble): part1 / part2 as launch_stats writes them, so the same
+// s1 reduction and finalisation follow.  Bop: stats_tc_bbytes of scratch.
+bool stats_tc_supported(int m, int p);
+int stats_tc_splits(int M, int N);
+size_t stats_tc_bbytes(int N, int p, int m);
+void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
+                     const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, int splits,
+                     int* err, cudaStream_t st);
 // Mixed-precision gain: FP64 Cholesky of Cyy (one CTA) into L [p][p], then
 // FP64 triangular solves per row of Cxy; bad: device flag (not SPD).
 void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st);
