@@ -46,11 +46,13 @@ struct Segs {
 };
 
 __global__ void philox_noise_kernel(float* __restrict__ out, unsigned long long total,
-                                    unsigned long long seed, unsigned long long solve, Segs segs)
+                                    unsigned long long seed, const unsigned long long* __restrict__ solve_ctr,
+                                    Segs segs)
 {
     const unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long e0 = q * 4ull;
     if (e0 >= total) return;
+    const unsigned long long solve = *solve_ctr;
     const uint4 ctr = make_uint4((uint32_t)q, (uint32_t)(q >> 32), (uint32_t)solve,
                                  (uint32_t)(solve >> 32));
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -81,10 +83,14 @@ __global__ void philox_noise_kernel(float* __restrict__ out, unsigned long long 
     }
 }
 
+// the solve index lives on the device, so a captured step graph draws fresh
+// noise on every replay
+__global__ void counter_tick_kernel(unsigned long long* ctr) { *ctr += 1ull; }
+
 }  // namespace
 
 void launch_philox_noise(float* out, size_t count_total, unsigned long long seed,
-                         unsigned long long counter_hi, const size_t* seg_end, const float* seg_sigma,
+                         unsigned long long* solve_ctr, const size_t* seg_end, const float* seg_sigma,
                          int n_seg, cudaStream_t st)
 {
     Segs s{};
@@ -95,7 +101,8 @@ void launch_philox_noise(float* out, size_t count_total, unsigned long long seed
     }
     const unsigned long long quads = (count_total + 3) / 4;
     const unsigned blocks = (unsigned)((quads + 255) / 256);
-    philox_noise_kernel<<<blocks, 256, 0, st>>>(out, count_total, seed, counter_hi, s);
+    philox_noise_kernel<<<blocks, 256, 0, st>>>(out, count_total, seed, solve_ctr, s);
+    counter_tick_kernel<<<1, 1, 0, st>>>(solve_ctr);
 }
 
 }  // namespace oic

@@ -27,8 +27,38 @@ struct Profiler {
     std::vector<int> stage;
 };
 
+// One control step captured as a CUDA graph (Philox noise mode: every input
+// sits at a fixed workspace address and the solve index is on the device).
+// The profiled variant carries an event-record node before and after each
+// launch of the profiled stages; before every replay those nodes are pointed
+// at fresh events of the profiler, so stage times come from the replays.
+struct StepGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    unsigned mask = 0;
+    unsigned long long launches = 0;
+    std::vector<cudaEvent_t> cap_ev;       // events named at capture, pairs
+    std::vector<cudaGraphNode_t> node;     // their record nodes, same order
+    std::vector<int> stage;                // stage of each pair
+    bool failed = false;
+    void reset()
+    {
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        for (cudaEvent_t e : cap_ev) cudaEventDestroy(e);
+        x = nullptr;
+        g = nullptr;
+        cap_ev.clear();
+        node.clear();
+        stage.clear();
+        launches = 0;
+        mask = 0;
+        failed = false;
+    }
+};
+
 struct Layout {
-    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, tB, rowtab, status, selftest;
+    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, tB, ctr, rowtab, status, selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -49,10 +79,11 @@ struct oic_handle {
     cudaStream_t st = nullptr;
     bool bound = false, plant_ready = false, fused = false, bf16 = false;
     std::vector<size_t> w16_off, b16_off;   // mixed-precision CNN: packed layer tiles, padded biases
-    unsigned long long solve_counter = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int> obs_host;
     Profiler prof;
+    StepGraph sg[2];                          // [0] plain, [1] with profiling event nodes
+    StepGraph* capturing = nullptr;
 
     template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
     bool full() const { return cfg.keep_full_history != 0; }
@@ -71,10 +102,31 @@ struct oic_handle {
 namespace {
 
 // Runs one kernel launch of stage `stage`, counting it and, when the stage is
-// being profiled, bracketing it with CUDA events on the bound stream.
+// being profiled, bracketing it with CUDA events on the bound stream (while a
+// step graph is being captured: with capture-time events that become the
+// graph's record nodes).
 template <typename F>
 void run_stage(oic_handle* h, int stage, F&& launch)
 {
+    if (h->capturing != nullptr) {
+        StepGraph& G = *h->capturing;
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        const bool rec = ((G.mask >> stage) & 1u) && cudaEventCreate(&e[0]) == cudaSuccess &&
+                         cudaEventCreate(&e[1]) == cudaSuccess;
+        if (rec) cudaEventRecord(e[0], h->st);
+        launch();
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (rec) {
+            cudaEventRecord(e[1], h->st);
+            G.cap_ev.push_back(e[0]);
+            G.cap_ev.push_back(e[1]);
+            G.stage.push_back(stage);
+        } else {
+            if (e[0]) cudaEventDestroy(e[0]);
+            if (e[1]) cudaEventDestroy(e[1]);
+        }
+        return;
+    }
     Profiler& P = h->prof;
     const bool rec = P.on && ((P.mask >> stage) & 1u) && P.used < P.max;
     if (rec) cudaEventRecord(P.ev[2 * P.used], h->st);
@@ -170,6 +222,7 @@ void compute_layout(oic_handle* h)
     L.L64 = take(c.precision == OIC_PREC_MIXED ? sizeof(double) * p * p : 0);
     // tensor-core anomaly products: the pre-split observation tiles
     L.tB = take(stats_tc_supported(c.m, (int)p) ? stats_tc_bbytes(c.N, (int)p, c.m) : 0);
+    L.ctr = take(sizeof(unsigned long long));            // Philox solve index
     L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
     L.status = take(64);
     L.selftest = take(64);
@@ -309,11 +362,12 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
         const float sig[4] = {(float)c.sigma_w, (float)c.sigma_w, (float)c.sigma_vx, (float)c.sigma_vu};
         float* buf = h->at<float>(h->lay.noise);
         run_stage(h, OIC_STAGE_NOISE, [&] {
-            launch_philox_noise(buf, h->noise_n, c.seed, h->solve_counter, ends, sig, 4, h->st);
+            launch_philox_noise(buf, h->noise_n, c.seed, h->at<unsigned long long>(h->lay.ctr), ends, sig, 4,
+                                h->st);
         });
+        g_launches.fetch_add(1, std::memory_order_relaxed);   // the counter tick
         noise = buf;
     }
-    h->solve_counter++;
     const float* W0 = noise;
     const float* W = W0 + N * l * m;
     const float* VX = W + H * N * l * m;
@@ -370,6 +424,83 @@ oic_status step_impl(oic_handle* h, const float* X_ref, const float* U_ref, cons
     if (X_next)
         OIC_CUDA_OK(cudaMemcpyAsync(X_next, pX, sizeof(float) * n * m, cudaMemcpyDeviceToDevice, h->st));
     return last_cuda();
+}
+
+// Captures step_impl on the workspace buffers into G (event nodes for the
+// stages in mask).  A failed capture leaves G.failed set and the caller runs
+// the step eagerly.
+bool capture_step(oic_handle* h, StepGraph& G, unsigned mask)
+{
+    G.reset();
+    G.mask = mask;
+    const Layout& L = h->lay;
+    const unsigned long long l0 = g_launches.load();
+    h->capturing = &G;
+    oic_status s = OIC_ECUDA;
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        s = step_impl(h, h->at<float>(L.xref), h->at<float>(L.uref), h->at<float>(L.noise), h->at<float>(L.uapp),
+                      h->at<float>(L.xnext));
+        if (cudaStreamEndCapture(h->st, &G.g) != cudaSuccess) s = OIC_ECUDA;
+    }
+    h->capturing = nullptr;
+    G.launches = g_launches.load() - l0;
+    g_launches.fetch_sub(G.launches);                     // captured, not run
+    if (s != OIC_OK || G.g == nullptr || cudaGraphInstantiate(&G.x, G.g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        G.reset();
+        G.failed = true;
+        return false;
+    }
+    if (!G.cap_ev.empty()) {
+        size_t n = 0;
+        cudaGraphGetNodes(G.g, nullptr, &n);
+        std::vector<cudaGraphNode_t> all(n);
+        cudaGraphGetNodes(G.g, all.data(), &n);
+        G.node.assign(G.cap_ev.size(), nullptr);
+        for (cudaGraphNode_t nd : all) {
+            cudaGraphNodeType t;
+            cudaEvent_t e = nullptr;
+            if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+            if (cudaGraphEventRecordNodeGetEvent(nd, &e) != cudaSuccess) continue;
+            for (size_t k = 0; k < G.cap_ev.size(); ++k)
+                if (G.cap_ev[k] == e) G.node[k] = nd;
+        }
+        for (cudaGraphNode_t nd : G.node)
+            if (nd == nullptr) {
+                G.reset();
+                G.failed = true;
+                return false;
+            }
+    }
+    return true;
+}
+
+// One control step through the step graph; false when no graph can be used
+// (the caller then runs step_impl eagerly).
+bool run_step_graph(oic_handle* h)
+{
+    if (h->cfg.noise_mode != OIC_NOISE_PHILOX || getenv("OIC_NO_GRAPH") != nullptr) return false;
+    Profiler& P = h->prof;
+    const bool prof = P.on && P.mask != 0;
+    StepGraph* G = &h->sg[prof ? 1 : 0];
+    if (prof && G->x && G->mask != P.mask) G->reset();
+    if (!G->x && !G->failed) capture_step(h, *G, prof ? P.mask : 0);
+    if (!G->x) return false;
+    if (prof) {
+        const int pairs = (int)G->stage.size();
+        if (P.used + pairs > P.max) return false;         // out of profiler slots: eager, untimed
+        for (int k = 0; k < pairs; ++k) {
+            if (cudaGraphExecEventRecordNodeSetEvent(G->x, G->node[2 * k], P.ev[2 * (P.used + k)]) != cudaSuccess ||
+                cudaGraphExecEventRecordNodeSetEvent(G->x, G->node[2 * k + 1], P.ev[2 * (P.used + k) + 1]) !=
+                    cudaSuccess)
+                return false;
+            P.stage[P.used + k] = G->stage[k];
+        }
+        P.used += pairs;
+    }
+    if (cudaGraphLaunch(G->x, h->st) != cudaSuccess) return false;
+    g_launches.fetch_add(G->launches, std::memory_order_relaxed);
+    return true;
 }
 
 oic_status read_status(oic_handle* h)
@@ -526,12 +657,14 @@ oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda
     OIC_CUDA_OK(cudaMemcpyAsync(h->at<int>(h->lay.rowtab), tab.data(), sizeof(int) * tab.size(),
                                 cudaMemcpyHostToDevice, h->st));
     OIC_CUDA_OK(cudaMemsetAsync(h->at<int>(h->lay.status), 0, 64, h->st));
+    OIC_CUDA_OK(cudaMemsetAsync(h->at<char>(h->lay.ctr), 0, sizeof(unsigned long long), h->st));
+    h->sg[0].reset();
+    h->sg[1].reset();
     if (!h->ev0) OIC_CUDA_OK(cudaEventCreate(&h->ev0));
     if (!h->ev1) OIC_CUDA_OK(cudaEventCreate(&h->ev1));
     OIC_CUDA_OK(cudaStreamSynchronize(h->st));
     h->bound = true;
     h->plant_ready = false;
-    h->solve_counter = 0;
     return OIC_OK;
 }
 
@@ -544,8 +677,8 @@ oic_status oic_reset(oic_handle* h, const float* X0, const float* U_prev)
                                 cudaMemcpyDeviceToDevice, h->st));
     OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantU), U_prev, sizeof(float) * l * m,
                                 cudaMemcpyDeviceToDevice, h->st));
+    OIC_CUDA_OK(cudaMemsetAsync(h->at<char>(h->lay.ctr), 0, sizeof(unsigned long long), h->st));
     h->plant_ready = true;
-    h->solve_counter = 0;
     return OIC_OK;
 }
 
@@ -569,7 +702,27 @@ oic_status oic_step(oic_handle* h, const float* X_ref, const float* U_ref, const
     if (!h->bound || !h->plant_ready) return OIC_ESTATE;
     if (h->cfg.noise_mode == OIC_NOISE_HOST && (!noise || !aligned16(noise))) return OIC_EINVAL;
     OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
-    oic_status s = step_impl(h, X_ref, U_ref, noise, U_applied, X_next);
+    oic_status s = OIC_OK;
+    if (h->cfg.noise_mode == OIC_NOISE_PHILOX) {
+        // inputs into the workspace, the step graph, outputs out of it
+        const Layout& L = h->lay;
+        const size_t n = h->cfg.n, m = h->cfg.m, l = h->cfg.l, H = h->cfg.H;
+        OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.xref), X_ref, sizeof(float) * (H + 1) * n * m,
+                                    cudaMemcpyDeviceToDevice, h->st));
+        OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.uref), U_ref, sizeof(float) * l * m, cudaMemcpyDeviceToDevice,
+                                    h->st));
+        if (!run_step_graph(h))
+            s = step_impl(h, h->at<float>(L.xref), h->at<float>(L.uref), h->at<float>(L.noise),
+                          h->at<float>(L.uapp), h->at<float>(L.xnext));
+        if (s == OIC_OK && U_applied)
+            OIC_CUDA_OK(cudaMemcpyAsync(U_applied, h->at<float>(L.uapp), sizeof(float) * l * m,
+                                        cudaMemcpyDeviceToDevice, h->st));
+        if (s == OIC_OK && X_next)
+            OIC_CUDA_OK(cudaMemcpyAsync(X_next, h->at<float>(L.xnext), sizeof(float) * n * m,
+                                        cudaMemcpyDeviceToDevice, h->st));
+    } else {
+        s = step_impl(h, X_ref, U_ref, noise, U_applied, X_next);
+    }
     OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
     return s;
 }
@@ -584,8 +737,8 @@ oic_status oic_reset_host(oic_handle* h, const float* X0, const float* U_prev)
     OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantU), U_prev, sizeof(float) * l * m,
                                 cudaMemcpyHostToDevice, h->st));
     OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    OIC_CUDA_OK(cudaMemsetAsync(h->at<char>(h->lay.ctr), 0, sizeof(unsigned long long), h->st));
     h->plant_ready = true;
-    h->solve_counter = 0;
     return OIC_OK;
 }
 
@@ -637,8 +790,10 @@ oic_status oic_step_host(oic_handle* h, const float* X_ref, const float* U_ref, 
     if (c.noise_mode == OIC_NOISE_HOST)
         OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(L.noise), noise, sizeof(float) * h->noise_n,
                                     cudaMemcpyHostToDevice, h->st));
-    oic_status s = step_impl(h, h->at<float>(L.xref), h->at<float>(L.uref), h->at<float>(L.noise),
-                             h->at<float>(L.uapp), h->at<float>(L.xnext));
+    oic_status s = OIC_OK;
+    if (!run_step_graph(h))
+        s = step_impl(h, h->at<float>(L.xref), h->at<float>(L.uref), h->at<float>(L.noise), h->at<float>(L.uapp),
+                      h->at<float>(L.xnext));
     if (s != OIC_OK) return s;
     if (U_applied)
         OIC_CUDA_OK(cudaMemcpyAsync(U_applied, h->at<float>(L.uapp), sizeof(float) * l * m,
@@ -755,6 +910,8 @@ void oic_destroy(oic_handle* h)
 {
     if (!h) return;
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+    h->sg[0].reset();
+    h->sg[1].reset();
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;

@@ -131,8 +131,10 @@ int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const flo
 void launch_tc_selftest(int* res, cudaStream_t st);
 
 // Philox-4x32-10 normal noise (Salmon et al., SC'11) for one solve.
+// Philox normals for one solve; the solve index is read from *solve_ctr
+// and then incremented on the device (two launches).
 void launch_philox_noise(float* out, size_t count_total, unsigned long long seed,
-                         unsigned long long counter_hi, const size_t* seg_end, const float* seg_sigma,
+                         unsigned long long* solve_ctr, const size_t* seg_end, const float* seg_sigma,
                          int n_seg, cudaStream_t st);
 
 }  // namespace oic

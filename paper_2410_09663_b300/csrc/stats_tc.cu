@@ -18,13 +18,16 @@
 // exponent range, so no scaling of rows is needed.
 //
 // Work split: CTA (row tile of 128 left rows, member split).  Eight
-// producer warps load each member's rows of the tile straight from the
-// ensemble (32 K values a stage), shift, split, accumulate the S1 sums and
-// store hi / lo into 128-byte-swizzled K-major tiles; a loader bulk-copies
-// the member's pre-split observation tile (written once per analysis by
-// yprep_kernel, which also writes the innovations D^i = Ybar_t - Y^i); one
-// thread issues the MMAs.  The issue order is K chunk outer, member inner,
-// so a producer keeps the member-0 row values of one chunk in registers.
+// producer warps stream each member's rows of the tile (32 K values a
+// stage) into a raw shared-memory ring with cp.async, RD - 1 stages ahead,
+// then shift, split, accumulate the S1 sums and store hi / lo into
+// 128-byte-swizzled K-major tiles; a loader bulk-copies the member's
+// pre-split observation tile; one thread issues the MMAs.  yprep_kernel
+// runs first, once per analysis: it writes the observation tiles, the
+// shifted observation rows e_i (the producers' source for left rows >= R,
+// so every left row is one plain row of some buffer) and the innovations
+// D^i = Ybar_t - Y^i.  The issue order is K chunk outer, member inner, so a
+// producer keeps the member-0 row values of one chunk in registers.
 #include <cuda_fp16.h>
 
 #include "oic_internal.cuh"
@@ -40,15 +43,18 @@ constexpr int ST_LOADER = ST_PW, ST_ISSUER = ST_PW + 1;
 constexpr int ST_NT = (ST_PW + 2) * 32;
 constexpr int ATILE = TM * 128;                         // one A part (hi or lo), bytes
 constexpr long long ST_WAIT = 4000000000LL;             // ~2 s at 2 GHz
+constexpr int RD = 4;                                   // raw ring depth (stages)
+constexpr int RTILE = TM * 128;                         // one raw stage, bytes
 
 // byte offset of (row r, 16-byte chunk k) in a 128-byte-swizzled K-major tile
 __host__ __device__ __forceinline__ int swz(int r, int k) { return r * 128 + ((k ^ (r & 7)) << 4); }
 
+// round to TF32 (10 stored mantissa bits), nearest with ties away from
+// zero: add half an ulp of the kept part to the magnitude bits, clear the
+// dropped 13 bits (a carry into the exponent is the correct rounding)
 __device__ __forceinline__ float tf32_rna(float x)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 __device__ __forceinline__ void split_tf32(const float4& d, float4& hi, float4& lo)
 {
@@ -74,10 +80,11 @@ __device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, in
 
 // One thread per (member, K chunk, observation row c < pp, 16-byte chunk):
 // e = Y^i - Y^0 split into the B tile [i][kh][hi rows pp | lo rows pp][128 B]
-// (swizzled; zero beyond p and beyond m), and D^i = Ybar - Y^i for c < p.
+// (swizzled; zero beyond p and beyond m); for c < p also e itself into
+// Ysh [i][c][m] and D^i = Ybar - Y^i.
 __global__ void yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, ObsNoise V,
                              const float* __restrict__ Yx, const float* __restrict__ Yu, int n_yx, int KH, int pp,
-                             float* __restrict__ Bop, float* __restrict__ Dbuf)
+                             float* __restrict__ Bop, float* __restrict__ Ysh, float* __restrict__ Dbuf)
 {
     const int p = obs.count;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,7 +100,9 @@ __global__ void yprep_kernel(const float* __restrict__ E, long ms, int N, int m,
     if (c < p && j < m) {
         const float4 y = yrow4(E, ms, m, obs, V, p, i, c, j);
         const float4 y0 = yrow4(E, ms, m, obs, V, p, 0, c, j);
-        split_tf32(f4sub(y, y0), hi, lo);
+        const float4 ev = f4sub(y, y0);
+        split_tf32(ev, hi, lo);
+        *reinterpret_cast<float4*>(Ysh + ((long)i * p + c) * m + j) = ev;
         const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
         *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + j) =
             f4sub(*reinterpret_cast<const float4*>(yb + j), y);
@@ -135,26 +144,35 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// a left row's source: member 0's row and the stride between members
+// (E rows, or the shifted observation rows, whose member-0 row is zero)
 struct RowSrc {
-    const float* e;      // E row for member 0
-    const float* v;      // noise row for member 0 (observation rows) or nullptr
-    long vs;             // noise stride between members
+    const float* e;
+    long stride;
     bool live;
 };
 
-__device__ __forceinline__ float4 load_unit(const RowSrc& s, long ms, int i, int j, int m)
+__device__ __forceinline__ float4 load_unit(const RowSrc& s, int i, int j, int m)
 {
     if (!s.live || j >= m) return make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 x = __ldg(reinterpret_cast<const float4*>(s.e + (long)i * ms + j));
-    if (s.v != nullptr) x = f4add(x, __ldg(reinterpret_cast<const float4*>(s.v + (long)i * s.vs + j)));
-    return x;
+    return __ldg(reinterpret_cast<const float4*>(s.e + (long)i * s.stride + j));
 }
+// 16 bytes global -> shared, asynchronous; zero-filled when !valid
+__device__ __forceinline__ void cp16(uint32_t dst, const float* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
-// ring of S stages: [A hi 16 KB][A lo 16 KB][B 2 pp x 128 B], 1024-aligned
+// ring of S stages: [A hi 16 KB][A lo 16 KB][B 2 pp x 128 B], 1024-aligned,
+// then the raw ring (RD x 16 KB), then the barriers
 __global__ void __launch_bounds__(ST_NT, 1)
-stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V,
-                const float* __restrict__ Bop, int pp, int KH, int S, int splits, int tmem_cols,
-                float* __restrict__ part1, float* __restrict__ part2, int* __restrict__ err)
+stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs,
+                const float* __restrict__ Ysh, const float* __restrict__ Bop, int pp, int KH, int S, int splits,
+                int tmem_cols, float* __restrict__ part1, float* __restrict__ part2, int* __restrict__ err)
 {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
@@ -162,7 +180,8 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
     unsigned char* smem = smem_raw + (s0 - raw);
     const int R = act.count, p = obs.count, M = R + p;
     const int STAGE = 2 * ATILE + 2 * pp * 128;
-    uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S * STAGE);   // full[S] bful[S] free[S] done
+    const uint32_t rawring = s0 + S * STAGE;
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S * STAGE + RD * RTILE);   // full bful free done
     uint64_t* full = mb;
     uint64_t* bful = mb + S;
     uint64_t* freeb = mb + 2 * S;
@@ -200,22 +219,28 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
         for (int u = 0; u < 4; ++u) {
             const int a = rt * TM + rb + 32 * u;
             src[u].live = a < M;
-            src[u].v = nullptr;
-            src[u].vs = 0;
             if (a < R) {
                 src[u].e = E + (long)act.rows[a] * m;
-            } else if (a < M) {
-                const int c = a - R;
-                src[u].e = E + (long)obs.rows[c] * m;
-                if (V.Va != nullptr) {
-                    src[u].v = c < V.pa ? V.Va + (long)c * m : V.Vb + (long)(c - V.pa) * m;
-                    src[u].vs = (long)(c < V.pa ? V.pa : p - V.pa) * m;
-                }
+                src[u].stride = ms;
             } else {
-                src[u].e = E;
+                src[u].e = Ysh + (long)(a < M ? a - R : 0) * m;
+                src[u].stride = (long)p * m;
             }
         }
-        float4 cur[4], nxt[4], v0[4], s1[4];
+        // raw ring: thread's unit u of stage q at raw(q % RD) + row * 128 + k * 16
+        auto issue = [&](int q) {
+            if (q < nst) {
+                const int kh = q / nmem, i = i0 + (q - kh * nmem), j = kh * KC + k * 4;
+                const uint32_t dst = rawring + (q % RD) * RTILE + rb * 128 + k * 16;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool v = src[u].live && j < m;
+                    cp16(dst + u * 32 * 128, v ? src[u].e + (long)i * src[u].stride + j : E, v);
+                }
+            }
+            cp_commit();                          // empty groups keep the count uniform
+        };
+        float4 v0[4], s1[4];
         auto flush = [&](int kh) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -223,27 +248,25 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
                 if (a < M && j < m) *reinterpret_cast<float4*>(part1 + ((long)sidx * M + a) * m + j) = s1[u];
             }
         };
-        if (nst > 0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) cur[u] = load_unit(src[u], ms, i0, k * 4, m);
-        }
+        for (int q = 0; q < RD - 1; ++q) issue(q);
         for (int q = 0; q < nst; ++q) {
             const int kh = q / nmem, qi = q - kh * nmem;
             const int j = kh * KC + k * 4;
-            if (q + 1 < nst) {
-                const int kh1 = (q + 1) / nmem;
-                const int i1n = i0 + (q + 1 - kh1 * nmem);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) nxt[u] = load_unit(src[u], ms, i1n, kh1 * KC + k * 4, m);
-            }
+            issue(q + RD - 1);
             if (qi == 0) {
                 if (kh > 0) flush(kh - 1);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    v0[u] = load_unit(src[u], ms, 0, j, m);
+                    v0[u] = load_unit(src[u], 0, j, m);
                     s1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
+            cp_wait<RD - 1>();                    // this thread's copies of stage q have landed
+            float4 cur[4];
+            const unsigned char* rq = smem + S * STAGE + (q % RD) * RTILE + rb * 128 + k * 16;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cur[u] = *reinterpret_cast<const float4*>(rq + u * 32 * 128);
             const int s = q % S;
             if (q >= S) {
                 bool ok = true;
@@ -270,9 +293,8 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(full + s);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) cur[u] = nxt[u];
         }
+        cp_wait<0>();
         if (!failed && nst > 0) flush(KH - 1);
 
         // ---- drain: warps w and w + 4 share TMEM lane quarter w % 4 and
@@ -349,7 +371,7 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
 int st_stages(int pp)
 {
     const size_t stage = 2 * (size_t)ATILE + (size_t)2 * pp * 128;
-    return 1024 + 3 * stage + 256 <= 232448 ? 3 : 2;
+    return 1024 + 3 * stage + RD * RTILE + 256 <= 232448 ? 3 : 2;
 }
 
 }  // namespace
@@ -357,17 +379,22 @@ int st_stages(int pp)
 int stats_tc_rtiles(int M) { return (M + TM - 1) / TM; }
 int stats_tc_pp(int p) { return (p + 15) / 16 * 16; }
 int stats_tc_kh(int m) { return (m + KC - 1) / KC; }
+// one wave of at most 148 CTAs, and at least ~6 members per split so the
+// partial sums stay small next to the products
 int stats_tc_splits(int M, int N)
 {
     int s = 148 / stats_tc_rtiles(M);
-    if (s > N) s = N;
+    if (s > N / 6) s = N / 6;
     return s < 1 ? 1 : s;
 }
-size_t stats_tc_bbytes(int N, int p, int m) { return (size_t)N * stats_tc_kh(m) * 2 * stats_tc_pp(p) * 128; }
+size_t stats_tc_bbytes(int N, int p, int m)
+{
+    return (size_t)N * stats_tc_kh(m) * 2 * stats_tc_pp(p) * 128 + (size_t)N * p * m * sizeof(float);
+}
 size_t stats_tc_smem(int p)
 {
     const int pp = stats_tc_pp(p);
-    return 1024 + (size_t)st_stages(pp) * (2 * (size_t)ATILE + (size_t)2 * pp * 128) + 256;
+    return 1024 + (size_t)st_stages(pp) * (2 * (size_t)ATILE + (size_t)2 * pp * 128) + RD * RTILE + 256;
 }
 bool stats_tc_supported(int m, int p)
 {
@@ -380,14 +407,15 @@ void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet o
 {
     const int p = obs.count, M = act.count + p, pp = stats_tc_pp(p), KH = stats_tc_kh(m);
     const long nprep = (long)N * KH * pp * 8;
+    float* Ysh = Bop + (size_t)N * KH * 2 * pp * 32;      // after the observation tiles
     yprep_kernel<<<(unsigned)((nprep + 255) / 256), 256, 0, st>>>(E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop,
-                                                                  Dbuf);
+                                                                  Ysh, Dbuf);
     const int S = st_stages(pp);
     const int cols = pp <= 32 ? 32 : pp <= 64 ? 64 : pp <= 128 ? 128 : 256;
     const size_t smem = stats_tc_smem(p);
     cudaFuncSetAttribute(stats_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    stats_tc_kernel<<<dim3(stats_tc_rtiles(M), splits), ST_NT, smem, st>>>(E, ms, N, m, act, obs, V, Bop, pp, KH, S,
-                                                                           splits, cols, part1, part2, err);
+    stats_tc_kernel<<<dim3(stats_tc_rtiles(M), splits), ST_NT, smem, st>>>(E, ms, N, m, act, obs, Ysh, Bop, pp, KH,
+                                                                           S, splits, cols, part1, part2, err);
 }
 
 }  // namespace oic

@@ -161,6 +161,43 @@ def test_philox_mode_matches_oracle_fed_host_philox(cuda_ok):
         assert rel(Xn, X) <= TOL
 
 
+def _philox_steps(wl, steps, profile=None):
+    s = solver(wl, noise_mode=oic.OIC_NOISE_PHILOX, seed=99)
+    xr_all = wl.X_ref_all(steps)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    if profile is not None:
+        s.oic_profile_begin(stages=profile, max_launches=4096)
+    out = []
+    for k in range(steps):
+        Ua = np.zeros((wl.l, wl.m), np.float32)
+        Xn = np.zeros((wl.n, wl.m), np.float32)
+        s.oic_step_host(xr_all[k:k + wl.H + 1], wl.U_ref(), None, Ua, Xn)
+        out.append((Ua, Xn))
+    prof = s.oic_profile_end() if profile is not None else None
+    s.close()
+    return out, prof
+
+
+@pytest.mark.parametrize("name", ["small_16", "working_64_n32"])
+def test_step_graph_replays_match_eager_launches(cuda_ok, name, monkeypatch):
+    """A control step replayed from its CUDA graph (plain, and with the
+    profiling event nodes re-pointed before each replay) gives bit-identical
+    controls and states to the same step launched kernel by kernel; the
+    device-side solve index advances the Philox stream on every replay."""
+    wl = W.small_16() if name == "small_16" else W.working_64().with_(N=32, H=3)
+    graph, _ = _philox_steps(wl, 3)
+    profiled, prof = _philox_steps(wl, 3, profile=["cov", "gain"])
+    monkeypatch.setenv("OIC_NO_GRAPH", "1")
+    eager, _ = _philox_steps(wl, 3)
+    for (ga, gx), (pa, px), (ea, ex) in zip(graph, profiled, eager):
+        assert np.array_equal(ga, ea) and np.array_equal(gx, ex)
+        assert np.array_equal(pa, ea) and np.array_equal(px, ex)
+    assert not np.array_equal(graph[0][0], graph[1][0])    # fresh noise each step
+    assert prof["cov"][1] == 3 * wl.H and prof["gain"][1] == 3 * wl.H
+    assert prof["cov"][0] > 0 and prof["gain"][0] > 0
+    assert set(prof) == {"cov", "gain"}
+
+
 @pytest.mark.parametrize("precision", [oic.OIC_PREC_FP32, oic.OIC_PREC_MIXED])
 def test_enks_update_matches_oracle(cuda_ok, precision):
     """FP32 mode: FP32 gain by elimination; mixed mode: FP64 mean correction,
