@@ -287,20 +287,18 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
 // ------------------------------------------------------------------ gain
 // K = Cxy Cyy^{-1}, written transposed: Kt = K^T = Cyy^{-1} Cxy^T, [p][R].
 //
-// Gauss-Jordan elimination on [Cyy | Cxy^T] without pivoting, FP32, the
-// matrix held in registers.  Cyy is symmetric positive definite, so the
-// pivots are the Schur complements (the squares of the Cholesky diagonal; no
-// growth, no pivoting needed) and a pivot <= 0 means "not positive definite".
-// Rows are never normalised: step j subtracts A[i][j] / A[j][j] times row j
-// from every row i != j.  At the end the left block is diagonal and
-// Kt[c][a] = A[c][p + a] / A[c][c].
-//
-// Warp w owns rows w + RG k (k < RPT), lane t owns columns t + 32 q (q < CPT);
-// per step only pivot column j and pivot row j go through shared memory
-// (double-buffered, so one barrier per step).  CTA b takes the right-hand
-// sides a in [b RC, (b+1) RC), RC = 32 CPT - p, and eliminates Cyy itself.
-// Register slots picked by the runtime step go through select chains, so
-// the loop body exists once (the kernel is bound by instruction issue).
+// Cyy = U^T U (Cholesky, FP32), then per gain row a: U^T z = Cxy[a]^T
+// (forward) and U k = z (backward), Kt[.][a] = k.  Each CTA (8 warps)
+// factors Cyy itself in shared memory, blocked by panels of 8 rows: warp 0
+// factors the panel in registers (lane = column; pivots and multipliers by
+// shuffles; a pivot <= 0 means "not positive definite") and writes the U
+// rows and their transpose L = U^T; then all warps apply the rank-8 update
+// A[i][c] -= sum_d U[j0+d][i] U[j0+d][c] to the trailing rows, two rows at a
+// time (two barriers per panel).  Both substitutions then read rows (U for
+// the forward pass, L for the backward one).  Warp w solves gain row
+// a = 8 b + w: lane t holds elements t + 32 s (s < SL); eight elements are
+// eliminated per block (shuffles to every lane, the 8 x 8 diagonal block
+// solved in registers, one 8-term update of the rest).
 template <int N>
 __device__ __forceinline__ float gsel(const float (&v)[N], int q)
 {
@@ -310,108 +308,261 @@ __device__ __forceinline__ float gsel(const float (&v)[N], int q)
     return r;
 }
 
-template <int RPT, int CPT, int RG>
-__global__ void __launch_bounds__(32 * RG, 1)
-gain_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
+constexpr int GC_W = 8;                           // warps per CTA = gain rows per CTA
+constexpr int GC_B = 8;                           // panel height = substitution block
+
+// 8-element block of a substitution: the lanes l0 .. l0+7 of slot `slot`
+// hold the block's right-hand sides; every lane receives them.
+template <int SL>
+__device__ __forceinline__ void block_gather(const float (&b)[SL], int slot, int l0, float (&z)[GC_B])
 {
-    constexpr int NT = 32 * RG, NCOL = 32 * CPT, NROW = RPT * RG;
+    const float bs = gsel<SL>(b, slot);
+#pragma unroll
+    for (int d = 0; d < GC_B; ++d) z[d] = __shfl_sync(0xffffffffu, bs, l0 + d);
+}
+template <int SL>
+__device__ __forceinline__ void block_put(float (&b)[SL], int slot, int l0, int lane, const float (&z)[GC_B])
+{
+    float v = z[0];
+#pragma unroll
+    for (int d = 1; d < GC_B; ++d) v = lane - l0 == d ? z[d] : v;
+#pragma unroll
+    for (int s = 0; s < SL; ++s)
+        if (s == slot && lane >= l0 && lane < l0 + GC_B) b[s] = v;
+}
+
+template <int SL>
+__global__ void __launch_bounds__(32 * GC_W)
+gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
+{
     extern __shared__ __align__(16) float gsm[];
-    float* stage = gsm;                           // [NROW][NCOL]: [Cyy | Cxy^T slice] as FP32
-    float (*colbuf)[NROW] = reinterpret_cast<float (*)[NROW]>(gsm + NROW * NCOL);
-    float (*rowbuf)[NCOL] = reinterpret_cast<float (*)[NCOL]>(gsm + NROW * NCOL + 2 * NROW);
-    float* diag = gsm + NROW * NCOL + 2 * NROW + 2 * NCOL;
-    const int RC = NCOL - p;
-    const int a0 = blockIdx.x * RC;
-    const int nr = R - a0 < RC ? R - a0 : RC;
-    const int W = p + nr;
-    const int tid = threadIdx.x, w = tid / 32, t = tid % 32;
+    constexpr int NT = 32 * GC_W;
+    const int pp = (p + GC_B - 1) & ~(GC_B - 1);  // whole panels (zero rows, rinv 0)
+    const int ld = pp | 1;
+    float* A = gsm;                               // [pp][ld]: Cyy, then U (upper rows)
+    float* L = gsm + pp * ld;                     // [pp][ld]: L = U^T
+    float* rinv = L + pp * ld;                    // [pp]: 1 / U[j][j]
+    __shared__ int bad;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const double* Cyy = C + (long)R * p;
-    // coalesced reads: Cyy row by row, the Cxy rows of this slice row by row
-    // (stored transposed); everything else zero
-    for (int e = tid; e < NROW * NCOL; e += NT) stage[e] = 0.f;
-    __syncthreads();
-    for (int e = tid; e < p * p; e += NT) stage[(e / p) * NCOL + e % p] = (float)Cyy[e];
-    for (int e = tid; e < nr * p; e += NT) stage[(e % p) * NCOL + p + e / p] = (float)C[(long)a0 * p + e];
-    __syncthreads();
-    float A[RPT][CPT];
-#pragma unroll
-    for (int k = 0; k < RPT; ++k)
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) A[k][q] = stage[(w + RG * k) * NCOL + t + 32 * q];
-    // owners of column j / row j publish them
-    auto publish = [&](int j, int buf) {
-        if ((j & 31) == t) {
-            const int qs = j / 32;
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) colbuf[buf][w + RG * k] = gsel<CPT>(A[k], qs);
+    // staging: zero the padding, then Cyy as 16-byte pairs (p even) with
+    // every load of a thread in flight at once
+    if (pp > p)
+        for (int e = tid; e < pp * ld; e += NT) {
+            const int i = e / ld, c = e % ld;
+            if (i >= p || c >= p) A[e] = 0.f;
         }
-        if (j % RG == w) {
-            const int ks = j / RG;
+    if ((p & 1) == 0 && ((R * p) & 1) == 0) {
+        const double2* C2 = reinterpret_cast<const double2*>(Cyy);
+        const int np = p * p / 2;
+        for (int q0 = tid; q0 < np; q0 += NT * 12) {
+            double2 v[12];
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                float v = A[0][q];
+            for (int u = 0; u < 12; ++u) {
+                const int q = q0 + NT * u;
+                v[u] = q < np ? __ldg(C2 + q) : make_double2(0.0, 0.0);
+            }
 #pragma unroll
-                for (int k = 1; k < RPT; ++k) v = ks == k ? A[k][q] : v;
-                rowbuf[buf][t + 32 * q] = v;
+            for (int u = 0; u < 12; ++u) {
+                const int q = q0 + NT * u;
+                if (q < np) {
+                    const int i = (2 * q) / p, c = (2 * q) % p;
+                    A[i * ld + c] = (float)v[u].x;
+                    A[i * ld + c + 1] = (float)v[u].y;
+                }
             }
         }
-    };
-    publish(0, 0);
+    } else {
+        for (int e = tid; e < p * p; e += NT) A[(e / p) * ld + e % p] = (float)__ldg(Cyy + e);
+    }
+    if (tid == 0) bad = 0;
     __syncthreads();
-    bool bad = false;
-    for (int j = 0; j < p; ++j) {
-        const int buf = j & 1;
-        const float piv = rowbuf[buf][j];
-        if (!(piv > 0.f)) { bad = true; break; }   // same value in every thread
-        const float ipiv = __fdividef(1.f, piv);
-        float rj[CPT];
+    for (int j0 = 0; j0 < pp; j0 += GC_B) {
+        if (w == 0) {
+            // panel rows j0 .. j0+7 in registers, lane = column (slots s)
+            float P[GC_B][SL];
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) rj[q] = rowbuf[buf][t + 32 * q];
+            for (int d = 0; d < GC_B; ++d)
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            const int i = w + RG * k;
-            const float f = (i == j) ? 0.f : colbuf[buf][i] * ipiv;
+                for (int s = 0; s < SL; ++s) {
+                    const int c = lane + 32 * s;
+                    P[d][s] = c < pp ? A[(j0 + d) * ld + c] : 0.f;
+                }
+            const int slot = j0 >> 5, l0 = j0 & 31;
+            bool badp = false;
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) A[k][q] = fmaf(-f, rj[q], A[k][q]);
+            for (int d = 0; d < GC_B; ++d) {
+                // row d as it stands: its pivot and the multipliers of the rows below
+                const float ds = gsel<SL>(P[d], slot);
+                float rowd[GC_B];
+#pragma unroll
+                for (int e = d; e < GC_B; ++e) rowd[e] = __shfl_sync(0xffffffffu, ds, l0 + e);
+                const float piv = rowd[d];
+                float rs = 0.f, ip = 0.f;             // padding rows: zero
+                if (j0 + d < p) {
+                    if (!(piv > 0.f)) badp = true;
+                    rs = piv > 0.f ? rsqrtf(piv) : 0.f;
+                    ip = rs * rs;
+                }
+#pragma unroll
+                for (int e = d + 1; e < GC_B; ++e) {
+                    const float f = rowd[e] * ip;
+#pragma unroll
+                    for (int s = 0; s < SL; ++s) P[e][s] = fmaf(-f, P[d][s], P[e][s]);
+                }
+#pragma unroll
+                for (int s = 0; s < SL; ++s) P[d][s] *= rs;
+                if (lane == 0) rinv[j0 + d] = rs;
+            }
+#pragma unroll
+            for (int d = 0; d < GC_B; ++d)
+#pragma unroll
+                for (int s = 0; s < SL; ++s) {
+                    const int c = lane + 32 * s;
+                    if (c >= j0 + d && c < pp) {
+                        A[(j0 + d) * ld + c] = P[d][s];
+                        L[c * ld + j0 + d] = P[d][s];
+                    }
+                }
+            if (badp && lane == 0) bad = 1;
         }
-        if (j + 1 < p) publish(j + 1, buf ^ 1);
+        __syncthreads();
+        if (bad) break;
+        // rank-8 update of rows i >= j0 + 8, columns c >= i, two rows at a time
+        const int t0 = j0 + GC_B;
+        if (t0 < p) {
+            float pc[SL][GC_B];
+#pragma unroll
+            for (int s = 0; s < SL; ++s) {
+                const int c = t0 + lane + 32 * s;
+#pragma unroll
+                for (int d = 0; d < GC_B; ++d) pc[s][d] = c < p ? L[c * ld + j0 + d] : 0.f;
+            }
+            for (int i = t0 + 2 * w; i < p; i += 2 * GC_W) {
+                const int i1 = i + 1 < p ? i + 1 : i;
+                float pi0[GC_B], pi1[GC_B];
+#pragma unroll
+                for (int d = 0; d < GC_B; ++d) {
+                    pi0[d] = L[i * ld + j0 + d];
+                    pi1[d] = L[i1 * ld + j0 + d];
+                }
+                float* a0 = A + i * ld;
+                float* a1 = A + i1 * ld;
+#pragma unroll
+                for (int s = 0; s < SL; ++s) {
+                    const int c = t0 + lane + 32 * s;
+                    const bool ok = c < p;
+                    const float x0 = ok && c >= i ? a0[c] : 0.f;
+                    const float x1 = ok && c >= i1 && i1 != i ? a1[c] : 0.f;
+                    float y0 = 0.f, y1 = 0.f, z0 = 0.f, z1 = 0.f;
+#pragma unroll
+                    for (int d = 0; d < GC_B; d += 2) {
+                        y0 = fmaf(pi0[d], pc[s][d], y0);
+                        z0 = fmaf(pi0[d + 1], pc[s][d + 1], z0);
+                        y1 = fmaf(pi1[d], pc[s][d], y1);
+                        z1 = fmaf(pi1[d + 1], pc[s][d + 1], z1);
+                    }
+                    if (ok && c >= i) a0[c] = x0 - (y0 + z0);
+                    if (ok && c >= i1 && i1 != i) a1[c] = x1 - (y1 + z1);
+                }
+            }
+        }
         __syncthreads();
     }
+    const int a = blockIdx.x * GC_W + w;
     if (bad) {
         if (tid == 0) atomicExch(status, DEV_NOTSPD);
-        for (int e = tid; e < nr * p; e += NT) Kt[(long)(e / nr) * R + a0 + e % nr] = 0.f;
+        if (a < R)
+            for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
         return;
     }
-    // diagonal of the eliminated block, then Kt[i][a0 + c - p] = A[i][c] / A[i][i]
+    if (a >= R) return;
+
+    float b[SL];
 #pragma unroll
-    for (int k = 0; k < RPT; ++k)
+    for (int s = 0; s < SL; ++s) {
+        const int i = lane + 32 * s;
+        b[s] = i < p ? (float)__ldg(C + (long)a * p + i) : 0.f;
+    }
+    // forward: U^T z = b, blocks of eight from the top
+    for (int k0 = 0; k0 < pp; k0 += GC_B) {
+        const int slot = k0 >> 5, l0 = k0 & 31;
+        float z[GC_B];
+        block_gather<SL>(b, slot, l0, z);
 #pragma unroll
-        for (int q = 0; q < CPT; ++q)
-            if (w + RG * k == t + 32 * q) diag[w + RG * k] = A[k][q];
-    __syncthreads();
+        for (int d = 0; d < GC_B; ++d) {
+            const float* ud = A + (k0 + d) * ld;
+            z[d] *= rinv[k0 + d];
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int i = w + RG * k;
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int c = t + 32 * q;
-            if (i < p && c >= p && c < W) Kt[(long)i * R + a0 + c - p] = A[k][q] / diag[i];
+            for (int e = d + 1; e < GC_B; ++e) z[e] = fmaf(-ud[k0 + e], z[d], z[e]);
         }
+        block_put<SL>(b, slot, l0, lane, z);
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            const int i = lane + 32 * s;
+            if (i >= k0 + GC_B && i < pp) {
+                float y = 0.f, x = 0.f;
+#pragma unroll
+                for (int d = 0; d < GC_B; d += 2) {
+                    y = fmaf(A[(k0 + d) * ld + i], z[d], y);
+                    x = fmaf(A[(k0 + d + 1) * ld + i], z[d + 1], x);
+                }
+                b[s] -= y + x;
+            }
+        }
+    }
+    // backward: U k = z, blocks of eight from the bottom
+    for (int k0 = pp - GC_B; k0 >= 0; k0 -= GC_B) {
+        const int slot = k0 >> 5, l0 = k0 & 31;
+        float x[GC_B];
+        block_gather<SL>(b, slot, l0, x);
+#pragma unroll
+        for (int d = GC_B - 1; d >= 0; --d) {
+            x[d] *= rinv[k0 + d];
+            const float* ld_row = L + (k0 + d) * ld;   // L[k0+d][k0+e] = U[k0+e][k0+d]
+#pragma unroll
+            for (int e = 0; e < d; ++e) x[e] = fmaf(-ld_row[k0 + e], x[d], x[e]);
+        }
+        block_put<SL>(b, slot, l0, lane, x);
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            const int i = lane + 32 * s;
+            if (i < k0) {
+                float y = 0.f, v = 0.f;
+#pragma unroll
+                for (int d = 0; d < GC_B; d += 2) {
+                    y = fmaf(L[(k0 + d) * ld + i], x[d], y);
+                    v = fmaf(L[(k0 + d + 1) * ld + i], x[d + 1], v);
+                }
+                b[s] -= y + v;
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int i = lane + 32 * s;
+        if (i < p) Kt[(long)i * R + a] = b[s];
     }
 }
 
-template <int RPT, int CPT, int RG>
-void gain_launch(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
+size_t gain_chol_smem(int p)
 {
-    constexpr int NCOL = 32 * CPT, NROW = RPT * RG;
-    const size_t smem = sizeof(float) * ((size_t)NROW * NCOL + 3 * NROW + 2 * NCOL);
+    const int pp = (p + GC_B - 1) & ~(GC_B - 1), ld = pp | 1;
+    return sizeof(float) * ((size_t)2 * pp * ld + pp);
+}
+
+template <int SL>
+void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st)
+{
+    const size_t smem = gain_chol_smem(p);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(gain_kernel<RPT, CPT, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(gain_chol_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gain_chol_smem(32 * SL));
         attr_set = true;
     }
-    const int RC = NCOL - p, grid = (R + RC - 1) / RC;
-    gain_kernel<RPT, CPT, RG><<<grid > 0 ? grid : 1, 32 * RG, smem, st>>>(C, R, p, K, status);
+    const int grid = (R + GC_W - 1) / GC_W;
+    gain_chol_kernel<SL><<<grid > 0 ? grid : 1, 32 * GC_W, smem, st>>>(C, R, p, Kt, status);
 }
 
 // ---------------------------------------------------------------- update
@@ -691,10 +842,13 @@ int gain_max_p() { return 144; }
 
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
 {
-    // rows = 16 warps x 5 (p <= 80, 128 columns) or 16 warps x 9 (p <= 144,
-    // 256 columns); the columns beyond p carry right-hand sides
-    if (p <= 80) gain_launch<5, 4, 16>(C, R, p, K, status, st);
-    else gain_launch<9, 8, 16>(C, R, p, K, status, st);
+    switch ((p + 31) / 32) {
+    case 1: gain_chol_launch<1>(C, R, p, K, status, st); break;
+    case 2: gain_chol_launch<2>(C, R, p, K, status, st); break;
+    case 3: gain_chol_launch<3>(C, R, p, K, status, st); break;
+    case 4: gain_chol_launch<4>(C, R, p, K, status, st); break;
+    default: gain_chol_launch<5>(C, R, p, K, status, st); break;
+    }
 }
 
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
