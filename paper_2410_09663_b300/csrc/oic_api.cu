@@ -58,7 +58,7 @@ struct StepGraph {
 };
 
 struct Layout {
-    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, tB, ctr, rowtab, status, selftest;
+    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, tB, tAop, tBd, ctr, rowtab, status, selftest;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -222,6 +222,10 @@ void compute_layout(oic_handle* h)
     L.L64 = take(c.precision == OIC_PREC_MIXED ? sizeof(double) * p * p : 0);
     // tensor-core anomaly products: the pre-split observation tiles
     L.tB = take(stats_tc_supported(c.m, (int)p) ? stats_tc_bbytes(c.N, (int)p, c.m) : 0);
+    // tensor-core update: gain tiles and the transposed innovations
+    const bool utc = stats_tc_supported(c.m, (int)p) && update_tc_supported(c.m, (int)p);
+    L.tAop = take(utc ? update_tc_abytes((int)Ra, (int)p) : 0);
+    L.tBd = take(utc ? update_tc_bbytes(c.N, c.m, (int)p) : 0);
     L.ctr = take(sizeof(unsigned long long));            // Philox solve index
     L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
     L.status = take(64);
@@ -320,11 +324,14 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
     float* Kt = h->at<float>(h->lay.K);
     const int R = act.count, p = obs.count, M = R + p;
     const bool mixed = c.precision == OIC_PREC_MIXED;
-    if (stats_tc_supported(c.m, p)) {
+    const bool tcs = stats_tc_supported(c.m, p);
+    const bool utc = tcs && update_tc_supported(c.m, p);
+    float* Bd = utc ? h->at<float>(h->lay.tBd) : nullptr;
+    if (tcs) {
         const int splits = stats_tc_splits(M, c.N);
         run_stage(h, OIC_STAGE_COV, [&] {
-            launch_stats_tc(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, h->at<float>(h->lay.tB), part1, part2, D,
-                            splits, h->at<int>(h->lay.status), h->st);
+            launch_stats_tc(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, h->at<float>(h->lay.tB), part1, part2,
+                            utc ? nullptr : D, Bd, splits, h->at<int>(h->lay.status), h->st);
         });
         run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
         run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
@@ -347,7 +354,13 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
         else
             launch_gain(C, R, p, Kt, h->at<int>(h->lay.status), h->st);
     });
-    run_stage(h, OIC_STAGE_UPDATE, [&] { launch_update(E, ms, c.N, c.m, act, Kt, p, D, h->st); });
+    if (utc)
+        run_stage(h, OIC_STAGE_UPDATE, [&] {
+            launch_update_tc(E, ms, c.N, c.m, act, Kt, p, h->at<float>(h->lay.tAop), Bd, h->at<int>(h->lay.status),
+                             h->st);
+        });
+    else
+        run_stage(h, OIC_STAGE_UPDATE, [&] { launch_update(E, ms, c.N, c.m, act, Kt, p, D, h->st); });
 }
 
 oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,

@@ -74,9 +74,19 @@ void launch_cov_finalize(const float* part2, const float* S1, int splits, int R,
 bool stats_tc_supported(int m, int p);
 int stats_tc_splits(int M, int N);
 size_t stats_tc_bbytes(int N, int p, int m);
+// The innovations go to Dbuf (plain [i][c][m]) or, when Bd is given, to
+// the tensor-core update's operand (launch_update_tc).
 void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
-                     const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, int splits,
-                     int* err, cudaStream_t st);
+                     const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, float* Bd,
+                     int splits, int* err, cudaStream_t st);
+
+// Member update on the tensor cores: E[act rows] += K D from Kt [p][R] and
+// the operand tiles yprep wrote (Bd); Aop: update_tc_abytes of scratch.
+bool update_tc_supported(int m, int p);
+size_t update_tc_abytes(int Rmax, int p);
+size_t update_tc_bbytes(int N, int m, int p);
+void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop,
+                      const float* Bd, int* err, cudaStream_t st);
 // Mixed-precision gain: FP64 Cholesky of Cyy (one CTA) into L [p][p], then
 // FP64 triangular solves per row of Cxy; bad: device flag (not SPD).
 void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st);

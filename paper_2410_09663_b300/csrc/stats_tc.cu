@@ -32,9 +32,12 @@
 
 #include "oic_internal.cuh"
 #include "tc_sm103.cuh"
+#include "tc_tf32.cuh"
 
 namespace oic {
 namespace {
+
+using namespace tf32;
 
 constexpr int TM = 128;                                 // left rows per tile (MMA M)
 constexpr int KC = 32;                                  // K values per stage: one 128-byte row
@@ -45,26 +48,6 @@ constexpr int ATILE = TM * 128;                         // one A part (hi or lo)
 constexpr long long ST_WAIT = 4000000000LL;             // ~2 s at 2 GHz
 constexpr int RD = 4;                                   // raw ring depth (stages)
 constexpr int RTILE = TM * 128;                         // one raw stage, bytes
-
-// byte offset of (row r, 16-byte chunk k) in a 128-byte-swizzled K-major tile
-__host__ __device__ __forceinline__ int swz(int r, int k) { return r * 128 + ((k ^ (r & 7)) << 4); }
-
-// round to TF32 (10 stored mantissa bits), nearest with ties away from
-// zero: add half an ulp of the kept part to the magnitude bits, clear the
-// dropped 13 bits (a carry into the exponent is the correct rounding)
-__device__ __forceinline__ float tf32_rna(float x)
-{
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-__device__ __forceinline__ void split_tf32(const float4& d, float4& hi, float4& lo)
-{
-    hi.x = tf32_rna(d.x); lo.x = tf32_rna(d.x - hi.x);
-    hi.y = tf32_rna(d.y); lo.y = tf32_rna(d.y - hi.y);
-    hi.z = tf32_rna(d.z); lo.z = tf32_rna(d.z - hi.z);
-    hi.w = tf32_rna(d.w); lo.w = tf32_rna(d.w - hi.w);
-}
-__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 
 // Observation row c of member i, columns j .. j+3 (E row plus noise).
 __device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, int m, const RowSet& obs,
@@ -78,70 +61,69 @@ __device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, in
     return v;
 }
 
-// One thread per (member, K chunk, observation row c < pp, 16-byte chunk):
-// e = Y^i - Y^0 split into the B tile [i][kh][hi rows pp | lo rows pp][128 B]
-// (swizzled; zero beyond p and beyond m); for c < p also e itself into
-// Ysh [i][c][m] and D^i = Ybar - Y^i.
-__global__ void yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, ObsNoise V,
-                             const float* __restrict__ Yx, const float* __restrict__ Yu, int n_yx, int KH, int pp,
-                             float* __restrict__ Bop, float* __restrict__ Ysh, float* __restrict__ Dbuf)
+// One block per (member i, K chunk kh of 32 columns j); thread units
+// (observation row c < pp, 16-byte chunk): e = Y^i - Y^0 split into the B
+// tile [i][kh][hi rows pp | lo rows pp][128 B] (swizzled; zero beyond p and
+// beyond m); for c < p also e itself into Ysh [i][c][m].  The innovations
+// D^i = Ybar - Y^i go either plainly to Dbuf [i][c][m] or, through a
+// transpose in shared memory, to the member update's operand Bd: rows
+// n = i m + j, K = c in chunks of 32, [kc][hi | lo][N m rows][128 B]
+// (swizzled, zero beyond p).
+__global__ void __launch_bounds__(256)
+yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, ObsNoise V,
+             const float* __restrict__ Yx, const float* __restrict__ Yu, int n_yx, int KH, int pp,
+             float* __restrict__ Bop, float* __restrict__ Ysh, float* __restrict__ Dbuf, float* __restrict__ Bd,
+             int KCD)
 {
+    extern __shared__ float Ds[];                 // [32][ldd]: D transposed, [j][c]
     const int p = obs.count;
-    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long per_member = (long)KH * pp * 8;
-    if (e >= (long)N * per_member) return;
-    const int i = (int)(e / per_member);
-    int rem = (int)(e % per_member);
-    const int kh = rem / (pp * 8);
-    rem %= pp * 8;
-    const int c = rem / 8, k = rem % 8;
-    const int j = kh * KC + k * 4;
-    float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
-    if (c < p && j < m) {
-        const float4 y = yrow4(E, ms, m, obs, V, p, i, c, j);
-        const float4 y0 = yrow4(E, ms, m, obs, V, p, 0, c, j);
-        const float4 ev = f4sub(y, y0);
-        split_tf32(ev, hi, lo);
-        *reinterpret_cast<float4*>(Ysh + ((long)i * p + c) * m + j) = ev;
-        const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
-        *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + j) =
-            f4sub(*reinterpret_cast<const float4*>(yb + j), y);
-    }
+    const int i = blockIdx.x / KH, kh = blockIdx.x % KH;
+    const int ldd = 32 * KCD + 1;
+    if (Bd != nullptr)
+        for (int e = threadIdx.x; e < 32 * (32 * KCD - pp); e += 256) {
+            const int jj = e / (32 * KCD - pp), c = pp + e % (32 * KCD - pp);
+            Ds[jj * ldd + c] = 0.f;
+        }
     char* tile = reinterpret_cast<char*>(Bop) + ((size_t)i * KH + kh) * (size_t)(2 * pp) * 128;
-    *reinterpret_cast<float4*>(tile + swz(c, k)) = hi;
-    *reinterpret_cast<float4*>(tile + swz(pp + c, k)) = lo;
-}
-
-__device__ __forceinline__ void st_expect_tx(uint64_t* mbar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void st_bulk(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
-                 : "memory");
-}
-// K-major, 128-byte swizzle: SBO = 1024 B between 8-row groups, LBO unused
-// (1), descriptor version bit 46, layout type 2 in bits 61-63.
-constexpr uint32_t SW_DESC_HI = (1024u >> 4) | (1u << 14) | (2u << 29);
-__device__ __forceinline__ uint32_t sw_desc(uint32_t saddr) { return ((saddr & 0x3FFFFu) >> 4) | (1u << 16); }
-__device__ __forceinline__ void st_mma(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .b64 da, db;\n\t.reg .pred p;\n\t"
-        "mov.b64 da, {%1, %5};\n\t"
-        "mov.b64 db, {%2, %5};\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %3, p;\n\t}\n" ::"r"(d),
-        "r"(a), "r"(b), "r"(idesc), "r"(acc), "r"(SW_DESC_HI)
-        : "memory");
-}
-// instruction descriptor: TF32 A and B (format 2), FP32 D, K-major, N, M
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    for (int e = threadIdx.x; e < pp * 8; e += 256) {
+        const int c = e / 8, k = e % 8;
+        const int j = kh * KC + k * 4;
+        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi, d = hi;
+        if (c < p && j < m) {
+            const float4 y = yrow4(E, ms, m, obs, V, p, i, c, j);
+            const float4 y0 = yrow4(E, ms, m, obs, V, p, 0, c, j);
+            const float4 ev = f4sub(y, y0);
+            split_tf32(ev, hi, lo);
+            *reinterpret_cast<float4*>(Ysh + ((long)i * p + c) * m + j) = ev;
+            const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
+            d = f4sub(*reinterpret_cast<const float4*>(yb + j), y);
+            if (Dbuf != nullptr) *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + j) = d;
+        }
+        if (Bd != nullptr) {
+            Ds[(k * 4 + 0) * ldd + c] = d.x;
+            Ds[(k * 4 + 1) * ldd + c] = d.y;
+            Ds[(k * 4 + 2) * ldd + c] = d.z;
+            Ds[(k * 4 + 3) * ldd + c] = d.w;
+        }
+        *reinterpret_cast<float4*>(tile + swz(c, k)) = hi;
+        *reinterpret_cast<float4*>(tile + swz(pp + c, k)) = lo;
+    }
+    if (Bd == nullptr) return;
+    __syncthreads();
+    const long NM = (long)N * m;
+    char* bd = reinterpret_cast<char*>(Bd);
+    for (int e = threadIdx.x; e < 32 * KCD * 8; e += 256) {
+        const int jj = e / (KCD * 8), kc = (e / 8) % KCD, q = e % 8;
+        const int j = kh * KC + jj;
+        if (j >= m) continue;
+        const long n = (long)i * m + j;
+        const float* src = Ds + jj * ldd + kc * 32 + q * 4;
+        float4 hi, lo;
+        split_tf32(make_float4(src[0], src[1], src[2], src[3]), hi, lo);
+        const int off = (int)((n & 7) ^ q) << 4;
+        *reinterpret_cast<float4*>(bd + ((size_t)(2 * kc) * NM + n) * 128 + off) = hi;
+        *reinterpret_cast<float4*>(bd + ((size_t)(2 * kc + 1) * NM + n) * 128 + off) = lo;
+    }
 }
 
 // a left row's source: member 0's row and the stride between members
@@ -402,14 +384,14 @@ bool stats_tc_supported(int m, int p)
 }
 
 void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
-                     const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, int splits,
-                     int* err, cudaStream_t st)
+                     const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, float* Bd,
+                     int splits, int* err, cudaStream_t st)
 {
     const int p = obs.count, M = act.count + p, pp = stats_tc_pp(p), KH = stats_tc_kh(m);
-    const long nprep = (long)N * KH * pp * 8;
+    const int KCD = (p + 31) / 32;
     float* Ysh = Bop + (size_t)N * KH * 2 * pp * 32;      // after the observation tiles
-    yprep_kernel<<<(unsigned)((nprep + 255) / 256), 256, 0, st>>>(E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop,
-                                                                  Ysh, Dbuf);
+    const size_t ysm = Bd != nullptr ? sizeof(float) * 32 * (32 * KCD + 1) : 0;
+    yprep_kernel<<<N * KH, 256, ysm, st>>>(E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop, Ysh, Dbuf, Bd, KCD);
     const int S = st_stages(pp);
     const int cols = pp <= 32 ? 32 : pp <= 64 ? 64 : pp <= 128 ? 128 : 256;
     const size_t smem = stats_tc_smem(p);
