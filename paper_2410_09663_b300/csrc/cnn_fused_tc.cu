@@ -287,6 +287,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                  const float* __restrict__ b1, const float* __restrict__ b2, const float* __restrict__ b3,
                  const __half* __restrict__ wpk, float rs, int* __restrict__ err)
 {
+    pdl_begin();
     using S = FS<C, G>;
     static_assert(C == 32, "16 drain warps = 4 lane quarters x 4 groups of 8 channels");
     static_assert(MB_COUNT * 8 + 4 <= 128, "MISC region");
@@ -592,7 +593,7 @@ int fused_launch(const float* X, long x_ms, const float* U, long u_ms, float* Xo
     }
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
-    cnn_fused_kernel<C, G><<<grid, FT, smem, st>>>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3,
+    pdl_launch(cnn_fused_kernel<C, G>, grid, FT, smem, st, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3,
                                                   static_cast<const __half*>(wpk), rs, err);
     return 0;
 }

@@ -20,6 +20,7 @@ __global__ void cnn_input_kernel(const float* __restrict__ X, long x_ms, const f
                                  long u_ms, const float* __restrict__ B, float* __restrict__ act0,
                                  int n, int m, int l)
 {
+    pdl_begin();
     const int b = blockIdx.y;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * m) return;
@@ -41,6 +42,7 @@ conv3x3_kernel(const float* __restrict__ in, int Cin, float* __restrict__ out, l
                int n, int m, const float* __restrict__ w, const float* __restrict__ bias,
                const float* __restrict__ xres, long xres_ms, float rs)
 {
+    pdl_begin();
     __shared__ float tile[CI_T][HALO][HALO + 1];
     __shared__ float ws[CO_T][CI_T * 9];
 
@@ -109,7 +111,7 @@ void launch_cnn_input(const float* X, long x_ms, const float* U, long u_ms, cons
                       float* act0, int Nb, int n, int m, int l, cudaStream_t st)
 {
     dim3 grid((n * m + 255) / 256, Nb);
-    cnn_input_kernel<<<grid, 256, 0, st>>>(X, x_ms, U, u_ms, B, act0, n, m, l);
+    pdl_launch(cnn_input_kernel, grid, 256, 0, st, X, x_ms, U, u_ms, B, act0, n, m, l);
 }
 
 void launch_conv_hidden(const float* in, int Cin, float* out, int Cout, int Nb, int n, int m,
@@ -118,7 +120,7 @@ void launch_conv_hidden(const float* in, int Cin, float* out, int Cout, int Nb, 
     const int tiles = ((m + TILE - 1) / TILE) * ((n + TILE - 1) / TILE);
     constexpr int CO = 16;
     dim3 grid(tiles, (Cout + CO - 1) / CO, Nb);
-    conv3x3_kernel<CO, 0><<<grid, TILE * TILE, 0, st>>>(in, Cin, out, 0, Cout, n, m, w, bias,
+    pdl_launch(conv3x3_kernel<CO, 0>, grid, TILE * TILE, 0, st, in, Cin, out, 0, Cout, n, m, w, bias,
                                                         nullptr, 0, 0.f);
 }
 
@@ -128,7 +130,7 @@ void launch_conv_out_residual(const float* in, int Cin, const float* Xin, long x
 {
     const int tiles = ((m + TILE - 1) / TILE) * ((n + TILE - 1) / TILE);
     dim3 grid(tiles, 1, Nb);
-    conv3x3_kernel<1, 1><<<grid, TILE * TILE, 0, st>>>(in, Cin, Xout, xout_ms, 1, n, m, w, bias,
+    pdl_launch(conv3x3_kernel<1, 1>, grid, TILE * TILE, 0, st, in, Cin, Xout, xout_ms, 1, n, m, w, bias,
                                                        Xin, xin_ms, rs);
 }
 

@@ -200,6 +200,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                  long x_ms, float* __restrict__ Xout, long o_ms, const __nv_bfloat16* __restrict__ wpk,
                  const float* __restrict__ bias, int Nb, int n, float rs, int* __restrict__ err)
 {
+    pdl_begin();
     using S = BS<CI, CO, MODE, G>;
     constexpr int m = BM / G;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -360,6 +361,7 @@ __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const 
                                   const float* __restrict__ Bmat, int Nb, int n, int l,
                                   __nv_bfloat16* __restrict__ act)
 {
+    pdl_begin();
     constexpr int m = BM / G, NPOS = BM + 2 * G;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int groups = (Nb + G - 1) / G;
@@ -393,7 +395,7 @@ int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const float* X, long
     }
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
-    conv_bf16_kernel<CI, CO, MODE, G><<<grid, S::NT, S::SMEM, st>>>(
+    pdl_launch(conv_bf16_kernel<CI, CO, MODE, G>, grid, S::NT, S::SMEM, st, 
         in, out, X, x_ms, Xout, o_ms, static_cast<const __nv_bfloat16*>(wpk), bias, Nb, n, rs, err);
     return 0;
 }
@@ -404,7 +406,7 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
 {
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n * BM;
-    bf16_input_kernel<G><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(X, x_ms, U, u_ms, Bmat, Nb, n, l,
+    pdl_launch(bf16_input_kernel<G>, (unsigned)((total + 255) / 256), 256, 0, st, X, x_ms, U, u_ms, Bmat, Nb, n, l,
                                                                          static_cast<__nv_bfloat16*>(net.act_in));
     const int C = net.C;
     const __nv_bfloat16* cur = static_cast<const __nv_bfloat16*>(net.act_in);

@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 conv_tc_split_kernel(const float* __restrict__ in, float* __restrict__ out, const __half* __restrict__ wpk,
                      const float* __restrict__ bias, int Nb, int n, int m, int* __restrict__ err)
 {
+    pdl_begin();
     using S = ConvTcShape<C>;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
@@ -255,6 +256,7 @@ conv_tc_split_kernel(const float* __restrict__ in, float* __restrict__ out, cons
 // res[1..4] = first mismatch (row, col, got, want).
 __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(int* __restrict__ res)
 {
+    pdl_begin();
     constexpr int M = 128, N = 64, K = 32;
     // operands use (K/8)*M*16 and (K/8)*N*16 bytes; the arrays are larger so a
     // misread stride still reads inside the CTA's shared memory
@@ -380,13 +382,13 @@ void launch_conv_tc(const float* in, float* out, const void* wpk, const float* b
     const int G = TILE_M / m;
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
-    conv_tc_split_kernel<32><<<grid, TC_THREADS, S::SMEM, st>>>(in, out, static_cast<const __half*>(wpk),
+    pdl_launch(conv_tc_split_kernel<32>, grid, TC_THREADS, S::SMEM, st, in, out, static_cast<const __half*>(wpk),
                                                                bias, Nb, n, m, err);
 }
 
 void launch_tc_selftest(int* res, cudaStream_t st)
 {
-    tc_selftest_kernel<<<1, 128, 0, st>>>(res);
+    pdl_launch(tc_selftest_kernel, 1, 128, 0, st, res);
 }
 
 }  // namespace oic

@@ -23,6 +23,7 @@ __global__ void init_kernel(float* __restrict__ E, long ms, int n, int m, int l,
                             const float* __restrict__ X_k, const float* __restrict__ U_prev,
                             const float* __restrict__ W0)
 {
+    pdl_begin();
     const int i = blockIdx.y;
     float* Ei = E + (long)i * ms;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (n + l) * m; e += gridDim.x * blockDim.x) {
@@ -38,6 +39,7 @@ __global__ void init_kernel(float* __restrict__ E, long ms, int n, int m, int l,
 __global__ void u_advance_kernel(float* __restrict__ E, long ms, int m, int l, int u_from, int u_to,
                                  const float* __restrict__ W)
 {
+    pdl_begin();
     const int i = blockIdx.y;
     float* Ei = E + (long)i * ms;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * m; e += gridDim.x * blockDim.x)
@@ -74,6 +76,7 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
              const float* __restrict__ Yx, const float* __restrict__ Yu, int n_yx, float* __restrict__ part1,
              float* __restrict__ part2, float* __restrict__ Dbuf, int splits)
 {
+    pdl_begin();
     constexpr int NT = S_NT;
     extern __shared__ __align__(16) float sm[];
     const int R = act.count, p = obs.count, M = R + p;
@@ -237,6 +240,7 @@ __device__ __forceinline__ float split_sum(const float* __restrict__ part, long 
 __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict__ part1, int splits, int M, int m,
                                                         float* __restrict__ S1)
 {
+    pdl_begin();
     __shared__ float red[8][33];
     const int idx = blockIdx.x * 32 + threadIdx.x % 32;
     const bool ok = idx < M * m;
@@ -253,6 +257,7 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
                                                            const float* __restrict__ S1, int splits, int R, int p,
                                                            int m, int N, double* __restrict__ C)
 {
+    pdl_begin();
     using T = typename std::conditional<F64, double, float>::type;
     __shared__ T red[8][33];
     const int M = R + p;
@@ -335,6 +340,7 @@ template <int SL>
 __global__ void __launch_bounds__(32 * GC_W)
 gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
 {
+    pdl_begin();
     extern __shared__ __align__(16) float gsm[];
     constexpr int NT = 32 * GC_W;
     const int pp = (p + GC_B - 1) & ~(GC_B - 1);  // whole panels (zero rows, rinv 0)
@@ -561,8 +567,8 @@ void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cud
                              (int)gain_chol_smem(32 * SL));
         attr_set = true;
     }
-    const int grid = (R + GC_W - 1) / GC_W;
-    gain_chol_kernel<SL><<<grid > 0 ? grid : 1, 32 * GC_W, smem, st>>>(C, R, p, Kt, status);
+    const int grid = R > 0 ? (R + GC_W - 1) / GC_W : 1;
+    pdl_launch(gain_chol_kernel<SL>, grid, 32 * GC_W, smem, st, C, R, p, Kt, status);
 }
 
 // ---------------------------------------------------------------- update
@@ -575,6 +581,7 @@ __global__ void __launch_bounds__(UT)
 update_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float* __restrict__ Kt, int p,
               const float* __restrict__ Dbuf)
 {
+    pdl_begin();
     extern __shared__ __align__(16) float sm[];
     const int R = act.count;
     const int ld = UBM + SPAD;
@@ -636,6 +643,7 @@ update_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float* __
 __global__ void block_means_kernel(const float* __restrict__ E, long ms, int N, int m, int row0,
                                    int rows_per_block, int n_blocks, float* __restrict__ out)
 {
+    pdl_begin();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_blocks * rows_per_block * m) return;
     const long off = (long)row0 * m + idx;      // blocks are contiguous rows
@@ -657,14 +665,14 @@ void launch_ensemble_init(float* E, long ms, int N, int n, int m, int l, int x_r
                           const float* W0, cudaStream_t st)
 {
     dim3 grid(((n + l) * m + 255) / 256, N);
-    init_kernel<<<grid, 256, 0, st>>>(E, ms, n, m, l, x_row0, u_row0, X_k, U_prev, W0);
+    pdl_launch(init_kernel, grid, 256, 0, st, E, ms, n, m, l, x_row0, u_row0, X_k, U_prev, W0);
 }
 
 void launch_u_advance(float* E, long ms, int N, int m, int l, int u_from, int u_to, const float* W,
                       cudaStream_t st)
 {
     dim3 grid((l * m + 255) / 256, N);
-    u_advance_kernel<<<grid, 256, 0, st>>>(E, ms, m, l, u_from, u_to, W);
+    pdl_launch(u_advance_kernel, grid, 256, 0, st, E, ms, m, l, u_from, u_to, W);
 }
 
 int stats_splits(int R, int p, int N)
@@ -692,24 +700,24 @@ void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs,
     }
     // loader chunks: SBM m / 4 and SBN m / 4 pieces over S_NT threads
     if (m <= 64)
-        stats_kernel<4, 4><<<grid, S_NT, smem, st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1, part2, Dbuf,
+        pdl_launch(stats_kernel<4, 4>, grid, S_NT, smem, st, E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1, part2, Dbuf,
                                                      splits);
     else
-        stats_kernel<8, 8><<<grid, S_NT, smem, st>>>(E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1, part2, Dbuf,
+        pdl_launch(stats_kernel<8, 8>, grid, S_NT, smem, st, E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1, part2, Dbuf,
                                                      splits);
 }
 
 void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st)
 {
-    s1_reduce_kernel<<<(M * m + 31) / 32, 256, 0, st>>>(part1, splits, M, m, S1);
+    pdl_launch(s1_reduce_kernel, (M * m + 31) / 32, 256, 0, st, part1, splits, M, m, S1);
 }
 
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
                          cudaStream_t st, bool f64)
 {
     const int total = (R + p) * p;
-    if (f64) cov_finalize_kernel<true><<<(total + 31) / 32, 256, 0, st>>>(part2, S1, splits, R, p, m, N, C);
-    else cov_finalize_kernel<false><<<(total + 31) / 32, 256, 0, st>>>(part2, S1, splits, R, p, m, N, C);
+    if (f64) pdl_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C);
+    else pdl_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C);
 }
 
 // ------------------------------------------------------------ FP64 gain
@@ -723,6 +731,7 @@ __global__ void __launch_bounds__(G64_T, 1)
 chol64_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ Lg, int* __restrict__ status,
               int* __restrict__ bad_out)
 {
+    pdl_begin();
     extern __shared__ double Ls[];                // [p][p + 1], lower triangle used
     __shared__ int bad;
     const int ld = p + 1, tid = threadIdx.x;
@@ -772,6 +781,7 @@ __global__ void __launch_bounds__(256)
 solve64_kernel(const double* __restrict__ C, int R, int p, const double* __restrict__ Lg,
                const int* __restrict__ bad_in, float* __restrict__ Kt)
 {
+    pdl_begin();
     extern __shared__ double rinv[];              // 1 / L_ii
     const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int i = threadIdx.x; i < p; i += blockDim.x) rinv[i] = 1.0 / Lg[(long)i * p + i];
@@ -833,8 +843,8 @@ void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt
         cudaFuncSetAttribute(chol64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    chol64_kernel<<<1, G64_T, smem, st>>>(C, R, p, L, status, bad);
-    solve64_kernel<<<(R + 7) / 8, 256, sizeof(double) * (size_t)p, st>>>(C, R, p, L, bad, Kt);
+    pdl_launch(chol64_kernel, 1, G64_T, smem, st, C, R, p, L, status, bad);
+    pdl_launch(solve64_kernel, (R + 7) / 8, 256, sizeof(double) * (size_t)p, st, C, R, p, L, bad, Kt);
 }
 
 size_t gain_smem_bytes(int p) { return p <= 144 ? 0 : (size_t)-1; }
@@ -861,14 +871,14 @@ void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt,
         attr_set = true;
     }
     dim3 grid((act.count + UBM - 1) / UBM, N * ((m + UBN - 1) / UBN));
-    update_kernel<<<grid, UT, smem, st>>>(E, ms, m, act, Kt, p, Dbuf);
+    pdl_launch(update_kernel, grid, UT, smem, st, E, ms, m, act, Kt, p, Dbuf);
 }
 
 void launch_block_means(const float* E, long ms, int N, int m, int row0, int rows_per_block,
                         int n_blocks, float* out, cudaStream_t st)
 {
     const int total = n_blocks * rows_per_block * m;
-    block_means_kernel<<<(total + 255) / 256, 256, 0, st>>>(E, ms, N, m, row0, rows_per_block,
+    pdl_launch(block_means_kernel, (total + 255) / 256, 256, 0, st, E, ms, N, m, row0, rows_per_block,
                                                             n_blocks, out);
 }
 

@@ -49,6 +49,7 @@ __global__ void philox_noise_kernel(float* __restrict__ out, unsigned long long 
                                     unsigned long long seed, const unsigned long long* __restrict__ solve_ctr,
                                     Segs segs)
 {
+    pdl_begin();
     const unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long e0 = q * 4ull;
     if (e0 >= total) return;
@@ -85,7 +86,8 @@ __global__ void philox_noise_kernel(float* __restrict__ out, unsigned long long 
 
 // the solve index lives on the device, so a captured step graph draws fresh
 // noise on every replay
-__global__ void counter_tick_kernel(unsigned long long* ctr) { *ctr += 1ull; }
+__global__ void counter_tick_kernel(unsigned long long* ctr) {
+    pdl_begin(); *ctr += 1ull; }
 
 }  // namespace
 
@@ -101,8 +103,8 @@ void launch_philox_noise(float* out, size_t count_total, unsigned long long seed
     }
     const unsigned long long quads = (count_total + 3) / 4;
     const unsigned blocks = (unsigned)((quads + 255) / 256);
-    philox_noise_kernel<<<blocks, 256, 0, st>>>(out, count_total, seed, solve_ctr, s);
-    counter_tick_kernel<<<1, 1, 0, st>>>(solve_ctr);
+    pdl_launch(philox_noise_kernel, blocks, 256, 0, st, out, count_total, seed, solve_ctr, s);
+    pdl_launch(counter_tick_kernel, 1, 1, 0, st, solve_ctr);
 }
 
 }  // namespace oic

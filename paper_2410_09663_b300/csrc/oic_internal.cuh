@@ -13,12 +13,41 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "oic.h"
 
 namespace oic {
 
 // Values of the device status word.
 enum : int { DEV_OK = 0, DEV_NOTSPD = 1, DEV_TIMEOUT = 2 };
+
+// Programmatic dependent launch: every kernel is launched with programmatic
+// stream serialisation, and its first statements let the next kernel in the
+// stream start launching and then wait until the previous one has finished
+// and its writes are visible.  No kernel reads anything before that wait, so
+// the only overlap is launch latency and CTA rasterisation.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... K, typename... A>
+inline cudaError_t pdl_launch(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // Where member i's row r lives: E + i * member_stride + row_off[r] * m.
 struct RowSet {

@@ -75,6 +75,7 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
              float* __restrict__ Bop, float* __restrict__ Ysh, float* __restrict__ Dbuf, float* __restrict__ Bd,
              int KCD)
 {
+    pdl_begin();
     extern __shared__ float Ds[];                 // [32][ldd]: D transposed, [j][c]
     const int p = obs.count;
     const int i = blockIdx.x / KH, kh = blockIdx.x % KH;
@@ -156,6 +157,7 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
                 const float* __restrict__ Ysh, const float* __restrict__ Bop, int pp, int KH, int S, int splits,
                 int tmem_cols, float* __restrict__ part1, float* __restrict__ part2, int* __restrict__ err)
 {
+    pdl_begin();
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t s0 = (raw + 1023u) & ~1023u;                     // swizzle atoms need 1024-byte alignment
@@ -391,12 +393,12 @@ void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet o
     const int KCD = (p + 31) / 32;
     float* Ysh = Bop + (size_t)N * KH * 2 * pp * 32;      // after the observation tiles
     const size_t ysm = Bd != nullptr ? sizeof(float) * 32 * (32 * KCD + 1) : 0;
-    yprep_kernel<<<N * KH, 256, ysm, st>>>(E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop, Ysh, Dbuf, Bd, KCD);
+    pdl_launch(yprep_kernel, N * KH, 256, ysm, st, E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop, Ysh, Dbuf, Bd, KCD);
     const int S = st_stages(pp);
     const int cols = pp <= 32 ? 32 : pp <= 64 ? 64 : pp <= 128 ? 128 : 256;
     const size_t smem = stats_tc_smem(p);
     cudaFuncSetAttribute(stats_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    stats_tc_kernel<<<dim3(stats_tc_rtiles(M), splits), ST_NT, smem, st>>>(E, ms, N, m, act, obs, Ysh, Bop, pp, KH,
+    pdl_launch(stats_tc_kernel, dim3(stats_tc_rtiles(M), splits), ST_NT, smem, st, E, ms, N, m, act, obs, Ysh, Bop, pp, KH,
                                                                            S, splits, cols, part1, part2, err);
 }
 

@@ -42,6 +42,7 @@ constexpr long long UT_WAIT = 4000000000LL;
 __global__ void kprep_kernel(const float* __restrict__ Kt, int R, int p, int rtiles, int KCH,
                              float* __restrict__ Aop)
 {
+    pdl_begin();
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long)rtiles * KCH * 8 * UT_M) return;
     const int r = (int)(e % UT_M);
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(UT_NT, 1)
 update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float* __restrict__ Aop,
                  const float* __restrict__ Bd, long NM, int KCH, int rtiles, int items, int* __restrict__ err)
 {
+    pdl_begin();
     extern __shared__ unsigned char usm_raw[];
     const uint32_t raw = tc::smem_u32(usm_raw);
     const uint32_t s0 = (raw + 1023u) & ~1023u;
@@ -226,7 +228,7 @@ void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* 
 {
     const int R = act.count, rtiles = (R + UT_M - 1) / UT_M, KCH = update_tc_kch(p);
     const long prep = (long)rtiles * KCH * 8 * UT_M;
-    kprep_kernel<<<(unsigned)((prep + 255) / 256), 256, 0, st>>>(Kt, R, p, rtiles, KCH, Aop);
+    pdl_launch(kprep_kernel, (unsigned)((prep + 255) / 256), 256, 0, st, Kt, R, p, rtiles, KCH, Aop);
     const long NM = (long)N * m;
     const int items = (int)((NM + UT_N - 1) / UT_N) * rtiles;
     const int grid = items < 148 ? items : 148;
@@ -236,7 +238,7 @@ void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* 
         cudaFuncSetAttribute(update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    update_tc_kernel<<<grid, UT_NT, smem, st>>>(E, ms, m, act, Aop, Bd, NM, KCH, rtiles, items, err);
+    pdl_launch(update_tc_kernel, grid, UT_NT, smem, st, E, ms, m, act, Aop, Bd, NM, KCH, rtiles, items, err);
 }
 
 }  // namespace oic
