@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "oic_internal.cuh"
+#include "tc_tf32.cuh"
 
 namespace oic {
 namespace {
@@ -315,6 +316,7 @@ __device__ __forceinline__ float gsel(const float (&v)[N], int q)
 
 constexpr int GC_W = 8;                           // warps per CTA = gain rows per CTA
 constexpr int GC_B = 8;                           // panel height = substitution block
+constexpr int GC_TILE = 128 * 128;                // one operand part of the update's gain tile, bytes
 
 // 8-element block of a substitution: the lanes l0 .. l0+7 of slot `slot`
 // hold the block's right-hand sides; every lane receives them.
@@ -338,7 +340,8 @@ __device__ __forceinline__ void block_put(float (&b)[SL], int slot, int l0, int 
 
 template <int SL>
 __global__ void __launch_bounds__(32 * GC_W)
-gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status)
+gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status,
+                 float* __restrict__ Aop)
 {
     pdl_begin();
     extern __shared__ __align__(16) float gsm[];
@@ -476,10 +479,16 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
         __syncthreads();
     }
     const int a = blockIdx.x * GC_W + w;
-    if (bad) {
+    if (bad) {                                    // K = 0: the update leaves the ensemble as it is
         if (tid == 0) atomicExch(status, DEV_NOTSPD);
-        if (a < R)
+        if (a < R) {
             for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
+            if (Aop != nullptr) {
+                char* t0 = reinterpret_cast<char*>(Aop) + (size_t)(a >> 7) * SL * 2 * GC_TILE;
+                const int off = tf32::swz(a & 127, lane >> 2) + (lane & 3) * 4;
+                for (int s = 0; s < 2 * SL; ++s) *reinterpret_cast<float*>(t0 + (size_t)s * GC_TILE + off) = 0.f;
+            }
+        }
         return;
     }
     if (a >= R) return;
@@ -549,6 +558,18 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
         const int i = lane + 32 * s;
         if (i < p) Kt[(long)i * R + a] = b[s];
     }
+    if (Aop != nullptr) {
+        // the member update's operand: row a of tile a / 128, K chunk s, hi and lo
+        // (128-byte-swizzled rows of 32 values; zero beyond p)
+        char* t0 = reinterpret_cast<char*>(Aop) + (size_t)(a >> 7) * SL * 2 * GC_TILE;
+        const int off = tf32::swz(a & 127, lane >> 2) + (lane & 3) * 4;
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            const float hi = tf32::tf32_rna(b[s]);
+            *reinterpret_cast<float*>(t0 + (size_t)s * 2 * GC_TILE + off) = hi;
+            *reinterpret_cast<float*>(t0 + ((size_t)s * 2 + 1) * GC_TILE + off) = tf32::tf32_rna(b[s] - hi);
+        }
+    }
 }
 
 size_t gain_chol_smem(int p)
@@ -558,7 +579,7 @@ size_t gain_chol_smem(int p)
 }
 
 template <int SL>
-void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st)
+void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st, float* Aop)
 {
     const size_t smem = gain_chol_smem(p);
     static bool attr_set = false;
@@ -568,7 +589,7 @@ void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cud
         attr_set = true;
     }
     const int grid = R > 0 ? (R + GC_W - 1) / GC_W : 1;
-    pdl_launch(gain_chol_kernel<SL>, grid, 32 * GC_W, smem, st, C, R, p, Kt, status);
+    pdl_launch(gain_chol_kernel<SL>, grid, 32 * GC_W, smem, st, C, R, p, Kt, status, Aop);
 }
 
 // ---------------------------------------------------------------- update
@@ -850,14 +871,14 @@ void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt
 size_t gain_smem_bytes(int p) { return p <= 144 ? 0 : (size_t)-1; }
 int gain_max_p() { return 144; }
 
-void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st)
+void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop)
 {
     switch ((p + 31) / 32) {
-    case 1: gain_chol_launch<1>(C, R, p, K, status, st); break;
-    case 2: gain_chol_launch<2>(C, R, p, K, status, st); break;
-    case 3: gain_chol_launch<3>(C, R, p, K, status, st); break;
-    case 4: gain_chol_launch<4>(C, R, p, K, status, st); break;
-    default: gain_chol_launch<5>(C, R, p, K, status, st); break;
+    case 1: gain_chol_launch<1>(C, R, p, K, status, st, Aop); break;
+    case 2: gain_chol_launch<2>(C, R, p, K, status, st, Aop); break;
+    case 3: gain_chol_launch<3>(C, R, p, K, status, st, Aop); break;
+    case 4: gain_chol_launch<4>(C, R, p, K, status, st, Aop); break;
+    default: gain_chol_launch<5>(C, R, p, K, status, st, Aop); break;
     }
 }
 

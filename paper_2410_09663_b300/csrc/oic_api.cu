@@ -352,12 +352,13 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
             launch_gain64(C, R, p, h->at<double>(h->lay.L64), h->at<int>(h->lay.status) + 1, Kt,
                           h->at<int>(h->lay.status), h->st);
         else
-            launch_gain(C, R, p, Kt, h->at<int>(h->lay.status), h->st);
+            launch_gain(C, R, p, Kt, h->at<int>(h->lay.status), h->st,
+                        utc ? h->at<float>(h->lay.tAop) : nullptr);
     });
     if (utc)
         run_stage(h, OIC_STAGE_UPDATE, [&] {
             launch_update_tc(E, ms, c.N, c.m, act, Kt, p, h->at<float>(h->lay.tAop), Bd, h->at<int>(h->lay.status),
-                             h->st);
+                             h->st, mixed);                // the FP32 gain writes the tiles itself
         });
     else
         run_stage(h, OIC_STAGE_UPDATE, [&] { launch_update(E, ms, c.N, c.m, act, Kt, p, D, h->st); });

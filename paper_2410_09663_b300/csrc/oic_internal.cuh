@@ -114,14 +114,16 @@ void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet o
 bool update_tc_supported(int m, int p);
 size_t update_tc_abytes(int Rmax, int p);
 size_t update_tc_bbytes(int N, int m, int p);
+// Kt is turned into the gain tiles Aop first unless the gain kernel already
+// wrote them (prep_gain = false).
 void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop,
-                      const float* Bd, int* err, cudaStream_t st);
+                      const float* Bd, int* err, cudaStream_t st, bool prep_gain = true);
 // Mixed-precision gain: FP64 Cholesky of Cyy (one CTA) into L [p][p], then
 // FP64 triangular solves per row of Cxy; bad: device flag (not SPD).
 void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st);
 // Kt = (Cxy Cyy^{-1})^T, [p][R].
 size_t gain_smem_bytes(int p);
-void launch_gain(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st);
+void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop = nullptr);
 // E^i[act rows] += K D^i for every member.
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
                    cudaStream_t st);

@@ -292,14 +292,35 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
             const int quarter = warp & 3;
             const int a = rt * TM + 32 * quarter + lane;
             const uint32_t tl = (uint32_t)(32 * quarter) << 16;
-            for (int c0 = (warp >> 2) * 16; c0 < pp; c0 += 32) {
-                float v[16];
-                tc::tmem_ld16(tmem + tl + c0, v);
+            // two 16-column groups per TMEM wait; 16-byte stores of the row
+            float* prow = part2 + ((long)sidx * M + a) * p;
+            const bool vec = (p & 3) == 0;
+            for (int c0 = (warp >> 2) * 16; c0 < pp; c0 += 64) {
+                float v[2][16];
+                const bool two = c0 + 32 < pp;       // warp-uniform
+                tc::tmem_ld16(tmem + tl + c0, v[0]);
+                if (two) tc::tmem_ld16(tmem + tl + c0 + 32, v[1]);
                 tc::tmem_ld_wait();
                 if (a < M) {
 #pragma unroll
-                    for (int u = 0; u < 16; ++u)
-                        if (c0 + u < p) part2[((long)sidx * M + a) * p + c0 + u] = nst > 0 ? v[u] : 0.f;
+                    for (int g = 0; g < 2; ++g) {
+                        const int cg = c0 + 32 * g;
+                        if (g == 1 && !two) break;
+#pragma unroll
+                        for (int u4 = 0; u4 < 4; ++u4) {
+                            const int c = cg + 4 * u4;
+                            float4 x = make_float4(v[g][4 * u4], v[g][4 * u4 + 1], v[g][4 * u4 + 2], v[g][4 * u4 + 3]);
+                            if (nst == 0) x = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (vec && c + 3 < p) {
+                                *reinterpret_cast<float4*>(prow + c) = x;
+                            } else {
+                                if (c < p) prow[c] = x.x;
+                                if (c + 1 < p) prow[c + 1] = x.y;
+                                if (c + 2 < p) prow[c + 2] = x.z;
+                                if (c + 3 < p) prow[c + 3] = x.w;
+                            }
+                        }
+                    }
                 }
             }
         }

@@ -224,11 +224,11 @@ size_t update_tc_abytes(int Rmax, int p) { return (size_t)((Rmax + UT_M - 1) / U
 size_t update_tc_bbytes(int N, int m, int p) { return (size_t)update_tc_kch(p) * 2 * N * m * 128; }
 
 void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop,
-                      const float* Bd, int* err, cudaStream_t st)
+                      const float* Bd, int* err, cudaStream_t st, bool prep_gain)
 {
     const int R = act.count, rtiles = (R + UT_M - 1) / UT_M, KCH = update_tc_kch(p);
     const long prep = (long)rtiles * KCH * 8 * UT_M;
-    pdl_launch(kprep_kernel, (unsigned)((prep + 255) / 256), 256, 0, st, Kt, R, p, rtiles, KCH, Aop);
+    if (prep_gain) pdl_launch(kprep_kernel, (unsigned)((prep + 255) / 256), 256, 0, st, Kt, R, p, rtiles, KCH, Aop);
     const long NM = (long)N * m;
     const int items = (int)((NM + UT_N - 1) / UT_N) * rtiles;
     const int grid = items < 148 ? items : 148;
