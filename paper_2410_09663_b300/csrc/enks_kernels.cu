@@ -741,135 +741,6 @@ void launch_cov_finalize(const float* part2, const float* S1, int splits, int R,
     else pdl_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C);
 }
 
-// ------------------------------------------------------------ FP64 gain
-// The mixed-precision mode's gain: Cyy = L L^T by a right-looking FP64
-// Cholesky in one CTA (L in shared memory, two barriers per column), then
-// one warp per row a of Cxy solves L z = Cxy[a]^T and L^T k = z in FP64
-// (lane-parallel dot products, shuffle reductions) and writes Kt[.][a].
-constexpr int G64_T = 1024;
-
-__global__ void __launch_bounds__(G64_T, 1)
-chol64_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ Lg, int* __restrict__ status,
-              int* __restrict__ bad_out)
-{
-    pdl_begin();
-    extern __shared__ double Ls[];                // [p][p + 1], lower triangle used
-    __shared__ int bad;
-    const int ld = p + 1, tid = threadIdx.x;
-    const double* Cyy = C + (long)R * p;
-    for (int e = tid; e < p * p; e += G64_T) Ls[(e / p) * ld + e % p] = Cyy[e];
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    for (int j = 0; j < p; ++j) {
-        const double d = Ls[j * ld + j];
-        if (!(d > 0.0)) {                         // same value in every thread
-            if (tid == 0) bad = 1;
-            break;
-        }
-        const double rd = 1.0 / sqrt(d);
-        // column j below the diagonal (rows i > j); the trailing update below
-        // reads these scaled values
-        for (int i = j + 1 + tid; i < p; i += G64_T) Ls[i * ld + j] *= rd;
-        __syncthreads();
-        // A[i][k] -= L[i][j] L[k][j] for j < k <= i: warp w takes rows
-        // j+1+w, +32, ..., lane t columns j+1+t, +32, ... (consecutive lanes,
-        // consecutive doubles)
-        {
-            const int w = tid / 32, t = tid % 32;
-            for (int i = j + 1 + w; i < p; i += G64_T / 32) {
-                const double lij = Ls[i * ld + j];
-                for (int k = j + 1 + t; k <= i; k += 32) Ls[i * ld + k] = fma(-lij, Ls[k * ld + j], Ls[i * ld + k]);
-            }
-        }
-        if (tid == 0) Ls[j * ld + j] = d * rd;
-        __syncthreads();
-    }
-    if (bad) {
-        if (tid == 0) { atomicExch(status, DEV_NOTSPD); *bad_out = 1; }
-        return;
-    }
-    if (tid == 0) *bad_out = 0;
-    for (int e = tid; e < p * p; e += G64_T) {
-        const int i = e / p, k = e % p;
-        Lg[e] = k <= i ? Ls[i * ld + k] : 0.0;
-    }
-}
-
-// lane t owns z_i for i = t + 32 q (q < 5, p <= 160), in registers
-constexpr int S64_Q = 5;
-
-__global__ void __launch_bounds__(256)
-solve64_kernel(const double* __restrict__ C, int R, int p, const double* __restrict__ Lg,
-               const int* __restrict__ bad_in, float* __restrict__ Kt)
-{
-    pdl_begin();
-    extern __shared__ double rinv[];              // 1 / L_ii
-    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int i = threadIdx.x; i < p; i += blockDim.x) rinv[i] = 1.0 / Lg[(long)i * p + i];
-    __syncthreads();
-    const int a = blockIdx.x * 8 + w;
-    if (a >= R) return;
-    if (*bad_in) {
-        for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
-        return;
-    }
-    double z[S64_Q];
-#pragma unroll
-    for (int q = 0; q < S64_Q; ++q) {
-        const int i = lane + 32 * q;
-        z[q] = i < p ? C[(long)a * p + i] : 0.0;
-    }
-    // forward, column by column: z_j /= L_jj, then z_i -= L_ij z_j for i > j
-    for (int j = 0; j < p; ++j) {
-        const int qj = j / 32, lj = j % 32;
-        double zj = 0.0;
-#pragma unroll
-        for (int q = 0; q < S64_Q; ++q)
-            if (q == qj) zj = z[q];
-        zj = __shfl_sync(0xffffffffu, zj, lj) * rinv[j];
-#pragma unroll
-        for (int q = 0; q < S64_Q; ++q) {
-            const int i = lane + 32 * q;
-            if (i == j) z[q] = zj;
-            else if (i > j && i < p) z[q] = fma(-Lg[(long)i * p + j], zj, z[q]);
-        }
-    }
-    // back, row by row of L: k_j = z_j / L_jj, then z_i -= L_ji k_j for i < j
-    for (int j = p - 1; j >= 0; --j) {
-        const int qj = j / 32, lj = j % 32;
-        double kj = 0.0;
-#pragma unroll
-        for (int q = 0; q < S64_Q; ++q)
-            if (q == qj) kj = z[q];
-        kj = __shfl_sync(0xffffffffu, kj, lj) * rinv[j];
-#pragma unroll
-        for (int q = 0; q < S64_Q; ++q) {
-            const int i = lane + 32 * q;
-            if (i == j) z[q] = kj;
-            else if (i < j) z[q] = fma(-Lg[(long)j * p + i], kj, z[q]);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < S64_Q; ++q) {
-        const int i = lane + 32 * q;
-        if (i < p) Kt[(long)i * R + a] = (float)z[q];
-    }
-}
-
-void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st)
-{
-    const size_t smem = sizeof(double) * (size_t)p * (p + 1);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(chol64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
-    pdl_launch(chol64_kernel, 1, G64_T, smem, st, C, R, p, L, status, bad);
-    pdl_launch(solve64_kernel, (R + 7) / 8, 256, sizeof(double) * (size_t)p, st, C, R, p, L, bad, Kt);
-}
-
-size_t gain_smem_bytes(int p) { return p <= 144 ? 0 : (size_t)-1; }
-int gain_max_p() { return 144; }
 
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop)
 {

@@ -1,0 +1,293 @@
+// gain64_cluster.cu -- the mixed-precision mode's FP64 gain,
+// K = Sigma^XY (Sigma^Y)^-1 by the Cholesky factorisation Sigma^Y = L L^T
+// and two substitutions per gain row (Eq. of the sample-wise ensemble
+// Kalman update; the factorisation as in the Appendix).
+//
+// B300's FP64 pipe does about 2 FMA/clk/SM, so a one-CTA factorisation of
+// p = 144 (p^3/3 = 1e6 FMA) costs at least 250 us.  Here it runs on a cluster
+// of 8 CTAs (8 SMs):
+//   - rows are distributed block-cyclically in panels of 8: panel B (rows
+//     8B .. 8B+7) lives in the shared memory of CTA B mod 8;
+//   - per panel, the owner eliminates its 8 pivots (right-looking, upper
+//     form Sigma^Y = U^T U with U = L^T), scales the rows to U and releases
+//     them with one remote mbarrier arrive (release, cluster scope) on every
+//     CTA of the cluster;
+//   - every CTA waits for that barrier (acquire, cluster scope, bounded),
+//     copies the panel out of the owner's shared memory (distributed shared
+//     memory) and applies the rank-8 update to its own later rows;
+//   - a pivot <= 0 ("not positive definite") is published with the panel, so
+//     every CTA leaves the loop after the same panel.
+// Each panel barrier is used once (parity 0), so no barrier ever has two
+// phases outstanding.  The cluster barrier at the end keeps every CTA's
+// shared memory alive until the others have read it.  Then solve64_kernel
+// gives each gain row one warp (L staged in shared memory; column-form FP64
+// forward and back substitution).
+#include "oic_internal.cuh"
+#include "tc_sm103.cuh"
+
+namespace oic {
+namespace {
+
+constexpr int CL = 8;                                   // CTAs per cluster
+constexpr int PB = 8;                                   // rows per panel
+constexpr int C64_T = 256;
+constexpr int C64_PMAX = 160;                           // largest p
+constexpr int C64_NB = C64_PMAX / PB;                   // panels at most
+constexpr int C64_OWN = (C64_NB + CL - 1) / CL;         // panels per CTA at most
+constexpr long long C64_WAIT = 4000000000LL;
+
+__device__ __forceinline__ uint32_t cl_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double cl_ld(uint32_t addr)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ int cl_ld_s32(uint32_t addr)
+{
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_arrive(uint32_t mbar_cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(mbar_cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool cl_wait(uint64_t* mbar, uint32_t parity, long long max_cycles)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(tc::smem_u32(mbar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > max_cycles) return false;
+    }
+}
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(C64_T, 1)
+chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ Lg, int* __restrict__ status,
+               int* __restrict__ bad_out)
+{
+    pdl_begin();
+    __shared__ __align__(16) double own[C64_OWN][PB][C64_PMAX];    // this CTA's panels (rows of A, then of U)
+    __shared__ __align__(16) double pan[PB][C64_PMAX];             // the current panel (U rows)
+    __shared__ double rsv[PB];
+    __shared__ __align__(8) uint64_t rdy[C64_NB];
+    __shared__ int bad_here, bad_seen, timeout;
+    const int tid = threadIdx.x, w = tid / 32, lane = tid % 32;
+    const uint32_t rank = cl_rank();
+    const int pp = (p + PB - 1) / PB * PB, NB = pp / PB;
+    const double* Cyy = C + (long)R * p;
+    for (int sl = 0; sl < C64_OWN; ++sl) {
+        const int B = (int)rank + CL * sl;
+        if (B >= NB) break;
+        for (int e = tid; e < PB * pp; e += C64_T) {
+            const int d = e / pp, c = e % pp, g = PB * B + d;
+            own[sl][d][c] = (g < p && c < p) ? Cyy[(long)g * p + c] : 0.0;
+        }
+    }
+    if (tid == 0) {
+        for (int B = 0; B < NB; ++B) tc::mbar_init(rdy + B, 1);
+        bad_here = 0;
+        bad_seen = 0;
+        timeout = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    cl_sync();                                          // every barrier initialised before any remote arrive
+
+    for (int B = 0; B < NB; ++B) {
+        const uint32_t o = (uint32_t)(B % CL);
+        const int sl = B / CL, c0 = PB * B;
+        if (rank == o) {
+            // ---- the owner eliminates the panel's pivots
+            double (*A)[C64_PMAX] = own[sl];
+            for (int d = 0; d < PB; ++d) {
+                const int g = c0 + d;
+                const double piv = A[d][g];
+                double ip = 0.0;
+                if (g < p) {
+                    if (!(piv > 0.0)) {
+                        if (tid == 0) bad_here = 1;
+                    } else {
+                        ip = 1.0 / piv;
+                    }
+                }
+                if (tid == 0) rsv[d] = (g < p && piv > 0.0) ? 1.0 / sqrt(piv) : 0.0;
+                // rows e > d of the panel, columns c >= c0 + e: warp w takes row d + 1 + w
+                const int e = d + 1 + w;
+                if (e < PB) {
+                    const double f = A[d][c0 + e] * ip;
+                    for (int c = c0 + e + lane; c < pp; c += 32) A[e][c] = fma(-f, A[d][c], A[e][c]);
+                }
+                __syncthreads();
+            }
+            for (int x = tid; x < PB * pp; x += C64_T) {
+                const int d = x / pp, c = x % pp;
+                if (c >= c0 + d) A[d][c] *= rsv[d];
+            }
+            __syncthreads();
+            if (tid == 0)
+                for (uint32_t t = 0; t < CL; ++t) cl_arrive(cl_map(rdy + B, t));
+        }
+        // ---- everyone: wait for the panel, copy it, check the owner's pivots
+        if (!cl_wait(rdy + B, 0u, C64_WAIT)) timeout = 1;
+        __syncthreads();
+        if (timeout) break;
+        for (int x = tid; x < PB * (pp - c0); x += C64_T) {
+            const int d = x / (pp - c0), c = c0 + x % (pp - c0);
+            pan[d][c] = cl_ld(cl_map(&own[sl][d][c], o));
+        }
+        if (tid == 0) bad_seen = cl_ld_s32(cl_map(&bad_here, o));
+        __syncthreads();
+        if (bad_seen) break;
+        // ---- rank-8 update of this CTA's rows in later panels, columns c >= row
+        for (int sl2 = 0; sl2 < C64_OWN; ++sl2) {
+            const int B2 = (int)rank + CL * sl2;
+            if (B2 <= B || B2 >= NB) continue;
+            for (int d2 = w; d2 < PB; d2 += C64_T / 32) {
+                const int g = PB * B2 + d2;
+                double pi[PB];
+#pragma unroll
+                for (int k = 0; k < PB; ++k) pi[k] = pan[k][g];
+                for (int c = g + lane; c < pp; c += 32) {
+                    double v = own[sl2][d2][c];
+#pragma unroll
+                    for (int k = 0; k < PB; ++k) v = fma(-pi[k], pan[k][c], v);
+                    own[sl2][d2][c] = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    cl_sync();                                          // nobody reads another CTA's shared memory after this
+    if (timeout && tid == 0) atomicExch(status, DEV_TIMEOUT);
+    if (bad_seen || timeout) {
+        if (rank == 0 && tid == 0) {
+            if (bad_seen) atomicExch(status, DEV_NOTSPD);
+            *bad_out = 1;
+        }
+        return;
+    }
+    if (rank == 0 && tid == 0) *bad_out = 0;
+    // L[i][g] = U[g][i] for i >= g, zero above the diagonal
+    for (int sl = 0; sl < C64_OWN; ++sl) {
+        const int B = (int)rank + CL * sl;
+        if (B >= NB) break;
+        for (int x = tid; x < PB * p; x += C64_T) {
+            const int d = x / p, i = x % p, g = PB * B + d;
+            if (g < p) Lg[(long)i * p + g] = i >= g ? own[sl][d][i] : 0.0;
+        }
+    }
+}
+
+// One warp per gain row a; L staged in shared memory with an odd leading
+// dimension (column reads of the forward pass and row reads of the backward
+// pass are both conflict-free); lane t holds z_i for i = t + 32 q.
+constexpr int S64_W = 4;                                // warps (gain rows) per CTA
+constexpr int S64_Q = 5;                                // p <= 160
+
+__global__ void __launch_bounds__(32 * S64_W)
+solve64s_kernel(const double* __restrict__ C, int R, int p, const double* __restrict__ Lg,
+                const int* __restrict__ bad_in, float* __restrict__ Kt)
+{
+    pdl_begin();
+    extern __shared__ double Ls[];                      // [p][p | 1], then 1 / L_ii
+    const int ld = p | 1;
+    double* rinv = Ls + (size_t)p * ld;
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int a = blockIdx.x * S64_W + w;
+    if (*bad_in) {
+        if (a < R)
+            for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
+        return;
+    }
+    for (int e = threadIdx.x; e < p * p; e += 32 * S64_W) {
+        const int i = e / p, k = e % p;
+        if (k <= i) Ls[i * ld + k] = __ldg(Lg + e);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += 32 * S64_W) rinv[i] = 1.0 / Ls[i * ld + i];
+    __syncthreads();
+    if (a >= R) return;
+    double z[S64_Q];
+#pragma unroll
+    for (int q = 0; q < S64_Q; ++q) {
+        const int i = lane + 32 * q;
+        z[q] = i < p ? C[(long)a * p + i] : 0.0;
+    }
+    // forward: z_j /= L_jj, then z_i -= L_ij z_j for i > j (column j of L)
+    for (int j = 0; j < p; ++j) {
+        const int qj = j / 32, lj = j % 32;
+        double zj = z[0];
+#pragma unroll
+        for (int q = 1; q < S64_Q; ++q) zj = q == qj ? z[q] : zj;
+        zj = __shfl_sync(0xffffffffu, zj, lj) * rinv[j];
+#pragma unroll
+        for (int q = 0; q < S64_Q; ++q) {
+            const int i = lane + 32 * q;
+            if (i == j) z[q] = zj;
+            else if (i > j && i < p) z[q] = fma(-Ls[i * ld + j], zj, z[q]);
+        }
+    }
+    // back: k_j = z_j / L_jj, then z_i -= L_ji k_j for i < j (row j of L)
+    for (int j = p - 1; j >= 0; --j) {
+        const int qj = j / 32, lj = j % 32;
+        double kj = z[0];
+#pragma unroll
+        for (int q = 1; q < S64_Q; ++q) kj = q == qj ? z[q] : kj;
+        kj = __shfl_sync(0xffffffffu, kj, lj) * rinv[j];
+#pragma unroll
+        for (int q = 0; q < S64_Q; ++q) {
+            const int i = lane + 32 * q;
+            if (i == j) z[q] = kj;
+            else if (i < j) z[q] = fma(-Ls[j * ld + i], kj, z[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < S64_Q; ++q) {
+        const int i = lane + 32 * q;
+        if (i < p) Kt[(long)i * R + a] = (float)z[q];
+    }
+}
+
+}  // namespace
+
+int gain64_max_p() { return C64_PMAX; }
+
+void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st)
+{
+    pdl_launch(chol64c_kernel, CL, C64_T, 0, st, C, R, p, L, status, bad);
+    const size_t smem = sizeof(double) * ((size_t)p * (p | 1) + p);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(solve64s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * ((size_t)C64_PMAX * (C64_PMAX | 1) + C64_PMAX)));
+        attr_set = true;
+    }
+    pdl_launch(solve64s_kernel, (R + S64_W - 1) / S64_W, 32 * S64_W, smem, st, C, R, p, L, bad, Kt);
+}
+
+}  // namespace oic

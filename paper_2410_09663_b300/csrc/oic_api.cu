@@ -150,7 +150,7 @@ bool valid_config(const oic_config* c)
     if (c->precision != OIC_PREC_FP32 && c->precision != OIC_PREC_MIXED) return false;
     if (c->noise_mode != OIC_NOISE_HOST && c->noise_mode != OIC_NOISE_PHILOX) return false;
     const long p = (long)c->n + c->l;
-    if (p > 144) return false;                  // the gain's elimination lives in registers
+    if (p > 144) return false;                  // the sizes the gain and covariance kernels are built and tested for
     if ((long)c->n * c->m > (1L << 26) || (long)c->N * c->m > (1L << 28)) return false;
     if (c->m > 128) return false;                // analysis tiles hold one member row of <= 128 columns
     return true;

@@ -118,11 +118,12 @@ size_t update_tc_bbytes(int N, int m, int p);
 // wrote them (prep_gain = false).
 void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop,
                       const float* Bd, int* err, cudaStream_t st, bool prep_gain = true);
-// Mixed-precision gain: FP64 Cholesky of Cyy (one CTA) into L [p][p], then
-// FP64 triangular solves per row of Cxy; bad: device flag (not SPD).
+// Mixed-precision gain: FP64 Cholesky of Cyy on a cluster of 8 CTAs into
+// L [p][p] (p <= 160), then FP64 triangular solves per row of Cxy; bad:
+// device flag (not SPD).
 void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st);
-// Kt = (Cxy Cyy^{-1})^T, [p][R].
-size_t gain_smem_bytes(int p);
+// Kt = (Cxy Cyy^{-1})^T, [p][R] (FP32 Cholesky, p <= 160); with Aop also the
+// member update's TF32 operand tiles of the gain.
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop = nullptr);
 // E^i[act rows] += K D^i for every member.
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
