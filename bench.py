@@ -227,6 +227,30 @@ def run_reference(args, wl):
     return 0
 
 
+def replica_workload(wl, rank):
+    """Each rank solves its own problem: the same workload, seed offset by
+    the rank (no data is shared between ranks)."""
+    return wl.with_(seed=wl.seed + rank)
+
+
+def max_over_ranks(times, world, device=None):
+    """Element-wise maximum of `times` over the ranks of the default process
+    group (the job's time is that of its slowest replica)."""
+    if world <= 1:
+        return [float(t) for t in times]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_value(steps_per_rank, world, t_slowest):
+    """Whole-job throughput: the control steps of every rank over the slowest
+    rank's time (weak scaling: per-rank work is fixed)."""
+    return world * steps_per_rank / t_slowest
+
+
 def config_dict(wl, extra=None):
     d = {"workload": wl.name, "n": wl.n, "m": wl.m, "l": wl.l, "N": wl.N, "H": wl.H,
          "cnn": "-".join(str(c) for c in wl.channels), "precision": "fp32",
@@ -251,7 +275,7 @@ def run_oic(args, wl):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    wl = wl.with_(seed=wl.seed + rank)                 # independent replica per rank
+    wl = replica_workload(wl, rank)                      # independent replica per rank
     w, b = wl.flat_weights()
     mixed = args.precision == "mixed"
     cfg = oic.config_from_workload(wl, noise_mode=oic.OIC_NOISE_PHILOX,
@@ -336,10 +360,7 @@ def run_oic(args, wl):
     h2d = (H + 1) * wl.n * wl.m * 4 + wl.l * wl.m * 4
     d2h = wl.l * wl.m * 4 + wl.n * wl.m * 4
 
-    if world > 1:
-        t = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e = float(t[0]), float(t[1])
+    t_dev, t_e2e = max_over_ranks([t_dev, t_e2e], world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -380,7 +401,7 @@ def run_oic(args, wl):
                         "avg_launch_ms": avg_s * 1e3}
     share = {k: round(v / max(sum(total_ms.values()), 1e-12), 4) for k, v in total_ms.items()}
     steps_total = world * args.steps
-    value = steps_total / t_dev
+    value = job_value(args.steps, world, t_dev)
     lat = sorted(per_step)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
