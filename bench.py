@@ -437,6 +437,138 @@ def run_oic(args, wl):
     return 0
 
 
+MIX_METRIC = "aggregate control steps/s over a batch of uneven problems (one batch graph per step)"
+
+
+def run_mix(args, name):
+    """Batched uneven problems: every problem of the mix takes one control
+    step per batch step (mixed precision, device noise); value = problems x
+    steps / time.  The same problems stepped one after another on one stream
+    are timed beside it."""
+    import torch
+    import torch.distributed as dist
+    import paper_2410_09663_b300 as oic
+    from paper_2410_09663_b300 import workloads
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wls = workloads.BATCHES[name](seed=2024 + 1000 * rank)
+    stream = torch.cuda.Stream(device=dev)
+    solvers, refs = [], []
+    S_ref = args.steps + args.warmup + 8
+    with torch.cuda.stream(stream):
+        for w in wls:
+            wt, bs = w.flat_weights()
+            cfg = oic.config_from_workload(w, noise_mode=oic.OIC_NOISE_PHILOX, precision=oic.OIC_PREC_MIXED)
+            sv = oic.Solver(cfg, wt, bs, w.B(), device=dev, stream=stream)
+            sv.oic_reset(torch.from_numpy(w.X0()).to(dev), torch.from_numpy(w.U_init()).to(dev))
+            solvers.append(sv)
+            refs.append(torch.from_numpy(w.X_ref_all(S_ref)).to(dev))
+        batch = oic.Batch(solvers, stream=stream)
+        slots = [sv.oic_io_slots() for sv in solvers]
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+        def fill(k):
+            for w, r, (xr, ur, _, _) in zip(wls, refs, slots):
+                xr.copy_(r[k:k + w.H + 1])
+                ur.zero_()
+
+        for k in range(args.warmup):
+            fill(k)
+            batch.step()
+        batch.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        launches0 = oic.oic_launch_count()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                fill(args.warmup + i)
+                batch.step()
+                ev[i][1].record(stream)
+            batch.sync()
+        launches = oic.oic_launch_count() - launches0
+        per_step = [a.elapsed_time(c) for a, c in ev]
+        t_batch = sum(per_step) / 1e3
+        # the same problems one after another, each through its own step graph
+        k_seq = min(args.steps, 3)
+        u_outs = [torch.zeros(w.l, w.m, device=dev) for w in wls]
+        x_outs = [torch.zeros(w.n, w.m, device=dev) for w in wls]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for i in range(k_seq):
+            k = args.warmup + args.steps + i
+            for w, r, sv, uo, xo in zip(wls, refs, solvers, u_outs, x_outs):
+                sv.oic_step(r[k:k + w.H + 1], torch.zeros(w.l, w.m, device=dev), None, uo, xo)
+        e1.record(stream)
+        stream.synchronize()
+        t_seq = e0.elapsed_time(e1) / 1e3
+        # end to end: host references in, controls and states out, every step
+        host_refs = [r.cpu().pin_memory() for r in refs]
+        host_out = [(torch.zeros(w.l, w.m).pin_memory(), torch.zeros(w.n, w.m).pin_memory()) for w in wls]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            k = i % (args.warmup + 1)
+            for w, hr, (xr, ur, _, _) in zip(wls, host_refs, slots):
+                xr.copy_(hr[k:k + w.H + 1], non_blocking=True)
+                ur.zero_()
+            batch.step()
+            for (_, _, ua, xn), (hu, hx) in zip(slots, host_out):
+                hu.copy_(ua, non_blocking=True)
+                hx.copy_(xn, non_blocking=True)
+            batch.sync()
+        t_e2e = time.perf_counter() - t0
+    h2d = sum((w.H + 1) * w.n * w.m * 4 for w in wls)
+    d2h = sum((w.l + w.n) * w.m * 4 for w in wls)
+    t_batch, t_seq, t_e2e = max_over_ranks([t_batch, t_seq, t_e2e], world, dev)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    P = len(wls)
+    lat = sorted(per_step)
+    line = {
+        "metric": MIX_METRIC, "value": job_value(P * args.steps, world, t_batch), "unit": "control steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64",
+        "data": "synthetic",
+        "config": {"workload": name, "problems": P,
+                   "sizes": "grids {32,64,96,128}^2, l = m/8, N {64..512}, H 5..20, CNN 2-32-32-1",
+                   "grids": {str(g): sum(1 for w in wls if w.m == g) for g in (32, 64, 96, 128)},
+                   "member_steps_per_batch_step": sum(w.N * w.H for w in wls),
+                   "precision": "mixed: BF16 conv (FP32 per-layer kernels at 96 x 96), FP32 covariance, "
+                                "FP64 mean correction and gain",
+                   "noise": "philox-4x32-10 on device, per-problem seeds",
+                   "launch": "one CUDA graph per batch step, one branch per problem",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "sequential_value": job_value(P * k_seq, world, t_seq),
+                   "sequential": "the same problems one after another, each through its own step graph",
+                   "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "roofline": None,
+        "e2e": {"value": job_value(P * args.steps, world, t_e2e), "unit": "control steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": {"value": None, "unit": "control steps/s", "cores": host_threads(), "kind": "oracle",
+                         "sample": "not run for the batch mode (the single-problem lines carry it)"},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +583,11 @@ def main(argv=None):
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     from paper_2410_09663_b300 import workloads
+    if args.workload in workloads.BATCHES:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batch mode has no oracle arm"}), flush=True)
+            return 0
+        return run_mix(args, args.workload)
     wl = workloads.WORKLOADS[args.workload]()
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -248,6 +248,45 @@ oic_status oic_sync(oic_handle* h);
  * around the call on the bound stream; valid after oic_sync). */
 float oic_last_ms(oic_handle* h);
 
+/* ---------------------------------------------------------------- batching
+ * Independent problems stepped together (a deployment extension; the paper
+ * solves one problem at a time): one receding-horizon control step of every
+ * problem (Algorithm 1) launched as ONE CUDA graph whose branches are the
+ * problems' own step graphs, so the GPU runs small problems side by side.
+ * Problems may differ in every size; each keeps its own workspace, seed and
+ * solve counter, and nothing is shared or reduced across problems, so each
+ * result is bit-identical to the same problem stepped alone. */
+
+/* Device addresses of the per-step slots inside h's workspace (valid while
+ * h stays bound to the same workspace): inputs X_ref [(H+1)][n][m] and
+ * U_ref [l][m], outputs U_applied [l][m] and X_next [n][m] of the last step.
+ * Any argument may be NULL.  OIC_ESTATE if h is not bound. */
+oic_status oic_io_slots(const oic_handle* h, float** X_ref, float** U_ref, float** U_applied,
+                        float** X_next);
+
+typedef struct oic_batch oic_batch;
+
+/* Builds the batch graph of `count` handles (1..4096), each bound, with its
+ * plant state set (oic_reset) and in OIC_NOISE_PHILOX mode; a handle appears
+ * at most once.  The batch launches on `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  The batch graph is captured once here: each
+ * problem's step on its own branch.  The handles must outlive the batch and
+ * stay bound to the same workspaces.  OIC_EINVAL / OIC_ESTATE / OIC_ENOMEM /
+ * OIC_ECUDA. */
+oic_status oic_batch_create(oic_handle* const* handles, int count, void* cuda_stream, oic_batch** out);
+
+/* One control step of every problem of the batch: each reads its X_ref and
+ * U_ref slots and writes its U_applied and X_next slots (oic_io_slots),
+ * asynchronously on the batch's stream.  Inputs must be in place, in stream
+ * order, before the call. */
+oic_status oic_batch_step(oic_batch* b);
+
+/* Waits for the batch's stream; returns the first non-OK device status of
+ * the handles, in handle order (and clears every handle's status). */
+oic_status oic_batch_sync(oic_batch* b);
+
+void oic_batch_destroy(oic_batch* b);
+
 void oic_destroy(oic_handle* h);
 const char* oic_status_string(oic_status s);
 const char* oic_version(void);

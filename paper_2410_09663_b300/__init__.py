@@ -14,7 +14,7 @@ import os
 
 from . import build as _build
 
-__all__ = ["OIC_OK", "OICError", "oic_config", "load", "Solver", "config_from_workload"]
+__all__ = ["OIC_OK", "OICError", "oic_config", "load", "Solver", "Batch", "config_from_workload"]
 
 MAX_LAYERS = 8
 OIC_OK, OIC_EINVAL, OIC_ENOMEM, OIC_ECUDA, OIC_ENOTSPD, OIC_ETIMEOUT, OIC_ESTATE = range(7)
@@ -68,6 +68,11 @@ _SIGS = {
     "oic_selftest": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "oic_enks_update_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                               _VP, _VP, _VP]),
+    "oic_io_slots": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "oic_batch_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "oic_batch_step": (ctypes.c_int, [_VP]),
+    "oic_batch_sync": (ctypes.c_int, [_VP]),
+    "oic_batch_destroy": (None, [_VP]),
     "oic_destroy": (None, [_VP]),
     "oic_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "oic_version": (ctypes.c_char_p, []),
@@ -104,6 +109,41 @@ def status_string(s) -> str:
 def _check(s, what):
     if s != OIC_OK:
         raise OICError(s, what)
+
+
+class Batch:
+    """oic_batch: one control step of several independent solvers as one
+    CUDA graph (each solver's step graph a branch).  Inputs go into each
+    solver's oic_io_slots() views before step(); outputs are read there."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self._lib = load()
+        self.solvers = list(solvers)
+        dev = self.solvers[0].workspace.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[sv.h for sv in self.solvers])
+        b = ctypes.c_void_p()
+        _check(self._lib.oic_batch_create(arr, len(self.solvers), ctypes.c_void_p(self.stream.cuda_stream),
+                                          ctypes.byref(b)), "oic_batch_create")
+        self.b = b
+
+    def step(self):
+        _check(self._lib.oic_batch_step(self.b), "oic_batch_step")
+
+    def sync(self):
+        _check(self._lib.oic_batch_sync(self.b), "oic_batch_sync")
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.oic_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def config_from_workload(wl, precision=OIC_PREC_FP32, keep_full_history=False,
@@ -246,6 +286,24 @@ class Solver:
         cnt = (ctypes.c_int * n)()
         _check(self._lib.oic_profile_end(self.h, ms, cnt), "oic_profile_end")
         return {STAGES[i]: (float(ms[i]), int(cnt[i])) for i in range(n) if cnt[i] > 0}
+
+    def oic_io_slots(self):
+        """Torch views of the per-step slots in this solver's workspace:
+        (X_ref [H+1, n, m], U_ref [l, m], U_applied [l, m], X_next [n, m])."""
+        import torch
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        _check(self._lib.oic_io_slots(self.h, *[ctypes.byref(q) for q in ptrs]), "oic_io_slots")
+        c = self.cfg
+        shapes = [(c.H + 1, c.n, c.m), (c.l, c.m), (c.l, c.m), (c.n, c.m)]
+        base = self.workspace.data_ptr()
+        out = []
+        for q, shp in zip(ptrs, shapes):
+            off = q.value - base
+            n = 4
+            for d in shp:
+                n *= d
+            out.append(self.workspace[off:off + n].view(torch.float32).view(*shp))
+        return tuple(out)
 
     def close(self):
         if getattr(self, "h", None):

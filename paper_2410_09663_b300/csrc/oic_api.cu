@@ -920,6 +920,134 @@ oic_status oic_selftest(oic_handle* h, int* result)
     return result[0] == 0 ? OIC_OK : OIC_ECUDA;
 }
 
+// ---------------------------------------------------------------- batching
+struct oic_batch {
+    std::vector<oic_handle*> hs;
+    cudaStream_t st = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    unsigned long long launches = 0;
+};
+
+oic_status oic_io_slots(const oic_handle* h, float** X_ref, float** U_ref, float** U_applied, float** X_next)
+{
+    if (!h) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    const Layout& L = h->lay;
+    if (X_ref) *X_ref = h->at<float>(L.xref);
+    if (U_ref) *U_ref = h->at<float>(L.uref);
+    if (U_applied) *U_applied = h->at<float>(L.uapp);
+    if (X_next) *X_next = h->at<float>(L.xnext);
+    return OIC_OK;
+}
+
+oic_status oic_batch_create(oic_handle* const* handles, int count, void* cuda_stream, oic_batch** out)
+{
+    if (!handles || !out || count < 1 || count > 4096) return OIC_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        oic_handle* h = handles[i];
+        if (!h) return OIC_EINVAL;
+        if (h->cfg.noise_mode != OIC_NOISE_PHILOX) return OIC_EINVAL;
+        if (!h->bound || !h->plant_ready) return OIC_ESTATE;
+        for (int k = 0; k < i; ++k)
+            if (handles[k] == h) return OIC_EINVAL;
+    }
+    oic_batch* b = new (std::nothrow) oic_batch;
+    if (!b) return OIC_ENOMEM;
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> join;
+    try {
+        b->hs.assign(handles, handles + count);
+        br.assign(count, nullptr);
+        join.assign(count, nullptr);
+    } catch (...) {
+        delete b;
+        return OIC_ENOMEM;
+    }
+    b->st = static_cast<cudaStream_t>(cuda_stream);
+    // One capture: an origin stream forks to one stream per problem, each
+    // problem's step is captured on its own stream (its kernels keep their
+    // programmatic-dependency edges inside the branch), and the branches
+    // join back.  The streams and events exist only during the capture.
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < count; ++i)
+        ok = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
+    const unsigned long long l0 = g_launches.load();
+    if (ok && cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        bool cap = cudaEventRecord(fork, origin) == cudaSuccess;
+        for (int i = 0; cap && i < count; ++i) {
+            oic_handle* h = handles[i];
+            cap = cudaStreamWaitEvent(br[i], fork, 0) == cudaSuccess;
+            StepGraph none;                       // capture mode, no profiling events
+            const cudaStream_t own = h->st;
+            h->st = br[i];
+            h->capturing = &none;
+            const Layout& L = h->lay;
+            cap = cap && step_impl(h, h->at<float>(L.xref), h->at<float>(L.uref), h->at<float>(L.noise),
+                                   h->at<float>(L.uapp), h->at<float>(L.xnext)) == OIC_OK;
+            h->capturing = nullptr;
+            h->st = own;
+            cap = cap && cudaEventRecord(join[i], br[i]) == cudaSuccess &&
+                  cudaStreamWaitEvent(origin, join[i], 0) == cudaSuccess;
+        }
+        cudaGraph_t g = nullptr;
+        const bool ended = cudaStreamEndCapture(origin, &g) == cudaSuccess;
+        b->g = g;
+        ok = cap && ended && g != nullptr;
+    } else {
+        ok = false;
+    }
+    b->launches = g_launches.load() - l0;
+    g_launches.fetch_sub(b->launches);                    // captured, not run
+    ok = ok && cudaGraphInstantiate(&b->x, b->g, 0) == cudaSuccess;
+    for (int i = 0; i < count; ++i) {
+        if (join[i]) cudaEventDestroy(join[i]);
+        if (br[i]) cudaStreamDestroy(br[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (origin) cudaStreamDestroy(origin);
+    if (!ok) {
+        cudaGetLastError();
+        oic_batch_destroy(b);
+        return OIC_ECUDA;
+    }
+    *out = b;
+    return OIC_OK;
+}
+
+oic_status oic_batch_step(oic_batch* b)
+{
+    if (!b || !b->x) return OIC_EINVAL;
+    OIC_CUDA_OK(cudaGraphLaunch(b->x, b->st));
+    g_launches.fetch_add(b->launches, std::memory_order_relaxed);
+    return OIC_OK;
+}
+
+oic_status oic_batch_sync(oic_batch* b)
+{
+    if (!b) return OIC_EINVAL;
+    OIC_CUDA_OK(cudaStreamSynchronize(b->st));
+    oic_status first = OIC_OK;
+    for (oic_handle* h : b->hs) {
+        const oic_status s = read_status(h);
+        if (first == OIC_OK) first = s;
+    }
+    return first;
+}
+
+void oic_batch_destroy(oic_batch* b)
+{
+    if (!b) return;
+    if (b->x) cudaGraphExecDestroy(b->x);
+    if (b->g) cudaGraphDestroy(b->g);
+    delete b;
+}
+
 void oic_destroy(oic_handle* h)
 {
     if (!h) return;

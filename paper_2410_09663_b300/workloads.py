@@ -182,7 +182,25 @@ def large_128():
                     N=1024, H=20, S=50, ref="blobs", blob_sigma=12.0)
 
 
+def mix64(seed: int = 2024, count: int = 64):
+    """Batched uneven problems: `count` independent problems with grids drawn
+    uniformly from {32, 64, 96, 128}^2 (n = m), l = m / 8, N uniformly from
+    {64, 128, 256, 512} and H uniformly from 5..20; CNN 2-32-32-1; each
+    problem its own seed (weights, B, initial field, noise) and moving-blob
+    reference (sigma m / 10)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.choice([32, 64, 96, 128]))
+        N = int(rng.choice([64, 128, 256, 512]))
+        H = int(rng.integers(5, 21))
+        out.append(Workload(f"mix{i}_{m}x{m}_N{N}_H{H}", n=m, m=m, l=m // 8, channels=[2, 32, 32, 1], N=N, H=H,
+                            S=50, ref="blobs", blob_sigma=m / 10.0, seed=seed + 1 + i))
+    return out
+
+
 WORKLOADS = {"small_16": small_16, "working_64": working_64, "large_128": large_128}
+BATCHES = {"mix64": mix64}
 
 
 # ------------------------------------------------------------------ Philox

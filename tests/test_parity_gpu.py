@@ -354,3 +354,47 @@ def test_mixed_precision_closed_loop_cost_within_half_percent(cuda_ok, name):
     assert abs(jg - jo) <= 5e-3 * abs(jo)
     assert rel(Ut, Uo) <= 4 * 2.0 ** -9
     assert rel(Xt, Xo) <= 1e-3
+
+
+def _steps_alone(wl, steps, precision):
+    s = solver(wl, noise_mode=oic.OIC_NOISE_PHILOX, precision=precision)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    xr_all = wl.X_ref_all(steps)
+    out = []
+    for k in range(steps):
+        Ua = np.zeros((wl.l, wl.m), np.float32)
+        Xn = np.zeros((wl.n, wl.m), np.float32)
+        s.oic_step_host(xr_all[k:k + wl.H + 1], wl.U_ref(), None, Ua, Xn)
+        out.append((Ua, Xn))
+    s.close()
+    return out
+
+
+def test_batched_uneven_problems_equal_each_problem_alone(cuda_ok):
+    """Problems of different grid, ensemble and horizon sizes (one of them in
+    the mixed-precision mode) stepped together as one batch graph give the
+    same controls and states, bit for bit, as each problem stepped alone."""
+    import torch
+    wls = [(W.small_16(), oic.OIC_PREC_FP32),
+           (W.small_16().with_(N=48, H=3, seed=7), oic.OIC_PREC_FP32),
+           (W.working_64().with_(N=32, H=3, seed=11), oic.OIC_PREC_FP32),
+           (MIXED_CASES["m32_c64"].with_(seed=5), oic.OIC_PREC_MIXED)]
+    steps = 3
+    alone = [_steps_alone(w, steps, pr) for w, pr in wls]
+    solvers = []
+    for w, pr in wls:
+        s = solver(w, noise_mode=oic.OIC_NOISE_PHILOX, precision=pr)
+        s.oic_reset_host(w.X0(), w.U_init())
+        solvers.append(s)
+    batch = oic.Batch(solvers)
+    slots = [s.oic_io_slots() for s in solvers]
+    for k in range(steps):
+        for (w, _), (xr, ur, _, _) in zip(wls, slots):
+            xr.copy_(torch.from_numpy(w.X_ref_all(steps)[k:k + w.H + 1]).to(xr.device))
+            ur.copy_(torch.from_numpy(w.U_ref()).to(ur.device))
+        batch.step()
+        batch.sync()
+        for (ua, xn), (_, _, sua, sxn) in zip([a[k] for a in alone], slots):
+            assert np.array_equal(sua.cpu().numpy(), ua)
+            assert np.array_equal(sxn.cpu().numpy(), xn)
+    batch.close()
