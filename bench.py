@@ -546,8 +546,7 @@ def run_mix(args, name):
                    "sizes": "grids {32,64,96,128}^2, l = m/8, N {64..512}, H 5..20, CNN 2-32-32-1",
                    "grids": {str(g): sum(1 for w in wls if w.m == g) for g in (32, 64, 96, 128)},
                    "member_steps_per_batch_step": sum(w.N * w.H for w in wls),
-                   "precision": "mixed: BF16 conv (FP32 per-layer kernels at 96 x 96), FP32 covariance, "
-                                "FP64 mean correction and gain",
+                   "precision": "mixed: BF16 conv, FP32 covariance, FP64 mean correction and gain",
                    "noise": "philox-4x32-10 on device, per-problem seeds",
                    "launch": "one CUDA graph per batch step, one branch per problem",
                    "l2": "flushed between timed steps (256 MB write)",

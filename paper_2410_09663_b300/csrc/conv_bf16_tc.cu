@@ -6,11 +6,13 @@
 // Activation rows in global memory are already in the tensor core's operand
 // layout: a row of one member group is [C/8 planes][NPOS positions][8
 // channels] BF16, where position G + G x + b holds pixel x of member b of the
-// group (G = 128/m members interleaved, zero pads of G positions at both
-// ends).  One 1-D bulk copy moves a whole row into shared memory, and a
-// horizontal stencil tap is a shift of the operand start by G positions.
+// group (G = floor(128/W) members of width W interleaved, zero pads of G
+// positions at both ends; positions beyond G + G W stay zero, so a width
+// that does not divide 128, e.g. 96, runs one member per tile).  One 1-D
+// bulk copy moves a whole row into shared memory, and a horizontal stencil
+// tap is a shift of the operand start by G positions.
 //
-// One kernel per layer: conv_bf16_kernel<CI, CO, MODE, G>.
+// One kernel per layer: conv_bf16_kernel<CI, CO, MODE, W>.
 //   MODE_HIDDEN  CO channels, tanh, BF16 rows out
 //   MODE_LAST    CO = 16 columns of which channel 0 is the output; X_next =
 //                X + s (out + b) in FP32
@@ -31,8 +33,9 @@ constexpr int BM = 128;                                 // tile rows (positions)
 constexpr long long B_WAIT = 4000000000LL;
 enum { MODE_HIDDEN = 0, MODE_LAST = 1 };
 
-template <int CI, int CO, int MODE, int G>
+template <int CI, int CO, int MODE, int W>
 struct BS {
+    static constexpr int G = BM / W;                    // members per tile
     static constexpr int NPOS = BM + 2 * G;
     static constexpr int PLANE = NPOS * 16;             // one 8-channel plane of a row
     static constexpr int INROW = (CI / 8) * PLANE;      // one input row
@@ -133,15 +136,15 @@ __device__ __forceinline__ void piece(uint32_t tmem, uint32_t a, uint32_t b, uin
 // All MMAs of input row j (ring position SR = (-j-1) mod 4: blocks b = 0, 1,
 // 2 = output rows j+1, j, j-1 in slots SR, SR+1, SR+2 mod 4).  The first MMA
 // starts output row j+1 (accumulate 0 on its block); INIT_ALL starts all.
-template <int CI, int CO, int MODE, int G, int SR, bool INIT_ALL>
+template <int CI, int CO, int MODE, int W, int SR, bool INIT_ALL>
 __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t b)
 {
-    using S = BS<CI, CO, MODE, G>;
+    using S = BS<CI, CO, MODE, W>;
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
         for (int ks = 0; ks < S::KS; ++ks) {
-            const uint32_t aa = a + (2 * ks * S::PLANE) / 16 + dx * G;
+            const uint32_t aa = a + (2 * ks * S::PLANE) / 16 + dx * S::G;
             const uint32_t bb = b + ((dx * S::KS + ks) * S::BTILE) / 16;
             const bool first = dx == 0 && ks == 0;
             if (first && !INIT_ALL) {
@@ -170,23 +173,23 @@ __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t 
     }
 }
 
-template <int CI, int CO, int MODE, int G>
+template <int CI, int CO, int MODE, int W>
 __device__ __forceinline__ void issue_row(uint32_t tmem, int j, bool init_all, uint32_t a, uint32_t b)
 {
     const int s = (-j - 1) & 3;
     if (init_all) {
         switch (s) {
-        case 0: issue_row_s<CI, CO, MODE, G, 0, true>(tmem, a, b); break;
-        case 1: issue_row_s<CI, CO, MODE, G, 1, true>(tmem, a, b); break;
-        case 2: issue_row_s<CI, CO, MODE, G, 2, true>(tmem, a, b); break;
-        default: issue_row_s<CI, CO, MODE, G, 3, true>(tmem, a, b); break;
+        case 0: issue_row_s<CI, CO, MODE, W, 0, true>(tmem, a, b); break;
+        case 1: issue_row_s<CI, CO, MODE, W, 1, true>(tmem, a, b); break;
+        case 2: issue_row_s<CI, CO, MODE, W, 2, true>(tmem, a, b); break;
+        default: issue_row_s<CI, CO, MODE, W, 3, true>(tmem, a, b); break;
         }
     } else {
         switch (s) {
-        case 0: issue_row_s<CI, CO, MODE, G, 0, false>(tmem, a, b); break;
-        case 1: issue_row_s<CI, CO, MODE, G, 1, false>(tmem, a, b); break;
-        case 2: issue_row_s<CI, CO, MODE, G, 2, false>(tmem, a, b); break;
-        default: issue_row_s<CI, CO, MODE, G, 3, false>(tmem, a, b); break;
+        case 0: issue_row_s<CI, CO, MODE, W, 0, false>(tmem, a, b); break;
+        case 1: issue_row_s<CI, CO, MODE, W, 1, false>(tmem, a, b); break;
+        case 2: issue_row_s<CI, CO, MODE, W, 2, false>(tmem, a, b); break;
+        default: issue_row_s<CI, CO, MODE, W, 3, false>(tmem, a, b); break;
         }
     }
 }
@@ -194,15 +197,16 @@ __device__ __forceinline__ void issue_row(uint32_t tmem, int j, bool init_all, u
 // in: activation rows [groups][n][CI/8][NPOS][8] BF16.  MODE_HIDDEN: out the
 // same layout with CO channels.  MODE_LAST: X_next[member][row][x] = X +
 // rs (out + bias) for member < Nb.
-template <int CI, int CO, int MODE, int G>
-__global__ void __launch_bounds__(BS<CI, CO, MODE, G>::NT, 1)
+template <int CI, int CO, int MODE, int W>
+__global__ void __launch_bounds__(BS<CI, CO, MODE, W>::NT, 1)
 conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out, const float* __restrict__ X,
                  long x_ms, float* __restrict__ Xout, long o_ms, const __nv_bfloat16* __restrict__ wpk,
                  const float* __restrict__ bias, int Nb, int n, float rs, int* __restrict__ err)
 {
     pdl_begin();
-    using S = BS<CI, CO, MODE, G>;
-    constexpr int m = BM / G;
+    using S = BS<CI, CO, MODE, W>;
+    constexpr int G = S::G, m = W;
+    constexpr int LIVE = G * W;                         // positions that hold pixels
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + BB_COUNT * 8);
@@ -285,7 +289,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                     // output row j+1 takes the ring slot of row j-3, drained in pass j-2
                     if (j - 2 >= f_lo) wait(BB_PASS + ((j - 2) & 3));
                     wait(BB_FULL + j % S::NIN);
-                    issue_row<CI, CO, MODE, G>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
+                    issue_row<CI, CO, MODE, W>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
                     tc::mma_commit(mb + BB_FREE + j % S::NIN);
                     tc::mma_commit(mb + BB_HDONE + (j & 1));
                 }
@@ -300,8 +304,9 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
             // last layer: X of the output row of the next pass, loaded one pass ahead
             const int xb = ep % G, xx = ep / G, xmb = g * G + xb;
             auto fetch_x = [&](int h) -> float {
-                return (MODE == MODE_LAST && h >= ys && h < ye && xmb < Nb) ? X[(long)xmb * x_ms + (long)h * m + xx]
-                                                                           : 0.f;
+                return (MODE == MODE_LAST && h >= ys && h < ye && xmb < Nb && ep < LIVE)
+                           ? X[(long)xmb * x_ms + (long)h * m + xx]
+                           : 0.f;
             };
             float xpf = fetch_x(f_lo - 1);
             for (int k = f_lo; k <= last_pass && !failed; ++k) {
@@ -325,15 +330,18 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                             pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
                         }
                         __nv_bfloat16* orow = out + ((size_t)g * n + h) * (CO / 8) * S::NPOS * 8;
+                        if (ep < LIVE) {                // beyond: zero padding, never written
 #pragma unroll
-                        for (int pl = 0; pl < CPW / 8; ++pl)
-                            *reinterpret_cast<uint4*>(orow + ((size_t)(cg * CPW / 8 + pl) * S::NPOS + G + ep) * 8) =
-                                make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
+                            for (int pl = 0; pl < CPW / 8; ++pl)
+                                *reinterpret_cast<uint4*>(orow + ((size_t)(cg * CPW / 8 + pl) * S::NPOS + G + ep) * 8) =
+                                    make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
+                        }
                     } else {
                         float v[8];
                         tmem_ldn<8>(tmem + tlane + col, v);
                         tc::tmem_ld_wait();
-                        if (xmb < Nb) Xout[(long)xmb * o_ms + (long)h * m + xx] = fmaf(rs, v[0] + sbias[0], xcur);
+                        if (xmb < Nb && ep < LIVE)
+                            Xout[(long)xmb * o_ms + (long)h * m + xx] = fmaf(rs, v[0] + sbias[0], xcur);
                     }
                 }
                 tc::fence_before_sync();
@@ -356,13 +364,13 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
 
 // [X, B U] of every member row into the first layer's input rows (CI = 16:
 // plane 0 = [X, BU, 0 ...], plane 1 stays zero; pads stay zero).
-template <int G>
+template <int W>
 __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
                                   const float* __restrict__ Bmat, int Nb, int n, int l,
                                   __nv_bfloat16* __restrict__ act)
 {
     pdl_begin();
-    constexpr int m = BM / G, NPOS = BM + 2 * G;
+    constexpr int G = BM / W, m = W, NPOS = BM + 2 * G;
     const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int groups = (Nb + G - 1) / G;
     if (e >= (long)groups * n * BM) return;
@@ -370,6 +378,7 @@ __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const 
     const long gr = e / BM;
     const int r = (int)(gr % n), g = (int)(gr / n);
     const int b = p % G, x = p / G, mbr = g * G + b;
+    if (p >= G * W) return;                             // zero padding, never written
     float xv = 0.f, bu = 0.f;
     if (mbr < Nb) {
         xv = X[(long)mbr * x_ms + (long)r * m + x];
@@ -381,32 +390,34 @@ __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const 
         make_uint4(*reinterpret_cast<const uint32_t*>(&v), 0u, 0u, 0u);
 }
 
-template <int CI, int CO, int MODE, int G>
+template <int CI, int CO, int MODE, int W>
 int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const float* X, long x_ms, float* Xout, long o_ms,
                const void* wpk, const float* bias, int Nb, int n, float rs, int n_sm, int* err, cudaStream_t st)
 {
-    using S = BS<CI, CO, MODE, G>;
+    using S = BS<CI, CO, MODE, W>;
+    constexpr int G = S::G;
     static bool configured = false;
     if (!configured) {
-        if (cudaFuncSetAttribute(conv_bf16_kernel<CI, CO, MODE, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(conv_bf16_kernel<CI, CO, MODE, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  S::SMEM) != cudaSuccess)
             return 1;
         configured = true;
     }
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
-    pdl_launch(conv_bf16_kernel<CI, CO, MODE, G>, grid, S::NT, S::SMEM, st, 
+    pdl_launch(conv_bf16_kernel<CI, CO, MODE, W>, grid, S::NT, S::SMEM, st, 
         in, out, X, x_ms, Xout, o_ms, static_cast<const __nv_bfloat16*>(wpk), bias, Nb, n, rs, err);
     return 0;
 }
 
-template <int G>
+template <int W>
 int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                    const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st)
 {
+    constexpr int G = BM / W;
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n * BM;
-    pdl_launch(bf16_input_kernel<G>, (unsigned)((total + 255) / 256), 256, 0, st, X, x_ms, U, u_ms, Bmat, Nb, n, l,
+    pdl_launch(bf16_input_kernel<W>, (unsigned)((total + 255) / 256), 256, 0, st, X, x_ms, U, u_ms, Bmat, Nb, n, l,
                                                                          static_cast<__nv_bfloat16*>(net.act_in));
     const int C = net.C;
     const __nv_bfloat16* cur = static_cast<const __nv_bfloat16*>(net.act_in);
@@ -414,28 +425,28 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
     int rc = 0;
     // first layer (input channels padded to 16)
     if (C == 64)
-        rc |= bf16_layer<16, 64, MODE_HIDDEN, G>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
+        rc |= bf16_layer<16, 64, MODE_HIDDEN, W>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
                                                  n_sm, err, st);
     else
-        rc |= bf16_layer<16, 32, MODE_HIDDEN, G>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
+        rc |= bf16_layer<16, 32, MODE_HIDDEN, W>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
                                                  n_sm, err, st);
     cur = bufs[0];
     for (int k = 1; k + 1 < net.n_layers; ++k) {
         __nv_bfloat16* o = bufs[k & 1];
         if (C == 64)
-            rc |= bf16_layer<64, 64, MODE_HIDDEN, G>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
+            rc |= bf16_layer<64, 64, MODE_HIDDEN, W>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
                                                      n_sm, err, st);
         else
-            rc |= bf16_layer<32, 32, MODE_HIDDEN, G>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
+            rc |= bf16_layer<32, 32, MODE_HIDDEN, W>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
                                                      n_sm, err, st);
         cur = o;
     }
     const int L = net.n_layers - 1;
     if (C == 64)
-        rc |= bf16_layer<64, 16, MODE_LAST, G>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
+        rc |= bf16_layer<64, 16, MODE_LAST, W>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
                                                n_sm, err, st);
     else
-        rc |= bf16_layer<32, 16, MODE_LAST, G>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
+        rc |= bf16_layer<32, 16, MODE_LAST, W>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
                                                n_sm, err, st);
     return rc;
 }
@@ -449,7 +460,7 @@ bool bf16_supported(int n_layers, const int* channels, int m)
     if (C != 32 && C != 64) return false;
     for (int k = 1; k < n_layers; ++k)
         if (channels[k] != C) return false;
-    return m == 16 || m == 32 || m == 64 || m == 128;
+    return m == 16 || m == 32 || m == 64 || m == 96 || m == 128;
 }
 
 size_t bf16_act_bytes(int N, int n, int m, int C)
@@ -483,10 +494,11 @@ int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const flo
                         cudaStream_t st)
 {
     switch (m) {
-    case 128: return bf16_forward_g<1>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
-    case 64: return bf16_forward_g<2>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
-    case 32: return bf16_forward_g<4>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
-    case 16: return bf16_forward_g<8>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 128: return bf16_forward_g<128>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 96: return bf16_forward_g<96>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 64: return bf16_forward_g<64>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 32: return bf16_forward_g<32>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 16: return bf16_forward_g<16>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
     }
     return 1;
 }

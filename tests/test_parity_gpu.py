@@ -297,6 +297,7 @@ MIXED_CASES = {
     "m64_c64": W.Workload("mixed_64x64_c64", n=64, m=64, l=8, channels=[2, 64, 64, 1], N=6, H=2, S=2, ref="zero"),
     "m128_c64": W.Workload("mixed_128x128_c64", n=128, m=128, l=16, channels=[2, 64, 64, 64, 1], N=3, H=2, S=2,
                            ref="zero"),
+    "m96_c32": W.Workload("mixed_96x96_c32", n=96, m=96, l=12, channels=[2, 32, 32, 1], N=5, H=2, S=2, ref="zero"),
 }
 
 
