@@ -19,6 +19,7 @@ CPU oracle (the only reference this method has) on the host cores.
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import os
@@ -568,6 +569,95 @@ def run_mix(args, name):
     return 0
 
 
+SERVE_METRIC = "served control requests/s (Poisson arrivals, continuous batching)"
+
+
+def run_serve(args, rate=200.0, budget_gb=150.0):
+    """Serving loop: Poisson arrivals of control requests (one control step
+    of one problem each) over the mix64 problem population, served with
+    continuous batching and admission by HBM footprint.  Reports the achieved
+    request rate and p50/p99 latency (arrival to completion), next to the
+    plain FP32 single-problem path (the 64 x 64 workload stepped alone)."""
+    import torch
+    import paper_2410_09663_b300 as oic
+    from paper_2410_09663_b300 import serving, workloads
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0                                        # one server per node
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    count = args.steps if args.steps != 200 else 10000
+    wls = workloads.mix64(seed=2024)
+    arrivals = serving.poisson_arrivals(rate, count, len(wls), seed=77)
+    per = collections.Counter(pid for _, pid in arrivals)
+    srv = serving.Server(dev, budget_bytes=budget_gb * 1e9, precision=oic.OIC_PREC_MIXED)
+    for pid, w in enumerate(wls):
+        srv.add(pid, w, steps_max=per[pid] + 1)
+    footprint = sum(p.bytes for p in srv.problems.values())
+    # warm-up: every problem admitted and stepped once (its step graph is
+    # captured), then every resident problem back to its initial state
+    srv.run([(0.0, pid) for pid in range(len(wls))])
+    for p in srv.problems.values():
+        if p.solver is not None:
+            with torch.cuda.stream(p.stream):
+                p.solver.oic_reset(torch.from_numpy(p.wl.X0()).to(dev), torch.from_numpy(p.wl.U_init()).to(dev))
+        p.k, p.state, p.evictions = 0, None, 0
+    torch.cuda.synchronize(dev)
+    srv2 = srv
+    launches0 = oic.oic_launch_count()
+    with ClockSampler(0) as clk:
+        rec, _, wall = srv2.run(arrivals)
+    launches = oic.oic_launch_count() - launches0
+    lat = sorted(1e3 * (r[4] - r[2]) for r in rec)
+    svc = sorted(1e3 * (r[4] - r[3]) for r in rec)
+    span = max(r[4] for r in rec) - min(r[2] for r in rec)
+    # the plain FP32 single-problem path, stepped alone back to back
+    wl1 = workloads.working_64()
+    w1, b1 = wl1.flat_weights()
+    s1 = oic.Solver(oic.config_from_workload(wl1, noise_mode=oic.OIC_NOISE_PHILOX), w1, b1, wl1.B(), device=dev)
+    xr1 = torch.from_numpy(wl1.X_ref_all(40)).to(dev)
+    ur1 = torch.zeros(wl1.l, wl1.m, device=dev)
+    uo1, xo1 = torch.zeros(wl1.l, wl1.m, device=dev), torch.zeros(wl1.n, wl1.m, device=dev)
+    s1.oic_reset(torch.from_numpy(wl1.X0()).to(dev), torch.from_numpy(wl1.U_init()).to(dev))
+    for k in range(5):
+        s1.oic_step(xr1[k:k + wl1.H + 1], ur1, None, uo1, xo1)
+    s1.oic_sync()
+    t0 = time.perf_counter()
+    lat1 = []
+    for k in range(5, 35):
+        a = time.perf_counter()
+        s1.oic_step(xr1[k:k + wl1.H + 1], ur1, None, uo1, xo1)
+        s1.oic_sync()
+        lat1.append(1e3 * (time.perf_counter() - a))
+    t1 = time.perf_counter() - t0
+    lat1.sort()
+    pick = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
+    line = {
+        "metric": SERVE_METRIC, "value": count / span, "unit": "requests/s", "n_gpus": 1, "steps": count,
+        "warmup": len(wls), "ms_per_step": 1e3 * span / count, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
+        "config": {"workload": "serve200", "offered_rate": rate, "requests": count,
+                   "problems": len(wls), "sizes": "mix64 (grids {32,64,96,128}^2, N {64..512}, H 5..20)",
+                   "hbm_budget_bytes": int(budget_gb * 1e9), "footprint_all_problems_bytes": int(footprint),
+                   "evictions": int(sum(p.evictions for p in srv2.problems.values())),
+                   "latency_ms_p50": pick(lat, 0.5), "latency_ms_p99": pick(lat, 0.99),
+                   "latency_ms_max": lat[-1], "service_ms_p50": pick(svc, 0.5), "service_ms_p99": pick(svc, 0.99),
+                   "wall_s": wall,
+                   "plain_fp32_single_problem": {
+                       "workload": wl1.name, "steps_per_s": 30 / t1,
+                       "latency_ms_p50": pick(lat1, 0.5), "latency_ms_p99": pick(lat1, 0.99)},
+                   "latency": "arrival to completion (includes queueing); service = launch to completion"},
+        "roofline": None,
+        "e2e": {"value": count / span, "unit": "requests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": {"value": None, "unit": "requests/s", "cores": host_threads(), "kind": "oracle",
+                         "sample": "not run for the serving mode (the single-problem lines carry it)"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -582,6 +672,11 @@ def main(argv=None):
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     from paper_2410_09663_b300 import workloads
+    if args.workload == "serve200":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving mode has no oracle arm"}), flush=True)
+            return 0
+        return run_serve(args)
     if args.workload in workloads.BATCHES:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batch mode has no oracle arm"}), flush=True)

@@ -264,6 +264,22 @@ float oic_last_ms(oic_handle* h);
 oic_status oic_io_slots(const oic_handle* h, float** X_ref, float** U_ref, float** U_applied,
                         float** X_next);
 
+/* A problem's state between control steps: the plant X_k [n][m], the last
+ * applied control U_{k-1} [l][m] and the Philox solve index -- everything a
+ * later oic_step needs besides the handle's configuration.  A server that
+ * evicts an idle problem from device memory saves it to the host and loads
+ * it into a new handle of the same configuration on re-admission; the next
+ * steps are then bit-identical to uninterrupted ones.  Size in bytes: */
+size_t oic_state_bytes(const oic_handle* h);
+/* Copies the state into host memory `dst` (oic_state_bytes of it) on the
+ * bound stream and waits.  OIC_ESTATE if h is not bound or has no plant. */
+oic_status oic_save_state(oic_handle* h, void* dst);
+/* Sets the state from host memory `src` written by oic_save_state of a
+ * handle with the same sizes (asynchronous on the bound stream; src must
+ * stay valid until the stream reaches it).  OIC_EINVAL on a size mismatch
+ * (the stored sizes are checked), OIC_ESTATE if h is not bound. */
+oic_status oic_load_state(oic_handle* h, const void* src);
+
 typedef struct oic_batch oic_batch;
 
 /* Builds the batch graph of `count` handles (1..4096), each bound, with its

@@ -68,6 +68,9 @@ _SIGS = {
     "oic_selftest": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "oic_enks_update_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                               _VP, _VP, _VP]),
+    "oic_state_bytes": (ctypes.c_size_t, [_VP]),
+    "oic_save_state": (ctypes.c_int, [_VP, _VP]),
+    "oic_load_state": (ctypes.c_int, [_VP, _VP]),
     "oic_io_slots": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "oic_batch_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "oic_batch_step": (ctypes.c_int, [_VP]),
@@ -286,6 +289,17 @@ class Solver:
         cnt = (ctypes.c_int * n)()
         _check(self._lib.oic_profile_end(self.h, ms, cnt), "oic_profile_end")
         return {STAGES[i]: (float(ms[i]), int(cnt[i])) for i in range(n) if cnt[i] > 0}
+
+    def oic_save_state(self):
+        """The problem's state (plant X, last control, solve index) as bytes."""
+        buf = ctypes.create_string_buffer(int(self._lib.oic_state_bytes(self.h)))
+        _check(self._lib.oic_save_state(self.h, buf), "oic_save_state")
+        return buf.raw
+
+    def oic_load_state(self, state: bytes):
+        buf = ctypes.create_string_buffer(state, len(state))
+        _check(self._lib.oic_load_state(self.h, buf), "oic_load_state")
+        self.stream.synchronize()                       # the buffer is local
 
     def oic_io_slots(self):
         """Torch views of the per-step slots in this solver's workspace:

@@ -920,6 +920,56 @@ oic_status oic_selftest(oic_handle* h, int* result)
     return result[0] == 0 ? OIC_OK : OIC_ECUDA;
 }
 
+// ------------------------------------------------------------- problem state
+// Host layout: int32 header {n, m, l, 0}, uint64 solve index, X [n][m],
+// U [l][m] (float32).
+namespace {
+constexpr size_t STATE_HDR = 4 * sizeof(int32_t) + sizeof(unsigned long long);
+}
+
+size_t oic_state_bytes(const oic_handle* h)
+{
+    if (!h) return 0;
+    return STATE_HDR + sizeof(float) * ((size_t)h->cfg.n * h->cfg.m + (size_t)h->cfg.l * h->cfg.m);
+}
+
+oic_status oic_save_state(oic_handle* h, void* dst)
+{
+    if (!h || !dst) return OIC_EINVAL;
+    if (!h->bound || !h->plant_ready) return OIC_ESTATE;
+    const oic_config& c = h->cfg;
+    char* d = static_cast<char*>(dst);
+    const int32_t hdr[4] = {c.n, c.m, c.l, 0};
+    std::memcpy(d, hdr, sizeof(hdr));
+    OIC_CUDA_OK(cudaMemcpyAsync(d + sizeof(hdr), h->at<char>(h->lay.ctr), sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(d + STATE_HDR, h->at<float>(h->lay.plantX), sizeof(float) * c.n * c.m,
+                                cudaMemcpyDeviceToHost, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(d + STATE_HDR + sizeof(float) * c.n * c.m, h->at<float>(h->lay.plantU),
+                                sizeof(float) * c.l * c.m, cudaMemcpyDeviceToHost, h->st));
+    OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    return OIC_OK;
+}
+
+oic_status oic_load_state(oic_handle* h, const void* src)
+{
+    if (!h || !src) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    const oic_config& c = h->cfg;
+    const char* d = static_cast<const char*>(src);
+    int32_t hdr[4];
+    std::memcpy(hdr, d, sizeof(hdr));
+    if (hdr[0] != c.n || hdr[1] != c.m || hdr[2] != c.l) return OIC_EINVAL;
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<char>(h->lay.ctr), d + sizeof(hdr), sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantX), d + STATE_HDR, sizeof(float) * c.n * c.m,
+                                cudaMemcpyHostToDevice, h->st));
+    OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.plantU), d + STATE_HDR + sizeof(float) * c.n * c.m,
+                                sizeof(float) * c.l * c.m, cudaMemcpyHostToDevice, h->st));
+    h->plant_ready = true;
+    return OIC_OK;
+}
+
 // ---------------------------------------------------------------- batching
 struct oic_batch {
     std::vector<oic_handle*> hs;

@@ -399,3 +399,26 @@ def test_batched_uneven_problems_equal_each_problem_alone(cuda_ok):
             assert np.array_equal(sua.cpu().numpy(), ua)
             assert np.array_equal(sxn.cpu().numpy(), xn)
     batch.close()
+
+
+def test_served_results_equal_each_problem_alone_with_evictions(cuda_ok):
+    """The serving loop (continuous batching, admission by HBM footprint)
+    under a budget that fits one problem at a time: requests of three
+    problems arrive interleaved, so problems are evicted (state to the host)
+    and re-admitted between their steps; every applied control equals, bit
+    for bit, the same problem stepped alone and uninterrupted."""
+    from paper_2410_09663_b300 import serving
+    wls = [W.small_16(), W.small_16().with_(N=48, H=3, seed=7), W.small_16().with_(N=24, H=4, seed=9)]
+    steps = 3
+    alone = [_steps_alone(w, steps, oic.OIC_PREC_FP32) for w in wls]
+    srv = serving.Server("cuda", budget_bytes=1, precision=oic.OIC_PREC_FP32, keep_outputs=True)
+    for pid, w in enumerate(wls):
+        srv.add(pid, w, steps_max=steps)
+    srv.budget = max(p.bytes for p in srv.problems.values())
+    arrivals = [(0.001 * i, i % 3) for i in range(3 * steps)]
+    rec, outs, _ = srv.run(arrivals)
+    for i, (t, pid) in enumerate(arrivals):
+        k = rec[i][1]
+        assert k == i // 3
+        assert np.array_equal(outs[i], alone[pid][k][0])
+    assert sum(p.evictions for p in srv.problems.values()) >= 2
