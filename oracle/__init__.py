@@ -18,6 +18,9 @@ Parity status per function (see the tests that pin each one):
                   (Theorem 1) for a vertical-tap linear CNN, as N*m grows
   run             pinned: closed-loop cost under control below the uncontrolled
                   cost (qualitative, Numerical Experiments section)
+  control_expand  pinned: a hand-worked product, T = I
+  control_reduce  pinned: column means for T = [1 ... 1], reduce(expand(u)) = u,
+                  T = I, rank-deficient T reported
   nonlinear multi-layer solves beyond these pins: parity unpinned -- the oracle
   itself is the authority there.
 """
@@ -73,8 +76,11 @@ def _load():
         _lib.oracle_enks_analysis.argtypes = [i, i, i, i, P, l_, P, P]
         _lib.oracle_enks_solve.argtypes = [ctypes.POINTER(_Net), i, i, P, P, P, P, P, P]
         _lib.oracle_run.argtypes = [ctypes.POINTER(_Net), i, i, i, P, P, P, P, P, P, P, P]
+        _lib.oracle_control_expand.argtypes = [i, i, i, P, P, P]
+        _lib.oracle_control_expand.restype = None
+        _lib.oracle_control_reduce.argtypes = [i, i, i, P, P, P]
         for f in ("oracle_cnn_step", "oracle_cnn_step_batch", "oracle_cholesky", "oracle_gain",
-                  "oracle_enks_analysis", "oracle_enks_solve", "oracle_run"):
+                  "oracle_enks_analysis", "oracle_enks_solve", "oracle_run", "oracle_control_reduce"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
 
@@ -254,3 +260,21 @@ def rmse(X, X_ref):
     """Tracking RMSE diagnostic sqrt(||X - X_ref||_F^2 / (n m))."""
     X, X_ref = _d(X), _d(X_ref)
     return float(np.sqrt(np.mean((X - X_ref) ** 2)))
+
+
+def control_expand(u, T):
+    """Narrow controls: U = u T (u: l x mu, T: mu x m)."""
+    u, T = _d(u), _d(T)
+    U = np.empty((u.shape[0], T.shape[1]))
+    _load().oracle_control_expand(u.shape[0], u.shape[1], T.shape[1], _p(u), _p(T), _p(U))
+    return U
+
+
+def control_reduce(U, T):
+    """Narrow controls: u = U T^T (T T^T)^{-1} (U: l x m, T: mu x m)."""
+    U, T = _d(U), _d(T)
+    u = np.empty((U.shape[0], T.shape[0]))
+    st = _load().oracle_control_reduce(U.shape[0], U.shape[1], T.shape[0], _p(U), _p(T), _p(u))
+    if st:
+        raise np.linalg.LinAlgError(f"T T^T not positive definite (status {st})")
+    return u

@@ -29,6 +29,10 @@
  *                         Eq. (prediction-concatenate) writes it
  *   oracle_run            the receding-horizon loop of Algorithm 1 with the
  *                         plant taken to be CNN_theta itself
+ *   oracle_control_expand U = u T, and
+ *   oracle_control_reduce u = U T^T (T T^T)^{-1}: the right transformation for
+ *                         controls with fewer columns than the state (the
+ *                         paragraph on narrow controls after Table I)
  *
  * Readings where the paper is silent or garbled (all fixed here):
  *   - means use 1/N (Eq. (mathcalX-prediction-sample-mean)); the sums printed
@@ -413,4 +417,59 @@ int oracle_run(const oracle_net *net, int N, int H, int S, const double *X_0,
     }
     free(xhat); free(uprev);
     return status;
+}
+
+/* Narrow controls (the paragraph after Table I): a control u with mu < m
+ * columns is widened to U = u T (l x m) with a right-transformation matrix T
+ * (mu x m, T T^T > 0), and a smoothed U is mapped back by
+ * u = U T^T (T T^T)^{-1}.  Row-major throughout. */
+void oracle_control_expand(int l, int mu, int m, const double *u, const double *T, double *U)
+{
+    for (int r = 0; r < l; ++r)
+        for (int j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int c = 0; c < mu; ++c) s += u[r * mu + c] * T[c * m + j];
+            U[r * m + j] = s;
+        }
+}
+
+/* u = U T^T (T T^T)^{-1}: with G = T T^T (symmetric) each row of u solves
+ * G u_r^T = (U T^T)_r^T, by the Cholesky factor of G and two substitutions.
+ * Returns the Cholesky status (0, or the pivot + 1 where T T^T is not
+ * positive definite), -1 if memory runs out. */
+int oracle_control_reduce(int l, int m, int mu, const double *U, const double *T, double *u)
+{
+    double *G = malloc(sizeof(double) * (size_t)mu * mu);
+    double *L = malloc(sizeof(double) * (size_t)mu * mu);
+    double *w = malloc(sizeof(double) * (size_t)mu);
+    double *z = malloc(sizeof(double) * (size_t)mu);
+    if (!G || !L || !w || !z) { free(G); free(L); free(w); free(z); return -1; }
+    for (int a = 0; a < mu; ++a)
+        for (int b = 0; b < mu; ++b) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += T[a * m + j] * T[b * m + j];
+            G[a * mu + b] = s;
+        }
+    int st = oracle_cholesky(mu, G, L);
+    if (st == 0) {
+        for (int r = 0; r < l; ++r) {
+            for (int a = 0; a < mu; ++a) {          /* w = (U T^T)_r */
+                double s = 0.0;
+                for (int j = 0; j < m; ++j) s += U[r * m + j] * T[a * m + j];
+                w[a] = s;
+            }
+            for (int i = 0; i < mu; ++i) {          /* L z = w */
+                double s = w[i];
+                for (int j = 0; j < i; ++j) s -= L[i * mu + j] * z[j];
+                z[i] = s / L[i * mu + i];
+            }
+            for (int i = mu - 1; i >= 0; --i) {     /* L^T u_r = z */
+                double s = z[i];
+                for (int j = i + 1; j < mu; ++j) s -= L[j * mu + i] * u[r * mu + j];
+                u[r * mu + i] = s / L[i * mu + i];
+            }
+        }
+    }
+    free(G); free(L); free(w); free(z);
+    return st;
 }

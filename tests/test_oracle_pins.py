@@ -407,3 +407,39 @@ def test_closed_loop_cost_below_uncontrolled():
     assert j_ctl < 0.95 * j_free, (j_ctl, j_free)
     # tracking error (zero reference) ends lower than without control
     assert oracle.rmse(Xt[-1], xr[S]) < oracle.rmse(X0[-1], xr[S])
+
+
+# ---------------------------------------------------------------- narrow controls
+# The right transformation of the paragraph after Table I: U = u T, and back
+# u = U T^T (T T^T)^{-1}.
+
+def test_control_expand_hand_worked():
+    u = np.array([[1.0, 2.0], [-1.0, 0.5]])
+    T = np.array([[1.0, 0.0, 1.0], [0.0, 1.0, 1.0]])
+    np.testing.assert_array_equal(oracle.control_expand(u, T), [[1.0, 2.0, 3.0], [-1.0, 0.5, -0.5]])
+
+
+def test_control_reduce_with_ones_row_is_the_column_mean():
+    """T = [1 ... 1] repeats a column vector; the map back is the mean over
+    the columns: U 1^T / m."""
+    rng = np.random.default_rng(1)
+    U = rng.standard_normal((5, 12))
+    u = oracle.control_reduce(U, np.ones((1, 12)))
+    np.testing.assert_allclose(u[:, 0], U.mean(axis=1), rtol=0, atol=1e-14)
+
+
+def test_control_reduce_inverts_expand_and_identity():
+    rng = np.random.default_rng(2)
+    for mu, m in ((1, 8), (3, 16), (7, 64)):
+        T = rng.standard_normal((mu, m))
+        u = rng.standard_normal((4, mu))
+        np.testing.assert_allclose(oracle.control_reduce(oracle.control_expand(u, T), T), u, rtol=0, atol=1e-12)
+    U = rng.standard_normal((3, 9))
+    np.testing.assert_allclose(oracle.control_reduce(U, np.eye(9)), U, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(oracle.control_expand(U, np.eye(9)), U, rtol=0, atol=0)
+
+
+def test_control_reduce_reports_rank_deficient_transform():
+    T = np.array([[1.0, 2.0, 3.0], [2.0, 4.0, 6.0]])      # T T^T singular
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.control_reduce(np.ones((2, 3)), T)
