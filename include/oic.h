@@ -248,6 +248,28 @@ oic_status oic_sync(oic_handle* h);
  * around the call on the bound stream; valid after oic_sync). */
 float oic_last_ms(oic_handle* h);
 
+/* ------------------------------------------------------- narrow controls
+ * The right transformation for controls with fewer columns than the state
+ * (the paragraph on narrow controls after the paper's Table I): a control u
+ * of mu < m columns enters the method as U = u T, with T (mu x m, T T^T > 0)
+ * chosen by the caller (T = [1 ... 1] repeats a column vector), and a
+ * smoothed U maps back to u = U T^T (T T^T)^{-1}.  Device pointers,
+ * row-major float32, asynchronous on `cuda_stream` except as noted. */
+
+/* U [l][m] = u [l][mu] T [mu][m].  OIC_EINVAL unless 1 <= mu <= m <= 1024
+ * and 1 <= l <= 4096. */
+oic_status oic_control_expand(const float* u, int l, int mu, const float* T, int m, float* U,
+                              void* cuda_stream);
+
+/* u [l][mu] = U [l][m] T^T (T T^T)^{-1}, in FP64 (Cholesky of T T^T, two
+ * substitutions per row), rounded to float32 at the end.  Limits 1 <= mu <=
+ * 64, mu <= m <= 1024, 1 <= l <= 256.  Synchronises the stream and returns
+ * OIC_ENOTSPD (u untouched) if T T^T is not positive definite.  Concurrent
+ * calls on several streams share one device status word and must be
+ * serialised by the caller. */
+oic_status oic_control_reduce(const float* U, int l, int m, const float* T, int mu, float* u,
+                              void* cuda_stream);
+
 /* ---------------------------------------------------------------- batching
  * Independent problems stepped together (a deployment extension; the paper
  * solves one problem at a time): one receding-horizon control step of every

@@ -68,6 +68,8 @@ _SIGS = {
     "oic_selftest": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "oic_enks_update_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                               _VP, _VP, _VP]),
+    "oic_control_expand": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP]),
+    "oic_control_reduce": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP]),
     "oic_state_bytes": (ctypes.c_size_t, [_VP]),
     "oic_save_state": (ctypes.c_int, [_VP, _VP]),
     "oic_load_state": (ctypes.c_int, [_VP, _VP]),
@@ -147,6 +149,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _stream_of(t, stream):
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream(t.device)
+    return ctypes.c_void_p(st.cuda_stream)
+
+
+def oic_control_expand(u, T, U, stream=None):
+    """U = u T for a control u [l, mu] with fewer columns than the state
+    (T [mu, m]); device tensors, float32, asynchronous on `stream`."""
+    l, mu = u.shape
+    _check(load().oic_control_expand(_ptr(u), l, mu, _ptr(T), T.shape[1], _ptr(U), _stream_of(u, stream)),
+           "oic_control_expand")
+
+
+def oic_control_reduce(U, T, u, stream=None):
+    """u = U T^T (T T^T)^{-1} (U [l, m], T [mu, m]); waits for the stream."""
+    l, m = U.shape
+    _check(load().oic_control_reduce(_ptr(U), l, m, _ptr(T), T.shape[0], _ptr(u), _stream_of(U, stream)),
+           "oic_control_reduce")
 
 
 def config_from_workload(wl, precision=OIC_PREC_FP32, keep_full_history=False,

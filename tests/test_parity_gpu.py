@@ -422,3 +422,33 @@ def test_served_results_equal_each_problem_alone_with_evictions(cuda_ok):
         assert k == i // 3
         assert np.array_equal(outs[i], alone[pid][k][0])
     assert sum(p.evictions for p in srv.problems.values()) >= 2
+
+
+@pytest.mark.parametrize("l,mu,m", [(4, 1, 16), (8, 3, 64), (16, 8, 128), (5, 7, 24)])
+def test_narrow_control_transform_matches_oracle(cuda_ok, l, mu, m):
+    """U = u T and u = U T^T (T T^T)^{-1} against the FP64 oracle (expand:
+    FP32 dot products of mu terms; reduce: FP64 inside, float32 out)."""
+    rng = np.random.default_rng(l * 100 + mu)
+    T = rng.standard_normal((mu, m)).astype(np.float32)
+    u = rng.standard_normal((l, mu)).astype(np.float32)
+    U = rng.standard_normal((l, m)).astype(np.float32)
+    Ud = dev(np.zeros((l, m)))
+    oic.oic_control_expand(dev(u), dev(T), Ud)
+    want = oracle.control_expand(u, T)
+    assert np.abs(Ud.cpu().numpy() - want).max() <= 1e-6 * max(1.0, np.abs(want).max()) * mu
+    ud = dev(np.zeros((l, mu)))
+    oic.oic_control_reduce(dev(U), dev(T), ud)
+    want = oracle.control_reduce(U, T)
+    assert np.abs(ud.cpu().numpy() - want).max() <= 2 ** -23 * np.abs(want).max() * 4
+    ones = dev(np.ones((1, m)))
+    u1 = dev(np.zeros((l, 1)))
+    oic.oic_control_reduce(dev(U), ones, u1)
+    np.testing.assert_allclose(u1.cpu().numpy()[:, 0], U.astype(np.float64).mean(axis=1), rtol=1e-6, atol=1e-7)
+
+
+def test_narrow_control_reduce_reports_rank_deficient_transform(cuda_ok):
+    T = np.array([[1.0, 2.0, 3.0, 4.0], [2.0, 4.0, 6.0, 8.0]], np.float32)
+    u = dev(np.zeros((3, 2)))
+    with pytest.raises(oic.OICError) as e:
+        oic.oic_control_reduce(dev(np.ones((3, 4))), dev(T), u)
+    assert e.value.status == oic.OIC_ENOTSPD
