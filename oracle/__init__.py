@@ -21,6 +21,15 @@ Parity status per function (see the tests that pin each one):
   control_expand  pinned: a hand-worked product, T = I
   control_reduce  pinned: column means for T = [1 ... 1], reduce(expand(u)) = u,
                   T = I, rank-deficient T reported
+  softplus_barrier pinned: closed forms phi(0) = ln 2 / alpha,
+                  phi(ln(e - 1) / beta) = 1 / alpha, phi(x) - phi(-x) = beta x / alpha,
+                  the two limits (0 far inside, beta x / alpha far outside)
+  constraint_obs  pinned: a hand-worked 2-row case
+  enks_solve / run with constraints: pinned by an H = 1 solve rebuilt from the
+                  pinned pieces (CNN step, constraint rows, textbook analysis)
+                  and by a solve whose control reference lies outside a box:
+                  the plan follows it without the rows and sits at the bound
+                  with them (sign and strength of the barrier's pull)
   nonlinear multi-layer solves beyond these pins: parity unpinned -- the oracle
   itself is the authority there.
 """
@@ -58,6 +67,16 @@ class _Net(ctypes.Structure):
     ]
 
 
+class _Cons(ctypes.Structure):
+    _fields_ = [
+        ("c", ctypes.c_int),
+        ("Gx", ctypes.POINTER(ctypes.c_double)),
+        ("Gu", ctypes.POINTER(ctypes.c_double)),
+        ("h", ctypes.POINTER(ctypes.c_double)),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+    ]
+
+
 _lib = None
 
 
@@ -79,8 +98,16 @@ def _load():
         _lib.oracle_control_expand.argtypes = [i, i, i, P, P, P]
         _lib.oracle_control_expand.restype = None
         _lib.oracle_control_reduce.argtypes = [i, i, i, P, P, P]
+        C = ctypes.POINTER(_Cons)
+        _lib.oracle_softplus_barrier.argtypes = [ctypes.c_double] * 3
+        _lib.oracle_softplus_barrier.restype = ctypes.c_double
+        _lib.oracle_constraint_obs.argtypes = [C, i, i, i, P, P, P, P]
+        _lib.oracle_constraint_obs.restype = None
+        _lib.oracle_enks_solve_c.argtypes = [ctypes.POINTER(_Net), i, i, P, P, P, P, P, C, P]
+        _lib.oracle_run_c.argtypes = [ctypes.POINTER(_Net), i, i, i, P, P, P, P, P, C, P, P, P]
         for f in ("oracle_cnn_step", "oracle_cnn_step_batch", "oracle_cholesky", "oracle_gain",
-                  "oracle_enks_analysis", "oracle_enks_solve", "oracle_run", "oracle_control_reduce"):
+                  "oracle_enks_analysis", "oracle_enks_solve", "oracle_run", "oracle_control_reduce",
+                  "oracle_enks_solve_c", "oracle_run_c"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
 
@@ -124,6 +151,48 @@ class Net:
     @property
     def p(self):
         return self.n + self.l
+
+
+class Cons:
+    """c virtual constraint observations z = phi(Gx X + Gu U - h 1^T) + eps with
+    reference 0, phi(x) = ln(1 + e^{beta x}) / alpha (the paragraph on
+    state/input constraints after Table I).  Gx: c x n, Gu: c x l, h: c."""
+
+    def __init__(self, Gx, Gu, h, alpha, beta):
+        self.Gx = _d(np.atleast_2d(Gx))
+        self.Gu = _d(np.atleast_2d(Gu))
+        self.h = _d(np.ravel(h))
+        self.c = self.h.size
+        assert self.Gx.shape[0] == self.c and self.Gu.shape[0] == self.c
+        self.alpha, self.beta = float(alpha), float(beta)
+        s = _Cons()
+        s.c = self.c
+        s.Gx, s.Gu, s.h = _p(self.Gx), _p(self.Gu), _p(self.h)
+        s.alpha, s.beta = self.alpha, self.beta
+        self._s = s
+
+
+def _cons_ptr(cons):
+    return ctypes.byref(cons._s) if cons is not None else None
+
+
+def softplus_barrier(x, alpha, beta):
+    """phi(x) = ln(1 + e^{beta x}) / alpha, element-wise."""
+    f = _load().oracle_softplus_barrier
+    x = np.asarray(x, np.float64)
+    return np.vectorize(lambda v: f(float(v), float(alpha), float(beta)))(x) if x.ndim else f(float(x), alpha, beta)
+
+
+def constraint_obs(cons: Cons, X, U, eps=None):
+    """z = phi(Gx X + Gu U - h 1^T) + eps for one member (X: n x m, U: l x m)."""
+    X, U = _d(X), _d(U)
+    n, m = X.shape
+    l = U.shape[0]
+    assert cons.Gx.shape[1] == n and cons.Gu.shape[1] == l
+    eps = np.zeros((cons.c, m)) if eps is None else _d(eps).reshape(cons.c, m)
+    z = np.empty((cons.c, m))
+    _load().oracle_constraint_obs(ctypes.byref(cons._s), n, l, m, _p(X), _p(U), _p(eps), _p(z))
+    return z
 
 
 def conv3x3(x, w, b, apply_tanh=False):
@@ -193,29 +262,31 @@ def enks_analysis(X, Y, Ybar):
     return X
 
 
-def noise_floats(n, m, l, N, H):
-    """Length of one solve's noise buffer: W0, W, VX, VU."""
-    return N * l * m + H * N * (l * m + n * m + l * m)
+def noise_floats(n, m, l, N, H, c=0):
+    """Length of one solve's noise buffer: W0, W, VX, VU (and VZ for c
+    constraint rows)."""
+    return N * l * m + H * N * (l * m + n * m + l * m + c * m)
 
 
-def enks_solve(net: Net, N, H, X_k, U_prev, X_ref, U_ref, noise):
-    """One receding-horizon solve (Algorithm 1 lines 4-15) with full history.
+def enks_solve(net: Net, N, H, X_k, U_prev, X_ref, U_ref, noise, cons: Cons | None = None):
+    """One receding-horizon solve (Algorithm 1 lines 4-15) with full history,
+    with the constraint rows of `cons` appended to the pseudo-observation.
 
     Returns Xbar_hat [(H+1)][q][m]: smoothed means of blocks k..k+H."""
     n, m, l = net.n, net.m, net.l
     X_k, U_prev, U_ref = _d(X_k), _d(U_prev), _d(U_ref)
     X_ref = _d(X_ref).reshape(H + 1, n, m)
     noise = _d(noise).ravel()
-    assert noise.size == noise_floats(n, m, l, N, H)
+    assert noise.size == noise_floats(n, m, l, N, H, cons.c if cons is not None else 0)
     out = np.empty((H + 1, net.q, m))
-    st = _load().oracle_enks_solve(ctypes.byref(net._s), N, H, _p(X_k), _p(U_prev), _p(X_ref),
-                                   _p(U_ref), _p(noise), _p(out))
+    st = _load().oracle_enks_solve_c(ctypes.byref(net._s), N, H, _p(X_k), _p(U_prev), _p(X_ref),
+                                     _p(U_ref), _p(noise), _cons_ptr(cons), _p(out))
     if st:
         raise np.linalg.LinAlgError(f"solve failed (status {st})")
     return out
 
 
-def run(net: Net, N, H, S, X_0, U_init, X_ref_all, U_ref, noise_all):
+def run(net: Net, N, H, S, X_0, U_init, X_ref_all, U_ref, noise_all, cons: Cons | None = None):
     """S receding-horizon steps (Algorithm 1), plant = CNN_theta.
 
     X_ref_all holds references for absolute times 0 .. S+H-1 (at least S+H
@@ -226,12 +297,12 @@ def run(net: Net, N, H, S, X_0, U_init, X_ref_all, U_ref, noise_all):
     X_ref_all = _d(X_ref_all).reshape(-1, n, m)
     assert X_ref_all.shape[0] >= S + H
     noise_all = _d(noise_all).ravel()
-    assert noise_all.size == S * noise_floats(n, m, l, N, H)
+    assert noise_all.size == S * noise_floats(n, m, l, N, H, cons.c if cons is not None else 0)
     Xt = np.empty((S + 1, n, m))
     Ut = np.empty((S, l, m))
     Uh = np.empty((S, H + 1, l, m))
-    st = _load().oracle_run(ctypes.byref(net._s), N, H, S, _p(X_0), _p(U_init), _p(X_ref_all),
-                            _p(U_ref), _p(noise_all), _p(Xt), _p(Ut), _p(Uh))
+    st = _load().oracle_run_c(ctypes.byref(net._s), N, H, S, _p(X_0), _p(U_init), _p(X_ref_all),
+                              _p(U_ref), _p(noise_all), _cons_ptr(cons), _p(Xt), _p(Ut), _p(Uh))
     if st:
         raise np.linalg.LinAlgError(f"run failed (status {st})")
     return Xt, Ut, Uh

@@ -33,6 +33,12 @@
  *   oracle_control_reduce u = U T^T (T T^T)^{-1}: the right transformation for
  *                         controls with fewer columns than the state (the
  *                         paragraph on narrow controls after Table I)
+ *   oracle_softplus_barrier phi(x) = ln(1 + e^{beta x}) / alpha, and
+ *   oracle_constraint_obs z = phi(g(X, U)) + eps: the virtual observation of
+ *                         a constraint g(X, U) <= 0 with reference 0 (the
+ *                         paragraph on state/input constraints after
+ *                         Table I); oracle_enks_solve_c and oracle_run_c
+ *                         append its rows to the pseudo-observation
  *
  * Readings where the paper is silent or garbled (all fixed here):
  *   - means use 1/N (Eq. (mathcalX-prediction-sample-mean)); the sums printed
@@ -45,7 +51,13 @@
  *   - ensemble initialisation at step k: X^i = X_k, U^i = U_{k-1} + W0^i,
  *     dU^i = W0^i;
  *   - updates happen at t = k+1 .. k+H (Algorithm 1); the applied control is the
- *     smoothed mean of the U block at time k after the last update.
+ *     smoothed mean of the U block at time k after the last update;
+ *   - constraints: the paper's scalar g is evaluated column by column, so a
+ *     constraint is one row of m values and c of them stack into a c x m
+ *     virtual observation; the family is affine per column,
+ *     g = Gx X_t + Gu U_t - h 1^T, taken at the predicted X_t and U_t of each
+ *     assimilation time t = k+1 .. k+H, observed with noise eps ~ N(0, s_z^2)
+ *     and reference 0; the rows are observations only, never state.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -62,6 +74,15 @@ typedef struct {
     const double *B;                          /* n x l input matrix             */
     double residual_scale;                    /* X_{k+1} = X_k + s * out        */
 } oracle_net;
+
+/* c virtual constraint observations (c = 0: none). */
+typedef struct {
+    int c;
+    const double *Gx;                         /* c x n                          */
+    const double *Gu;                         /* c x l                          */
+    const double *h;                          /* c                              */
+    double alpha, beta;                       /* softplus barrier parameters    */
+} oracle_cons;
 
 /* ------------------------------------------------------------------------ */
 /* Eq. (1): one 3x3 convolution layer, stride 1, zero padding ("same"),
@@ -282,6 +303,30 @@ int oracle_enks_analysis(int N, int R, int p, int m, double *X, long xs,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Constraint rows (the paragraph on state/input constraints after Table I).
+ * phi is evaluated as max(y, 0) + log1p(e^{-|y|}) with y = beta x, which is
+ * ln(1 + e^{y}) rewritten so that e^{y} cannot overflow. */
+double oracle_softplus_barrier(double x, double alpha, double beta)
+{
+    const double y = beta * x;
+    return ((y > 0.0 ? y : 0.0) + log1p(exp(-fabs(y)))) / alpha;
+}
+
+/* z[r][j] = phi( sum_a Gx[r][a] X[a][j] + sum_b Gu[r][b] U[b][j] - h[r] )
+ *           + eps[r][j]                       (X: n x m, U: l x m, z: c x m) */
+void oracle_constraint_obs(const oracle_cons *cs, int n, int l, int m, const double *X,
+                           const double *U, const double *eps, double *z)
+{
+    for (int r = 0; r < cs->c; ++r)
+        for (int j = 0; j < m; ++j) {
+            double g = -cs->h[r];
+            for (int a = 0; a < n; ++a) g += cs->Gx[r * n + a] * X[a * m + j];
+            for (int b = 0; b < l; ++b) g += cs->Gu[r * l + b] * U[b * m + j];
+            z[r * m + j] = oracle_softplus_barrier(g, cs->alpha, cs->beta) + eps[r * m + j];
+        }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 1, lines 4-15, for one control step k.
  *
  * Augmented state X̄ = [X; U; dU] has q = n + 2l rows; the pseudo-observation
@@ -292,23 +337,28 @@ int oracle_enks_analysis(int N, int R, int p, int m, double *X, long xs,
  *   U_prev l x m          control applied at k-1
  *   X_ref  (H+1) x n x m  references for times k .. k+H
  *   U_ref  l x m
- *   noise  W0 [N][l][m], then W [H][N][l][m], VX [H][N][n][m], VU [H][N][l][m]
+ *   noise  W0 [N][l][m], then W [H][N][l][m], VX [H][N][n][m], VU [H][N][l][m],
+ *          then, with c > 0 constraint rows, VZ [H][N][c][m] (eps of z)
+ *   cs     constraint rows (oracle_enks_solve_c only; NULL or c = 0: none);
+ *          they extend Ȳ to p = n + l + c rows [X^ref; U^ref; 0]
  * Output:
  *   Xbar_hat (H+1) x q x m: smoothed means of blocks k .. k+H after the update
  *            at t = k+H (Eq. (ensemble-based-Kalman-update-mean)).
  * Returns 0, or the first nonzero Cholesky status. */
-int oracle_enks_solve(const oracle_net *net, int N, int H, const double *X_k,
-                      const double *U_prev, const double *X_ref, const double *U_ref,
-                      const double *noise, double *Xbar_hat)
+int oracle_enks_solve_c(const oracle_net *net, int N, int H, const double *X_k,
+                        const double *U_prev, const double *X_ref, const double *U_ref,
+                        const double *noise, const oracle_cons *cs, double *Xbar_hat)
 {
     const int n = net->n, m = net->m, l = net->l;
-    const int q = n + 2 * l, p = n + l;
+    const int nc = cs ? cs->c : 0;
+    const int q = n + 2 * l, p = n + l + nc;
     const size_t bq = (size_t)q * m;                   /* one block        */
     const long xs = (long)(H + 1) * (long)bq;          /* member stride    */
     const double *W0 = noise;
     const double *W = W0 + (size_t)N * l * m;
     const double *VX = W + (size_t)H * N * l * m;
     const double *VU = VX + (size_t)H * N * n * m;
+    const double *VZ = VU + (size_t)H * N * l * m;     /* [H][N][c][m] */
 
     double *hist = calloc((size_t)N * xs, sizeof(double));
     double *Y = malloc(sizeof(double) * (size_t)N * p * m);
@@ -356,10 +406,16 @@ int oracle_enks_solve(const oracle_net *net, int N, int H, const double *X_k,
             for (int r = 0; r < n * m; ++r) Yi[r] = cur[r] + VXs[(size_t)i * n * m + r];
             for (int r = 0; r < l * m; ++r)
                 Yi[(size_t)n * m + r] = cur[(size_t)n * m + r] + VUs[(size_t)i * l * m + r];
+            /* constraint rows z^i_t = phi(g(X^i_t, U^i_t)) + eps^i_t */
+            if (nc > 0)
+                oracle_constraint_obs(cs, n, l, m, cur, cur + (size_t)n * m,
+                                      VZ + ((size_t)(s - 1) * N + i) * nc * m,
+                                      Yi + (size_t)(n + l) * m);
         }
-        /* Ȳ_t = [X^ref_t; U^ref] */
+        /* Ȳ_t = [X^ref_t; U^ref; 0] */
         memcpy(Ybar, X_ref + (size_t)s * n * m, sizeof(double) * (size_t)n * m);
         memcpy(Ybar + (size_t)n * m, U_ref, sizeof(double) * (size_t)l * m);
+        memset(Ybar + (size_t)(n + l) * m, 0, sizeof(double) * (size_t)nc * m);
 
         /* lines 9-10, Eq. (Ybar-sample-mean-cov), Eq. (ensemble-based-
          * Kalman-update): update every block 0..s of every member.          */
@@ -378,6 +434,13 @@ int oracle_enks_solve(const oracle_net *net, int N, int H, const double *X_k,
     return status;
 }
 
+int oracle_enks_solve(const oracle_net *net, int N, int H, const double *X_k,
+                      const double *U_prev, const double *X_ref, const double *U_ref,
+                      const double *noise, double *Xbar_hat)
+{
+    return oracle_enks_solve_c(net, N, H, X_k, U_prev, X_ref, U_ref, noise, NULL, Xbar_hat);
+}
+
 /* Algorithm 1, lines 3-19, for S control steps with the plant taken to be
  * CNN_theta itself (no model mismatch, no plant noise):
  *   solve at k -> U_k = smoothed U block at time k -> X_{k+1} = CNN(X_k, U_k).
@@ -387,14 +450,16 @@ int oracle_enks_solve(const oracle_net *net, int N, int H, const double *X_k,
  * Outputs: X_traj (S+1) x n x m (X_0 .. X_S), U_traj S x l x m (applied
  * controls), U_hat_all S x (H+1) x l x m (the smoothed U blocks of each solve;
  * may be NULL).  Returns 0 or the first failing status. */
-int oracle_run(const oracle_net *net, int N, int H, int S, const double *X_0,
-               const double *U_init, const double *X_ref_all, const double *U_ref,
-               const double *noise_all, double *X_traj, double *U_traj, double *U_hat_all)
+int oracle_run_c(const oracle_net *net, int N, int H, int S, const double *X_0,
+                 const double *U_init, const double *X_ref_all, const double *U_ref,
+                 const double *noise_all, const oracle_cons *cs, double *X_traj, double *U_traj,
+                 double *U_hat_all)
 {
     const int n = net->n, m = net->m, l = net->l;
     const int q = n + 2 * l;
     const size_t nx = (size_t)n * m, nu = (size_t)l * m;
-    const size_t noise_per = (size_t)N * nu + (size_t)H * N * (nu + nx + nu);
+    const size_t nz = (size_t)(cs ? cs->c : 0) * m;
+    const size_t noise_per = (size_t)N * nu + (size_t)H * N * (nu + nx + nu + nz);
     double *xhat = malloc(sizeof(double) * (size_t)(H + 1) * q * m);
     double *uprev = malloc(sizeof(double) * nu);
     if (!xhat || !uprev) { free(xhat); free(uprev); return -1; }
@@ -402,8 +467,8 @@ int oracle_run(const oracle_net *net, int N, int H, int S, const double *X_0,
     memcpy(uprev, U_init, sizeof(double) * nu);
     int status = 0;
     for (int k = 0; k < S; ++k) {
-        status = oracle_enks_solve(net, N, H, X_traj + k * nx, uprev, X_ref_all + k * nx,
-                                   U_ref, noise_all + k * noise_per, xhat);
+        status = oracle_enks_solve_c(net, N, H, X_traj + k * nx, uprev, X_ref_all + k * nx,
+                                     U_ref, noise_all + k * noise_per, cs, xhat);
         if (status != 0) break;
         double *Uk = U_traj + k * nu;
         memcpy(Uk, xhat + nx, sizeof(double) * nu);        /* block 0, U rows */
@@ -417,6 +482,14 @@ int oracle_run(const oracle_net *net, int N, int H, int S, const double *X_0,
     }
     free(xhat); free(uprev);
     return status;
+}
+
+int oracle_run(const oracle_net *net, int N, int H, int S, const double *X_0,
+               const double *U_init, const double *X_ref_all, const double *U_ref,
+               const double *noise_all, double *X_traj, double *U_traj, double *U_hat_all)
+{
+    return oracle_run_c(net, N, H, S, X_0, U_init, X_ref_all, U_ref, noise_all, NULL, X_traj,
+                        U_traj, U_hat_all);
 }
 
 /* Narrow controls (the paragraph after Table I): a control u with mu < m

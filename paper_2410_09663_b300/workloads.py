@@ -26,6 +26,10 @@ available, so every workload here is synthetic and stands in for it:
     50 control steps; U^ref = 0.
   * noise: W0, W ~ N(0, sigma_w^2), V_X ~ N(0, sigma_vx^2), V_U ~ N(0, sigma_vu^2),
     all 0.01, drawn per control step k from a generator keyed by (seed, k).
+  * constraints (optional): a box |U| <= u_max on every control entry as 2 l
+    affine rows (Gx = 0, Gu = [I; -I], h = u_max), softplus barrier alpha = 10,
+    beta = 100 and eps ~ N(0, 0.01^2) drawn from its own generator keyed by
+    (seed, k), so the other noise of a step is the same with or without it.
 """
 from __future__ import annotations
 
@@ -35,11 +39,34 @@ import numpy as np
 
 SIGMA = 0.01
 
-_PURPOSE = {"weights": 1, "B": 2, "X0": 3, "noise": 4, "generic": 5}
+_PURPOSE = {"weights": 1, "B": 2, "X0": 3, "noise": 4, "generic": 5, "cnoise": 6}
 
 
 def _rng(seed: int, purpose: str, *extra: int) -> np.random.Generator:
     return np.random.default_rng([int(seed), _PURPOSE[purpose], *[int(e) for e in extra]])
+
+
+@dataclass
+class Constraints:
+    """Inputs of c virtual constraint observations z = phi(Gx X + Gu U - h) +
+    eps (reference 0, phi(x) = ln(1 + e^{beta x}) / alpha, eps ~ N(0, sigma_z^2))."""
+    Gx: np.ndarray                    # c x n, float32
+    Gu: np.ndarray                    # c x l, float32
+    h: np.ndarray                     # c, float32
+    alpha: float = 10.0
+    beta: float = 100.0
+    sigma_z: float = SIGMA
+
+    @property
+    def c(self):
+        return int(self.h.size)
+
+
+def u_box(n: int, l: int, u_max: float, alpha: float = 10.0, beta: float = 100.0, sigma_z: float = SIGMA):
+    """|U[b][j]| <= u_max for every control entry: rows U - u_max and -U - u_max."""
+    Gu = np.concatenate([np.eye(l), -np.eye(l)]).astype(np.float32)
+    return Constraints(np.zeros((2 * l, n), np.float32), Gu, np.full(2 * l, u_max, np.float32), alpha, beta,
+                       sigma_z)
 
 
 @dataclass
@@ -61,14 +88,19 @@ class Workload:
     sigma_vu: float = SIGMA
     seed: int = 0
     extra: dict = field(default_factory=dict)
+    cons: Constraints | None = None
 
     @property
     def q(self):
         return self.n + 2 * self.l
 
     @property
+    def c(self):
+        return self.cons.c if self.cons is not None else 0
+
+    @property
     def p(self):
-        return self.n + self.l
+        return self.n + self.l + self.c
 
     @property
     def n_layers(self):
@@ -138,18 +170,22 @@ class Workload:
     # ------------------------------------------------------------------- noise
     def noise_floats(self):
         n, m, l, N, H = self.n, self.m, self.l, self.N, self.H
-        return N * l * m + H * N * (l * m + n * m + l * m)
+        return N * l * m + H * N * (l * m + n * m + l * m + self.c * m)
 
     def noise(self, k: int):
         """Random numbers of the solve at control step k, float32, laid out as
-        W0 [N][l][m], W [H][N][l][m], V_X [H][N][n][m], V_U [H][N][l][m]."""
+        W0 [N][l][m], W [H][N][l][m], V_X [H][N][n][m], V_U [H][N][l][m], then
+        with constraints eps [H][N][c][m]."""
         n, m, l, N, H = self.n, self.m, self.l, self.N, self.H
         rng = _rng(self.seed, "noise", k)
         w0 = rng.standard_normal((N, l, m)) * self.sigma_w
         w = rng.standard_normal((H, N, l, m)) * self.sigma_w
         vx = rng.standard_normal((H, N, n, m)) * self.sigma_vx
         vu = rng.standard_normal((H, N, l, m)) * self.sigma_vu
-        return np.concatenate([w0.ravel(), w.ravel(), vx.ravel(), vu.ravel()]).astype(np.float32)
+        parts = [w0.ravel(), w.ravel(), vx.ravel(), vu.ravel()]
+        if self.c:
+            parts.append(_rng(self.seed, "cnoise", k).standard_normal((H, N, self.c, m)).ravel() * self.cons.sigma_z)
+        return np.concatenate(parts).astype(np.float32)
 
     def noise_all(self, S: int | None = None):
         S = self.S if S is None else S
@@ -257,5 +293,8 @@ def philox_noise(wl: Workload, solve: int, seed: int | None = None):
     sig = np.empty_like(z)
     sig[:e1] = np.float32(wl.sigma_w)
     sig[e1:e2] = np.float32(wl.sigma_vx)
-    sig[e2:] = np.float32(wl.sigma_vu)
+    e3 = e2 + H * N * l * m
+    sig[e2:e3] = np.float32(wl.sigma_vu)
+    if wl.c:
+        sig[e3:] = np.float32(wl.cons.sigma_z)
     return (sig.astype(np.float32) * z.astype(np.float32)).astype(np.float32)
