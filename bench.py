@@ -174,9 +174,10 @@ def oracle_step_seconds(wl, N_sample, k=0):
     w = wl.with_(N=N_sample)
     net = oracle.Net(w.n, w.m, w.l, w.channels, w.weights(), w.B(), w.residual_scale)
     xr = w.X_ref_all(k + 1)
-    nz = w.noise_all(k + 1)[k:k + 1]
+    nz = w.noise(k)[None]
+    cons = oracle.Cons(w.cons.Gx, w.cons.Gu, w.cons.h, w.cons.alpha, w.cons.beta) if w.cons is not None else None
     t0 = time.perf_counter()
-    oracle.run(net, w.N, w.H, 1, w.X0(), w.U_init(), xr[k:], w.U_ref(), nz)
+    oracle.run(net, w.N, w.H, 1, w.X0(), w.U_init(), xr[k:], w.U_ref(), nz, cons)
     return time.perf_counter() - t0
 
 
@@ -257,6 +258,10 @@ def config_dict(wl, extra=None):
          "cnn": "-".join(str(c) for c in wl.channels), "precision": "fp32",
          "noise": "philox-4x32-10 on device", "history": "U blocks + current X",
          "l2": "flushed between timed steps (256 MB write)"}
+    if wl.cons is not None:
+        d["constraint"] = ("|U| <= %g on every control entry: %d softplus-barrier rows (alpha %g, beta %g, "
+                           "sigma_z %g), p = %d observed rows" % (float(wl.cons.h[0]), wl.c, wl.cons.alpha,
+                                                                 wl.cons.beta, wl.cons.sigma_z, wl.p))
     if extra:
         d.update(extra)
     return d
@@ -282,7 +287,7 @@ def run_oic(args, wl):
     cfg = oic.config_from_workload(wl, noise_mode=oic.OIC_NOISE_PHILOX,
                                    precision=oic.OIC_PREC_MIXED if mixed else oic.OIC_PREC_FP32)
     stream = torch.cuda.Stream(device=dev)
-    s = oic.Solver(cfg, w, b, wl.B(), device=dev, stream=stream)
+    s = oic.Solver(cfg, w, b, wl.B(), device=dev, stream=stream, constraints=wl.cons)
 
     n_break = min(10, args.steps)                       # instrumented breakdown steps
     S_ref = args.steps + args.warmup + n_break + 5
@@ -668,6 +673,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--constraint", choices=["none", "u_box"], default="none",
+                    help="u_box: |U| <= 0.1 on every control entry as 2 l softplus-barrier rows")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -683,6 +690,8 @@ def main(argv=None):
             return 0
         return run_mix(args, args.workload)
     wl = workloads.WORKLOADS[args.workload]()
+    if args.constraint == "u_box":
+        wl = wl.with_(cons=workloads.u_box(wl.n, wl.l, 0.1))
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_oic(args, wl)

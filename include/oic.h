@@ -96,6 +96,41 @@ size_t oic_noise_floats(const oic_config* cfg);
 oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* conv_b,
                       const float* B, oic_handle** out);
 
+/* State/input constraints as virtual observations (the paragraph on
+ * constraints after Table I of the paper).  A constraint g(X, U) <= 0 is
+ * observed as
+ *     z_t = phi(g(X̄_t, Ū_t)) + eps_t,   reference 0,
+ *     phi(x) = ln(1 + e^{beta x}) / alpha   (softplus barrier, alpha, beta > 0),
+ * and z_t joins the pseudo-observation Ȳ_t at every assimilation time
+ * t = k+1 .. k+H, so p = n + l + c rows are observed.  The paper's scalar g is
+ * evaluated column by column: each of the c constraints is one row of m
+ * values, affine in the predicted field and control of the member,
+ *     g[r][j] = sum_a Gx[r][a] X_t[a][j] + sum_b Gu[r][b] U_t[b][j] - h[r].
+ * (A box |U| <= u on every control entry is c = 2 l rows with Gx = 0,
+ * Gu = [I; -I], h = u.)  The rows are observations only: they are not part of
+ * the smoothed state.  eps ~ N(0, sigma_z^2): in OIC_NOISE_HOST mode the solve's
+ * noise buffer carries VZ [H][N][c][m] after VU (oic_handle_noise_floats), in
+ * OIC_NOISE_PHILOX mode it is drawn as a fifth segment after VU, so the other
+ * segments are unchanged. */
+typedef struct {
+    int c;               /* constraint rows, 0 .. 144 - n - l                 */
+    const float* Gx;     /* c x n, host, copied at create                     */
+    const float* Gu;     /* c x l, host, copied at create                     */
+    const float* h;      /* c, host, copied at create                         */
+    double alpha, beta;  /* softplus barrier parameters, both > 0             */
+    double sigma_z;      /* std of eps (OIC_NOISE_PHILOX)                     */
+} oic_constraints;
+
+/* oic_create with constraint rows (cons NULL or cons->c == 0: oic_create).
+ * OIC_EINVAL when n + l + c > 144, alpha or beta <= 0, or a pointer is NULL
+ * with c > 0. */
+oic_status oic_create_constrained(const oic_config* cfg, const float* conv_w, const float* conv_b,
+                                  const float* B, const oic_constraints* cons, oic_handle** out);
+
+/* Floats of one solve's OIC_NOISE_HOST noise buffer for this handle:
+ * oic_noise_floats(cfg) plus H N c m with constraint rows. */
+size_t oic_handle_noise_floats(const oic_handle* h);
+
 /* Device workspace (bytes) the handle needs: ensemble, CNN activations,
  * statistics, gain, plant state and staging for the _host entry points. */
 size_t oic_workspace_bytes(const oic_handle* h);
@@ -183,6 +218,7 @@ typedef enum {
     OIC_STAGE_BLOCK_MEANS,     /* smoothed output means                         */
     OIC_STAGE_CNN_FUSED,       /* whole CNN step in one kernel (all layers)     */
     OIC_STAGE_CNN_BF16,        /* CNN step in BF16, one kernel per layer        */
+    OIC_STAGE_CONSTRAINT,      /* constraint rows z = phi(g(X_t, U_t)) + eps    */
     OIC_NUM_STAGES
 } oic_stage;
 oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launches);

@@ -21,7 +21,8 @@ OIC_OK, OIC_EINVAL, OIC_ENOMEM, OIC_ECUDA, OIC_ENOTSPD, OIC_ETIMEOUT, OIC_ESTATE
 OIC_PREC_FP32, OIC_PREC_MIXED = 0, 1
 OIC_NOISE_HOST, OIC_NOISE_PHILOX = 0, 1
 STAGES = ["noise", "init", "cnn_input", "conv_first", "conv_hidden", "conv_out", "u_advance",
-          "means", "cov", "cov_reduce", "gain", "update", "block_means", "cnn_fused", "cnn_bf16"]
+          "means", "cov", "cov_reduce", "gain", "update", "block_means", "cnn_fused", "cnn_bf16",
+          "constraint"]
 
 
 class OICError(RuntimeError):
@@ -42,6 +43,15 @@ class oic_config(ctypes.Structure):
     ]
 
 
+class oic_constraints(ctypes.Structure):
+    _fields_ = [
+        ("c", ctypes.c_int),
+        ("Gx", ctypes.POINTER(ctypes.c_float)), ("Gu", ctypes.POINTER(ctypes.c_float)),
+        ("h", ctypes.POINTER(ctypes.c_float)),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("sigma_z", ctypes.c_double),
+    ]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 _FP = ctypes.POINTER(ctypes.c_float)
@@ -49,6 +59,9 @@ _FP = ctypes.POINTER(ctypes.c_float)
 _SIGS = {
     "oic_noise_floats": (ctypes.c_size_t, [ctypes.POINTER(oic_config)]),
     "oic_create": (ctypes.c_int, [ctypes.POINTER(oic_config), _VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "oic_create_constrained": (ctypes.c_int, [ctypes.POINTER(oic_config), _VP, _VP, _VP,
+                                              ctypes.POINTER(oic_constraints), ctypes.POINTER(_VP)]),
+    "oic_handle_noise_floats": (ctypes.c_size_t, [_VP]),
     "oic_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "oic_max_rows": (ctypes.c_int, [_VP]),
     "oic_bind": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _VP]),
@@ -199,7 +212,9 @@ class Solver:
     Methods mirror the C entry points; tensors are passed by address.
     """
 
-    def __init__(self, cfg: oic_config, conv_w, conv_b, B, device="cuda", stream=None):
+    def __init__(self, cfg: oic_config, conv_w, conv_b, B, device="cuda", stream=None, constraints=None):
+        """constraints: None, or an object with Gx (c x n), Gu (c x l), h (c),
+        alpha, beta, sigma_z (workloads.Constraints) -> oic_create_constrained."""
         import numpy as np
         import torch
         lib = load()
@@ -209,8 +224,18 @@ class Solver:
         b = np.ascontiguousarray(conv_b, dtype=np.float32)
         Bm = np.ascontiguousarray(B, dtype=np.float32)
         h = _VP()
-        _check(lib.oic_create(ctypes.byref(cfg), w.ctypes.data, b.ctypes.data, Bm.ctypes.data,
-                              ctypes.byref(h)), "oic_create")
+        cs = None
+        if constraints is not None:
+            self._cons_arrays = [np.ascontiguousarray(a, dtype=np.float32).ravel()
+                                 for a in (constraints.Gx, constraints.Gu, constraints.h)]
+            cs = oic_constraints()
+            cs.c = int(self._cons_arrays[2].size)
+            cs.Gx, cs.Gu, cs.h = (a.ctypes.data_as(_FP) for a in self._cons_arrays)
+            cs.alpha, cs.beta, cs.sigma_z = float(constraints.alpha), float(constraints.beta), \
+                float(constraints.sigma_z)
+        _check(lib.oic_create_constrained(ctypes.byref(cfg), w.ctypes.data, b.ctypes.data, Bm.ctypes.data,
+                                          None if cs is None else ctypes.byref(cs), ctypes.byref(h)),
+               "oic_create")
         self.h = h
         self.ws_bytes = lib.oic_workspace_bytes(h)
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
@@ -223,7 +248,7 @@ class Solver:
     # -- sizes
     @property
     def noise_floats(self):
-        return self._lib.oic_noise_floats(ctypes.byref(self.cfg))
+        return self._lib.oic_handle_noise_floats(self.h)
 
     @property
     def max_rows(self):

@@ -100,13 +100,13 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
     long avo[QA], bvo[QB];
     float4 pa[QA], pb[QB], s1[QA];
     const float4 Z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int pb_rows = p - V.pa;
+    const int pb_rows = p - obs.nc - V.pa;              // V rows of Vb per member
     auto resolve = [&](int a, long& off, int& vs, long& vo) {
         vs = 0; vo = 0;
         if (a < R) { off = (long)act.rows[a] * m; return; }
         const int c = a - R;
         off = (long)obs.rows[c] * m;
-        if (V.Va == nullptr) return;
+        if (V.Va == nullptr || c >= p - obs.nc) return;   // constraint rows carry their noise in E
         if (c < V.pa) { vs = 1; vo = (long)c * m; }
         else { vs = 2; vo = (long)(c - V.pa) * m; }
     };
@@ -173,9 +173,10 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
                 *reinterpret_cast<float4*>(Bs + br[q] * ld + bj[q]) = d;
                 const int c = bn0 + br[q];
                 if (do_d && c < p) {
-                    const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
-                    *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + bj[q]) =
-                        f4sub(*reinterpret_cast<const float4*>(yb + bj[q]), pb[q]);
+                    const float4 ref = c >= p - obs.nc ? Z   // constraint rows: reference 0
+                                       : *reinterpret_cast<const float4*>(
+                                             (c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m) + bj[q]);
+                    *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + bj[q]) = f4sub(ref, pb[q]);
                 }
             }
         __syncthreads();

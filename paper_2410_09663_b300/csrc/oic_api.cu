@@ -59,6 +59,7 @@ struct StepGraph {
 
 struct Layout {
     size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, tB, tAop, tBd, ctr, rowtab, status, selftest;
+    size_t cG, ccols, ch;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
     size_t total;
@@ -79,6 +80,11 @@ struct oic_handle {
     cudaStream_t st = nullptr;
     bool bound = false, plant_ready = false, fused = false, bf16 = false;
     std::vector<size_t> w16_off, b16_off;   // mixed-precision CNN: packed layer tiles, padded biases
+    // constraint rows: G packed over the nk non-zero columns of [Gx Gu]
+    int nc = 0, nk = 0, zrow = 0;
+    std::vector<float> cG, ch;
+    std::vector<int> ccols;
+    float c_alpha = 1.f, c_beta = 1.f, c_sigma = 0.f;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int> obs_host;
     Profiler prof;
@@ -156,10 +162,10 @@ bool valid_config(const oic_config* c)
     return true;
 }
 
-size_t noise_count(const oic_config* c)
+size_t noise_count(const oic_config* c, int nc = 0)
 {
     const size_t N = c->N, n = c->n, m = c->m, l = c->l, H = c->H;
-    return N * l * m + H * N * (l * m + n * m + l * m);
+    return N * l * m + H * N * (l * m + n * m + l * m + (size_t)nc * m);
 }
 
 void compute_layout(oic_handle* h)
@@ -230,6 +236,9 @@ void compute_layout(oic_handle* h)
     L.rowtab = take(sizeof(int) * (H + 2) * (Ra + p));
     L.status = take(64);
     L.selftest = take(64);
+    L.cG = take(sizeof(float) * h->cG.size());
+    L.ccols = take(sizeof(int) * h->ccols.size());
+    L.ch = take(sizeof(float) * h->ch.size());
     L.plantX = take(sizeof(float) * n * m);
     L.plantU = take(sizeof(float) * l * m);
     L.plantTmp = take(sizeof(float) * n * m);
@@ -371,13 +380,13 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
     const size_t N = c.N, n = c.n, m = c.m, l = c.l, H = c.H;
     if (c.noise_mode == OIC_NOISE_PHILOX) {
         const size_t e0 = N * l * m, e1 = e0 + H * N * l * m, e2 = e1 + H * N * n * m,
-                     e3 = e2 + H * N * l * m;
-        const size_t ends[4] = {e0, e1, e2, e3};
-        const float sig[4] = {(float)c.sigma_w, (float)c.sigma_w, (float)c.sigma_vx, (float)c.sigma_vu};
+                     e3 = e2 + H * N * l * m, e4 = e3 + H * N * (size_t)h->nc * m;
+        const size_t ends[5] = {e0, e1, e2, e3, e4};
+        const float sig[5] = {(float)c.sigma_w, (float)c.sigma_w, (float)c.sigma_vx, (float)c.sigma_vu, h->c_sigma};
         float* buf = h->at<float>(h->lay.noise);
         run_stage(h, OIC_STAGE_NOISE, [&] {
-            launch_philox_noise(buf, h->noise_n, c.seed, h->at<unsigned long long>(h->lay.ctr), ends, sig, 4,
-                                h->st);
+            launch_philox_noise(buf, h->noise_n, c.seed, h->at<unsigned long long>(h->lay.ctr), ends, sig,
+                                h->nc > 0 ? 5 : 4, h->st);
         });
         g_launches.fetch_add(1, std::memory_order_relaxed);   // the counter tick
         noise = buf;
@@ -386,6 +395,7 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
     const float* W = W0 + N * l * m;
     const float* VX = W + H * N * l * m;
     const float* VU = VX + H * N * n * m;
+    const float* VZ = VU + H * N * l * m;
     float* E = h->at<float>(h->lay.E);
     const long ms = h->ms();
 
@@ -400,9 +410,17 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
             launch_u_advance(E, ms, c.N, c.m, c.l, h->urow(s - 1), h->urow(s), W + (s - 1) * N * l * m,
                              h->st);
         });
-        // analysis at t = k + s with Ybar_t = [X_ref[s]; U_ref]
+        // constraint rows z_t = phi(g(X_t, U_t)) + eps_t (reference 0)
+        if (h->nc > 0)
+            run_stage(h, OIC_STAGE_CONSTRAINT, [&] {
+                launch_constraint_obs(E, ms, c.N, c.m, c.n, h->xrow(s), h->urow(s), h->zrow, h->nc,
+                                      h->at<float>(h->lay.cG), h->at<int>(h->lay.ccols), h->nk,
+                                      h->at<float>(h->lay.ch), h->c_alpha, h->c_beta,
+                                      VZ + (s - 1) * N * (size_t)h->nc * m, h->st);
+            });
+        // analysis at t = k + s with Ybar_t = [X_ref[s]; U_ref; 0]
         RowSet act{h->act_rows(s), h->R_of(s)};
-        RowSet obs{h->obs_rows(s), h->p};
+        RowSet obs{h->obs_rows(s), h->p, h->nc};
         ObsNoise V{VX + (s - 1) * N * n * m, VU + (s - 1) * N * l * m, c.n};
         analysis(h, E, ms, act, obs, V, X_ref + (size_t)s * n * m, U_ref, c.n);
     }
@@ -537,12 +555,25 @@ extern "C" {
 
 size_t oic_noise_floats(const oic_config* cfg) { return valid_config(cfg) ? noise_count(cfg) : 0; }
 
+size_t oic_handle_noise_floats(const oic_handle* h) { return h ? h->noise_n : 0; }
+
 oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* conv_b, const float* B,
                       oic_handle** out)
+{
+    return oic_create_constrained(cfg, conv_w, conv_b, B, nullptr, out);
+}
+
+oic_status oic_create_constrained(const oic_config* cfg, const float* conv_w, const float* conv_b,
+                                  const float* B, const oic_constraints* cons, oic_handle** out)
 {
     if (!out) return OIC_EINVAL;
     *out = nullptr;
     if (!valid_config(cfg) || !conv_w || !conv_b || !B) return OIC_EINVAL;
+    const int nc = cons ? cons->c : 0;
+    if (nc < 0 || (long)cfg->n + cfg->l + nc > 144) return OIC_EINVAL;
+    if (nc > 0 && (!cons->Gx || !cons->Gu || !cons->h || !(cons->alpha > 0.0) || !(cons->beta > 0.0) ||
+                   !(cons->sigma_z >= 0.0)))
+        return OIC_EINVAL;
     oic_handle* h = new (std::nothrow) oic_handle();
     if (!h) return OIC_ENOMEM;
     h->cfg = *cfg;
@@ -563,13 +594,38 @@ oic_status oic_create(const oic_config* cfg, const float* conv_w, const float* c
         return OIC_ENOMEM;
     }
     h->q = c.n + 2 * c.l;
-    h->p = c.n + c.l;
+    h->nc = nc;
+    h->p = c.n + c.l + nc;
     h->R_mem = h->full() ? (c.H + 1) * (c.n + c.l) : 2 * c.n + (c.H + 1) * c.l;
+    h->zrow = h->R_mem;                       // constraint block after the state rows
+    h->R_mem += nc;
+    if (nc > 0) {
+        // keep the columns of [Gx Gu] that are not all zero, in order
+        const int nl = c.n + c.l;
+        for (int a = 0; a < nl; ++a) {
+            bool any = false;
+            for (int r = 0; r < nc; ++r)
+                any = any || (a < c.n ? cons->Gx[(size_t)r * c.n + a] : cons->Gu[(size_t)r * c.l + (a - c.n)]) != 0.f;
+            if (any) h->ccols.push_back(a);
+        }
+        h->nk = (int)h->ccols.size();
+        h->cG.assign((size_t)nc * (h->nk > 0 ? h->nk : 1), 0.f);
+        for (int r = 0; r < nc; ++r)
+            for (int k = 0; k < h->nk; ++k) {
+                const int a = h->ccols[k];
+                h->cG[(size_t)r * h->nk + k] =
+                    a < c.n ? cons->Gx[(size_t)r * c.n + a] : cons->Gu[(size_t)r * c.l + (a - c.n)];
+            }
+        h->ch.assign(cons->h, cons->h + nc);
+        h->c_alpha = (float)cons->alpha;
+        h->c_beta = (float)cons->beta;
+        h->c_sigma = (float)cons->sigma_z;
+    }
     h->Ubase = h->full() ? (c.H + 1) * c.n : 2 * c.n;
     h->R_act_max = h->R_of(c.H);
     h->splits_max = stats_splits(1, h->p, c.N);
     if (stats_tc_splits(1, c.N) > h->splits_max) h->splits_max = stats_tc_splits(1, c.N);
-    h->noise_n = noise_count(&c);
+    h->noise_n = noise_count(&c, nc);
     h->bf16 = c.precision == OIC_PREC_MIXED && bf16_supported(c.n_layers, c.channels, c.m);
     h->fused = !h->bf16 && cnn_fused_supported(c.n_layers, c.channels, c.n, c.m, c.l) &&
                getenv("OIC_NO_FUSED_CNN") == nullptr;
@@ -665,11 +721,21 @@ oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda
             for (int y = 0; y < c.l; ++y) a[r++] = h->urow(t) + y;
         for (int y = 0; y < c.n; ++y) o[y] = h->xrow(s) + y;
         for (int y = 0; y < c.l; ++y) o[c.n + y] = h->urow(s) + y;
+        for (int y = 0; y < h->nc; ++y) o[c.n + c.l + y] = h->zrow + y;
     }
     int* gen = tab.data() + (size_t)(c.H + 1) * stride;
     for (int r = 0; r < h->R_act_max; ++r) gen[r] = r;
     OIC_CUDA_OK(cudaMemcpyAsync(h->at<int>(h->lay.rowtab), tab.data(), sizeof(int) * tab.size(),
                                 cudaMemcpyHostToDevice, h->st));
+    if (h->nc > 0) {
+        OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.cG), h->cG.data(), sizeof(float) * h->cG.size(),
+                                    cudaMemcpyHostToDevice, h->st));
+        if (h->nk > 0)
+            OIC_CUDA_OK(cudaMemcpyAsync(h->at<int>(h->lay.ccols), h->ccols.data(), sizeof(int) * h->ccols.size(),
+                                        cudaMemcpyHostToDevice, h->st));
+        OIC_CUDA_OK(cudaMemcpyAsync(h->at<float>(h->lay.ch), h->ch.data(), sizeof(float) * h->ch.size(),
+                                    cudaMemcpyHostToDevice, h->st));
+    }
     OIC_CUDA_OK(cudaMemsetAsync(h->at<int>(h->lay.status), 0, 64, h->st));
     OIC_CUDA_OK(cudaMemsetAsync(h->at<char>(h->lay.ctr), 0, sizeof(unsigned long long), h->st));
     h->sg[0].reset();
@@ -840,7 +906,7 @@ oic_status oic_enks_update(oic_handle* h, int R, const int* obs_rows, float* E, 
     if (!h->bound) return OIC_ESTATE;
     if (R < 1 || R > h->R_act_max) return OIC_EINVAL;
     if (!aligned16(E) || !aligned16(V)) return OIC_EINVAL;
-    const int p = h->p;
+    const int p = h->p - h->nc;                          // p_obs = n + l
     for (int c = 0; c < p; ++c)
         if (obs_rows[c] < 0 || obs_rows[c] >= R) return OIC_EINVAL;
     int* gen = h->act_rows(h->cfg.H + 1);

@@ -50,14 +50,17 @@ inline cudaError_t pdl_launch(void (*kernel)(K...), dim3 grid, dim3 block, size_
 }
 
 // Where member i's row r lives: E + i * member_stride + row_off[r] * m.
+// For observation rows, the last nc rows are constraint observations: their
+// perturbation is already in E and their reference is 0.
 struct RowSet {
     const int* rows;   // device: row offsets (in rows) inside a member block
     int count;
+    int nc = 0;
 };
 
-// Observation perturbation V^i (p rows): rows c < pa come from Va (member
-// stride pa*m), rows c >= pa from Vb (member stride (p-pa)*m).  Va == nullptr
-// means V = 0.
+// Observation perturbation V^i of the p - nc rows before the constraint rows:
+// rows c < pa come from Va (member stride pa*m), rows pa <= c < p - nc from
+// Vb (member stride (p-nc-pa)*m).  Va == nullptr means V = 0.
 struct ObsNoise {
     const float* Va;
     const float* Vb;
@@ -171,6 +174,16 @@ int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const flo
                         cudaStream_t st);
 // Known-answer check of the tcgen05 path: res[0] = mismatches (-1 timeout).
 void launch_tc_selftest(int* res, cudaStream_t st);
+
+// Constraint observations of every member at one assimilation time:
+// E[i][zrow + r][j] = phi(sum_k G[r][k] S_i[cols[k]][j] - h[r]) + eps[i][r][j]
+// with S_i = [X rows from xrow; U rows from urow] of member i (cols[k] < n:
+// X row, else U row cols[k] - n), phi(x) = ln(1 + e^{beta x}) / alpha.
+// G: [c][nk] packed over the nk columns of [Gx Gu] that are not all zero.
+// eps == nullptr: no perturbation.
+void launch_constraint_obs(float* E, long ms, int N, int m, int n, int xrow, int urow, int zrow, int c,
+                           const float* G, const int* cols, int nk, const float* h, float alpha, float beta,
+                           const float* eps, cudaStream_t st);
 
 // Philox-4x32-10 normal noise (Salmon et al., SC'11) for one solve.
 // Philox normals for one solve; the solve index is read from *solve_ctr

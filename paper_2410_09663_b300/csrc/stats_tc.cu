@@ -54,8 +54,8 @@ __device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, in
                                         const ObsNoise& V, int p, int i, int c, int j)
 {
     float4 v = __ldg(reinterpret_cast<const float4*>(E + (long)i * ms + (long)obs.rows[c] * m + j));
-    if (V.Va != nullptr) {
-        const float* vr = c < V.pa ? V.Va + ((long)i * V.pa + c) * m : V.Vb + ((long)i * (p - V.pa) + (c - V.pa)) * m;
+    if (V.Va != nullptr && c < p - obs.nc) {         // constraint rows carry their noise in E
+        const float* vr = c < V.pa ? V.Va + ((long)i * V.pa + c) * m : V.Vb + ((long)i * (p - obs.nc - V.pa) + (c - V.pa)) * m;
         v = f4add(v, __ldg(reinterpret_cast<const float4*>(vr + j)));
     }
     return v;
@@ -65,7 +65,8 @@ __device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, in
 // (observation row c < pp, 16-byte chunk): e = Y^i - Y^0 split into the B
 // tile [i][kh][hi rows pp | lo rows pp][128 B] (swizzled; zero beyond p and
 // beyond m); for c < p also e itself into Ysh [i][c][m].  The innovations
-// D^i = Ybar - Y^i go either plainly to Dbuf [i][c][m] or, through a
+// D^i = Ybar - Y^i (Ybar = 0 on the obs.nc trailing constraint rows, whose
+// perturbation is already in E) go either plainly to Dbuf [i][c][m] or, through a
 // transpose in shared memory, to the member update's operand Bd: rows
 // n = i m + j, K = c in chunks of 32, [kc][hi | lo][N m rows][128 B]
 // (swizzled, zero beyond p).
@@ -96,8 +97,12 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
             const float4 ev = f4sub(y, y0);
             split_tf32(ev, hi, lo);
             *reinterpret_cast<float4*>(Ysh + ((long)i * p + c) * m + j) = ev;
-            const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
-            d = f4sub(*reinterpret_cast<const float4*>(yb + j), y);
+            if (c < p - obs.nc) {
+                const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
+                d = f4sub(*reinterpret_cast<const float4*>(yb + j), y);
+            } else {
+                d = f4sub(make_float4(0.f, 0.f, 0.f, 0.f), y);     // constraint rows: reference 0
+            }
             if (Dbuf != nullptr) *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + j) = d;
         }
         if (Bd != nullptr) {

@@ -96,3 +96,65 @@ def test_unbound_handle_reports_state_error():
     assert lib.oic_step(h, x.ctypes.data, x.ctypes.data, x.ctypes.data, None, None) == oic.OIC_ESTATE
     assert lib.oic_bind(h, None, 0, None) == oic.OIC_EINVAL
     lib.oic_destroy(h)
+
+
+def _constraints(c_spec, alpha=None):
+    arrs = [np.ascontiguousarray(a, np.float32).ravel() for a in (c_spec.Gx, c_spec.Gu, c_spec.h)]
+    cs = oic.oic_constraints()
+    cs.c = int(arrs[2].size)
+    cs.Gx, cs.Gu, cs.h = (a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in arrs)
+    cs.alpha = c_spec.alpha if alpha is None else alpha
+    cs.beta, cs.sigma_z = c_spec.beta, c_spec.sigma_z
+    return cs, arrs
+
+
+def _create_constrained(wl, cs):
+    lib = oic.load()
+    cfg = oic.config_from_workload(wl)
+    w, b = wl.flat_weights()
+    B = wl.B()
+    h = ctypes.c_void_p()
+    s = lib.oic_create_constrained(ctypes.byref(cfg), w.ctypes.data, b.ctypes.data, B.ctypes.data,
+                                   None if cs is None else ctypes.byref(cs), ctypes.byref(h))
+    return s, h
+
+
+def test_constrained_create_sizes_noise_and_workspace():
+    lib = oic.load()
+    wl = W.small_16()
+    s0, h0 = _create_constrained(wl, None)
+    wc = wl.with_(cons=W.u_box(wl.n, wl.l, 0.1))
+    cs, keep = _constraints(wc.cons)
+    s1, h1 = _create_constrained(wl, cs)
+    try:
+        assert s0 == s1 == oic.OIC_OK
+        assert lib.oic_handle_noise_floats(h0) == wl.noise_floats()
+        assert lib.oic_handle_noise_floats(h1) == wc.noise_floats() == wl.noise_floats() + wl.H * wl.N * 2 * wl.l * wl.m
+        assert lib.oic_workspace_bytes(h1) > lib.oic_workspace_bytes(h0)
+    finally:
+        lib.oic_destroy(h0)
+        lib.oic_destroy(h1)
+
+
+def test_constrained_create_rejects_bad_constraints():
+    wl = W.small_16()
+    spec = W.u_box(wl.n, wl.l, 0.1)
+    for alpha in (0.0, -1.0):
+        cs, keep = _constraints(spec, alpha=alpha)
+        assert _create_constrained(wl, cs)[0] == oic.OIC_EINVAL
+    cs, keep = _constraints(spec)
+    cs.beta = 0.0
+    assert _create_constrained(wl, cs)[0] == oic.OIC_EINVAL
+    cs, keep = _constraints(spec)
+    cs.Gu = ctypes.POINTER(ctypes.c_float)()
+    assert _create_constrained(wl, cs)[0] == oic.OIC_EINVAL
+    # n + l + c <= 144
+    big = W.Workload("b", n=128, m=16, l=8, channels=[2, 4, 1], N=8, H=2, S=1)
+    cs, keep = _constraints(W.u_box(big.n, big.l, 0.1))          # c = 16
+    assert _create_constrained(big, cs)[0] == oic.OIC_EINVAL
+    edge = W.Constraints(np.zeros((8, big.n), np.float32), np.eye(8, dtype=np.float32),
+                         np.full(8, 0.1, np.float32))                 # c = 8: 128 + 8 + 8 = 144
+    cs, keep = _constraints(edge)
+    s, h = _create_constrained(big, cs)
+    assert s == oic.OIC_OK
+    oic.load().oic_destroy(h)
