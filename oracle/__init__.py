@@ -25,6 +25,12 @@ Parity status per function (see the tests that pin each one):
                   phi(ln(e - 1) / beta) = 1 / alpha, phi(x) - phi(-x) = beta x / alpha,
                   the two limits (0 far inside, beta x / alpha far outside)
   constraint_obs  pinned: a hand-worked 2-row case
+  row_cov         pinned: numpy's biased per-column covariance summed over the
+                  columns, the lambda factor
+  enks_solve_cov  pinned: an H = 1 solve rebuilt from pinned pieces (CNN step,
+                  row_cov, textbook analysis), and the exact sample identity
+                  Sigma_post = Sigma_pred - S_XY S_Y^{-1} S_YX of the perturbed-
+                  observation update (the "-" sign of the Appendix)
   enks_solve / run with constraints: pinned by an H = 1 solve rebuilt from the
                   pinned pieces (CNN step, constraint rows, textbook analysis)
                   and by a solve whose control reference lies outside a box:
@@ -105,9 +111,12 @@ def _load():
         _lib.oracle_constraint_obs.restype = None
         _lib.oracle_enks_solve_c.argtypes = [ctypes.POINTER(_Net), i, i, P, P, P, P, P, C, P]
         _lib.oracle_run_c.argtypes = [ctypes.POINTER(_Net), i, i, i, P, P, P, P, P, C, P, P, P]
+        _lib.oracle_row_cov.argtypes = [i, i, i, P, l_, ctypes.c_double, P]
+        _lib.oracle_enks_solve_cov.argtypes = [ctypes.POINTER(_Net), i, i, P, P, P, P, P, C, ctypes.c_double,
+                                               P, P, P]
         for f in ("oracle_cnn_step", "oracle_cnn_step_batch", "oracle_cholesky", "oracle_gain",
                   "oracle_enks_analysis", "oracle_enks_solve", "oracle_run", "oracle_control_reduce",
-                  "oracle_enks_solve_c", "oracle_run_c"):
+                  "oracle_enks_solve_c", "oracle_run_c", "oracle_row_cov", "oracle_enks_solve_cov"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
 
@@ -284,6 +293,39 @@ def enks_solve(net: Net, N, H, X_k, U_prev, X_ref, U_ref, noise, cons: Cons | No
     if st:
         raise np.linalg.LinAlgError(f"solve failed (status {st})")
     return out
+
+
+def row_cov(X, lam=1.0):
+    """(lam / N) sum_i (X^i - Xhat)(X^i - Xhat)^T for X [N][R][m] (R x R)."""
+    X = _d(X)
+    N, R, m = X.shape
+    S = np.empty((R, R))
+    if _load().oracle_row_cov(N, R, m, _p(X), R * m, float(lam), _p(S)):
+        raise MemoryError("oracle_row_cov")
+    return S
+
+
+def enks_solve_cov(net: Net, N, H, X_k, U_prev, X_ref, U_ref, noise, cons: Cons | None = None, lam=1.0):
+    """enks_solve with Algorithm 1's optional covariance steps executed.
+
+    Returns (Xbar_hat, pred, post): pred[s-1] / post[s-1] is the (s+1) q x
+    (s+1) q row covariance (factor lam / N) of the history blocks 0..s after
+    the prediction to t = k+s and after the update at t."""
+    n, m, l = net.n, net.m, net.l
+    X_k, U_prev, U_ref = _d(X_k), _d(U_prev), _d(U_ref)
+    X_ref = _d(X_ref).reshape(H + 1, n, m)
+    noise = _d(noise).ravel()
+    assert noise.size == noise_floats(n, m, l, N, H, cons.c if cons is not None else 0)
+    Rf = (H + 1) * net.q
+    out = np.empty((H + 1, net.q, m))
+    pred = np.zeros((H, Rf * Rf))
+    post = np.zeros((H, Rf * Rf))
+    st = _load().oracle_enks_solve_cov(ctypes.byref(net._s), N, H, _p(X_k), _p(U_prev), _p(X_ref), _p(U_ref),
+                                       _p(noise), _cons_ptr(cons), float(lam), _p(pred), _p(post), _p(out))
+    if st:
+        raise np.linalg.LinAlgError(f"solve failed (status {st})")
+    sl = lambda a, s: a[s - 1, :((s + 1) * net.q) ** 2].reshape((s + 1) * net.q, (s + 1) * net.q)
+    return out, [sl(pred, s) for s in range(1, H + 1)], [sl(post, s) for s in range(1, H + 1)]
 
 
 def run(net: Net, N, H, S, X_0, U_init, X_ref_all, U_ref, noise_all, cons: Cons | None = None):

@@ -33,6 +33,15 @@
  *   oracle_control_reduce u = U T^T (T T^T)^{-1}: the right transformation for
  *                         controls with fewer columns than the state (the
  *                         paragraph on narrow controls after Table I)
+ *   oracle_row_cov        lambda/N sum_i (X^i - Xhat)(X^i - Xhat)^T, the
+ *                         ensemble row covariance of Eq. (ensemble-based-
+ *                         Kalman-update-cov) and Eq. (prediction-cov); and
+ *   oracle_enks_solve_cov the solve with Algorithm 1's optional covariance
+ *                         steps executed: Sigma^X_{t|t-1} (whose last block
+ *                         row and column are Eq. (prediction-cov) and Eq.
+ *                         (prediction-cross-cov), concatenated as in Eq.
+ *                         (prediction-cov-concatenate)) after each prediction
+ *                         and Sigma^X_{t|t} after each update
  *   oracle_softplus_barrier phi(x) = ln(1 + e^{beta x}) / alpha, and
  *   oracle_constraint_obs z = phi(g(X, U)) + eps: the virtual observation of
  *                         a constraint g(X, U) <= 0 with reference 0 (the
@@ -303,6 +312,33 @@ int oracle_enks_analysis(int N, int R, int p, int m, double *X, long xs,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Eq. (ensemble-based-Kalman-update-cov) / Eq. (prediction-cov): the row
+ * covariance of an ensemble of R x m matrices X^i (at X + i*xs),
+ *   S = (lambda / N) sum_i (X^i - Xhat)(X^i - Xhat)^T,  Xhat = (1/N) sum_i X^i,
+ * pooled over the m columns as the matrix-normal moments are (R x R). */
+int oracle_row_cov(int N, int R, int m, const double *X, long xs, double lambda, double *S)
+{
+    double *mean = calloc((size_t)R * m, sizeof(double));
+    if (!mean) return -1;
+    for (int i = 0; i < N; ++i)
+        for (size_t e = 0; e < (size_t)R * m; ++e) mean[e] += X[i * xs + e];
+    for (size_t e = 0; e < (size_t)R * m; ++e) mean[e] /= N;
+#pragma omp parallel for schedule(dynamic)
+    for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b) {
+            double t = 0.0;
+            for (int i = 0; i < N; ++i) {
+                const double *xi = X + i * xs;
+                for (int j = 0; j < m; ++j)
+                    t += (xi[a * m + j] - mean[a * m + j]) * (xi[b * m + j] - mean[b * m + j]);
+            }
+            S[(size_t)a * R + b] = lambda / N * t;
+        }
+    free(mean);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Constraint rows (the paragraph on state/input constraints after Table I).
  * phi is evaluated as max(y, 0) + log1p(e^{-|y|}) with y = beta x, which is
  * ln(1 + e^{y}) rewritten so that e^{y} cannot overflow. */
@@ -345,9 +381,17 @@ void oracle_constraint_obs(const oracle_cons *cs, int n, int l, int m, const dou
  *   Xbar_hat (H+1) x q x m: smoothed means of blocks k .. k+H after the update
  *            at t = k+H (Eq. (ensemble-based-Kalman-update-mean)).
  * Returns 0, or the first nonzero Cholesky status. */
-int oracle_enks_solve_c(const oracle_net *net, int N, int H, const double *X_k,
-                        const double *U_prev, const double *X_ref, const double *U_ref,
-                        const double *noise, const oracle_cons *cs, double *Xbar_hat)
+/* The solve above (cs: constraint rows, may be NULL) with Algorithm 1's
+ * optional covariance steps executed: for
+ * s = 1..H, slot s-1 of Sigma_pred / Sigma_post ((H+1) q x (H+1) q doubles
+ * each) holds, compact row-major, the (s+1) q x (s+1) q row covariance of the
+ * history blocks 0..s after the prediction to t = k+s (Sigma^X_{t|t-1}) and
+ * after the update at t (Sigma^X_{t|t}), with factor lambda / N.  Either
+ * output may be NULL. */
+int oracle_enks_solve_cov(const oracle_net *net, int N, int H, const double *X_k,
+                          const double *U_prev, const double *X_ref, const double *U_ref,
+                          const double *noise, const oracle_cons *cs, double lambda,
+                          double *Sigma_pred, double *Sigma_post, double *Xbar_hat)
 {
     const int n = net->n, m = net->m, l = net->l;
     const int nc = cs ? cs->c : 0;
@@ -419,8 +463,18 @@ int oracle_enks_solve_c(const oracle_net *net, int N, int H, const double *X_k,
 
         /* lines 9-10, Eq. (Ybar-sample-mean-cov), Eq. (ensemble-based-
          * Kalman-update): update every block 0..s of every member.          */
-        int st = oracle_enks_analysis(N, (s + 1) * q, p, m, hist, xs, Y, Ybar);
+        const int Rs = (s + 1) * q;
+        const size_t slot = (size_t)(H + 1) * q * (size_t)(H + 1) * q;
+        if (Sigma_pred && oracle_row_cov(N, Rs, m, hist, xs, lambda, Sigma_pred + (s - 1) * slot)) {
+            status = -1;
+            break;
+        }
+        int st = oracle_enks_analysis(N, Rs, p, m, hist, xs, Y, Ybar);
         if (st != 0) { status = st; break; }
+        if (Sigma_post && oracle_row_cov(N, Rs, m, hist, xs, lambda, Sigma_post + (s - 1) * slot)) {
+            status = -1;
+            break;
+        }
     }
 
     /* line 15: smoothed means of all blocks */
@@ -432,6 +486,14 @@ int oracle_enks_solve_c(const oracle_net *net, int N, int H, const double *X_k,
     }
     free(hist); free(Y); free(Ybar);
     return status;
+}
+
+int oracle_enks_solve_c(const oracle_net *net, int N, int H, const double *X_k,
+                        const double *U_prev, const double *X_ref, const double *U_ref,
+                        const double *noise, const oracle_cons *cs, double *Xbar_hat)
+{
+    return oracle_enks_solve_cov(net, N, H, X_k, U_prev, X_ref, U_ref, noise, cs, 1.0, NULL, NULL,
+                                 Xbar_hat);
 }
 
 int oracle_enks_solve(const oracle_net *net, int N, int H, const double *X_k,
