@@ -574,6 +574,75 @@ def run_mix(args, name):
     return 0
 
 
+COV_METRIC = "control solves/s with Algorithm 1's optional covariance outputs (Sigma^X_{t|t-1}, Sigma^X_{t|t})"
+
+
+def run_cov(args, wl):
+    """Solves of the 64 x 64 workload (device noise, eager launches) with and
+    without the optional covariance outputs of every assimilation time, timed
+    with CUDA events on the solver's stream, L2 flushed between solves."""
+    import torch
+    import paper_2410_09663_b300 as oic
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w, b = wl.flat_weights()
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    for full in (False, True):
+        cfg = oic.config_from_workload(wl, noise_mode=oic.OIC_NOISE_PHILOX, keep_full_history=full)
+        s = oic.Solver(cfg, w, b, wl.B(), device=dev, stream=stream)
+        H, R = wl.H, s.oic_cov_rows(wl.H)
+        with torch.cuda.stream(stream):
+            X0 = torch.from_numpy(wl.X0()).to(dev)
+            U0 = torch.from_numpy(wl.U_init()).to(dev)
+            xr = torch.from_numpy(wl.X_ref_window(0)).to(dev)
+            ur = torch.from_numpy(wl.U_ref()).to(dev)
+            U_hat = torch.zeros(H + 1, wl.l, wl.m, device=dev)
+            pred = torch.zeros(H * R * R, dtype=torch.float64, device=dev)
+            post = torch.zeros_like(pred)
+            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+            times = {}
+            for mode in ("plain", "cov"):
+                def one():
+                    if mode == "plain":
+                        s.oic_solve(X0, U0, xr, ur, None, U_hat)
+                    else:
+                        s.oic_solve_cov(X0, U0, xr, ur, None, U_hat, None, 1.0, pred, post)
+                for _ in range(args.warmup):
+                    one()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                stream.synchronize()
+                for i in range(args.steps):
+                    flush.fill_(float(i))
+                    ev[i][0].record(stream)
+                    one()
+                    ev[i][1].record(stream)
+                stream.synchronize()
+                times[mode] = sum(a.elapsed_time(c) for a, c in ev) / args.steps
+            s.oic_profile_begin(stages=["cov_out"], max_launches=4096)
+            s.oic_solve_cov(X0, U0, xr, ur, None, U_hat, None, 1.0, pred, post)
+            prof = s.oic_profile_end()
+        s.close()
+        rows = [s2 for s2 in range(1, H + 1)]
+        flops = sum(2.0 * 2 * (wl.n * (t if full else 1) + (t + 1) * wl.l) ** 2 * wl.N * wl.m for t in rows)
+        out["full_history" if full else "u_history"] = {
+            "solve_ms": times["plain"], "solve_cov_ms": times["cov"],
+            "cov_out_ms": prof.get("cov_out", (0.0, 0))[0], "cov_out_launches": prof.get("cov_out", (0.0, 0))[1],
+            "kept_rows_at_H": R, "cov_flops_per_solve": flops,
+            "cov_tflops": flops / (prof.get("cov_out", (1e30, 0))[0] / 1e3) / 1e12}
+    line = {"metric": COV_METRIC, "value": 1e3 / out["u_history"]["solve_cov_ms"], "unit": "control solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["u_history"]["solve_cov_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 products, f64 sums", "data": "synthetic",
+            "config": config_dict(wl, {"launch": "eager (oic_solve / oic_solve_cov)", "modes": out})}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 SERVE_METRIC = "served control requests/s (Poisson arrivals, continuous batching)"
 
 
@@ -673,6 +742,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cov-outputs", action="store_true",
+                    help="time solves with the optional covariance outputs against plain solves")
     ap.add_argument("--constraint", choices=["none", "u_box"], default="none",
                     help="u_box: |U| <= 0.1 on every control entry as 2 l softplus-barrier rows")
     args = ap.parse_args(argv)
@@ -694,6 +765,8 @@ def main(argv=None):
         wl = wl.with_(cons=workloads.u_box(wl.n, wl.l, 0.1))
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.cov_outputs:
+        return run_cov(args, wl)
     return run_oic(args, wl)
 
 

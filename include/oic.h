@@ -159,6 +159,34 @@ oic_status oic_reset(oic_handle* h, const float* X0, const float* U_prev);
 oic_status oic_solve(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
                      const float* U_ref, const float* noise, float* U_hat, float* X_hat);
 
+/* oic_solve with Algorithm 1's optional covariance steps executed (lines 8
+ * and 11, which the paper lets be skipped because the update does not use
+ * them): for s = 1 .. H (t = k + s)
+ *   Sigma_pred slot s-1: Sigma^X_{t|t-1} after the prediction to t, whose last
+ *                        block row / column are Sigma^{X̄}_{t|t-1} and
+ *                        Sigma^{X X̄}_{t|t-1} (Eq. (prediction-cov) ..
+ *                        Eq. (prediction-cov-concatenate));
+ *   Sigma_post slot s-1: Sigma^X_{t|t} after the update at t
+ *                        (Eq. (ensemble-based-Kalman-update-cov));
+ * each = (lambda / N) sum_i (X^i - mean)(X^i - mean)^T over the rows the
+ * handle keeps at s, pooled over the m columns (lambda = 1 / tr Psi in the
+ * paper; Psi is not estimated, so the caller chooses it).  Slot s-1 starts at
+ * (s-1) R^2 doubles, R = oic_cov_rows(h, H), and holds the oic_cov_rows(h, s)^2
+ * matrix compact, row-major.  Rows kept at s, in order: with keep_full_history
+ * the field blocks k+1 .. k+s (n rows each; block k has no spread) then the
+ * control blocks k .. k+s (l rows each); otherwise the field at k+s (n rows)
+ * then the control blocks k .. k+s.  The dU rows are not kept (the prediction
+ * and the observation never read them).
+ * scratch: device, 256-byte aligned, >= oic_cov_scratch_bytes(h).  Either
+ * Sigma output may be NULL.  Device pointers; asynchronous; FP64 outputs
+ * from FP32 products with FP64 split sums and mean correction. */
+oic_status oic_solve_cov(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
+                         const float* U_ref, const float* noise, float* U_hat, float* X_hat, double lambda,
+                         double* Sigma_pred, double* Sigma_post, void* scratch, size_t scratch_bytes);
+size_t oic_cov_scratch_bytes(const oic_handle* h);
+/* Rows kept at s (1 .. H; 0 otherwise). */
+int oic_cov_rows(const oic_handle* h, int s);
+
 /* One control step (Algorithm 1, lines 4-17) on the device-resident plant:
  * solve from the plant state, apply U_k = Û_{k|k:k+H} to the plant
  * X_{k+1} = CNN_theta(X_k, U_k) (the plant is the surrogate itself), and
@@ -219,6 +247,7 @@ typedef enum {
     OIC_STAGE_CNN_FUSED,       /* whole CNN step in one kernel (all layers)     */
     OIC_STAGE_CNN_BF16,        /* CNN step in BF16, one kernel per layer        */
     OIC_STAGE_CONSTRAINT,      /* constraint rows z = phi(g(X_t, U_t)) + eps    */
+    OIC_STAGE_COV_OUT,         /* optional covariance outputs (oic_solve_cov)   */
     OIC_NUM_STAGES
 } oic_stage;
 oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launches);

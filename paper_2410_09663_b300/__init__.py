@@ -22,7 +22,7 @@ OIC_PREC_FP32, OIC_PREC_MIXED = 0, 1
 OIC_NOISE_HOST, OIC_NOISE_PHILOX = 0, 1
 STAGES = ["noise", "init", "cnn_input", "conv_first", "conv_hidden", "conv_out", "u_advance",
           "means", "cov", "cov_reduce", "gain", "update", "block_means", "cnn_fused", "cnn_bf16",
-          "constraint"]
+          "constraint", "cov_out"]
 
 
 class OICError(RuntimeError):
@@ -62,6 +62,10 @@ _SIGS = {
     "oic_create_constrained": (ctypes.c_int, [ctypes.POINTER(oic_config), _VP, _VP, _VP,
                                               ctypes.POINTER(oic_constraints), ctypes.POINTER(_VP)]),
     "oic_handle_noise_floats": (ctypes.c_size_t, [_VP]),
+    "oic_solve_cov": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, _VP,
+                                     ctypes.c_size_t]),
+    "oic_cov_scratch_bytes": (ctypes.c_size_t, [_VP]),
+    "oic_cov_rows": (ctypes.c_int, [_VP, ctypes.c_int]),
     "oic_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "oic_max_rows": (ctypes.c_int, [_VP]),
     "oic_bind": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _VP]),
@@ -261,6 +265,22 @@ class Solver:
     def oic_solve(self, X_k, U_prev, X_ref, U_ref, noise, U_hat, X_hat=None):
         _check(self._lib.oic_solve(self.h, _ptr(X_k), _ptr(U_prev), _ptr(X_ref), _ptr(U_ref),
                                    _ptr(noise), _ptr(U_hat), _ptr(X_hat)), "oic_solve")
+
+    def oic_solve_cov(self, X_k, U_prev, X_ref, U_ref, noise, U_hat, X_hat=None, lam=1.0, Sigma_pred=None,
+                      Sigma_post=None):
+        """oic_solve plus the optional covariance outputs (float64 device
+        tensors of H * R * R, R = oic_cov_rows(H)); scratch is allocated here."""
+        import torch
+        nb = int(self._lib.oic_cov_scratch_bytes(self.h))
+        scratch = torch.empty(nb + 256, dtype=torch.uint8, device=self.workspace.device)
+        sp = (scratch.data_ptr() + 255) // 256 * 256
+        _check(self._lib.oic_solve_cov(self.h, _ptr(X_k), _ptr(U_prev), _ptr(X_ref), _ptr(U_ref), _ptr(noise),
+                                       _ptr(U_hat), _ptr(X_hat), float(lam), _ptr(Sigma_pred), _ptr(Sigma_post),
+                                       ctypes.c_void_p(sp), nb), "oic_solve_cov")
+        self._cov_scratch = scratch                  # alive until the stream has used it
+
+    def oic_cov_rows(self, s):
+        return int(self._lib.oic_cov_rows(self.h, int(s)))
 
     def oic_step(self, X_ref, U_ref, noise, U_applied=None, X_next=None):
         _check(self._lib.oic_step(self.h, _ptr(X_ref), _ptr(U_ref), _ptr(noise), _ptr(U_applied),

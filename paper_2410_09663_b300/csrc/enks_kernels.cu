@@ -90,7 +90,7 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
     const int i0 = (int)((long)sidx * N / splits), i1 = (int)((long)(sidx + 1) * N / splits);
     const int tid = threadIdx.x, tx = tid % S_TX, ty = tid / S_TX;
     const int m4 = m / 4;
-    const bool do_s1 = blockIdx.y == 0, do_d = blockIdx.x == 0;
+    const bool do_s1 = blockIdx.y == 0, do_d = blockIdx.x == 0 && Dbuf != nullptr;
 
     // loader chunks: consecutive threads take consecutive 16-byte pieces of a
     // row.  Row offsets and the noise source are resolved once: off < 0 marks
@@ -250,14 +250,14 @@ __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict_
     if (threadIdx.x < 32 && ok) S1[idx] = t;
 }
 
-// C[a][c] = sum over splits of part2 - (1/N) sum_j S1[a][j] S1[R + c][j]
+// C[a][c] = scale (sum over splits of part2 - (1/N) sum_j S1[a][j] S1[R + c][j])
 // (S1 == nullptr: the partials already have the means removed).
 // F64: the split sum, the mean correction and the subtraction in FP64 (the
 // mixed-precision mode's FP64 anomaly step); else FP32 with an FP64 result.
 template <bool F64>
 __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restrict__ part2,
                                                            const float* __restrict__ S1, int splits, int R, int p,
-                                                           int m, int N, double* __restrict__ C)
+                                                           int m, int N, double* __restrict__ C, double scale)
 {
     pdl_begin();
     using T = typename std::conditional<F64, double, float>::type;
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
             }
             corr = (d0 + d1) / (T)N;
         }
-        C[idx] = (double)(t - corr);
+        C[idx] = (double)(t - corr) * scale;
     }
 }
 
@@ -735,11 +735,13 @@ void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, c
 }
 
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st, bool f64)
+                         cudaStream_t st, bool f64, double scale)
 {
     const int total = (R + p) * p;
-    if (f64) pdl_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C);
-    else pdl_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C);
+    if (f64)
+        pdl_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C, scale);
+    else
+        pdl_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C, scale);
 }
 
 

@@ -3,6 +3,7 @@
 // (Kalman-MPC) over the kernels of cnn_kernels.cu, enks_kernels.cu and
 // noise_kernels.cu.  The library never allocates device memory: every buffer
 // below is carved out of the caller's workspace at oic_bind.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -373,8 +374,62 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
         run_stage(h, OIC_STAGE_UPDATE, [&] { launch_update(E, ms, c.N, c.m, act, Kt, p, D, h->st); });
 }
 
+// Algorithm 1's optional covariance steps (lines 8 and 11): where to write
+// them and the scratch the products use.
+struct CovOut {
+    double lambda = 1.0;
+    double* pred = nullptr;          // [H][R_max][R_max] slots, compact R_of(s)^2 each
+    double* post = nullptr;
+    char* scratch = nullptr;
+};
+
+// part1 / part2 / S1 of the row covariance of R kept rows (no state rows,
+// the kept rows as the observed side of the anomaly products)
+struct CovScratch {
+    size_t part1, part2, S1, total;
+};
+CovScratch cov_scratch(const oic_handle* h)
+{
+    CovScratch c{0, 0, 0, 0};
+    size_t p1 = 0, p2 = 0, s1 = 0;
+    for (int s = 1; s <= h->cfg.H; ++s) {
+        const size_t R = h->R_of(s), sp = stats_splits(0, (int)R, h->cfg.N);
+        p1 = std::max(p1, sp * R * h->cfg.m);
+        p2 = std::max(p2, sp * R * R);
+        s1 = std::max(s1, R * h->cfg.m);
+    }
+    c.part1 = 0;
+    c.part2 = align_up(sizeof(float) * p1, 256);
+    c.S1 = c.part2 + align_up(sizeof(float) * p2, 256);
+    c.total = c.S1 + align_up(sizeof(float) * s1, 256);
+    return c;
+}
+
+// out = (lambda / N) sum_i (E^i[rows] - mean)(E^i[rows] - mean)^T over the
+// kept rows `rows` (pooled over the m columns), FP64 split sums and mean
+// correction.
+void ensemble_cov(oic_handle* h, const float* E, long ms, RowSet rows, const CovOut& co, double* out)
+{
+    const oic_config& c = h->cfg;
+    const CovScratch cs = cov_scratch(h);
+    float* part1 = reinterpret_cast<float*>(co.scratch + cs.part1);
+    float* part2 = reinterpret_cast<float*>(co.scratch + cs.part2);
+    float* S1 = reinterpret_cast<float*>(co.scratch + cs.S1);
+    const int R = rows.count;
+    const int splits = stats_splits(0, R, c.N);
+    RowSet none{rows.rows, 0};
+    run_stage(h, OIC_STAGE_COV_OUT, [&] {
+        launch_stats(E, ms, c.N, c.m, none, rows, ObsNoise{nullptr, nullptr, 0}, nullptr, nullptr, 0, part1, part2,
+                     nullptr, splits, h->st);
+    });
+    run_stage(h, OIC_STAGE_COV_OUT, [&] { launch_s1_reduce(part1, splits, R, c.m, S1, h->st); });
+    run_stage(h, OIC_STAGE_COV_OUT, [&] {
+        launch_cov_finalize(part2, S1, splits, 0, R, c.m, c.N, out, h->st, true, co.lambda / c.N);
+    });
+}
+
 oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
-                      const float* U_ref, const float* noise, float* U_hat, float* X_hat)
+                      const float* U_ref, const float* noise, float* U_hat, float* X_hat, const CovOut* cov = nullptr)
 {
     const oic_config& c = h->cfg;
     const size_t N = c.N, n = c.n, m = c.m, l = c.l, H = c.H;
@@ -422,7 +477,10 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
         RowSet act{h->act_rows(s), h->R_of(s)};
         RowSet obs{h->obs_rows(s), h->p, h->nc};
         ObsNoise V{VX + (s - 1) * N * n * m, VU + (s - 1) * N * l * m, c.n};
+        const size_t slot = (size_t)(s - 1) * h->R_act_max * h->R_act_max;
+        if (cov && cov->pred) ensemble_cov(h, E, ms, act, *cov, cov->pred + slot);     // Sigma^X_{t|t-1}
         analysis(h, E, ms, act, obs, V, X_ref + (size_t)s * n * m, U_ref, c.n);
+        if (cov && cov->post) ensemble_cov(h, E, ms, act, *cov, cov->post + slot);     // Sigma^X_{t|t}
     }
     run_stage(h, OIC_STAGE_BLOCK_MEANS, [&] {
         launch_block_means(E, ms, c.N, c.m, h->urow(0), c.l, c.H + 1, U_hat, h->st);
@@ -771,6 +829,36 @@ oic_status oic_solve(oic_handle* h, const float* X_k, const float* U_prev, const
     if (X_hat && !h->full()) return OIC_EINVAL;
     OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
     oic_status s = solve_impl(h, X_k, U_prev, X_ref, U_ref, noise, U_hat, X_hat);
+    OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
+    return s;
+}
+
+size_t oic_cov_scratch_bytes(const oic_handle* h) { return h ? cov_scratch(h).total : 0; }
+
+int oic_cov_rows(const oic_handle* h, int s)
+{
+    if (!h || s < 1 || s > h->cfg.H) return 0;
+    return h->R_of(s);
+}
+
+oic_status oic_solve_cov(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
+                         const float* U_ref, const float* noise, float* U_hat, float* X_hat, double lambda,
+                         double* Sigma_pred, double* Sigma_post, void* scratch, size_t scratch_bytes)
+{
+    if (!h || !X_k || !U_prev || !X_ref || !U_ref || !U_hat) return OIC_EINVAL;
+    if (!h->bound) return OIC_ESTATE;
+    if (h->cfg.noise_mode == OIC_NOISE_HOST && (!noise || !aligned16(noise))) return OIC_EINVAL;
+    if (X_hat && !h->full()) return OIC_EINVAL;
+    if ((Sigma_pred || Sigma_post) &&
+        (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 255u) != 0 || scratch_bytes < cov_scratch(h).total))
+        return OIC_EINVAL;
+    CovOut co;
+    co.lambda = lambda;
+    co.pred = Sigma_pred;
+    co.post = Sigma_post;
+    co.scratch = static_cast<char*>(scratch);
+    OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
+    oic_status s = solve_impl(h, X_k, U_prev, X_ref, U_ref, noise, U_hat, X_hat, &co);
     OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
     return s;
 }

@@ -97,9 +97,9 @@ size_t stats_smem_bytes(int m);
 void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
                   const float* Yu, int n_yx, float* part1, float* part2, float* Dbuf, int splits, cudaStream_t st);
 void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st);
-// C = sum_s part2 - S1 S1_Y^T / N  ([(R + p) x p], Cxy on top, Cyy below).
+// C = scale (sum_s part2 - S1 S1_Y^T / N)  ([(R + p) x p], Cxy on top, Cyy below).
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st, bool f64 = false);
+                         cudaStream_t st, bool f64 = false, double scale = 1.0);
 // Anomaly products on the tensor cores (TF32 hi / lo split, one pass over
 // the ensemble): part1 / part2 as launch_stats writes them, so the same
 // s1 reduction and finalisation follow.  Bop: stats_tc_bbytes of scratch.
