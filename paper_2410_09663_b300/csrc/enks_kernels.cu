@@ -227,8 +227,19 @@ __device__ __forceinline__ float split_sum(const float* __restrict__ part, long 
 {
     const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
     float s = 0.f;
-    if (ok)
-        for (int k = w; k < splits; k += 8) s += part[(long)k * stride + idx];
+    if (ok) {
+        // four splits' loads in flight before they are added (same order)
+        int k = w;
+        for (; k + 24 < splits; k += 32) {
+            const float v0 = part[(long)k * stride + idx], v1 = part[(long)(k + 8) * stride + idx];
+            const float v2 = part[(long)(k + 16) * stride + idx], v3 = part[(long)(k + 24) * stride + idx];
+            s += v0;
+            s += v1;
+            s += v2;
+            s += v3;
+        }
+        for (; k < splits; k += 8) s += part[(long)k * stride + idx];
+    }
     red[w][ln] = s;
     __syncthreads();
     float t = 0.f;
@@ -267,8 +278,20 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
     const bool ok = idx < M * p;
     const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
     T sp = 0;
-    if (ok)
-        for (int k = w; k < splits; k += 8) sp += (T)part2[(long)k * M * p + idx];
+    if (ok) {
+        // four splits' loads in flight before they are added (same order)
+        const long st = (long)M * p;
+        int k = w;
+        for (; k + 24 < splits; k += 32) {
+            const float v0 = part2[k * st + idx], v1 = part2[(k + 8) * st + idx];
+            const float v2 = part2[(k + 16) * st + idx], v3 = part2[(k + 24) * st + idx];
+            sp += (T)v0;
+            sp += (T)v1;
+            sp += (T)v2;
+            sp += (T)v3;
+        }
+        for (; k < splits; k += 8) sp += (T)part2[k * st + idx];
+    }
     red[w][ln] = sp;
     __syncthreads();
     if (threadIdx.x < 32 && ok) {

@@ -43,6 +43,7 @@ struct Segs {
     unsigned long long end[MAX_SEG];
     float sigma[MAX_SEG];
     int n;
+    int quad_ends;       // every end is a multiple of 4
 };
 
 __global__ void philox_noise_kernel(float* __restrict__ out, unsigned long long total,
@@ -73,14 +74,34 @@ __global__ void philox_noise_kernel(float* __restrict__ out, unsigned long long 
         z[2] = r * c;
         z[3] = r * s;
     }
+    // sigma of each element's segment; the search is unrolled over the fixed
+    // table size so the table stays in registers (a runtime index would put
+    // it in local memory).  With every segment end a multiple of 4 (quad_ends)
+    // the four elements share one segment and one search.
+    float sg[4];
+    const int nsearch = segs.quad_ends ? 1 : 4;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
+        if (t >= nsearch) {
+            sg[t] = sg[0];
+            continue;
+        }
         const unsigned long long e = e0 + t;
-        if (e >= total) break;
-        float sg = 0.f;
-        for (int g = 0; g < segs.n; ++g)
-            if (e < segs.end[g]) { sg = segs.sigma[g]; break; }
-        out[e] = sg * z[t];
+        sg[t] = 0.f;
+        bool found = false;
+#pragma unroll
+        for (int g = 0; g < MAX_SEG; ++g)
+            if (!found && g < segs.n && e < segs.end[g]) {
+                sg[t] = segs.sigma[g];
+                found = true;
+            }
+    }
+    if (e0 + 4 <= total && (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+        *reinterpret_cast<float4*>(out + e0) = make_float4(sg[0] * z[0], sg[1] * z[1], sg[2] * z[2], sg[3] * z[3]);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (e0 + t < total) out[e0 + t] = sg[t] * z[t];
     }
 }
 
@@ -97,9 +118,11 @@ void launch_philox_noise(float* out, size_t count_total, unsigned long long seed
 {
     Segs s{};
     s.n = n_seg < MAX_SEG ? n_seg : MAX_SEG;
+    s.quad_ends = 1;
     for (int g = 0; g < s.n; ++g) {
         s.end[g] = seg_end[g];
         s.sigma[g] = seg_sigma[g];
+        if (seg_end[g] % 4 != 0) s.quad_ends = 0;
     }
     const unsigned long long quads = (count_total + 3) / 4;
     const unsigned blocks = (unsigned)((quads + 255) / 256);
