@@ -389,12 +389,13 @@ int st_stages(int pp)
 int stats_tc_rtiles(int M) { return (M + TM - 1) / TM; }
 int stats_tc_pp(int p) { return (p + 15) / 16 * 16; }
 int stats_tc_kh(int m) { return (m + KC - 1) / KC; }
-// one wave of at most 148 CTAs, and at least ~6 members per split so the
-// partial sums stay small next to the products
+// one wave of at most 148 CTAs, and at least 4 members per split: fewer
+// stages per CTA against more partial sums to reduce (measured at 64 x 64,
+// N = 256: 4 members per split beat 6 and 3)
 int stats_tc_splits(int M, int N)
 {
     int s = 148 / stats_tc_rtiles(M);
-    if (s > N / 6) s = N / 6;
+    if (s > N / 4) s = N / 4;
     return s < 1 ? 1 : s;
 }
 size_t stats_tc_bbytes(int N, int p, int m)
