@@ -192,9 +192,14 @@ def cpu_baseline(wl, budget_s=30.0):
     scaled to control steps/s of the full ensemble (its cost is linear in N)."""
     # the sample covariance needs (N - 1) m >= n + l samples to be definite
     n0 = max(8, -(-(wl.n + wl.l) // wl.m) + 2)
-    t0 = oracle_step_seconds(wl, n0)
-    n_s = int(max(n0, min(wl.N, budget_s / max(t0 / n0, 1e-4))))
-    t = oracle_step_seconds(wl, n_s) if n_s > n0 else t0
+    n_s, t = n0, oracle_step_seconds(wl, n0)
+    # grow the sample until it takes about the budget (a small sample's time
+    # is dominated by fixed costs, so one extrapolation undershoots)
+    for _ in range(4):
+        if t >= 0.5 * budget_s or n_s >= wl.N:
+            break
+        n_s = int(min(wl.N, max(n_s + 1, n_s * budget_s / max(t, 1e-3))))
+        t = oracle_step_seconds(wl, n_s)
     value = (n_s / wl.N) / t
     return {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
             "sample": f"1 control step with {n_s} of {wl.N} members ({t:.1f} s), scaled by "
