@@ -747,6 +747,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--members", type=int, default=0,
+                    help="ensemble size N other than the workload's (smaller cases for profiling)")
     ap.add_argument("--cov-outputs", action="store_true",
                     help="time solves with the optional covariance outputs against plain solves")
     ap.add_argument("--constraint", choices=["none", "u_box"], default="none",
@@ -766,6 +768,8 @@ def main(argv=None):
             return 0
         return run_mix(args, args.workload)
     wl = workloads.WORKLOADS[args.workload]()
+    if args.members:
+        wl = wl.with_(N=args.members, name=f"{wl.name}_N{args.members}")
     if args.constraint == "u_box":
         wl = wl.with_(cons=workloads.u_box(wl.n, wl.l, 0.1))
     if args.impl == "reference":

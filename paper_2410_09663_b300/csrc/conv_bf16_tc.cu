@@ -18,8 +18,10 @@
 //                X + s (out + b) in FP32
 // Like the FP32 kernel, the three VERTICAL taps are stacked along N: each
 // input row j is read once per (horizontal tap, 16-channel step) and feeds
-// output rows j+1, j, j-1 (N = 3 CO) into a ring of 4 TMEM slots of CO
-// columns.  Roles: one thread loads input rows (bulk copies), one thread
+// output rows j+1, j, j-1 (N = 3 CO) into a ring of NS = 8 TMEM slots of CO
+// columns: the issuing thread runs up to NS - 2 rows ahead of the drain, and
+// only the two ring positions where the window of three wraps split an MMA.
+// Roles: one thread loads input rows (bulk copies), one thread
 // issues the MMAs, NDW warps drain finished output rows.
 #include <cuda_bf16.h>
 
@@ -56,7 +58,11 @@ struct BS {
     static constexpr int OFF_BIAS = OFF_B + BBYTES;
     static constexpr int OFF_MISC = OFF_BIAS + (CO * 4 + 15) / 16 * 16;
     static constexpr int SMEM = OFF_MISC + 512;
-    static constexpr int TMEM_COLS = 4 * CO <= 32 ? 32 : 4 * CO <= 64 ? 64 : 4 * CO <= 128 ? 128 : 256;
+    static constexpr int NS = 8;                        // TMEM ring slots (output rows); the HDONE and
+                                                        // PASS barrier arrays have NS entries
+    static constexpr int TMEM_COLS = NS * CO <= 32 ? 32 : NS * CO <= 64 ? 64 : NS * CO <= 128 ? 128
+                                     : NS * CO <= 256 ? 256 : 512;
+    static_assert(NS * CO <= 512, "tensor memory");
     static_assert(CI % 16 == 0 && (CO == 16 || CO == 32 || CO == 64), "shapes");
     static_assert(MODE != MODE_LAST || CO == 16, "last layer: 16 columns, channel 0 used");
 };
@@ -65,10 +71,11 @@ struct BS {
 enum : int {
     BB_FULL = 0,       // [12] input row landed (bulk copy), by slot
     BB_FREE = 12,      // [12] MMAs of the input row in the slot done
-    BB_HDONE = 24,     // [2]  MMAs of input row j done (parity of j)
-    BB_PASS = 26,      // [4]  drain pass k done (k mod 4)
-    BB_FIN = 30,
-    BB_COUNT = 31
+    BB_HDONE = 24,     // [8]  MMAs of input row j done (j mod 8: the issuer runs up to 6
+                       //      rows ahead, so each barrier has one phase outstanding)
+    BB_PASS = 32,      // [8]  drain pass k done (k mod 8)
+    BB_FIN = 40,
+    BB_COUNT = 41
 };
 
 constexpr uint32_t DESC_HI = (128u >> 4) | (1u << 14);
@@ -133,13 +140,15 @@ __device__ __forceinline__ void piece(uint32_t tmem, uint32_t a, uint32_t b, uin
     mma_bf16(tmem + COL, a, b + (CO * B0 * 16) / 16, id, acc);
 }
 
-// All MMAs of input row j (ring position SR = (-j-1) mod 4: blocks b = 0, 1,
-// 2 = output rows j+1, j, j-1 in slots SR, SR+1, SR+2 mod 4).  The first MMA
-// starts output row j+1 (accumulate 0 on its block); INIT_ALL starts all.
+// All MMAs of input row j (ring position SR = (-j-1) mod NS: blocks b = 0,
+// 1, 2 = output rows j+1, j, j-1 in slots SR, SR+1, SR+2 mod NS; the window
+// is split where it wraps).  The first MMA starts output row j+1 (accumulate
+// 0 on its block); INIT_ALL starts all.
 template <int CI, int CO, int MODE, int W, int SR, bool INIT_ALL>
 __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t b)
 {
     using S = BS<CI, CO, MODE, W>;
+    constexpr int NS = S::NS;
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
@@ -149,23 +158,23 @@ __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t 
             const bool first = dx == 0 && ks == 0;
             if (first && !INIT_ALL) {
                 piece<CO, 0, 1, CO * SR>(tmem, aa, bb, 0u);
-                if constexpr (SR == 2) {
-                    piece<CO, 1, 2, CO * 3>(tmem, aa, bb, 1u);
-                    piece<CO, 2, 3, 0>(tmem, aa, bb, 1u);
-                } else if constexpr (SR == 3) {
+                if constexpr (SR + 1 == NS) {
                     piece<CO, 1, 3, 0>(tmem, aa, bb, 1u);
+                } else if constexpr (SR + 2 == NS) {
+                    piece<CO, 1, 2, CO * (SR + 1)>(tmem, aa, bb, 1u);
+                    piece<CO, 2, 3, 0>(tmem, aa, bb, 1u);
                 } else {
                     piece<CO, 1, 3, CO * (SR + 1)>(tmem, aa, bb, 1u);
                 }
             } else {
                 const uint32_t acc = first ? 0u : 1u;
-                if constexpr (SR <= 1) {
+                if constexpr (SR + 3 <= NS) {
                     piece<CO, 0, 3, CO * SR>(tmem, aa, bb, acc);
-                } else if constexpr (SR == 2) {
-                    piece<CO, 0, 2, CO * 2>(tmem, aa, bb, acc);
+                } else if constexpr (SR + 2 == NS) {
+                    piece<CO, 0, 2, CO * SR>(tmem, aa, bb, acc);
                     piece<CO, 2, 3, 0>(tmem, aa, bb, acc);
                 } else {
-                    piece<CO, 0, 1, CO * 3>(tmem, aa, bb, acc);
+                    piece<CO, 0, 1, CO * SR>(tmem, aa, bb, acc);
                     piece<CO, 1, 3, 0>(tmem, aa, bb, acc);
                 }
             }
@@ -173,25 +182,28 @@ __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t 
     }
 }
 
+template <int CI, int CO, int MODE, int W, bool INIT_ALL>
+__device__ __forceinline__ void issue_row_r(uint32_t tmem, int s, uint32_t a, uint32_t b)
+{
+    static_assert(BS<CI, CO, MODE, W>::NS == 8, "ring dispatch");
+    switch (s) {
+    case 0: issue_row_s<CI, CO, MODE, W, 0, INIT_ALL>(tmem, a, b); break;
+    case 1: issue_row_s<CI, CO, MODE, W, 1, INIT_ALL>(tmem, a, b); break;
+    case 2: issue_row_s<CI, CO, MODE, W, 2, INIT_ALL>(tmem, a, b); break;
+    case 3: issue_row_s<CI, CO, MODE, W, 3, INIT_ALL>(tmem, a, b); break;
+    case 4: issue_row_s<CI, CO, MODE, W, 4, INIT_ALL>(tmem, a, b); break;
+    case 5: issue_row_s<CI, CO, MODE, W, 5, INIT_ALL>(tmem, a, b); break;
+    case 6: issue_row_s<CI, CO, MODE, W, 6, INIT_ALL>(tmem, a, b); break;
+    default: issue_row_s<CI, CO, MODE, W, 7, INIT_ALL>(tmem, a, b); break;
+    }
+}
+
 template <int CI, int CO, int MODE, int W>
 __device__ __forceinline__ void issue_row(uint32_t tmem, int j, bool init_all, uint32_t a, uint32_t b)
 {
-    const int s = (-j - 1) & 3;
-    if (init_all) {
-        switch (s) {
-        case 0: issue_row_s<CI, CO, MODE, W, 0, true>(tmem, a, b); break;
-        case 1: issue_row_s<CI, CO, MODE, W, 1, true>(tmem, a, b); break;
-        case 2: issue_row_s<CI, CO, MODE, W, 2, true>(tmem, a, b); break;
-        default: issue_row_s<CI, CO, MODE, W, 3, true>(tmem, a, b); break;
-        }
-    } else {
-        switch (s) {
-        case 0: issue_row_s<CI, CO, MODE, W, 0, false>(tmem, a, b); break;
-        case 1: issue_row_s<CI, CO, MODE, W, 1, false>(tmem, a, b); break;
-        case 2: issue_row_s<CI, CO, MODE, W, 2, false>(tmem, a, b); break;
-        default: issue_row_s<CI, CO, MODE, W, 3, false>(tmem, a, b); break;
-        }
-    }
+    const int s = (-j - 1) & (BS<CI, CO, MODE, W>::NS - 1);
+    if (init_all) issue_row_r<CI, CO, MODE, W, true>(tmem, s, a, b);
+    else issue_row_r<CI, CO, MODE, W, false>(tmem, s, a, b);
 }
 
 // in: activation rows [groups][n][CI/8][NPOS][8] BF16.  MODE_HIDDEN: out the
@@ -218,7 +230,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
         reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk)[e];
     for (int e = tid; e < CO; e += S::NT) sbias[e] = bias[e];
     if (tid == 0) {
-        for (int i = 0; i < BB_COUNT; ++i) tc::mbar_init(mb + i, (i >= BB_PASS && i < BB_PASS + 4) ? S::NDW : 1);
+        for (int i = 0; i < BB_COUNT; ++i) tc::mbar_init(mb + i, (i >= BB_PASS && i < BB_PASS + S::NS) ? S::NDW : 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -234,14 +246,15 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n;
     const long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
-    uint32_t ph = 0;
+    static_assert(BB_COUNT <= 64, "phase bits");
+    uint64_t ph = 0;                                    // this thread's phase bit per mbarrier
     bool failed = false;
     auto wait = [&](int i) {
-        if (!tc::mbar_wait_bounded(mb + i, (ph >> i) & 1u, B_WAIT)) {
+        if (!tc::mbar_wait_bounded(mb + i, (uint32_t)((ph >> i) & 1ull), B_WAIT)) {
             failed = true;
             atomicExch(err, DEV_TIMEOUT);
         }
-        ph ^= 1u << i;
+        ph ^= 1ull << i;
         tc::fence_after_sync();
     };
     auto wait_w = [&](int i) {
@@ -286,16 +299,17 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                 const uint32_t dIn = desc_lo(s0 + S::OFF_IN, S::PLANE);
                 const uint32_t dB = desc_lo(s0 + S::OFF_B, S::NB * 16);
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
-                    // output row j+1 takes the ring slot of row j-3, drained in pass j-2
-                    if (j - 2 >= f_lo) wait(BB_PASS + ((j - 2) & 3));
+                    // output row j+1 takes the ring slot of row j+1-NS, drained in
+                    // pass j+2-NS
+                    if (j + 2 - S::NS >= f_lo) wait(BB_PASS + ((j + 2 - S::NS) & (S::NS - 1)));
                     wait(BB_FULL + j % S::NIN);
                     issue_row<CI, CO, MODE, W>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
                     tc::mma_commit(mb + BB_FREE + j % S::NIN);
-                    tc::mma_commit(mb + BB_HDONE + (j & 1));
+                    tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
                 }
                 // the remaining drain passes
-                for (int k = f_hi - 1; k <= f_hi + 1 && !failed; ++k)
-                    if (k >= f_lo && k <= (ye < n ? ye : n)) wait(BB_PASS + (k & 3));
+                for (int k = f_hi + 3 - S::NS; k <= f_hi + 1 && !failed; ++k)
+                    if (k >= f_lo && k <= (ye < n ? ye : n)) wait(BB_PASS + (k & (S::NS - 1)));
             }
             __syncwarp();
         } else {
@@ -309,13 +323,15 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                            : 0.f;
             };
             float xpf = fetch_x(f_lo - 1);
+            // every pass waits the MMAs of its input row, so a pass with none
+            // (the image bottom) follows the previous pass's wait
             for (int k = f_lo; k <= last_pass && !failed; ++k) {
                 const float xcur = xpf;
                 xpf = fetch_x(k);
-                if (Fv(k)) wait_w(BB_HDONE + (k & 1));
+                if (Fv(k)) wait_w(BB_HDONE + (k & (S::NS - 1)));
                 const int h = k - 1;
                 if (Ov(h)) {
-                    const uint32_t col = (uint32_t)(CO * ((-h) & 3));
+                    const uint32_t col = (uint32_t)(CO * ((-h) & (S::NS - 1)));
                     if constexpr (MODE == MODE_HIDDEN) {
                         constexpr int CPW = CO / 4;             // channels per warp
                         float v[CPW];
@@ -346,7 +362,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                 }
                 tc::fence_before_sync();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & 3));
+                if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
             }
         }
         tc::fence_before_sync();
