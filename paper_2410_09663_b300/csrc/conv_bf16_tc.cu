@@ -14,8 +14,11 @@
 //
 // One kernel per layer: conv_bf16_kernel<CI, CO, MODE, W>.
 //   MODE_HIDDEN  CO channels, tanh, BF16 rows out
-//   MODE_LAST    CO = 16 columns of which channel 0 is the output; X_next =
-//                X + s (out + b) in FP32
+//   MODE_LAST    one output channel: the nine taps of each input row stacked
+//                along N (16 columns, unshifted row, one MMA per 16-channel
+//                step); the drain warps add the horizontal neighbours (+-G
+//                positions, through shared memory) and keep rolling sums of
+//                output rows h-1, h, h+1; X_next = X + s (out + b) in FP32
 // Like the FP32 kernel, the three VERTICAL taps are stacked along N: each
 // input row j is read once per (horizontal tap, 16-channel step) and feeds
 // output rows j+1, j, j-1 (N = 3 CO) into a ring of NS = 8 TMEM slots of CO
@@ -42,9 +45,10 @@ struct BS {
     static constexpr int PLANE = NPOS * 16;             // one 8-channel plane of a row
     static constexpr int INROW = (CI / 8) * PLANE;      // one input row
     static constexpr int KS = CI / 16;
-    static constexpr int NB = 3 * CO;                   // B rows: vertical taps stacked
+    static constexpr int NB = MODE == MODE_LAST ? 16 : 3 * CO;   // B rows: vertical taps (hidden) or
+                                                        // the nine taps, padded (last)
     static constexpr int BTILE = 2 * NB * 16;           // one (dx, ks) tile, 2 K chunks
-    static constexpr int BBYTES = 3 * KS * BTILE;
+    static constexpr int BBYTES = (MODE == MODE_LAST ? 1 : 3) * KS * BTILE;
     // input rows in flight (bulk copies from HBM): as many as fit next to the
     // weights, up to 12
     static constexpr int NIN_FIT = (200 * 1024 - BBYTES) / INROW;
@@ -56,13 +60,16 @@ struct BS {
     static constexpr int OFF_IN = 0;
     static constexpr int OFF_B = OFF_IN + NIN * INROW;
     static constexpr int OFF_BIAS = OFF_B + BBYTES;
-    static constexpr int OFF_MISC = OFF_BIAS + (CO * 4 + 15) / 16 * 16;
+    static constexpr int OFF_EX = OFF_BIAS + (CO * 4 + 15) / 16 * 16;   // last layer: neighbour exchange
+    static constexpr int EXBYTES = MODE == MODE_LAST ? (2 * 6 * NPOS * 4 + 15) / 16 * 16 : 0;
+    static constexpr int OFF_MISC = OFF_EX + EXBYTES;
     static constexpr int SMEM = OFF_MISC + 512;
     static constexpr int NS = 8;                        // TMEM ring slots (output rows); the HDONE and
                                                         // PASS barrier arrays have NS entries
-    static constexpr int TMEM_COLS = NS * CO <= 32 ? 32 : NS * CO <= 64 ? 64 : NS * CO <= 128 ? 128
-                                     : NS * CO <= 256 ? 256 : 512;
-    static_assert(NS * CO <= 512, "tensor memory");
+    static constexpr int TCOL = MODE == MODE_LAST ? 16 : CO;   // TMEM columns per ring slot
+    static constexpr int TMEM_COLS = NS * TCOL <= 32 ? 32 : NS * TCOL <= 64 ? 64 : NS * TCOL <= 128 ? 128
+                                     : NS * TCOL <= 256 ? 256 : 512;
+    static_assert(NS * TCOL <= 512, "tensor memory");
     static_assert(CI % 16 == 0 && (CO == 16 || CO == 32 || CO == 64), "shapes");
     static_assert(MODE != MODE_LAST || CO == 16, "last layer: 16 columns, channel 0 used");
 };
@@ -228,6 +235,8 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
 
     for (int e = tid; e < S::BBYTES / 16; e += S::NT)
         reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk)[e];
+    for (int e = tid; e < S::EXBYTES / 16; e += S::NT)            // pads of the exchange stay zero
+        reinterpret_cast<uint4*>(smem + S::OFF_EX)[e] = make_uint4(0u, 0u, 0u, 0u);
     for (int e = tid; e < CO; e += S::NT) sbias[e] = bias[e];
     if (tid == 0) {
         for (int i = 0; i < BB_COUNT; ++i) tc::mbar_init(mb + i, (i >= BB_PASS && i < BB_PASS + S::NS) ? S::NDW : 1);
@@ -298,17 +307,28 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
             if (lane == 0) {
                 const uint32_t dIn = desc_lo(s0 + S::OFF_IN, S::PLANE);
                 const uint32_t dB = desc_lo(s0 + S::OFF_B, S::NB * 16);
+                // hidden: output row j+1 takes the ring slot of row j+1-NS, drained in
+                // pass j+2-NS.  last: input row j's taps take the slot of row j-NS,
+                // read in pass j-NS.
+                constexpr int LAG = MODE == MODE_LAST ? S::NS : S::NS - 2;
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
-                    // output row j+1 takes the ring slot of row j+1-NS, drained in
-                    // pass j+2-NS
-                    if (j + 2 - S::NS >= f_lo) wait(BB_PASS + ((j + 2 - S::NS) & (S::NS - 1)));
+                    if (j - LAG >= f_lo) wait(BB_PASS + ((j - LAG) & (S::NS - 1)));
                     wait(BB_FULL + j % S::NIN);
-                    issue_row<CI, CO, MODE, W>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
+                    const uint32_t a = dIn + (j % S::NIN) * (S::INROW / 16);
+                    if constexpr (MODE == MODE_LAST) {
+                        constexpr uint32_t id = tc::idesc_f16(BM, 16, true);
+#pragma unroll
+                        for (int ks = 0; ks < S::KS; ++ks)
+                            mma_bf16(tmem + (j & (S::NS - 1)) * S::TCOL, a + (2 * ks * S::PLANE) / 16 + G,
+                                     dB + (ks * S::BTILE) / 16, id, ks > 0 ? 1u : 0u);
+                    } else {
+                        issue_row<CI, CO, MODE, W>(tmem, j, j == f_lo, a, dB);
+                    }
                     tc::mma_commit(mb + BB_FREE + j % S::NIN);
                     tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
                 }
                 // the remaining drain passes
-                for (int k = f_hi + 3 - S::NS; k <= f_hi + 1 && !failed; ++k)
+                for (int k = f_hi + 1 - LAG; k <= f_hi + 1 && !failed; ++k)
                     if (k >= f_lo && k <= (ye < n ? ye : n)) wait(BB_PASS + (k & (S::NS - 1)));
             }
             __syncwarp();
@@ -322,17 +342,58 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                            ? X[(long)xmb * x_ms + (long)h * m + xx]
                            : 0.f;
             };
-            float xpf = fetch_x(f_lo - 1);
-            // every pass waits the MMAs of its input row, so a pass with none
-            // (the image bottom) follows the previous pass's wait
-            for (int k = f_lo; k <= last_pass && !failed; ++k) {
-                const float xcur = xpf;
-                xpf = fetch_x(k);
-                if (Fv(k)) wait_w(BB_HDONE + (k & (S::NS - 1)));
-                const int h = k - 1;
-                if (Ov(h)) {
-                    const uint32_t col = (uint32_t)(CO * ((-h) & (S::NS - 1)));
-                    if constexpr (MODE == MODE_HIDDEN) {
+            if constexpr (MODE == MODE_LAST) {
+                // pass k: the taps of input row k -> contributions to output rows
+                // k+1, k, k-1; output row k-1 is then complete.  X rows are loaded
+                // two passes ahead.
+                float* ex = reinterpret_cast<float*>(smem + S::OFF_EX);
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f;               // output rows k-1, k, k+1
+                float xq0 = fetch_x(f_lo - 1), xq1 = fetch_x(f_lo);
+                for (int k = f_lo; k <= last_pass && !failed; ++k) {
+                    const float xcur = xq0;
+                    xq0 = xq1;
+                    xq1 = fetch_x(k + 1);
+                    if (Fv(k)) {
+                        wait_w(BB_HDONE + (k & (S::NS - 1)));
+                        float v[16];
+                        tmem_ldn<16>(tmem + tlane + (k & (S::NS - 1)) * S::TCOL, v);
+                        tc::tmem_ld_wait();
+                        // tap t = 3 dy + dx; output pixel x takes tap dx from input pixel
+                        // x + dx - 1, i.e. position ep + (dx - 1) G
+                        float* e0 = ex + (k & 1) * 6 * S::NPOS;
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) {
+                            e0[(2 * dy) * S::NPOS + G + ep] = v[3 * dy];
+                            e0[(2 * dy + 1) * S::NPOS + G + ep] = v[3 * dy + 2];
+                        }
+                        tc::named_bar(1, S::NDW * 32);
+                        float c3[3];
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+                            c3[dy] = v[3 * dy + 1] + e0[(2 * dy) * S::NPOS + ep] +
+                                     e0[(2 * dy + 1) * S::NPOS + 2 * G + ep];
+                        a0 += c3[2];
+                        a1 += c3[1];
+                        a2 += c3[0];
+                    }
+                    const int h = k - 1;
+                    if (Ov(h) && xmb < Nb && ep < LIVE)
+                        Xout[(long)xmb * o_ms + (long)h * m + xx] = fmaf(rs, a0 + sbias[0], xcur);
+                    a0 = a1;
+                    a1 = a2;
+                    a2 = 0.f;
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
+                }
+            } else {
+                // every pass waits the MMAs of its input row, so a pass with none
+                // (the image bottom) follows the previous pass's wait
+                for (int k = f_lo; k <= last_pass && !failed; ++k) {
+                    if (Fv(k)) wait_w(BB_HDONE + (k & (S::NS - 1)));
+                    const int h = k - 1;
+                    if (Ov(h)) {
+                        const uint32_t col = (uint32_t)(CO * ((-h) & (S::NS - 1)));
                         constexpr int CPW = CO / 4;             // channels per warp
                         float v[CPW];
                         tmem_ldn<CPW>(tmem + tlane + col + cg * CPW, v);
@@ -352,17 +413,11 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                                 *reinterpret_cast<uint4*>(orow + ((size_t)(cg * CPW / 8 + pl) * S::NPOS + G + ep) * 8) =
                                     make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
                         }
-                    } else {
-                        float v[8];
-                        tmem_ldn<8>(tmem + tlane + col, v);
-                        tc::tmem_ld_wait();
-                        if (xmb < Nb && ep < LIVE)
-                            Xout[(long)xmb * o_ms + (long)h * m + xx] = fmaf(rs, v[0] + sbias[0], xcur);
                     }
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
                 }
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
             }
         }
         tc::fence_before_sync();
@@ -487,13 +542,26 @@ size_t bf16_act_bytes(int N, int n, int m, int C)
 
 // Packed B tiles of one layer: [dx][ks] tiles of 2 K chunks x 3 CO rows; row
 // b CO + co, K index e = ci - 16 ks: w[co][ci][dy = b][dx] as BF16 (zero for
-// co >= cout or ci >= cin).  CI, CO: padded sizes.
+// co >= cout or ci >= cin).  CI, CO: padded sizes.  The last layer (CO = 16,
+// one output channel) instead packs [ks] tiles of 2 K chunks x 16 rows, row
+// t = 3 dy + dx (t < 9, the rest zero): w[0][ci][dy][dx].
 size_t bf16_layer_bytes(int CI, int CO) { return (size_t)3 * (CI / 16) * 2 * 3 * CO * 16; }
 
 void bf16_pack_layer(const float* w, int cin, int cout, int CI, int CO, void* dst_host)
 {
     __nv_bfloat16* out = static_cast<__nv_bfloat16*>(dst_host);
     const int KS = CI / 16, NB = 3 * CO;
+    if (CO == 16) {
+        for (int ks = 0; ks < KS; ++ks)
+            for (int kc = 0; kc < 2; ++kc)
+                for (int t = 0; t < 16; ++t)
+                    for (int e = 0; e < 8; ++e) {
+                        const int ci = ks * 16 + kc * 8 + e, dy = t / 3, dx = t % 3;
+                        const float v = (t < 9 && ci < cin && cout >= 1) ? w[(ci * 3 + dy) * 3 + dx] : 0.f;
+                        out[(((size_t)ks * 2 + kc) * 16 + t) * 8 + e] = __float2bfloat16_rn(v);
+                    }
+        return;
+    }
     for (int dx = 0; dx < 3; ++dx)
         for (int ks = 0; ks < KS; ++ks)
             for (int kc = 0; kc < 2; ++kc)
