@@ -36,7 +36,7 @@ namespace {
 
 constexpr int BM = 128;                                 // tile rows (positions)
 constexpr long long B_WAIT = 4000000000LL;
-enum { MODE_HIDDEN = 0, MODE_LAST = 1 };
+enum { MODE_HIDDEN = 0, MODE_LAST = 1, MODE_FUSED = 2 };
 
 template <int CI, int CO, int MODE, int W>
 struct BS {
@@ -45,31 +45,42 @@ struct BS {
     static constexpr int PLANE = NPOS * 16;             // one 8-channel plane of a row
     static constexpr int INROW = (CI / 8) * PLANE;      // one input row
     static constexpr int KS = CI / 16;
-    static constexpr int NB = MODE == MODE_LAST ? 16 : 3 * CO;   // B rows: vertical taps (hidden) or
+    static constexpr bool LAST = MODE == MODE_LAST, FUSED = MODE == MODE_FUSED;
+    static constexpr int NB = LAST ? 16 : 3 * CO;       // B rows: vertical taps (hidden) or
                                                         // the nine taps, padded (last)
     static constexpr int BTILE = 2 * NB * 16;           // one (dx, ks) tile, 2 K chunks
-    static constexpr int BBYTES = (MODE == MODE_LAST ? 1 : 3) * KS * BTILE;
+    static constexpr int BBYTES = (LAST ? 1 : 3) * KS * BTILE;
+    // fused hidden + last layer: the last layer's tiles (K = CO), and two
+    // hidden rows in the operand layout that the last layer's MMAs read
+    static constexpr int BLBYTES = FUSED ? (CO / 16) * 2 * 16 * 16 : 0;
+    static constexpr int OUTROW = (CO / 8) * PLANE;
+    static constexpr int H2BYTES = FUSED ? 2 * OUTROW : 0;
+    static constexpr int EXBYTES = (LAST || FUSED) ? (2 * 6 * NPOS * 4 + 15) / 16 * 16 : 0;
     // input rows in flight (bulk copies from HBM): as many as fit next to the
-    // weights, up to 12
-    static constexpr int NIN_FIT = (200 * 1024 - BBYTES) / INROW;
+    // rest, up to 12
+    static constexpr int NIN_FIT = ((FUSED ? 219 : 200) * 1024 - BBYTES - BLBYTES - H2BYTES - EXBYTES) / INROW;
     static constexpr int NIN = NIN_FIT > 12 ? 12 : NIN_FIT;
     static_assert(NIN >= 4, "input ring");
-    static constexpr int NDW = MODE == MODE_LAST ? 4 : 16;   // drain warps
-    static constexpr int LOAD_WARP = NDW, ISSUE_WARP = NDW + 1;
-    static constexpr int NT = 32 * (NDW + 2);
+    static constexpr int NDW = LAST ? 4 : 16;           // drain warps (hidden rows, or the last layer)
+    static constexpr int NDL = FUSED ? 4 : 0;           // fused: last-layer drain warps
+    static constexpr int LOAD_WARP = NDW + NDL, ISSUE_WARP = NDW + NDL + 1;
+    static constexpr int NT = 32 * (NDW + NDL + 2);
     static constexpr int OFF_IN = 0;
     static constexpr int OFF_B = OFF_IN + NIN * INROW;
-    static constexpr int OFF_BIAS = OFF_B + BBYTES;
-    static constexpr int OFF_EX = OFF_BIAS + (CO * 4 + 15) / 16 * 16;   // last layer: neighbour exchange
-    static constexpr int EXBYTES = MODE == MODE_LAST ? (2 * 6 * NPOS * 4 + 15) / 16 * 16 : 0;
+    static constexpr int OFF_BL = OFF_B + BBYTES;
+    static constexpr int OFF_H2 = OFF_BL + BLBYTES;
+    static constexpr int OFF_BIAS = OFF_H2 + H2BYTES;   // CO floats, then the last layer's bias (fused)
+    static constexpr int OFF_EX = OFF_BIAS + ((CO + 4) * 4 + 15) / 16 * 16;   // neighbour exchange
     static constexpr int OFF_MISC = OFF_EX + EXBYTES;
     static constexpr int SMEM = OFF_MISC + 512;
-    static constexpr int NS = 8;                        // TMEM ring slots (output rows); the HDONE and
-                                                        // PASS barrier arrays have NS entries
-    static constexpr int TCOL = MODE == MODE_LAST ? 16 : CO;   // TMEM columns per ring slot
-    static constexpr int TMEM_COLS = NS * TCOL <= 32 ? 32 : NS * TCOL <= 64 ? 64 : NS * TCOL <= 128 ? 128
-                                     : NS * TCOL <= 256 ? 256 : 512;
-    static_assert(NS * TCOL <= 512, "tensor memory");
+    static_assert(SMEM <= 232448, "shared memory");
+    static constexpr int NS = FUSED ? 4 : 8;            // TMEM ring slots (rows); the HDONE and PASS
+                                                        // barrier arrays have NS entries
+    static constexpr int TCOL = LAST ? 16 : CO;         // TMEM columns per ring slot
+    static constexpr int T_L = NS * TCOL;               // fused: the last layer's 2 slots of 16
+    static constexpr int TMEM_COLS = FUSED ? 512 : NS * TCOL <= 32 ? 32 : NS * TCOL <= 64 ? 64
+                                     : NS * TCOL <= 128 ? 128 : NS * TCOL <= 256 ? 256 : 512;
+    static_assert(NS * TCOL + (FUSED ? 32 : 0) <= 512, "tensor memory");
     static_assert(CI % 16 == 0 && (CO == 16 || CO == 32 || CO == 64), "shapes");
     static_assert(MODE != MODE_LAST || CO == 16, "last layer: 16 columns, channel 0 used");
 };
@@ -82,7 +93,9 @@ enum : int {
                        //      rows ahead, so each barrier has one phase outstanding)
     BB_PASS = 32,      // [8]  drain pass k done (k mod 8)
     BB_FIN = 40,
-    BB_COUNT = 41
+    BB_LDONE = 41,     // [2]  fused: last-layer MMAs of hidden row h done (h mod 2)
+    BB_LPASS = 43,     // [2]  fused: last-layer drain of hidden row h done (h mod 2)
+    BB_COUNT = 45
 };
 
 constexpr uint32_t DESC_HI = (128u >> 4) | (1u << 14);
@@ -192,7 +205,16 @@ __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t 
 template <int CI, int CO, int MODE, int W, bool INIT_ALL>
 __device__ __forceinline__ void issue_row_r(uint32_t tmem, int s, uint32_t a, uint32_t b)
 {
-    static_assert(BS<CI, CO, MODE, W>::NS == 8, "ring dispatch");
+    static_assert(BS<CI, CO, MODE, W>::NS == 8 || BS<CI, CO, MODE, W>::NS == 4, "ring dispatch");
+    if constexpr (BS<CI, CO, MODE, W>::NS == 4) {
+        switch (s) {
+        case 0: issue_row_s<CI, CO, MODE, W, 0, INIT_ALL>(tmem, a, b); break;
+        case 1: issue_row_s<CI, CO, MODE, W, 1, INIT_ALL>(tmem, a, b); break;
+        case 2: issue_row_s<CI, CO, MODE, W, 2, INIT_ALL>(tmem, a, b); break;
+        default: issue_row_s<CI, CO, MODE, W, 3, INIT_ALL>(tmem, a, b); break;
+        }
+        return;
+    }
     switch (s) {
     case 0: issue_row_s<CI, CO, MODE, W, 0, INIT_ALL>(tmem, a, b); break;
     case 1: issue_row_s<CI, CO, MODE, W, 1, INIT_ALL>(tmem, a, b); break;
@@ -433,6 +455,256 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
     if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
+// The final hidden layer (C -> C, tanh) fused with the last layer (C -> 1):
+// the hidden rows never leave shared memory.  Warps 0-15 drain hidden rows
+// into two shared-memory slots in the operand layout; warps 16-19 drain the
+// last layer as MODE_LAST does (nine taps along N, neighbour exchange, rolling
+// sums, X_next = X + s (out + b)); one warp loads input rows; one thread
+// issues both layers' MMAs.  A segment owns output rows [ys, ye) of one member
+// group; its hidden rows are [r_lo, r_hi] = [ys-1, ye] within the image, its
+// input rows [f_lo, f_hi] one further on each side.
+//
+// Ordering (each barrier has one phase outstanding per waiter):
+//   hidden pass k waits HDONE(k), writes hidden row h = k-1 into slot h mod 2
+//   after LDONE(h-2) (the last layer's MMAs that read the slot), then arrives
+//   on PASS(k); the issuer waits PASS(k) before the last layer's MMAs of row
+//   k-1 (and, as in MODE_HIDDEN, before reusing the ring slot of pass k's row);
+//   those MMAs reuse the last layer's TMEM slot h mod 2 after LPASS(h-2).
+template <int C, int W>
+__global__ void __launch_bounds__(BS<C, C, MODE_FUSED, W>::NT, 1)
+conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __restrict__ X, long x_ms,
+                       float* __restrict__ Xout, long o_ms, const __nv_bfloat16* __restrict__ wpk,
+                       const float* __restrict__ bias, const __nv_bfloat16* __restrict__ wlast,
+                       const float* __restrict__ blast, int Nb, int n, float rs, int* __restrict__ err)
+{
+    pdl_begin();
+    using S = BS<C, C, MODE_FUSED, W>;
+    constexpr int G = S::G, m = W;
+    constexpr int LIVE = G * W;
+    constexpr int CPW = C / 4;                          // hidden drain: channels per warp
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + BB_COUNT * 8);
+    float* sbias = reinterpret_cast<float*>(smem + S::OFF_BIAS);
+    float* ex = reinterpret_cast<float*>(smem + S::OFF_EX);
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const uint32_t s0 = tc::smem_u32(smem);
+
+    for (int e = tid; e < S::BBYTES / 16; e += S::NT)
+        reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk)[e];
+    for (int e = tid; e < S::BLBYTES / 16; e += S::NT)
+        reinterpret_cast<uint4*>(smem + S::OFF_BL)[e] = reinterpret_cast<const uint4*>(wlast)[e];
+    for (int e = tid; e < S::H2BYTES / 16; e += S::NT)            // pads of the hidden rows stay zero
+        reinterpret_cast<uint4*>(smem + S::OFF_H2)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < S::EXBYTES / 16; e += S::NT)            // pads of the exchange stay zero
+        reinterpret_cast<uint4*>(smem + S::OFF_EX)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < C; e += S::NT) sbias[e] = bias[e];
+    if (tid == 0) {
+        sbias[C] = blast[0];
+        for (int i = 0; i < BB_COUNT; ++i) {
+            const int cnt = (i >= BB_PASS && i < BB_PASS + S::NS) ? S::NDW : (i >= BB_LPASS && i < BB_LPASS + 2) ? S::NDL : 1;
+            tc::mbar_init(mb + i, cnt);
+        }
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_holder, S::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+
+    const int groups = (Nb + G - 1) / G;
+    const long total = (long)groups * n;
+    const long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+    static_assert(BB_COUNT <= 64, "phase bits");
+    uint64_t ph = 0;
+    bool failed = false;
+    auto wait = [&](int i) {
+        if (!tc::mbar_wait_bounded(mb + i, (uint32_t)((ph >> i) & 1ull), B_WAIT)) {
+            failed = true;
+            atomicExch(err, DEV_TIMEOUT);
+        }
+        ph ^= 1ull << i;
+        tc::fence_after_sync();
+    };
+    auto wait_w = [&](int i) {
+        wait(i);
+        failed = __any_sync(0xffffffffu, failed);
+    };
+    auto passed = [&](int i) { ph ^= 1ull << i; };
+    const int q4 = warp & 3;                            // drains: lane quarter
+    const int ep = 32 * q4 + lane;
+    const uint32_t tlane = (uint32_t)(32 * q4) << 16;
+
+    for (long t = t0; t < t1;) {
+        const int g = (int)(t / n);
+        const int ys = (int)(t % n);
+        const long rem = t1 - t;
+        const int ye = (long)(n - ys) < rem ? n : (int)(ys + rem);
+        t += ye - ys;
+        const int r_lo = ys > 0 ? ys - 1 : 0, r_hi = ye < n ? ye : n - 1;            // hidden rows
+        const int f_lo = r_lo > 0 ? r_lo - 1 : 0, f_hi = r_hi < n - 1 ? r_hi + 1 : n - 1;   // input rows
+        const int hlast = r_hi + 1;                     // hidden pass k finishes hidden row k-1
+        auto Fv = [&](int f) { return f >= f_lo && f <= f_hi; };
+        auto Hv = [&](int h) { return h >= r_lo && h <= r_hi; };
+        auto Ov = [&](int h) { return h >= ys && h < ye; };
+        const __nv_bfloat16* in_g = in + (size_t)g * n * (S::INROW / 2);
+
+        if (warp == S::LOAD_WARP) {
+            // ============ loads: input row j into slot j % NIN ============
+            if (lane == 0) {
+                for (int j = f_lo; j <= f_hi && !failed; ++j) {
+                    const int sl = j % S::NIN;
+                    if (j - S::NIN >= f_lo) wait(BB_FREE + sl);    // MMAs of row j - NIN done
+                    mbar_expect_tx(mb + BB_FULL + sl, S::INROW);
+                    bulk_g2s(smem + S::OFF_IN + sl * S::INROW, in_g + (size_t)j * (S::INROW / 2), S::INROW,
+                             mb + BB_FULL + sl);
+                }
+                for (int j = f_hi - S::NIN + 1; j <= f_hi && !failed; ++j)
+                    if (j >= f_lo) wait(BB_FREE + j % S::NIN);
+            }
+            __syncwarp();
+        } else if (warp == S::ISSUE_WARP) {
+            // ============ MMAs of both layers ============
+            if (lane == 0) {
+                const uint32_t dIn = desc_lo(s0 + S::OFF_IN, S::PLANE);
+                const uint32_t dB = desc_lo(s0 + S::OFF_B, S::NB * 16);
+                const uint32_t dH2 = desc_lo(s0 + S::OFF_H2, S::PLANE);
+                const uint32_t dBL = desc_lo(s0 + S::OFF_BL, 16 * 16);
+                // last layer of hidden row h (in its shared-memory slot h mod 2)
+                auto issue_last = [&](int h) {
+                    if (!Hv(h) || failed) return;
+                    if (h - 2 >= r_lo) wait(BB_LPASS + (h & 1));      // its TMEM slot, read for row h-2
+                    constexpr uint32_t id = tc::idesc_f16(BM, 16, true);
+                    const uint32_t a = dH2 + (h & 1) * (S::OUTROW / 16);
+#pragma unroll
+                    for (int ks = 0; ks < C / 16; ++ks)
+                        mma_bf16(tmem + S::T_L + (h & 1) * 16, a + (2 * ks * S::PLANE) / 16 + G,
+                                 dBL + (ks * 2 * 16 * 16) / 16, id, ks > 0 ? 1u : 0u);
+                    tc::mma_commit(mb + BB_LDONE + (h & 1));
+                };
+                for (int j = f_lo; j <= f_hi && !failed; ++j) {
+                    // hidden output row j+1 takes the ring slot of row j-3, drained
+                    // in pass j-2, which also put hidden row j-3 in shared memory
+                    if (j - 2 >= f_lo) {
+                        wait(BB_PASS + ((j - 2) & (S::NS - 1)));
+                        issue_last(j - 3);
+                    }
+                    wait(BB_FULL + j % S::NIN);
+                    issue_row<C, C, MODE_FUSED, W>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
+                    tc::mma_commit(mb + BB_FREE + j % S::NIN);
+                    tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
+                }
+                for (int k = f_hi - 1; k <= hlast && !failed; ++k)
+                    if (k >= f_lo) {
+                        wait(BB_PASS + (k & (S::NS - 1)));
+                        issue_last(k - 1);
+                    }
+                // the last layer's drains of the final two hidden rows
+                for (int h = r_hi - 1; h <= r_hi && !failed; ++h)
+                    if (Hv(h)) wait(BB_LPASS + (h & 1));
+            }
+            __syncwarp();
+        } else if (warp >= S::NDW) {
+            // ============ last-layer drain (warps 16-19) ============
+            // hidden row h: contributions to output rows h+1, h, h-1; output row
+            // h-1 is then complete.  X rows are loaded two rows ahead.
+            const int xb = ep % G, xx = ep / G, xmb = g * G + xb;
+            auto fetch_x = [&](int h) -> float {
+                return (Ov(h) && xmb < Nb && ep < LIVE) ? X[(long)xmb * x_ms + (long)h * m + xx] : 0.f;
+            };
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;               // output rows h-1, h, h+1
+            float xq0 = fetch_x(r_lo - 1), xq1 = fetch_x(r_lo);
+            for (int h = r_lo; h <= r_hi && !failed; ++h) {
+                const float xcur = xq0;
+                xq0 = xq1;
+                xq1 = fetch_x(h + 1);
+                wait_w(BB_LDONE + (h & 1));
+                float v[16];
+                tmem_ldn<16>(tmem + tlane + S::T_L + (h & 1) * 16, v);
+                tc::tmem_ld_wait();
+                float* e0 = ex + (h & 1) * 6 * S::NPOS;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    e0[(2 * dy) * S::NPOS + G + ep] = v[3 * dy];
+                    e0[(2 * dy + 1) * S::NPOS + G + ep] = v[3 * dy + 2];
+                }
+                tc::named_bar(1, S::NDL * 32);
+                float c3[3];
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+                    c3[dy] = v[3 * dy + 1] + e0[(2 * dy) * S::NPOS + ep] + e0[(2 * dy + 1) * S::NPOS + 2 * G + ep];
+                a0 += c3[2];
+                a1 += c3[1];
+                a2 += c3[0];
+                if (Ov(h - 1) && xmb < Nb && ep < LIVE)
+                    Xout[(long)xmb * o_ms + (long)(h - 1) * m + xx] = fmaf(rs, a0 + sbias[C], xcur);
+                a0 = a1;
+                a1 = a2;
+                a2 = 0.f;
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + BB_LPASS + (h & 1));
+            }
+            // bottom row: the hidden row below the image is zero
+            if (!failed && ye == n && xmb < Nb && ep < LIVE)
+                Xout[(long)xmb * o_ms + (long)(n - 1) * m + xx] = fmaf(rs, a0 + sbias[C], xq0);
+        } else {
+            // ============ hidden drain (warps 0-15) ============
+            const int cg = warp >> 2;
+            for (int k = f_lo; k <= hlast && !failed; ++k) {
+                if (Fv(k)) wait_w(BB_HDONE + (k & (S::NS - 1)));
+                const int h = k - 1;
+                if (Hv(h)) {
+                    // its shared-memory slot held row h-2, read by the last layer's MMAs
+                    if (h - 2 >= r_lo) wait_w(BB_LDONE + (h & 1));
+                    const uint32_t col = (uint32_t)(C * ((-h) & (S::NS - 1)));
+                    float v[CPW];
+                    tmem_ldn<CPW>(tmem + tlane + col + cg * CPW, v);
+                    tc::tmem_ld_wait();
+                    uint32_t pk[CPW / 2];
+#pragma unroll
+                    for (int i = 0; i < CPW / 2; ++i) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(tanh_approx(v[2 * i] + sbias[cg * CPW + 2 * i]),
+                                                                        tanh_approx(v[2 * i + 1] + sbias[cg * CPW + 2 * i + 1]));
+                        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+                    }
+                    unsigned char* slot = smem + S::OFF_H2 + (h & 1) * S::OUTROW;
+                    if (ep < LIVE) {                    // beyond: zero padding, never written
+#pragma unroll
+                        for (int pl = 0; pl < CPW / 8; ++pl)
+                            *reinterpret_cast<uint4*>(slot + ((size_t)(cg * CPW / 8 + pl) * S::NPOS + G + ep) * 16) =
+                                make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
+                    }
+                    tc::fence_proxy_async_smem();       // the stores -> the tensor core's reads
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
+            }
+            // the last layer's MMAs of the final two hidden rows were not waited
+            // for here; they finish before the segment's closing barrier (the
+            // issuer waits their drains first)
+            for (int h = r_hi - 1; h <= r_hi; ++h)
+                if (h >= r_lo) passed(BB_LDONE + (h & 1));
+        }
+        tc::fence_before_sync();
+        if (__syncthreads_or(failed)) { failed = true; break; }
+        tc::fence_after_sync();
+    }
+    if (warp == S::ISSUE_WARP && lane == 0) {
+        tc::mma_commit(mb + BB_FIN);
+        if (!tc::mbar_wait_bounded(mb + BB_FIN, 0u, B_WAIT)) atomicExch(err, DEV_TIMEOUT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
 // [X, B U] of every member row into the first layer's input rows (CI = 16:
 // plane 0 = [X, BU, 0 ...], plane 1 stays zero; pads stay zero).
 template <int W>
@@ -481,6 +753,28 @@ int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const float* X, long
     return 0;
 }
 
+template <int C, int W>
+int bf16_fused_layer(const __nv_bfloat16* in, const float* X, long x_ms, float* Xout, long o_ms, const void* wpk,
+                     const float* bias, const void* wlast, const float* blast, int Nb, int n, float rs, int n_sm,
+                     int* err, cudaStream_t st)
+{
+    using S = BS<C, C, MODE_FUSED, W>;
+    constexpr int G = S::G;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(conv_bf16_fused_kernel<C, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
+            cudaSuccess)
+            return 1;
+        configured = true;
+    }
+    const long tiles = (long)((Nb + G - 1) / G) * n;
+    const int grid = (int)(tiles < n_sm ? tiles : n_sm);
+    pdl_launch(conv_bf16_fused_kernel<C, W>, grid, S::NT, S::SMEM, st, in, X, x_ms, Xout, o_ms,
+               static_cast<const __nv_bfloat16*>(wpk), bias, static_cast<const __nv_bfloat16*>(wlast), blast, Nb, n,
+               rs, err);
+    return 0;
+}
+
 template <int W>
 int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                    const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st)
@@ -502,7 +796,9 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
         rc |= bf16_layer<16, 32, MODE_HIDDEN, W>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
                                                  n_sm, err, st);
     cur = bufs[0];
-    for (int k = 1; k + 1 < net.n_layers; ++k) {
+    // hidden layers 1 .. L-3; the last hidden layer (L-2) runs fused with the
+    // last layer (L-1), so its rows stay in shared memory
+    for (int k = 1; k + 2 < net.n_layers; ++k) {
         __nv_bfloat16* o = bufs[k & 1];
         if (C == 64)
             rc |= bf16_layer<64, 64, MODE_HIDDEN, W>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
@@ -514,11 +810,11 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
     }
     const int L = net.n_layers - 1;
     if (C == 64)
-        rc |= bf16_layer<64, 16, MODE_LAST, W>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
-                                               n_sm, err, st);
+        rc |= bf16_fused_layer<64, W>(cur, X, x_ms, Xout, o_ms, net.w[L - 1], net.b[L - 1], net.w[L], net.b[L], Nb, n,
+                                      rs, n_sm, err, st);
     else
-        rc |= bf16_layer<32, 16, MODE_LAST, W>(cur, nullptr, X, x_ms, Xout, o_ms, net.w[L], net.b[L], Nb, n, rs,
-                                               n_sm, err, st);
+        rc |= bf16_fused_layer<32, W>(cur, X, x_ms, Xout, o_ms, net.w[L - 1], net.b[L - 1], net.w[L], net.b[L], Nb, n,
+                                      rs, n_sm, err, st);
     return rc;
 }
 
