@@ -12,13 +12,14 @@
 // bulk copy moves a whole row into shared memory, and a horizontal stencil
 // tap is a shift of the operand start by G positions.
 //
-// One kernel per layer: conv_bf16_kernel<CI, CO, MODE, W>.
-//   MODE_HIDDEN  CO channels, tanh, BF16 rows out
-//   MODE_LAST    one output channel: the nine taps of each input row stacked
-//                along N (16 columns, unshifted row, one MMA per 16-channel
-//                step); the drain warps add the horizontal neighbours (+-G
-//                positions, through shared memory) and keep rolling sums of
-//                output rows h-1, h, h+1; X_next = X + s (out + b) in FP32
+// One kernel per hidden layer, conv_bf16_kernel<CI, CO, MODE_HIDDEN, W>
+// (CO channels, tanh, BF16 rows out), and one for the last hidden layer and
+// the last layer together, conv_bf16_fused_kernel<C, W>: the hidden rows stay
+// in shared memory, the last layer's nine taps of each row are stacked along
+// N (16 columns, unshifted row, one MMA per 16-channel step), and its drain
+// warps add the horizontal neighbours (+-G positions, through shared memory)
+// and keep rolling sums of output rows h-1, h, h+1; X_next = X + s (out + b)
+// in FP32.
 // Like the FP32 kernel, the three VERTICAL taps are stacked along N: each
 // input row j is read once per (horizontal tap, 16-channel step) and feeds
 // output rows j+1, j, j-1 (N = 3 CO) into a ring of NS = 8 TMEM slots of CO
@@ -36,7 +37,7 @@ namespace {
 
 constexpr int BM = 128;                                 // tile rows (positions)
 constexpr long long B_WAIT = 4000000000LL;
-enum { MODE_HIDDEN = 0, MODE_LAST = 1, MODE_FUSED = 2 };
+enum { MODE_HIDDEN = 0, MODE_FUSED = 2 };
 
 template <int CI, int CO, int MODE, int W>
 struct BS {
@@ -45,23 +46,22 @@ struct BS {
     static constexpr int PLANE = NPOS * 16;             // one 8-channel plane of a row
     static constexpr int INROW = (CI / 8) * PLANE;      // one input row
     static constexpr int KS = CI / 16;
-    static constexpr bool LAST = MODE == MODE_LAST, FUSED = MODE == MODE_FUSED;
-    static constexpr int NB = LAST ? 16 : 3 * CO;       // B rows: vertical taps (hidden) or
-                                                        // the nine taps, padded (last)
+    static constexpr bool FUSED = MODE == MODE_FUSED;
+    static constexpr int NB = 3 * CO;                   // B rows: vertical taps stacked
     static constexpr int BTILE = 2 * NB * 16;           // one (dx, ks) tile, 2 K chunks
-    static constexpr int BBYTES = (LAST ? 1 : 3) * KS * BTILE;
+    static constexpr int BBYTES = 3 * KS * BTILE;
     // fused hidden + last layer: the last layer's tiles (K = CO), and two
     // hidden rows in the operand layout that the last layer's MMAs read
     static constexpr int BLBYTES = FUSED ? (CO / 16) * 2 * 16 * 16 : 0;
     static constexpr int OUTROW = (CO / 8) * PLANE;
     static constexpr int H2BYTES = FUSED ? 2 * OUTROW : 0;
-    static constexpr int EXBYTES = (LAST || FUSED) ? (2 * 6 * NPOS * 4 + 15) / 16 * 16 : 0;
+    static constexpr int EXBYTES = FUSED ? (2 * 6 * NPOS * 4 + 15) / 16 * 16 : 0;
     // input rows in flight (bulk copies from HBM): as many as fit next to the
     // rest, up to 12
     static constexpr int NIN_FIT = ((FUSED ? 219 : 200) * 1024 - BBYTES - BLBYTES - H2BYTES - EXBYTES) / INROW;
     static constexpr int NIN = NIN_FIT > 12 ? 12 : NIN_FIT;
     static_assert(NIN >= 4, "input ring");
-    static constexpr int NDW = LAST ? 4 : 16;           // drain warps (hidden rows, or the last layer)
+    static constexpr int NDW = 16;                      // hidden-row drain warps
     static constexpr int NDL = FUSED ? 4 : 0;           // fused: last-layer drain warps
     static constexpr int LOAD_WARP = NDW + NDL, ISSUE_WARP = NDW + NDL + 1;
     static constexpr int NT = 32 * (NDW + NDL + 2);
@@ -76,13 +76,11 @@ struct BS {
     static_assert(SMEM <= 232448, "shared memory");
     static constexpr int NS = FUSED ? 4 : 8;            // TMEM ring slots (rows); the HDONE and PASS
                                                         // barrier arrays have NS entries
-    static constexpr int TCOL = LAST ? 16 : CO;         // TMEM columns per ring slot
-    static constexpr int T_L = NS * TCOL;               // fused: the last layer's 2 slots of 16
+    static constexpr int TCOL = CO;                     // TMEM columns per ring slot
     static constexpr int TMEM_COLS = FUSED ? 512 : NS * TCOL <= 32 ? 32 : NS * TCOL <= 64 ? 64
                                      : NS * TCOL <= 128 ? 128 : NS * TCOL <= 256 ? 256 : 512;
     static_assert(NS * TCOL + (FUSED ? 32 : 0) <= 512, "tensor memory");
     static_assert(CI % 16 == 0 && (CO == 16 || CO == 32 || CO == 64), "shapes");
-    static_assert(MODE != MODE_LAST || CO == 16, "last layer: 16 columns, channel 0 used");
 };
 
 // mbarriers (8 bytes each)
@@ -235,18 +233,18 @@ __device__ __forceinline__ void issue_row(uint32_t tmem, int j, bool init_all, u
     else issue_row_r<CI, CO, MODE, W, false>(tmem, s, a, b);
 }
 
-// in: activation rows [groups][n][CI/8][NPOS][8] BF16.  MODE_HIDDEN: out the
-// same layout with CO channels.  MODE_LAST: X_next[member][row][x] = X +
-// rs (out + bias) for member < Nb.
+// in: activation rows [groups][n][CI/8][NPOS][8] BF16; out: the same layout
+// with CO channels (MODE_HIDDEN).
 template <int CI, int CO, int MODE, int W>
 __global__ void __launch_bounds__(BS<CI, CO, MODE, W>::NT, 1)
-conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out, const float* __restrict__ X,
-                 long x_ms, float* __restrict__ Xout, long o_ms, const __nv_bfloat16* __restrict__ wpk,
-                 const float* __restrict__ bias, int Nb, int n, float rs, int* __restrict__ err)
+conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                 const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int Nb, int n,
+                 int* __restrict__ err)
 {
     pdl_begin();
     using S = BS<CI, CO, MODE, W>;
-    constexpr int G = S::G, m = W;
+    static_assert(MODE == MODE_HIDDEN, "hidden layers");
+    constexpr int G = S::G;
     constexpr int LIVE = G * W;                         // positions that hold pixels
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
@@ -257,8 +255,6 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
 
     for (int e = tid; e < S::BBYTES / 16; e += S::NT)
         reinterpret_cast<uint4*>(smem + S::OFF_B)[e] = reinterpret_cast<const uint4*>(wpk)[e];
-    for (int e = tid; e < S::EXBYTES / 16; e += S::NT)            // pads of the exchange stay zero
-        reinterpret_cast<uint4*>(smem + S::OFF_EX)[e] = make_uint4(0u, 0u, 0u, 0u);
     for (int e = tid; e < CO; e += S::NT) sbias[e] = bias[e];
     if (tid == 0) {
         for (int i = 0; i < BB_COUNT; ++i) tc::mbar_init(mb + i, (i >= BB_PASS && i < BB_PASS + S::NS) ? S::NDW : 1);
@@ -329,23 +325,13 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
             if (lane == 0) {
                 const uint32_t dIn = desc_lo(s0 + S::OFF_IN, S::PLANE);
                 const uint32_t dB = desc_lo(s0 + S::OFF_B, S::NB * 16);
-                // hidden: output row j+1 takes the ring slot of row j+1-NS, drained in
-                // pass j+2-NS.  last: input row j's taps take the slot of row j-NS,
-                // read in pass j-NS.
-                constexpr int LAG = MODE == MODE_LAST ? S::NS : S::NS - 2;
+                // output row j+1 takes the ring slot of row j+1-NS, drained in pass
+                // j+2-NS
+                constexpr int LAG = S::NS - 2;
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
                     if (j - LAG >= f_lo) wait(BB_PASS + ((j - LAG) & (S::NS - 1)));
                     wait(BB_FULL + j % S::NIN);
-                    const uint32_t a = dIn + (j % S::NIN) * (S::INROW / 16);
-                    if constexpr (MODE == MODE_LAST) {
-                        constexpr uint32_t id = tc::idesc_f16(BM, 16, true);
-#pragma unroll
-                        for (int ks = 0; ks < S::KS; ++ks)
-                            mma_bf16(tmem + (j & (S::NS - 1)) * S::TCOL, a + (2 * ks * S::PLANE) / 16 + G,
-                                     dB + (ks * S::BTILE) / 16, id, ks > 0 ? 1u : 0u);
-                    } else {
-                        issue_row<CI, CO, MODE, W>(tmem, j, j == f_lo, a, dB);
-                    }
+                    issue_row<CI, CO, MODE, W>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
                     tc::mma_commit(mb + BB_FREE + j % S::NIN);
                     tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
                 }
@@ -357,89 +343,36 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
         } else {
             // ============ drain: pass k finishes output row k-1 ============
             const int last_pass = ye < n ? ye : n;              // = f_hi + 1 at the image bottom
-            // last layer: X of the output row of the next pass, loaded one pass ahead
-            const int xb = ep % G, xx = ep / G, xmb = g * G + xb;
-            auto fetch_x = [&](int h) -> float {
-                return (MODE == MODE_LAST && h >= ys && h < ye && xmb < Nb && ep < LIVE)
-                           ? X[(long)xmb * x_ms + (long)h * m + xx]
-                           : 0.f;
-            };
-            if constexpr (MODE == MODE_LAST) {
-                // pass k: the taps of input row k -> contributions to output rows
-                // k+1, k, k-1; output row k-1 is then complete.  X rows are loaded
-                // two passes ahead.
-                float* ex = reinterpret_cast<float*>(smem + S::OFF_EX);
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f;               // output rows k-1, k, k+1
-                float xq0 = fetch_x(f_lo - 1), xq1 = fetch_x(f_lo);
-                for (int k = f_lo; k <= last_pass && !failed; ++k) {
-                    const float xcur = xq0;
-                    xq0 = xq1;
-                    xq1 = fetch_x(k + 1);
-                    if (Fv(k)) {
-                        wait_w(BB_HDONE + (k & (S::NS - 1)));
-                        float v[16];
-                        tmem_ldn<16>(tmem + tlane + (k & (S::NS - 1)) * S::TCOL, v);
-                        tc::tmem_ld_wait();
-                        // tap t = 3 dy + dx; output pixel x takes tap dx from input pixel
-                        // x + dx - 1, i.e. position ep + (dx - 1) G
-                        float* e0 = ex + (k & 1) * 6 * S::NPOS;
+            // every pass waits the MMAs of its input row, so a pass with none
+            // (the image bottom) follows the previous pass's wait
+            for (int k = f_lo; k <= last_pass && !failed; ++k) {
+                if (Fv(k)) wait_w(BB_HDONE + (k & (S::NS - 1)));
+                const int h = k - 1;
+                if (Ov(h)) {
+                    const uint32_t col = (uint32_t)(CO * ((-h) & (S::NS - 1)));
+                    constexpr int CPW = CO / 4;             // channels per warp
+                    float v[CPW];
+                    tmem_ldn<CPW>(tmem + tlane + col + cg * CPW, v);
+                    tc::tmem_ld_wait();
+                    uint32_t pk[CPW / 2];
 #pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            e0[(2 * dy) * S::NPOS + G + ep] = v[3 * dy];
-                            e0[(2 * dy + 1) * S::NPOS + G + ep] = v[3 * dy + 2];
-                        }
-                        tc::named_bar(1, S::NDW * 32);
-                        float c3[3];
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy)
-                            c3[dy] = v[3 * dy + 1] + e0[(2 * dy) * S::NPOS + ep] +
-                                     e0[(2 * dy + 1) * S::NPOS + 2 * G + ep];
-                        a0 += c3[2];
-                        a1 += c3[1];
-                        a2 += c3[0];
+                    for (int i = 0; i < CPW / 2; ++i) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(
+                            tanh_approx(v[2 * i] + sbias[cg * CPW + 2 * i]),
+                            tanh_approx(v[2 * i + 1] + sbias[cg * CPW + 2 * i + 1]));
+                        pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
                     }
-                    const int h = k - 1;
-                    if (Ov(h) && xmb < Nb && ep < LIVE)
-                        Xout[(long)xmb * o_ms + (long)h * m + xx] = fmaf(rs, a0 + sbias[0], xcur);
-                    a0 = a1;
-                    a1 = a2;
-                    a2 = 0.f;
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
-                }
-            } else {
-                // every pass waits the MMAs of its input row, so a pass with none
-                // (the image bottom) follows the previous pass's wait
-                for (int k = f_lo; k <= last_pass && !failed; ++k) {
-                    if (Fv(k)) wait_w(BB_HDONE + (k & (S::NS - 1)));
-                    const int h = k - 1;
-                    if (Ov(h)) {
-                        const uint32_t col = (uint32_t)(CO * ((-h) & (S::NS - 1)));
-                        constexpr int CPW = CO / 4;             // channels per warp
-                        float v[CPW];
-                        tmem_ldn<CPW>(tmem + tlane + col + cg * CPW, v);
-                        tc::tmem_ld_wait();
-                        uint32_t pk[CPW / 2];
+                    __nv_bfloat16* orow = out + ((size_t)g * n + h) * (CO / 8) * S::NPOS * 8;
+                    if (ep < LIVE) {                // beyond: zero padding, never written
 #pragma unroll
-                        for (int i = 0; i < CPW / 2; ++i) {
-                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(
-                                tanh_approx(v[2 * i] + sbias[cg * CPW + 2 * i]),
-                                tanh_approx(v[2 * i + 1] + sbias[cg * CPW + 2 * i + 1]));
-                            pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
-                        }
-                        __nv_bfloat16* orow = out + ((size_t)g * n + h) * (CO / 8) * S::NPOS * 8;
-                        if (ep < LIVE) {                // beyond: zero padding, never written
-#pragma unroll
-                            for (int pl = 0; pl < CPW / 8; ++pl)
-                                *reinterpret_cast<uint4*>(orow + ((size_t)(cg * CPW / 8 + pl) * S::NPOS + G + ep) * 8) =
-                                    make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
-                        }
+                        for (int pl = 0; pl < CPW / 8; ++pl)
+                            *reinterpret_cast<uint4*>(orow + ((size_t)(cg * CPW / 8 + pl) * S::NPOS + G + ep) * 8) =
+                                make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
                     }
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
                 }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + BB_PASS + (k & (S::NS - 1)));
             }
         }
         tc::fence_before_sync();
@@ -482,6 +415,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
     constexpr int G = S::G, m = W;
     constexpr int LIVE = G * W;
     constexpr int CPW = C / 4;                          // hidden drain: channels per warp
+    constexpr int T_L = S::NS * S::TCOL;                // the last layer's 2 TMEM slots of 16 columns
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S::OFF_MISC);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + S::OFF_MISC + BB_COUNT * 8);
@@ -583,7 +517,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
                     const uint32_t a = dH2 + (h & 1) * (S::OUTROW / 16);
 #pragma unroll
                     for (int ks = 0; ks < C / 16; ++ks)
-                        mma_bf16(tmem + S::T_L + (h & 1) * 16, a + (2 * ks * S::PLANE) / 16 + G,
+                        mma_bf16(tmem + T_L + (h & 1) * 16, a + (2 * ks * S::PLANE) / 16 + G,
                                  dBL + (ks * 2 * 16 * 16) / 16, id, ks > 0 ? 1u : 0u);
                     tc::mma_commit(mb + BB_LDONE + (h & 1));
                 };
@@ -625,7 +559,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
                 xq1 = fetch_x(h + 1);
                 wait_w(BB_LDONE + (h & 1));
                 float v[16];
-                tmem_ldn<16>(tmem + tlane + S::T_L + (h & 1) * 16, v);
+                tmem_ldn<16>(tmem + tlane + T_L + (h & 1) * 16, v);
                 tc::tmem_ld_wait();
                 float* e0 = ex + (h & 1) * 6 * S::NPOS;
 #pragma unroll
@@ -734,8 +668,8 @@ __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const 
 }
 
 template <int CI, int CO, int MODE, int W>
-int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const float* X, long x_ms, float* Xout, long o_ms,
-               const void* wpk, const float* bias, int Nb, int n, float rs, int n_sm, int* err, cudaStream_t st)
+int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const void* wpk, const float* bias, int Nb, int n,
+               int n_sm, int* err, cudaStream_t st)
 {
     using S = BS<CI, CO, MODE, W>;
     constexpr int G = S::G;
@@ -749,7 +683,7 @@ int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const float* X, long
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
     pdl_launch(conv_bf16_kernel<CI, CO, MODE, W>, grid, S::NT, S::SMEM, st, 
-        in, out, X, x_ms, Xout, o_ms, static_cast<const __nv_bfloat16*>(wpk), bias, Nb, n, rs, err);
+        in, out, static_cast<const __nv_bfloat16*>(wpk), bias, Nb, n, err);
     return 0;
 }
 
@@ -790,22 +724,18 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
     int rc = 0;
     // first layer (input channels padded to 16)
     if (C == 64)
-        rc |= bf16_layer<16, 64, MODE_HIDDEN, W>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
-                                                 n_sm, err, st);
+        rc |= bf16_layer<16, 64, MODE_HIDDEN, W>(cur, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
     else
-        rc |= bf16_layer<16, 32, MODE_HIDDEN, W>(cur, bufs[0], nullptr, 0, nullptr, 0, net.w[0], net.b[0], Nb, n, rs,
-                                                 n_sm, err, st);
+        rc |= bf16_layer<16, 32, MODE_HIDDEN, W>(cur, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
     cur = bufs[0];
     // hidden layers 1 .. L-3; the last hidden layer (L-2) runs fused with the
     // last layer (L-1), so its rows stay in shared memory
     for (int k = 1; k + 2 < net.n_layers; ++k) {
         __nv_bfloat16* o = bufs[k & 1];
         if (C == 64)
-            rc |= bf16_layer<64, 64, MODE_HIDDEN, W>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
-                                                     n_sm, err, st);
+            rc |= bf16_layer<64, 64, MODE_HIDDEN, W>(cur, o, net.w[k], net.b[k], Nb, n, n_sm, err, st);
         else
-            rc |= bf16_layer<32, 32, MODE_HIDDEN, W>(cur, o, nullptr, 0, nullptr, 0, net.w[k], net.b[k], Nb, n, rs,
-                                                     n_sm, err, st);
+            rc |= bf16_layer<32, 32, MODE_HIDDEN, W>(cur, o, net.w[k], net.b[k], Nb, n, n_sm, err, st);
         cur = o;
     }
     const int L = net.n_layers - 1;
