@@ -452,3 +452,35 @@ def test_narrow_control_reduce_reports_rank_deficient_transform(cuda_ok):
     with pytest.raises(oic.OICError) as e:
         oic.oic_control_reduce(dev(np.ones((3, 4))), dev(T), u)
     assert e.value.status == oic.OIC_ENOTSPD
+
+
+# ------------------------------------------------------------ edge cases
+EDGE = {
+    # the smallest ensemble (N = 2: the pooled sample covariance has (N-1) m = 16
+    # samples for p = 5 rows), one assimilation, one control row
+    "min_ensemble": W.Workload("edge_N2_H1", n=4, m=16, l=1, channels=[2, 32, 32, 1], N=2, H=1, S=2,
+                               ref="blobs", blob_sigma=1.5),
+    # the largest observation stack the FP32 path takes (p = n + l = 144)
+    "max_p": W.Workload("edge_p144", n=128, m=16, l=16, channels=[2, 32, 32, 1], N=24, H=2, S=2, ref="blobs",
+                        blob_sigma=8.0),
+    # the widest grid (m = 128: one member per 128-position tile)
+    "max_m": W.Workload("edge_m128", n=12, m=128, l=4, channels=[2, 32, 32, 1], N=6, H=2, S=2, ref="blobs",
+                        blob_sigma=6.0),
+}
+
+
+@pytest.mark.parametrize("name", list(EDGE))
+@pytest.mark.parametrize("full", [False, True])
+def test_edge_case_solve_matches_oracle(cuda_ok, name, full):
+    wl = EDGE[name]
+    s = solver(wl, keep_full_history=full)
+    Up = (0.01 * np.random.default_rng(9).standard_normal((wl.l, wl.m))).astype(np.float32)
+    xr, ur, nz = wl.X_ref_window(1), wl.U_ref(), wl.noise(1)
+    U_hat = np.zeros((wl.H + 1, wl.l, wl.m), np.float32)
+    X_hat = np.zeros((wl.H + 1, wl.n, wl.m), np.float32) if full else None
+    s.oic_solve_host(wl.X0(), Up, xr, ur, nz, U_hat, X_hat)
+    xh = oracle.enks_solve(onet(wl), wl.N, wl.H, wl.X0(), Up, xr, ur, nz)
+    assert rel(U_hat, xh[:, wl.n:wl.n + wl.l]) <= TOL
+    if full:
+        assert rel(X_hat, xh[:, :wl.n]) <= TOL
+    s.close()
