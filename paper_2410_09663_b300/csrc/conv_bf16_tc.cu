@@ -162,10 +162,9 @@ __device__ __forceinline__ void piece(uint32_t tmem, uint32_t a, uint32_t b, uin
 // 1, 2 = output rows j+1, j, j-1 in slots SR, SR+1, SR+2 mod NS; the window
 // is split where it wraps).  The first MMA starts output row j+1 (accumulate
 // 0 on its block); INIT_ALL starts all.
-template <int CI, int CO, int MODE, int W, int SR, bool INIT_ALL>
+template <class S, int CO, int SR, bool INIT_ALL>
 __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t b)
 {
-    using S = BS<CI, CO, MODE, W>;
     constexpr int NS = S::NS;
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
@@ -200,37 +199,38 @@ __device__ __forceinline__ void issue_row_s(uint32_t tmem, uint32_t a, uint32_t 
     }
 }
 
-template <int CI, int CO, int MODE, int W, bool INIT_ALL>
+// S: ring geometry (NS, KS, PLANE, G, BTILE) of the layer being issued.
+template <class S, int CO, bool INIT_ALL>
 __device__ __forceinline__ void issue_row_r(uint32_t tmem, int s, uint32_t a, uint32_t b)
 {
-    static_assert(BS<CI, CO, MODE, W>::NS == 8 || BS<CI, CO, MODE, W>::NS == 4, "ring dispatch");
-    if constexpr (BS<CI, CO, MODE, W>::NS == 4) {
+    static_assert(S::NS == 8 || S::NS == 4, "ring dispatch");
+    if constexpr (S::NS == 4) {
         switch (s) {
-        case 0: issue_row_s<CI, CO, MODE, W, 0, INIT_ALL>(tmem, a, b); break;
-        case 1: issue_row_s<CI, CO, MODE, W, 1, INIT_ALL>(tmem, a, b); break;
-        case 2: issue_row_s<CI, CO, MODE, W, 2, INIT_ALL>(tmem, a, b); break;
-        default: issue_row_s<CI, CO, MODE, W, 3, INIT_ALL>(tmem, a, b); break;
+        case 0: issue_row_s<S, CO, 0, INIT_ALL>(tmem, a, b); break;
+        case 1: issue_row_s<S, CO, 1, INIT_ALL>(tmem, a, b); break;
+        case 2: issue_row_s<S, CO, 2, INIT_ALL>(tmem, a, b); break;
+        default: issue_row_s<S, CO, 3, INIT_ALL>(tmem, a, b); break;
         }
-        return;
-    }
-    switch (s) {
-    case 0: issue_row_s<CI, CO, MODE, W, 0, INIT_ALL>(tmem, a, b); break;
-    case 1: issue_row_s<CI, CO, MODE, W, 1, INIT_ALL>(tmem, a, b); break;
-    case 2: issue_row_s<CI, CO, MODE, W, 2, INIT_ALL>(tmem, a, b); break;
-    case 3: issue_row_s<CI, CO, MODE, W, 3, INIT_ALL>(tmem, a, b); break;
-    case 4: issue_row_s<CI, CO, MODE, W, 4, INIT_ALL>(tmem, a, b); break;
-    case 5: issue_row_s<CI, CO, MODE, W, 5, INIT_ALL>(tmem, a, b); break;
-    case 6: issue_row_s<CI, CO, MODE, W, 6, INIT_ALL>(tmem, a, b); break;
-    default: issue_row_s<CI, CO, MODE, W, 7, INIT_ALL>(tmem, a, b); break;
+    } else {
+        switch (s) {
+        case 0: issue_row_s<S, CO, 0, INIT_ALL>(tmem, a, b); break;
+        case 1: issue_row_s<S, CO, 1, INIT_ALL>(tmem, a, b); break;
+        case 2: issue_row_s<S, CO, 2, INIT_ALL>(tmem, a, b); break;
+        case 3: issue_row_s<S, CO, 3, INIT_ALL>(tmem, a, b); break;
+        case 4: issue_row_s<S, CO, 4, INIT_ALL>(tmem, a, b); break;
+        case 5: issue_row_s<S, CO, 5, INIT_ALL>(tmem, a, b); break;
+        case 6: issue_row_s<S, CO, 6, INIT_ALL>(tmem, a, b); break;
+        default: issue_row_s<S, CO, 7, INIT_ALL>(tmem, a, b); break;
+        }
     }
 }
 
-template <int CI, int CO, int MODE, int W>
+template <class S, int CO>
 __device__ __forceinline__ void issue_row(uint32_t tmem, int j, bool init_all, uint32_t a, uint32_t b)
 {
-    const int s = (-j - 1) & (BS<CI, CO, MODE, W>::NS - 1);
-    if (init_all) issue_row_r<CI, CO, MODE, W, true>(tmem, s, a, b);
-    else issue_row_r<CI, CO, MODE, W, false>(tmem, s, a, b);
+    const int s = (-j - 1) & (S::NS - 1);
+    if (init_all) issue_row_r<S, CO, true>(tmem, s, a, b);
+    else issue_row_r<S, CO, false>(tmem, s, a, b);
 }
 
 // in: activation rows [groups][n][CI/8][NPOS][8] BF16; out: the same layout
@@ -331,7 +331,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
                     if (j - LAG >= f_lo) wait(BB_PASS + ((j - LAG) & (S::NS - 1)));
                     wait(BB_FULL + j % S::NIN);
-                    issue_row<CI, CO, MODE, W>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
+                    issue_row<S, CO>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
                     tc::mma_commit(mb + BB_FREE + j % S::NIN);
                     tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
                 }
@@ -529,7 +529,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
                         issue_last(j - 3);
                     }
                     wait(BB_FULL + j % S::NIN);
-                    issue_row<C, C, MODE_FUSED, W>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
+                    issue_row<S, C>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
                     tc::mma_commit(mb + BB_FREE + j % S::NIN);
                     tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
                 }
@@ -639,6 +639,273 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
     if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
+// The first layer ([X, B U] -> C, tanh) fused with the second (C -> C, tanh):
+// the first layer's input rows are built in shared memory from X and U, and
+// its output rows never leave shared memory.  Warps 0-15 drain, warps 16-19
+// build input rows, one thread issues both layers' MMAs.  A segment owns the
+// second layer's output rows [ys, ye) of one member group; they need its
+// input rows (the first layer's outputs) [r_lo, r_hi] = [ys-1, ye] and those
+// need first-layer input rows [f_lo, f_hi] one further on each side (within
+// the image).
+//
+// Drain pass k: (A) first-layer output row k-1 -> shared slot (k-1) mod 2 once
+// the first layer's MMAs of input row k are done; (B) second-layer output row
+// k-3 -> HBM once the second layer's MMAs of its input row k-2 are done.  The
+// issuer waits pass k before the second layer's MMAs of row k-1 (the slot
+// they read was filled in pass k) and, for both TMEM rings, before reusing the
+// slot drained in pass k.  One drain group runs the passes in order, so a
+// pass barrier also covers every earlier pass, and the second layer's wait in
+// pass k+1 covers reuse of shared slot (k-1) mod 2 in pass k+2.
+enum : int {
+    FB_A0FULL = 0,     // [4] first-layer input row f built (f mod 4), 4 producer warps
+    FB_A0FREE = 4,     // [4] first-layer MMAs of input row f done (f mod 4)
+    FB_HDA = 8,        // [2] first-layer MMAs of input row f done (f mod 2), for the drain
+    FB_L1 = 10,        // [2] second-layer MMAs of input row j done (j mod 2)
+    FB_PASS = 12,      // [4] drain pass k done (k mod 4), 16 drain warps
+    FB_FIN = 16,
+    FB_COUNT = 17
+};
+
+// ring geometry of one layer issued by issue_row: NS TMEM slots of CO columns
+template <int CI, int CO, int W, int NS_>
+struct RingGeom {
+    static constexpr int G = BM / W, NPOS = BM + 2 * G, PLANE = NPOS * 16, KS = CI / 16, NS = NS_;
+    static constexpr int NB = 3 * CO, BTILE = 2 * NB * 16, BBYTES = 3 * KS * BTILE;
+};
+
+template <int C, int W>
+struct FBS {
+    using S0 = RingGeom<16, C, W, 4>;                   // first layer (ring of 4)
+    using S1 = RingGeom<C, C, W, 4>;                    // second layer (ring of 4)
+    static constexpr int G = S1::G, NPOS = S1::NPOS, PLANE = S1::PLANE;
+    static constexpr int IN0 = 2 * PLANE;               // one first-layer input row (16 channels)
+    static constexpr int IN1 = (C / 8) * PLANE;         // one second-layer input row
+    static constexpr int NA0 = 4, NA1 = 2;
+    static constexpr int OFF_A0 = 0;
+    static constexpr int OFF_W0 = OFF_A0 + NA0 * IN0;
+    static constexpr int OFF_A1 = OFF_W0 + S0::BBYTES;
+    static constexpr int OFF_W1 = OFF_A1 + NA1 * IN1;
+    static constexpr int OFF_BIAS = OFF_W1 + S1::BBYTES;    // b0[C], b1[C]
+    static constexpr int OFF_MISC = OFF_BIAS + 2 * C * 4;
+    static constexpr int OFF_DYN = OFF_MISC + 256;          // U of the group [G][m][l], then B [n][l]
+    static constexpr int NDW = 16, NPW = 4;
+    static constexpr int PROD_WARP0 = NDW, ISSUE_WARP = NDW + NPW;
+    static constexpr int NT = 32 * (ISSUE_WARP + 1);
+    static constexpr int T_B = 4 * C;                   // ring B after ring A
+    static_assert(8 * C <= 512, "tensor memory");
+    static_assert(FB_COUNT * 8 + 4 <= 256, "barrier region");
+};
+
+template <int C, int W>
+__global__ void __launch_bounds__(FBS<C, W>::NT, 1)
+conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
+                       const float* __restrict__ Bmat, int l, const __nv_bfloat16* __restrict__ w0,
+                       const float* __restrict__ b0, const __nv_bfloat16* __restrict__ w1,
+                       const float* __restrict__ b1, __nv_bfloat16* __restrict__ out, int Nb, int n,
+                       int* __restrict__ err)
+{
+    pdl_begin();
+    using F = FBS<C, W>;
+    using S0 = typename F::S0;
+    using S1 = typename F::S1;
+    constexpr int G = F::G, m = W;
+    constexpr int LIVE = G * W;
+    constexpr int CPW = C / 4;                          // drain: channels per warp
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smem + F::OFF_MISC);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + F::OFF_MISC + FB_COUNT * 8);
+    float* sbias = reinterpret_cast<float*>(smem + F::OFF_BIAS);
+    float* su = reinterpret_cast<float*>(smem + F::OFF_DYN);                 // [G][m][l]
+    float* sB = su + G * l * m;                                             // [n][l]
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const uint32_t s0 = tc::smem_u32(smem);
+
+    for (int e = tid; e < S0::BBYTES / 16; e += F::NT)
+        reinterpret_cast<uint4*>(smem + F::OFF_W0)[e] = reinterpret_cast<const uint4*>(w0)[e];
+    for (int e = tid; e < S1::BBYTES / 16; e += F::NT)
+        reinterpret_cast<uint4*>(smem + F::OFF_W1)[e] = reinterpret_cast<const uint4*>(w1)[e];
+    // input and hand-off rows: pads (and the second 8-channel plane of the
+    // first layer's input rows) stay zero
+    for (int e = tid; e < (F::OFF_W0 - F::OFF_A0) / 16; e += F::NT)
+        reinterpret_cast<uint4*>(smem + F::OFF_A0)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < (F::OFF_W1 - F::OFF_A1) / 16; e += F::NT)
+        reinterpret_cast<uint4*>(smem + F::OFF_A1)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < C; e += F::NT) { sbias[e] = b0[e]; sbias[C + e] = b1[e]; }
+    for (int e = tid; e < n * l; e += F::NT) sB[e] = Bmat[e];
+    if (tid == 0) {
+        for (int i = 0; i < FB_COUNT; ++i) {
+            const int cnt = (i >= FB_A0FULL && i < FB_A0FULL + 4) ? F::NPW : (i >= FB_PASS && i < FB_PASS + 4) ? F::NDW : 1;
+            tc::mbar_init(mb + i, cnt);
+        }
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_holder, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+
+    const int groups = (Nb + G - 1) / G;
+    const long total = (long)groups * n;
+    const long t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+    uint32_t ph = 0;
+    bool failed = false;
+    auto wait = [&](int i) {
+        if (!tc::mbar_wait_bounded(mb + i, (ph >> i) & 1u, B_WAIT)) {
+            failed = true;
+            atomicExch(err, DEV_TIMEOUT);
+        }
+        ph ^= 1u << i;
+        tc::fence_after_sync();
+    };
+    auto wait_w = [&](int i) {
+        wait(i);
+        failed = __any_sync(0xffffffffu, failed);
+    };
+
+    for (long t = t0; t < t1;) {
+        const int g = (int)(t / n);
+        const int ys = (int)(t % n);
+        const long rem = t1 - t;
+        const int ye = (long)(n - ys) < rem ? n : (int)(ys + rem);
+        t += ye - ys;
+        const int r_lo = ys > 0 ? ys - 1 : 0, r_hi = ye < n ? ye : n - 1;            // second layer's inputs
+        const int f_lo = r_lo > 0 ? r_lo - 1 : 0, f_hi = r_hi < n - 1 ? r_hi + 1 : n - 1;   // first layer's inputs
+        const int last = (ye < n ? ye : n) + 2;         // pass k drains second-layer output row k-3
+        auto Fv = [&](int f) { return f >= f_lo && f <= f_hi; };
+        auto Rv = [&](int r) { return r >= r_lo && r <= r_hi; };
+        auto Ov = [&](int h) { return h >= ys && h < ye; };
+
+        if (warp == F::ISSUE_WARP) {
+            if (lane == 0) {
+                const uint32_t dA0 = desc_lo(s0 + F::OFF_A0, F::PLANE);
+                const uint32_t dW0 = desc_lo(s0 + F::OFF_W0, S0::NB * 16);
+                const uint32_t dA1 = desc_lo(s0 + F::OFF_A1, F::PLANE);
+                const uint32_t dW1 = desc_lo(s0 + F::OFF_W1, S1::NB * 16);
+                // second layer of input row j (in shared slot j mod 2, filled in pass j+1)
+                auto issue_second = [&](int j) {
+                    if (!Rv(j) || failed) return;
+                    issue_row<S1, C>(tmem + F::T_B, j, j == r_lo, dA1 + (j & 1) * (F::IN1 / 16), dW1);
+                    tc::mma_commit(mb + FB_L1 + (j & 1));
+                };
+                for (int f = f_lo; f <= f_hi && !failed; ++f) {
+                    // pass f-2 drained first-layer output row f-3 (its ring A slot is
+                    // the one row f+1 starts in) and second-layer output row f-5
+                    if (f - 2 >= f_lo) {
+                        wait(FB_PASS + ((f - 2) & 3));
+                        issue_second(f - 3);
+                    }
+                    wait(FB_A0FULL + (f & 3));
+                    issue_row<S0, C>(tmem, f, f == f_lo, dA0 + (f & 3) * (F::IN0 / 16), dW0);
+                    tc::mma_commit(mb + FB_A0FREE + (f & 3));
+                    tc::mma_commit(mb + FB_HDA + (f & 1));
+                }
+                for (int k = f_hi - 1; k <= last && !failed; ++k)
+                    if (k >= f_lo) {
+                        wait(FB_PASS + (k & 3));
+                        issue_second(k - 1);
+                    }
+            }
+            __syncwarp();
+        } else if (warp >= F::PROD_WARP0) {
+            // ============ first-layer input rows: [X, B U] at each position ============
+            const int pt = tid - 32 * F::PROD_WARP0;            // position G + pt
+            for (int e = pt; e < G * l * m; e += 32 * F::NPW) {
+                const int b = e / (l * m), rr = e % (l * m), c = rr / m, xx = rr % m;
+                const int mbr = g * G + b;
+                su[(b * m + xx) * l + c] = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
+            }
+            tc::named_bar(2, 32 * F::NPW);
+            const int pb = pt % G, px = pt / G, pmb = g * G + pb;
+            const bool live = pt < LIVE && pmb < Nb;
+            for (int f = f_lo; f <= f_hi && !failed; ++f) {
+                if (f - 4 >= f_lo) wait_w(FB_A0FREE + (f & 3));      // MMAs of row f-4 done
+                float xv = 0.f, bu = 0.f;
+                if (live) {
+                    xv = X[(long)pmb * x_ms + (long)f * m + px];
+                    const float* ub = su + (pb * m + px) * l;
+                    const float* bb = sB + f * l;
+                    for (int c = 0; c < l; ++c) bu = fmaf(bb[c], ub[c], bu);
+                }
+                const __nv_bfloat162 v = __floats2bfloat162_rn(xv, bu);
+                *reinterpret_cast<uint4*>(smem + F::OFF_A0 + (f & 3) * F::IN0 + (G + pt) * 16) =
+                    make_uint4(*reinterpret_cast<const uint32_t*>(&v), 0u, 0u, 0u);
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + FB_A0FULL + (f & 3));
+            }
+            // the first layer's MMAs of the last rows (their slots' phases), so the
+            // next segment starts with every slot free
+            for (int f = f_hi - 3; f <= f_hi && !failed; ++f)
+                if (f >= f_lo) wait_w(FB_A0FREE + (f & 3));
+        } else {
+            // ============ drains (warps 0-15) ============
+            const int q4 = warp & 3, cg = warp >> 2;
+            const int ep = 32 * q4 + lane;
+            const uint32_t tlane = (uint32_t)(32 * q4) << 16;
+            auto act = [&](uint32_t col, const float* bias, uint32_t (&pk)[CPW / 2]) {
+                float v[CPW];
+                tmem_ldn<CPW>(tmem + tlane + col + cg * CPW, v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < CPW / 2; ++i) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(tanh_approx(v[2 * i] + bias[cg * CPW + 2 * i]),
+                                                                    tanh_approx(v[2 * i + 1] + bias[cg * CPW + 2 * i + 1]));
+                    pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+                }
+            };
+            for (int k = f_lo; k <= last && !failed; ++k) {
+                // (A) first-layer output row k-1 -> shared slot (k-1) mod 2
+                if (Fv(k)) wait_w(FB_HDA + (k & 1));
+                const int r = k - 1;
+                if (Rv(r)) {
+                    uint32_t pk[CPW / 2];
+                    act((uint32_t)(C * ((-r) & 3)), sbias, pk);
+                    unsigned char* slot = smem + F::OFF_A1 + (r & 1) * F::IN1;
+                    if (ep < LIVE) {
+#pragma unroll
+                        for (int pl = 0; pl < CPW / 8; ++pl)
+                            *reinterpret_cast<uint4*>(slot + ((size_t)(cg * CPW / 8 + pl) * F::NPOS + G + ep) * 16) =
+                                make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
+                    }
+                    tc::fence_proxy_async_smem();
+                }
+                // (B) second-layer output row k-3 -> HBM
+                if (Rv(k - 2)) wait_w(FB_L1 + ((k - 2) & 1));
+                const int h = k - 3;
+                if (Ov(h)) {
+                    uint32_t pk[CPW / 2];
+                    act((uint32_t)(F::T_B + C * ((-h) & 3)), sbias + C, pk);
+                    __nv_bfloat16* orow = out + ((size_t)g * n + h) * (C / 8) * F::NPOS * 8;
+                    if (ep < LIVE) {
+#pragma unroll
+                        for (int pl = 0; pl < CPW / 8; ++pl)
+                            *reinterpret_cast<uint4*>(orow + ((size_t)(cg * CPW / 8 + pl) * F::NPOS + G + ep) * 8) =
+                                make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
+                    }
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + FB_PASS + (k & 3));
+            }
+        }
+        tc::fence_before_sync();
+        if (__syncthreads_or(failed)) { failed = true; break; }
+        tc::fence_after_sync();
+    }
+    if (warp == F::ISSUE_WARP && lane == 0) {
+        tc::mma_commit(mb + FB_FIN);
+        if (!tc::mbar_wait_bounded(mb + FB_FIN, 0u, B_WAIT)) atomicExch(err, DEV_TIMEOUT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 // [X, B U] of every member row into the first layer's input rows (CI = 16:
 // plane 0 = [X, BU, 0 ...], plane 1 stays zero; pads stay zero).
 template <int W>
@@ -688,6 +955,25 @@ int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const void* wpk, con
 }
 
 template <int C, int W>
+int bf16_first_layers(const float* X, long x_ms, const float* U, long u_ms, const float* Bmat, int l, const void* w0,
+                      const float* b0, const void* w1, const float* b1, __nv_bfloat16* out, int Nb, int n, int n_sm,
+                      int* err, cudaStream_t st)
+{
+    using F = FBS<C, W>;
+    constexpr int G = F::G;
+    const size_t smem = (size_t)F::OFF_DYN + sizeof(float) * ((size_t)G * l * W + (size_t)n * l);
+    if (smem > 232448) return 1;
+    if (cudaFuncSetAttribute(conv_bf16_first_kernel<C, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 1;
+    const long tiles = (long)((Nb + G - 1) / G) * n;
+    const int grid = (int)(tiles < n_sm ? tiles : n_sm);
+    pdl_launch(conv_bf16_first_kernel<C, W>, grid, F::NT, smem, st, X, x_ms, U, u_ms, Bmat, l,
+               static_cast<const __nv_bfloat16*>(w0), b0, static_cast<const __nv_bfloat16*>(w1), b1, out, Nb, n, err);
+    return 0;
+}
+
+template <int C, int W>
 int bf16_fused_layer(const __nv_bfloat16* in, const float* X, long x_ms, float* Xout, long o_ms, const void* wpk,
                      const float* bias, const void* wlast, const float* blast, int Nb, int n, float rs, int n_sm,
                      int* err, cudaStream_t st)
@@ -713,29 +999,39 @@ template <int W>
 int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                    const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st)
 {
-    constexpr int G = BM / W;
-    const int groups = (Nb + G - 1) / G;
-    const long total = (long)groups * n * BM;
-    pdl_launch(bf16_input_kernel<W>, (unsigned)((total + 255) / 256), 256, 0, st, X, x_ms, U, u_ms, Bmat, Nb, n, l,
-                                                                         static_cast<__nv_bfloat16*>(net.act_in));
     const int C = net.C;
-    const __nv_bfloat16* cur = static_cast<const __nv_bfloat16*>(net.act_in);
     __nv_bfloat16* bufs[2] = {static_cast<__nv_bfloat16*>(net.act[0]), static_cast<__nv_bfloat16*>(net.act[1])};
-    int rc = 0;
-    // first layer (input channels padded to 16)
-    if (C == 64)
-        rc |= bf16_layer<16, 64, MODE_HIDDEN, W>(cur, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
-    else
-        rc |= bf16_layer<16, 32, MODE_HIDDEN, W>(cur, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
-    cur = bufs[0];
-    // hidden layers 1 .. L-3; the last hidden layer (L-2) runs fused with the
-    // last layer (L-1), so its rows stay in shared memory
-    for (int k = 1; k + 2 < net.n_layers; ++k) {
-        __nv_bfloat16* o = bufs[k & 1];
+    const __nv_bfloat16* cur = nullptr;
+    int rc = 0, k0;
+    if (net.n_layers >= 4) {
+        // layers 0 and 1 fused: the first layer's input and output rows stay on chip
         if (C == 64)
-            rc |= bf16_layer<64, 64, MODE_HIDDEN, W>(cur, o, net.w[k], net.b[k], Nb, n, n_sm, err, st);
+            rc |= bf16_first_layers<64, W>(X, x_ms, U, u_ms, Bmat, l, net.w[0], net.b[0], net.w[1], net.b[1], bufs[1],
+                                           Nb, n, n_sm, err, st);
         else
-            rc |= bf16_layer<32, 32, MODE_HIDDEN, W>(cur, o, net.w[k], net.b[k], Nb, n, n_sm, err, st);
+            rc |= bf16_first_layers<32, W>(X, x_ms, U, u_ms, Bmat, l, net.w[0], net.b[0], net.w[1], net.b[1], bufs[1],
+                                           Nb, n, n_sm, err, st);
+        cur = bufs[1];
+        k0 = 2;
+    } else {
+        constexpr int G = BM / W;
+        const int groups = (Nb + G - 1) / G;
+        const long total = (long)groups * n * BM;
+        pdl_launch(bf16_input_kernel<W>, (unsigned)((total + 255) / 256), 256, 0, st, X, x_ms, U, u_ms, Bmat, Nb, n,
+                   l, static_cast<__nv_bfloat16*>(net.act_in));
+        // first layer (input channels padded to 16)
+        const __nv_bfloat16* in = static_cast<const __nv_bfloat16*>(net.act_in);
+        if (C == 64) rc |= bf16_layer<16, 64, MODE_HIDDEN, W>(in, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
+        else rc |= bf16_layer<16, 32, MODE_HIDDEN, W>(in, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
+        cur = bufs[0];
+        k0 = 1;
+    }
+    // hidden layers k0 .. L-3; the last hidden layer (L-2) runs fused with the
+    // last layer (L-1), so its rows stay in shared memory
+    for (int k = k0; k + 2 < net.n_layers; ++k) {
+        __nv_bfloat16* o = cur == bufs[0] ? bufs[1] : bufs[0];
+        if (C == 64) rc |= bf16_layer<64, 64, MODE_HIDDEN, W>(cur, o, net.w[k], net.b[k], Nb, n, n_sm, err, st);
+        else rc |= bf16_layer<32, 32, MODE_HIDDEN, W>(cur, o, net.w[k], net.b[k], Nb, n, n_sm, err, st);
         cur = o;
     }
     const int L = net.n_layers - 1;
