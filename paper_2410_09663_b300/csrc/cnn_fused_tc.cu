@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(FT, 1)
 cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
                  float* __restrict__ Xout, long o_ms, const float* __restrict__ Bmat, int Nb, int n, int l,
                  const float* __restrict__ b1, const float* __restrict__ b2, const float* __restrict__ b3,
-                 const __half* __restrict__ wpk, float rs, int* __restrict__ err)
+                 const __half* __restrict__ wpk, float rs, int* __restrict__ err, UAdvance ua)
 {
     pdl_begin();
     using S = FS<C, G>;
@@ -453,10 +453,14 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
             // ================= 16 drain warps =================
             // U of the group, transposed to [member][pixel][control] so that one
             // pixel's l controls are contiguous
+            // (the segment that starts at row 0 also advances U_t = U_{t-1} + W)
+            const bool adv = ua.next != nullptr && ys == 0;
             for (int e = tid; e < G * l * m; e += ND) {
                 const int b = e / (l * m), rr = e % (l * m), c = rr / m, xx = rr % m;
                 const int mbr = g * G + b;
-                su[(b * m + xx) * l + c] = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
+                const float uv = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
+                su[(b * m + xx) * l + c] = uv;
+                if (adv && mbr < Nb) ua.next[(long)mbr * u_ms + rr] = uv + ua.w[(long)mbr * l * m + rr];
             }
             tc::named_bar(BAR_DRAIN, ND);
 
@@ -580,7 +584,7 @@ size_t fused_smem(int n, int l)
 template <int C, int G>
 int fused_launch(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                  const float* Bmat, int Nb, int n, int l, const float* b1, const float* b2, const float* b3,
-                 const void* wpk, float rs, int n_sm, int* err, cudaStream_t st)
+                 const void* wpk, float rs, int n_sm, int* err, cudaStream_t st, UAdvance ua)
 {
     const size_t smem = fused_smem<C, G>(n, l);
     if (smem > 227 * 1024) return 1;
@@ -594,7 +598,7 @@ int fused_launch(const float* X, long x_ms, const float* U, long u_ms, float* Xo
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
     pdl_launch(cnn_fused_kernel<C, G>, grid, FT, smem, st, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3,
-                                                  static_cast<const __half*>(wpk), rs, err);
+                                                  static_cast<const __half*>(wpk), rs, err, ua);
     return 0;
 }
 
@@ -683,13 +687,13 @@ void cnn_fused_pack_weights(const float* w1, const float* w2, const float* w3, v
 
 int launch_cnn_fused(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                      const float* Bmat, int Nb, int n, int m, int l, const float* b1, const float* b2,
-                     const float* b3, const void* wpk, float rs, int n_sm, int* err, cudaStream_t st)
+                     const float* b3, const void* wpk, float rs, int n_sm, int* err, cudaStream_t st, UAdvance ua)
 {
     switch (m) {
-    case 128: return fused_launch<32, 1>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
-    case 64: return fused_launch<32, 2>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
-    case 32: return fused_launch<32, 4>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
-    case 16: return fused_launch<32, 8>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st);
+    case 128: return fused_launch<32, 1>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st, ua);
+    case 64: return fused_launch<32, 2>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st, ua);
+    case 32: return fused_launch<32, 4>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st, ua);
+    case 16: return fused_launch<32, 8>(X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3, wpk, rs, n_sm, err, st, ua);
     }
     return 1;
 }

@@ -702,7 +702,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                        const float* __restrict__ Bmat, int l, const __nv_bfloat16* __restrict__ w0,
                        const float* __restrict__ b0, const __nv_bfloat16* __restrict__ w1,
                        const float* __restrict__ b1, __nv_bfloat16* __restrict__ out, int Nb, int n,
-                       int* __restrict__ err)
+                       int* __restrict__ err, UAdvance ua)
 {
     pdl_begin();
     using F = FBS<C, W>;
@@ -814,10 +814,14 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
         } else if (warp >= F::PROD_WARP0) {
             // ============ first-layer input rows: [X, B U] at each position ============
             const int pt = tid - 32 * F::PROD_WARP0;            // position G + pt
+            // (the segment that starts at row 0 also advances U_t = U_{t-1} + W)
+            const bool adv = ua.next != nullptr && ys == 0;
             for (int e = pt; e < G * l * m; e += 32 * F::NPW) {
                 const int b = e / (l * m), rr = e % (l * m), c = rr / m, xx = rr % m;
                 const int mbr = g * G + b;
-                su[(b * m + xx) * l + c] = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
+                const float uv = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
+                su[(b * m + xx) * l + c] = uv;
+                if (adv && mbr < Nb) ua.next[(long)mbr * u_ms + rr] = uv + ua.w[(long)mbr * l * m + rr];
             }
             tc::named_bar(2, 32 * F::NPW);
             const int pb = pt % G, px = pt / G, pmb = g * G + pb;
@@ -911,7 +915,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
 template <int W>
 __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
                                   const float* __restrict__ Bmat, int Nb, int n, int l,
-                                  __nv_bfloat16* __restrict__ act)
+                                  __nv_bfloat16* __restrict__ act, UAdvance ua)
 {
     pdl_begin();
     constexpr int G = BM / W, m = W, NPOS = BM + 2 * G;
@@ -927,6 +931,10 @@ __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const 
     if (mbr < Nb) {
         xv = X[(long)mbr * x_ms + (long)r * m + x];
         for (int c = 0; c < l; ++c) bu = fmaf(Bmat[r * l + c], U[(long)mbr * u_ms + (long)c * m + x], bu);
+        if (ua.next != nullptr && r == 0)               // U_t = U_{t-1} + W, once per member and pixel
+            for (int c = 0; c < l; ++c)
+                ua.next[(long)mbr * u_ms + (long)c * m + x] =
+                    U[(long)mbr * u_ms + (long)c * m + x] + ua.w[((long)mbr * l + c) * m + x];
     }
     const __nv_bfloat162 v = __floats2bfloat162_rn(xv, bu);
     __nv_bfloat16* row = act + ((size_t)g * n + r) * 2 * NPOS * 8;
@@ -957,7 +965,7 @@ int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const void* wpk, con
 template <int C, int W>
 int bf16_first_layers(const float* X, long x_ms, const float* U, long u_ms, const float* Bmat, int l, const void* w0,
                       const float* b0, const void* w1, const float* b1, __nv_bfloat16* out, int Nb, int n, int n_sm,
-                      int* err, cudaStream_t st)
+                      int* err, cudaStream_t st, UAdvance ua)
 {
     using F = FBS<C, W>;
     constexpr int G = F::G;
@@ -969,7 +977,7 @@ int bf16_first_layers(const float* X, long x_ms, const float* U, long u_ms, cons
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
     pdl_launch(conv_bf16_first_kernel<C, W>, grid, F::NT, smem, st, X, x_ms, U, u_ms, Bmat, l,
-               static_cast<const __nv_bfloat16*>(w0), b0, static_cast<const __nv_bfloat16*>(w1), b1, out, Nb, n, err);
+               static_cast<const __nv_bfloat16*>(w0), b0, static_cast<const __nv_bfloat16*>(w1), b1, out, Nb, n, err, ua);
     return 0;
 }
 
@@ -997,7 +1005,8 @@ int bf16_fused_layer(const __nv_bfloat16* in, const float* X, long x_ms, float* 
 
 template <int W>
 int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
-                   const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st)
+                   const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st,
+                   UAdvance ua)
 {
     const int C = net.C;
     __nv_bfloat16* bufs[2] = {static_cast<__nv_bfloat16*>(net.act[0]), static_cast<__nv_bfloat16*>(net.act[1])};
@@ -1007,10 +1016,10 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
         // layers 0 and 1 fused: the first layer's input and output rows stay on chip
         if (C == 64)
             rc |= bf16_first_layers<64, W>(X, x_ms, U, u_ms, Bmat, l, net.w[0], net.b[0], net.w[1], net.b[1], bufs[1],
-                                           Nb, n, n_sm, err, st);
+                                           Nb, n, n_sm, err, st, ua);
         else
             rc |= bf16_first_layers<32, W>(X, x_ms, U, u_ms, Bmat, l, net.w[0], net.b[0], net.w[1], net.b[1], bufs[1],
-                                           Nb, n, n_sm, err, st);
+                                           Nb, n, n_sm, err, st, ua);
         cur = bufs[1];
         k0 = 2;
     } else {
@@ -1018,7 +1027,7 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
         const int groups = (Nb + G - 1) / G;
         const long total = (long)groups * n * BM;
         pdl_launch(bf16_input_kernel<W>, (unsigned)((total + 255) / 256), 256, 0, st, X, x_ms, U, u_ms, Bmat, Nb, n,
-                   l, static_cast<__nv_bfloat16*>(net.act_in));
+                   l, static_cast<__nv_bfloat16*>(net.act_in), ua);
         // first layer (input channels padded to 16)
         const __nv_bfloat16* in = static_cast<const __nv_bfloat16*>(net.act_in);
         if (C == 64) rc |= bf16_layer<16, 64, MODE_HIDDEN, W>(in, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
@@ -1097,14 +1106,14 @@ void bf16_pack_layer(const float* w, int cin, int cout, int CI, int CO, void* ds
 
 int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout,
                         long o_ms, const float* Bmat, int Nb, int n, int m, int l, float rs, int n_sm, int* err,
-                        cudaStream_t st)
+                        cudaStream_t st, UAdvance ua)
 {
     switch (m) {
-    case 128: return bf16_forward_g<128>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
-    case 96: return bf16_forward_g<96>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
-    case 64: return bf16_forward_g<64>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
-    case 32: return bf16_forward_g<32>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
-    case 16: return bf16_forward_g<16>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 128: return bf16_forward_g<128>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
+    case 96: return bf16_forward_g<96>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
+    case 64: return bf16_forward_g<64>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
+    case 32: return bf16_forward_g<32>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
+    case 16: return bf16_forward_g<16>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
     }
     return 1;
 }

@@ -263,8 +263,12 @@ oic_status last_cuda()
 }
 
 // X_next[b] = CNN_theta(X[b], U[b]) for b < Nb, member strides x_ms / u_ms / o_ms.
+// ua: the control advance U_t = U_{t-1} + W, done by the fused and BF16 CNN
+// kernels while they read U (cnn_advances_u); the caller launches it otherwise.
+bool cnn_advances_u(const oic_handle* h) { return h->bf16 || h->fused; }
+
 void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* U, long u_ms,
-                 float* Xout, long o_ms)
+                 float* Xout, long o_ms, UAdvance ua = UAdvance())
 {
     const oic_config& c = h->cfg;
     if (h->bf16) {
@@ -280,7 +284,7 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
         net.act[1] = h->at<char>(h->lay.act1);
         run_stage(h, OIC_STAGE_CNN_BF16, [&] {
             launch_bf16_forward(net, X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l,
-                                c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st);
+                                c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st, ua);
         });
         return;
     }
@@ -290,7 +294,7 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
         run_stage(h, OIC_STAGE_CNN_FUSED, [&] {
             launch_cnn_fused(X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l, b,
                              b + C, b + 2 * C, h->at<char>(h->lay.wfused), c.residual_scale, h->n_sm,
-                             h->at<int>(h->lay.status), h->st);
+                             h->at<int>(h->lay.status), h->st, ua);
         });
         return;
     }
@@ -459,12 +463,18 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
     });
     for (int s = 1; s <= c.H; ++s) {
         // prediction, Eq. (prediction-samplewise): X̄_t = f_CNN(X̄_{t-1}) + W̄_{t-1}
+        const float* Ws = W + (s - 1) * N * l * m;
+        UAdvance ua;
+        if (cnn_advances_u(h)) {
+            ua.next = E + (size_t)h->urow(s) * m;
+            ua.w = Ws;
+        }
         cnn_forward(h, c.N, E + (size_t)h->xrow(s - 1) * m, ms, E + (size_t)h->urow(s - 1) * m, ms,
-                    E + (size_t)h->xrow(s) * m, ms);
-        run_stage(h, OIC_STAGE_U_ADVANCE, [&] {
-            launch_u_advance(E, ms, c.N, c.m, c.l, h->urow(s - 1), h->urow(s), W + (s - 1) * N * l * m,
-                             h->st);
-        });
+                    E + (size_t)h->xrow(s) * m, ms, ua);
+        if (!cnn_advances_u(h))
+            run_stage(h, OIC_STAGE_U_ADVANCE, [&] {
+                launch_u_advance(E, ms, c.N, c.m, c.l, h->urow(s - 1), h->urow(s), Ws, h->st);
+            });
         // constraint rows z_t = phi(g(X_t, U_t)) + eps_t (reference 0)
         if (h->nc > 0)
             run_stage(h, OIC_STAGE_CONSTRAINT, [&] {

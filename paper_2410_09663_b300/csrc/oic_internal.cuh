@@ -149,9 +149,17 @@ void launch_conv_tc(const float* in, float* out, const void* wpk, const float* b
 bool cnn_fused_supported(int n_layers, const int* channels, int n, int m, int l);
 size_t cnn_fused_packed_bytes();
 void cnn_fused_pack_weights(const float* w1, const float* w2, const float* w3, void* dst_host);
+// Optional control advance done by the CNN kernels while they read U_{t-1}:
+// next[i] = U[i] + w[i] (member stride u_ms for next, l m for w), written
+// once per member.  next == nullptr: no advance.
+struct UAdvance {
+    float* next = nullptr;
+    const float* w = nullptr;
+};
 int launch_cnn_fused(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                      const float* Bmat, int Nb, int n, int m, int l, const float* b1, const float* b2,
-                     const float* b3, const void* wpk, float rs, int n_sm, int* err, cudaStream_t st);
+                     const float* b3, const void* wpk, float rs, int n_sm, int* err, cudaStream_t st,
+                     UAdvance ua = UAdvance());
 // Mixed-precision CNN (BF16 operands, FP32 accumulation, FP32 residual):
 // one tcgen05 kernel per layer, activations as BF16 rows in the tensor
 // core's operand layout.  w[k]: packed tiles of layer k (bf16_pack_layer
@@ -171,7 +179,7 @@ size_t bf16_layer_bytes(int CI, int CO);
 void bf16_pack_layer(const float* w, int cin, int cout, int CI, int CO, void* dst_host);
 int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout,
                         long o_ms, const float* Bmat, int Nb, int n, int m, int l, float rs, int n_sm, int* err,
-                        cudaStream_t st);
+                        cudaStream_t st, UAdvance ua = UAdvance());
 // Known-answer check of the tcgen05 path: res[0] = mismatches (-1 timeout).
 void launch_tc_selftest(int* res, cudaStream_t st);
 
