@@ -318,17 +318,24 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
 // K = Cxy Cyy^{-1}, written transposed: Kt = K^T = Cyy^{-1} Cxy^T, [p][R].
 //
 // Cyy = U^T U (Cholesky, FP32), then per gain row a: U^T z = Cxy[a]^T
-// (forward) and U k = z (backward), Kt[.][a] = k.  Each CTA (8 warps)
-// factors Cyy itself in shared memory, blocked by panels of 8 rows: warp 0
-// factors the panel in registers (lane = column; pivots and multipliers by
-// shuffles; a pivot <= 0 means "not positive definite") and writes the U
-// rows and their transpose L = U^T; then all warps apply the rank-8 update
-// A[i][c] -= sum_d U[j0+d][i] U[j0+d][c] to the trailing rows, two rows at a
-// time (two barriers per panel).  Both substitutions then read rows (U for
-// the forward pass, L for the backward one).  Warp w solves gain row
-// a = 8 b + w: lane t holds elements t + 32 s (s < SL); eight elements are
-// eliminated per block (shuffles to every lane, the 8 x 8 diagonal block
-// solved in registers, one 8-term update of the rest).
+// (forward) and U k = z (backward), Kt[.][a] = k.  Each CTA factors Cyy
+// itself in shared memory, blocked by panels of 8 rows, one CTA barrier per
+// panel.  Panel j's rank-8 update A[i][c] -= sum_d U[j0+d][i] U[j0+d][c]
+// goes to panel j+1's rows first (one row per worker warp), which then
+// signal the factor warp on a named barrier; the factor warp factors that
+// panel (its 8 x 8 diagonal block read into every lane and factored there
+// redundantly, so the pivot chain has no shuffles in it; each lane then forms
+// the panel's U rows for its own columns; a pivot <= 0 means "not positive
+// definite") while the workers update the remaining rows and run their
+// forward substitutions.  Worker w solves gain row a = 9 b + w: lane t holds
+// elements t + 32 s (s < SL); its forward substitution takes one block of
+// eight per panel inside the loop, the backward one follows, eight elements
+// per block from the bottom.  Only U's upper rows are stored: U[i][c] with
+// lane = i (ld odd) reads conflict-free for the backward updates.
+//
+// Warp roles: warp 0 factors; warps 4 and 8, which share its scheduler
+// (warp w issues from sub-partition w mod 4), stay idle; the other nine are
+// the workers.
 template <int N>
 __device__ __forceinline__ float gsel(const float (&v)[N], int q)
 {
@@ -338,9 +345,27 @@ __device__ __forceinline__ float gsel(const float (&v)[N], int q)
     return r;
 }
 
-constexpr int GC_W = 8;                           // warps per CTA = gain rows per CTA
+constexpr int GC_NW = 12;                         // warps per CTA
+constexpr int GC_T = 32 * GC_NW;
+constexpr int GC_W = 9;                           // worker warps = gain rows per CTA
 constexpr int GC_B = 8;                           // panel height = substitution block
+constexpr int GC_BAR_PANEL = 1;                   // named barrier: next panel's rows updated
 constexpr int GC_TILE = 128 * 128;                // one operand part of the update's gain tile, bytes
+
+__device__ __forceinline__ int gc_worker(int w) { return w & 3 ? w - 1 - (w >> 2) : -1; }
+
+// v = pick ? a : v, kept a select: written as a ternary over an unrolled
+// loop, the compiler turns the chain below into an indexed local-memory array
+__device__ __forceinline__ void sel_f32(float& v, float a, bool pick)
+{
+    asm("{ .reg .pred q; setp.ne.s32 q, %2, 0; selp.f32 %0, %1, %0, q; }" : "+f"(v) : "f"(a), "r"((int)pick));
+}
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // 8-element block of a substitution: the lanes l0 .. l0+7 of slot `slot`
 // hold the block's right-hand sides; every lane receives them.
@@ -356,156 +381,201 @@ __device__ __forceinline__ void block_put(float (&b)[SL], int slot, int l0, int 
 {
     float v = z[0];
 #pragma unroll
-    for (int d = 1; d < GC_B; ++d) v = lane - l0 == d ? z[d] : v;
+    for (int d = 1; d < GC_B; ++d) sel_f32(v, z[d], lane - l0 == d);
 #pragma unroll
     for (int s = 0; s < SL; ++s)
         if (s == slot && lane >= l0 && lane < l0 + GC_B) b[s] = v;
 }
 
+// Factor the panel of rows n0 .. n0+7 (up to date in A) and store its U rows
+// and 1 / U[j][j].  Returns true on a pivot <= 0 among the real rows
+// (j < p); padding rows become zero.
 template <int SL>
-__global__ void __launch_bounds__(32 * GC_W)
+__device__ __forceinline__ bool factor_panel(int n0, int p, int pp, int ld, int lane, float* __restrict__ A,
+                                             float* __restrict__ rinv)
+{
+    float P[GC_B][SL], g[GC_B][GC_B];             // the panel (lane = column); its diagonal block
+#pragma unroll
+    for (int d = 0; d < GC_B; ++d) {
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            const int c = lane + 32 * s;
+            P[d][s] = c < pp ? A[(n0 + d) * ld + c] : 0.f;
+        }
+#pragma unroll
+        for (int e = d; e < GC_B; ++e) g[d][e] = A[(n0 + d) * ld + n0 + e];
+    }
+    float rs[GC_B];
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < GC_B; ++d) {
+        const float piv = g[d][d];
+        const bool real = n0 + d < p;
+        if (real && !(piv > 0.f)) bad = true;
+        rs[d] = real && piv > 0.f ? rsqrt_ftz(piv) : 0.f;
+#pragma unroll
+        for (int e = d + 1; e < GC_B; ++e) g[d][e] *= rs[d];
+#pragma unroll
+        for (int e = d + 1; e < GC_B; ++e)
+#pragma unroll
+            for (int f = e; f < GC_B; ++f) g[e][f] = fmaf(-g[d][e], g[d][f], g[e][f]);
+    }
+    // U rows of the panel for this lane's columns: row d = (P[d] - sum_{e<d} U[e][d] U[e]) / U[d][d]
+#pragma unroll
+    for (int d = 0; d < GC_B; ++d)
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            P[d][s] *= rs[d];
+#pragma unroll
+            for (int e = d + 1; e < GC_B; ++e) P[e][s] = fmaf(-g[d][e], P[d][s], P[e][s]);
+        }
+#pragma unroll
+    for (int d = 0; d < GC_B; ++d)
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+            const int c = lane + 32 * s;
+            if (c >= n0 + d && c < pp) A[(n0 + d) * ld + c] = P[d][s];
+        }
+    if (lane < GC_B) rinv[n0 + lane] = gsel<GC_B>(rs, lane);
+    return bad;
+}
+
+// A[i][c] -= sum_d U[j0+d][i] U[j0+d][c] for the columns c >= i of row i
+// (U's panel rows in pu, lane = column)
+template <int SL>
+__device__ __forceinline__ void panel_update_row(float* __restrict__ A, int ld, int p, int j0, int i, int lane,
+                                                 const float (&pu)[GC_B][SL])
+{
+    float q[GC_B];
+#pragma unroll
+    for (int d = 0; d < GC_B; ++d) q[d] = A[(j0 + d) * ld + i];
+    float* ai = A + i * ld;
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int c = lane + 32 * s;
+        if (c >= i && c < p) {
+            float y = 0.f, z = 0.f;
+#pragma unroll
+            for (int d = 0; d < GC_B; d += 2) {
+                y = fmaf(q[d], pu[d][s], y);
+                z = fmaf(q[d + 1], pu[d + 1][s], z);
+            }
+            ai[c] -= y + z;
+        }
+    }
+}
+
+template <int SL>
+__global__ void __launch_bounds__(GC_T, 1)
 gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status,
                  float* __restrict__ Aop)
 {
     pdl_begin();
     extern __shared__ __align__(16) float gsm[];
-    constexpr int NT = 32 * GC_W;
     const int pp = (p + GC_B - 1) & ~(GC_B - 1);  // whole panels (zero rows, rinv 0)
     const int ld = pp | 1;
+    const int nb = pp / GC_B;
     float* A = gsm;                               // [pp][ld]: Cyy, then U (upper rows)
-    float* L = gsm + pp * ld;                     // [pp][ld]: L = U^T
-    float* rinv = L + pp * ld;                    // [pp]: 1 / U[j][j]
-    __shared__ int bad;
+    float* rinv = A + pp * ld;                    // [pp]: 1 / U[j][j]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const bool factor = w == 0;
+    const int wk = gc_worker(w);                  // worker index, -1: not a worker
     const double* Cyy = C + (long)R * p;
-    // staging: zero the padding, then Cyy as 16-byte pairs (p even) with
-    // every load of a thread in flight at once
+    // staging: zero the padding, then Cyy row by row (each warp a row, the
+    // lanes its columns), every load of a thread in flight at once
     if (pp > p)
-        for (int e = tid; e < pp * ld; e += NT) {
+        for (int e = tid; e < pp * ld; e += GC_T) {
             const int i = e / ld, c = e % ld;
             if (i >= p || c >= p) A[e] = 0.f;
         }
-    if ((p & 1) == 0 && ((R * p) & 1) == 0) {
-        const double2* C2 = reinterpret_cast<const double2*>(Cyy);
-        const int np = p * p / 2;
-        for (int q0 = tid; q0 < np; q0 += NT * 12) {
-            double2 v[12];
+    {
+        constexpr int U = 2 * SL;                 // (row, column) pairs per lane: rows w, w + 12, ...
+        for (int i0 = w; i0 < p; i0 += GC_NW * U / SL) {
+            double v[U];
 #pragma unroll
-            for (int u = 0; u < 12; ++u) {
-                const int q = q0 + NT * u;
-                v[u] = q < np ? __ldg(C2 + q) : make_double2(0.0, 0.0);
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + GC_NW * (u / SL), c = lane + 32 * (u % SL);
+                v[u] = i < p && c < p ? __ldg(Cyy + (long)i * p + c) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < 12; ++u) {
-                const int q = q0 + NT * u;
-                if (q < np) {
-                    const int i = (2 * q) / p, c = (2 * q) % p;
-                    A[i * ld + c] = (float)v[u].x;
-                    A[i * ld + c + 1] = (float)v[u].y;
-                }
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + GC_NW * (u / SL), c = lane + 32 * (u % SL);
+                if (i < p && c < p) A[i * ld + c] = (float)v[u];
             }
         }
-    } else {
-        for (int e = tid; e < p * p; e += NT) A[(e / p) * ld + e % p] = (float)__ldg(Cyy + e);
     }
-    if (tid == 0) bad = 0;
+    // the worker's gain row, loaded while panel 0 is factored
+    const int a = blockIdx.x * GC_W + wk;
+    const bool mine = wk >= 0 && a < R;
+    float b[SL];
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int i = lane + 32 * s;
+        b[s] = mine && i < p ? (float)__ldg(C + (long)a * p + i) : 0.f;
+    }
     __syncthreads();
-    for (int j0 = 0; j0 < pp; j0 += GC_B) {
-        if (w == 0) {
-            // panel rows j0 .. j0+7 in registers, lane = column (slots s)
-            float P[GC_B][SL];
+    bool fbad = false;                            // the factor warp: a panel failed
+    if (factor) fbad = factor_panel<SL>(0, p, pp, ld, lane, A, rinv);
+    // one CTA barrier per panel; it also tells every thread whether a panel failed
+    bool failed = __syncthreads_or(fbad);
+    for (int j = 0; j < nb; ++j) {
+        if (failed) break;
+        const int j0 = j * GC_B, n0 = j0 + GC_B;
+        const bool next = j + 1 < nb;
+        if (factor) {
+            if (next) {
+                asm volatile("bar.sync %0, %1;" ::"n"(GC_BAR_PANEL), "n"(32 * (GC_W + 1)) : "memory");
+                fbad = factor_panel<SL>(n0, p, pp, ld, lane, A, rinv);
+            }
+        } else if (wk >= 0) {
+            float pu[GC_B][SL];                   // panel j's U rows, lane = column
 #pragma unroll
             for (int d = 0; d < GC_B; ++d)
 #pragma unroll
                 for (int s = 0; s < SL; ++s) {
                     const int c = lane + 32 * s;
-                    P[d][s] = c < pp ? A[(j0 + d) * ld + c] : 0.f;
+                    pu[d][s] = c < pp ? A[(j0 + d) * ld + c] : 0.f;
                 }
-            const int slot = j0 >> 5, l0 = j0 & 31;
-            bool badp = false;
-#pragma unroll
-            for (int d = 0; d < GC_B; ++d) {
-                // row d as it stands: its pivot and the multipliers of the rows below
-                const float ds = gsel<SL>(P[d], slot);
-                float rowd[GC_B];
-#pragma unroll
-                for (int e = d; e < GC_B; ++e) rowd[e] = __shfl_sync(0xffffffffu, ds, l0 + e);
-                const float piv = rowd[d];
-                float rs = 0.f, ip = 0.f;             // padding rows: zero
-                if (j0 + d < p) {
-                    if (!(piv > 0.f)) badp = true;
-                    rs = piv > 0.f ? rsqrtf(piv) : 0.f;
-                    ip = rs * rs;
-                }
-#pragma unroll
-                for (int e = d + 1; e < GC_B; ++e) {
-                    const float f = rowd[e] * ip;
-#pragma unroll
-                    for (int s = 0; s < SL; ++s) P[e][s] = fmaf(-f, P[d][s], P[e][s]);
-                }
-#pragma unroll
-                for (int s = 0; s < SL; ++s) P[d][s] *= rs;
-                if (lane == 0) rinv[j0 + d] = rs;
+            if (next) {
+                // panel j+1's rows first, then tell the factor warp
+                if (wk < GC_B && n0 + wk < p) panel_update_row<SL>(A, ld, p, j0, n0 + wk, lane, pu);
+                asm volatile("bar.arrive %0, %1;" ::"n"(GC_BAR_PANEL), "n"(32 * (GC_W + 1)) : "memory");
             }
-#pragma unroll
-            for (int d = 0; d < GC_B; ++d)
-#pragma unroll
-                for (int s = 0; s < SL; ++s) {
-                    const int c = lane + 32 * s;
-                    if (c >= j0 + d && c < pp) {
-                        A[(j0 + d) * ld + c] = P[d][s];
-                        L[c * ld + j0 + d] = P[d][s];
-                    }
-                }
-            if (badp && lane == 0) bad = 1;
-        }
-        __syncthreads();
-        if (bad) break;
-        // rank-8 update of rows i >= j0 + 8, columns c >= i, two rows at a time
-        const int t0 = j0 + GC_B;
-        if (t0 < p) {
-            float pc[SL][GC_B];
-#pragma unroll
-            for (int s = 0; s < SL; ++s) {
-                const int c = t0 + lane + 32 * s;
-#pragma unroll
-                for (int d = 0; d < GC_B; ++d) pc[s][d] = c < p ? L[c * ld + j0 + d] : 0.f;
-            }
-            for (int i = t0 + 2 * w; i < p; i += 2 * GC_W) {
-                const int i1 = i + 1 < p ? i + 1 : i;
-                float pi0[GC_B], pi1[GC_B];
+            // the rows from panel j+2 on
+            for (int i = n0 + GC_B + wk; i < p; i += GC_W) panel_update_row<SL>(A, ld, p, j0, i, lane, pu);
+            // forward substitution, block j of the own gain row: U^T z = b
+            if (mine) {
+                const int slot = j0 >> 5, l0 = j0 & 31;
+                float z[GC_B];
+                block_gather<SL>(b, slot, l0, z);
 #pragma unroll
                 for (int d = 0; d < GC_B; ++d) {
-                    pi0[d] = L[i * ld + j0 + d];
-                    pi1[d] = L[i1 * ld + j0 + d];
+                    const float* ud = A + (j0 + d) * ld;
+                    z[d] *= rinv[j0 + d];
+#pragma unroll
+                    for (int e = d + 1; e < GC_B; ++e) z[e] = fmaf(-ud[j0 + e], z[d], z[e]);
                 }
-                float* a0 = A + i * ld;
-                float* a1 = A + i1 * ld;
+                block_put<SL>(b, slot, l0, lane, z);
 #pragma unroll
                 for (int s = 0; s < SL; ++s) {
-                    const int c = t0 + lane + 32 * s;
-                    const bool ok = c < p;
-                    const float x0 = ok && c >= i ? a0[c] : 0.f;
-                    const float x1 = ok && c >= i1 && i1 != i ? a1[c] : 0.f;
-                    float y0 = 0.f, y1 = 0.f, z0 = 0.f, z1 = 0.f;
+                    const int i = lane + 32 * s;
+                    if (i >= n0 && i < pp) {
+                        float y = 0.f, x = 0.f;
 #pragma unroll
-                    for (int d = 0; d < GC_B; d += 2) {
-                        y0 = fmaf(pi0[d], pc[s][d], y0);
-                        z0 = fmaf(pi0[d + 1], pc[s][d + 1], z0);
-                        y1 = fmaf(pi1[d], pc[s][d], y1);
-                        z1 = fmaf(pi1[d + 1], pc[s][d + 1], z1);
+                        for (int d = 0; d < GC_B; d += 2) {
+                            y = fmaf(pu[d][s], z[d], y);
+                            x = fmaf(pu[d + 1][s], z[d + 1], x);
+                        }
+                        b[s] -= y + x;
                     }
-                    if (ok && c >= i) a0[c] = x0 - (y0 + z0);
-                    if (ok && c >= i1 && i1 != i) a1[c] = x1 - (y1 + z1);
                 }
             }
         }
-        __syncthreads();
+        failed = __syncthreads_or(fbad);
     }
-    const int a = blockIdx.x * GC_W + w;
-    if (bad) {                                    // K = 0: the update leaves the ensemble as it is
+    if (failed) {                                 // K = 0: the update leaves the ensemble as it is
         if (tid == 0) atomicExch(status, DEV_NOTSPD);
-        if (a < R) {
+        if (mine) {
             for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
             if (Aop != nullptr) {
                 char* t0 = reinterpret_cast<char*>(Aop) + (size_t)(a >> 7) * SL * 2 * GC_TILE;
@@ -515,63 +585,30 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
         }
         return;
     }
-    if (a >= R) return;
-
-    float b[SL];
-#pragma unroll
-    for (int s = 0; s < SL; ++s) {
-        const int i = lane + 32 * s;
-        b[s] = i < p ? (float)__ldg(C + (long)a * p + i) : 0.f;
-    }
-    // forward: U^T z = b, blocks of eight from the top
-    for (int k0 = 0; k0 < pp; k0 += GC_B) {
-        const int slot = k0 >> 5, l0 = k0 & 31;
-        float z[GC_B];
-        block_gather<SL>(b, slot, l0, z);
-#pragma unroll
-        for (int d = 0; d < GC_B; ++d) {
-            const float* ud = A + (k0 + d) * ld;
-            z[d] *= rinv[k0 + d];
-#pragma unroll
-            for (int e = d + 1; e < GC_B; ++e) z[e] = fmaf(-ud[k0 + e], z[d], z[e]);
-        }
-        block_put<SL>(b, slot, l0, lane, z);
-#pragma unroll
-        for (int s = 0; s < SL; ++s) {
-            const int i = lane + 32 * s;
-            if (i >= k0 + GC_B && i < pp) {
-                float y = 0.f, x = 0.f;
-#pragma unroll
-                for (int d = 0; d < GC_B; d += 2) {
-                    y = fmaf(A[(k0 + d) * ld + i], z[d], y);
-                    x = fmaf(A[(k0 + d + 1) * ld + i], z[d + 1], x);
-                }
-                b[s] -= y + x;
-            }
-        }
-    }
+    if (!mine) return;
     // backward: U k = z, blocks of eight from the bottom
     for (int k0 = pp - GC_B; k0 >= 0; k0 -= GC_B) {
         const int slot = k0 >> 5, l0 = k0 & 31;
         float x[GC_B];
         block_gather<SL>(b, slot, l0, x);
 #pragma unroll
-        for (int d = GC_B - 1; d >= 0; --d) {
+        for (int dd = 0; dd < GC_B; ++dd) {
+            const int d = GC_B - 1 - dd;
             x[d] *= rinv[k0 + d];
-            const float* ld_row = L + (k0 + d) * ld;   // L[k0+d][k0+e] = U[k0+e][k0+d]
 #pragma unroll
-            for (int e = 0; e < d; ++e) x[e] = fmaf(-ld_row[k0 + e], x[d], x[e]);
+            for (int e = 0; e < d; ++e) x[e] = fmaf(-A[(k0 + e) * ld + k0 + d], x[d], x[e]);
         }
         block_put<SL>(b, slot, l0, lane, x);
 #pragma unroll
         for (int s = 0; s < SL; ++s) {
             const int i = lane + 32 * s;
             if (i < k0) {
+                const float* ui = A + i * ld + k0;
                 float y = 0.f, v = 0.f;
 #pragma unroll
                 for (int d = 0; d < GC_B; d += 2) {
-                    y = fmaf(L[(k0 + d) * ld + i], x[d], y);
-                    v = fmaf(L[(k0 + d + 1) * ld + i], x[d + 1], v);
+                    y = fmaf(ui[d], x[d], y);
+                    v = fmaf(ui[d + 1], x[d + 1], v);
                 }
                 b[s] -= y + v;
             }
@@ -599,7 +636,7 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
 size_t gain_chol_smem(int p)
 {
     const int pp = (p + GC_B - 1) & ~(GC_B - 1), ld = pp | 1;
-    return sizeof(float) * ((size_t)2 * pp * ld + pp);
+    return sizeof(float) * ((size_t)pp * ld + pp);
 }
 
 template <int SL>
@@ -613,7 +650,7 @@ void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cud
         attr_set = true;
     }
     const int grid = R > 0 ? (R + GC_W - 1) / GC_W : 1;
-    pdl_launch(gain_chol_kernel<SL>, grid, 32 * GC_W, smem, st, C, R, p, Kt, status, Aop);
+    pdl_launch(gain_chol_kernel<SL>, grid, GC_T, smem, st, C, R, p, Kt, status, Aop);
 }
 
 // ---------------------------------------------------------------- update
