@@ -14,7 +14,10 @@
 //     CTA of the cluster;
 //   - every CTA waits for that barrier (acquire, cluster scope, bounded),
 //     copies the panel out of the owner's shared memory (distributed shared
-//     memory) and applies the rank-8 update to its own later rows;
+//     memory) and applies the rank-8 update to its own later rows, the next
+//     panel's rows first: their owner then eliminates and releases the next
+//     panel before it updates the rest (look-ahead), so a panel's release
+//     waits for one panel's update of 8 rows, not of every later row;
 //   - a pivot <= 0 ("not positive definite") is published with the panel, so
 //     every CTA leaves the loop after the same panel.
 // Each panel barrier is used once (parity 0), so no barrier ever has two
@@ -85,6 +88,19 @@ __device__ __forceinline__ void cl_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// 1/sqrt(x) in FP64: an FP32 seed refined by two Newton steps for 1/y^2 = x
+// (each step squares the relative error: 2^-23 -> 2^-46 -> FP64 rounding)
+__device__ __forceinline__ double rsqrt64(double x)
+{
+    const float xf = (float)x;
+    if (!(xf > 0.f) || xf > 1e37f) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf(xf);
+    const double hx = 0.5 * x;
+    y = y * fma(-hx, y * y, 1.5);
+    y = y * fma(-hx, y * y, 1.5);
+    return y;
+}
+
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(C64_T, 1)
 chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ Lg, int* __restrict__ status,
                int* __restrict__ bad_out)
@@ -117,40 +133,54 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
     __syncthreads();
     cl_sync();                                          // every barrier initialised before any remote arrive
 
+    // the owner eliminates panel B's pivots (right-looking, rows in own[B / CL]),
+    // scales the rows to U and releases the panel to every CTA
+    auto eliminate = [&](int B) {
+        double (*A)[C64_PMAX] = own[B / CL];
+        const int c0 = PB * B;
+        for (int d = 0; d < PB; ++d) {
+            const int g = c0 + d;
+            const double piv = A[d][g];
+            const double r = (g < p && piv > 0.0) ? rsqrt64(piv) : 0.0;
+            const double ip = r * r;
+            if (g < p && !(piv > 0.0) && tid == 0) bad_here = 1;
+            if (tid == 0) rsv[d] = r;
+            // rows e > d of the panel, columns c >= c0 + e: warp w takes row d + 1 + w
+            const int e = d + 1 + w;
+            if (e < PB) {
+                const double f = A[d][c0 + e] * ip;
+                for (int c = c0 + e + lane; c < pp; c += 32) A[e][c] = fma(-f, A[d][c], A[e][c]);
+            }
+            __syncthreads();
+        }
+        for (int x = tid; x < PB * pp; x += C64_T) {
+            const int d = x / pp, c = x % pp;
+            if (c >= c0 + d) A[d][c] *= rsv[d];
+        }
+        __syncthreads();
+        if (tid == 0)
+            for (uint32_t t = 0; t < CL; ++t) cl_arrive(cl_map(rdy + B, t));
+    };
+    // rank-8 update of panel B2's rows (this CTA's), columns c >= row, by the panel in pan
+    auto update = [&](int B2) {
+        double (*A)[C64_PMAX] = own[B2 / CL];
+        for (int d2 = w; d2 < PB; d2 += C64_T / 32) {
+            const int g = PB * B2 + d2;
+            double pi[PB];
+#pragma unroll
+            for (int k = 0; k < PB; ++k) pi[k] = pan[k][g];
+            for (int c = g + lane; c < pp; c += 32) {
+                double v = A[d2][c];
+#pragma unroll
+                for (int k = 0; k < PB; ++k) v = fma(-pi[k], pan[k][c], v);
+                A[d2][c] = v;
+            }
+        }
+    };
+    if (rank == 0) eliminate(0);
     for (int B = 0; B < NB; ++B) {
         const uint32_t o = (uint32_t)(B % CL);
         const int sl = B / CL, c0 = PB * B;
-        if (rank == o) {
-            // ---- the owner eliminates the panel's pivots
-            double (*A)[C64_PMAX] = own[sl];
-            for (int d = 0; d < PB; ++d) {
-                const int g = c0 + d;
-                const double piv = A[d][g];
-                double ip = 0.0;
-                if (g < p) {
-                    if (!(piv > 0.0)) {
-                        if (tid == 0) bad_here = 1;
-                    } else {
-                        ip = 1.0 / piv;
-                    }
-                }
-                if (tid == 0) rsv[d] = (g < p && piv > 0.0) ? 1.0 / sqrt(piv) : 0.0;
-                // rows e > d of the panel, columns c >= c0 + e: warp w takes row d + 1 + w
-                const int e = d + 1 + w;
-                if (e < PB) {
-                    const double f = A[d][c0 + e] * ip;
-                    for (int c = c0 + e + lane; c < pp; c += 32) A[e][c] = fma(-f, A[d][c], A[e][c]);
-                }
-                __syncthreads();
-            }
-            for (int x = tid; x < PB * pp; x += C64_T) {
-                const int d = x / pp, c = x % pp;
-                if (c >= c0 + d) A[d][c] *= rsv[d];
-            }
-            __syncthreads();
-            if (tid == 0)
-                for (uint32_t t = 0; t < CL; ++t) cl_arrive(cl_map(rdy + B, t));
-        }
         // ---- everyone: wait for the panel, copy it, check the owner's pivots
         if (!cl_wait(rdy + B, 0u, C64_WAIT)) timeout = 1;
         __syncthreads();
@@ -162,22 +192,19 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
         if (tid == 0) bad_seen = cl_ld_s32(cl_map(&bad_here, o));
         __syncthreads();
         if (bad_seen) break;
-        // ---- rank-8 update of this CTA's rows in later panels, columns c >= row
+        // ---- look-ahead: the next panel's owner updates and releases it first
+        const int Bn = B + 1;
+        const bool ahead = Bn < NB && (int)rank == Bn % CL;
+        if (ahead) {
+            update(Bn);
+            __syncthreads();
+            eliminate(Bn);
+        }
+        // ---- then this CTA's other rows in later panels
         for (int sl2 = 0; sl2 < C64_OWN; ++sl2) {
             const int B2 = (int)rank + CL * sl2;
-            if (B2 <= B || B2 >= NB) continue;
-            for (int d2 = w; d2 < PB; d2 += C64_T / 32) {
-                const int g = PB * B2 + d2;
-                double pi[PB];
-#pragma unroll
-                for (int k = 0; k < PB; ++k) pi[k] = pan[k][g];
-                for (int c = g + lane; c < pp; c += 32) {
-                    double v = own[sl2][d2][c];
-#pragma unroll
-                    for (int k = 0; k < PB; ++k) v = fma(-pi[k], pan[k][c], v);
-                    own[sl2][d2][c] = v;
-                }
-            }
+            if (B2 <= B || B2 >= NB || (ahead && B2 == Bn)) continue;
+            update(B2);
         }
         __syncthreads();
     }
@@ -247,6 +274,7 @@ solve64s_kernel(const double* __restrict__ C, int R, int p, const double* __rest
         zj = __shfl_sync(0xffffffffu, zj, lj) * rinv[j];
 #pragma unroll
         for (int q = 0; q < S64_Q; ++q) {
+            if (32 * q + 31 < j || 32 * q >= p) continue;      // slot wholly above the pivot: untouched
             const int i = lane + 32 * q;
             if (i == j) z[q] = zj;
             else if (i > j && i < p) z[q] = fma(-Ls[i * ld + j], zj, z[q]);
@@ -261,6 +289,7 @@ solve64s_kernel(const double* __restrict__ C, int R, int p, const double* __rest
         kj = __shfl_sync(0xffffffffu, kj, lj) * rinv[j];
 #pragma unroll
         for (int q = 0; q < S64_Q; ++q) {
+            if (32 * q > j) continue;                           // slot wholly below the pivot: done
             const int i = lane + 32 * q;
             if (i == j) z[q] = kj;
             else if (i < j) z[q] = fma(-Ls[j * ld + i], kj, z[q]);
