@@ -272,12 +272,12 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
 {
     pdl_begin();
     using T = typename std::conditional<F64, double, float>::type;
-    __shared__ T red[8][33];
+    __shared__ T red[8][33], cred[8][33];
     const int M = R + p;
     const int idx = blockIdx.x * 32 + threadIdx.x % 32;
     const bool ok = idx < M * p;
     const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
-    T sp = 0;
+    T sp = 0, cp = 0;
     if (ok) {
         // four splits' loads in flight before they are added (same order)
         const long st = (long)M * p;
@@ -291,25 +291,31 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
             sp += (T)v3;
         }
         for (; k < splits; k += 8) sp += (T)part2[k * st + idx];
-    }
-    red[w][ln] = sp;
-    __syncthreads();
-    if (threadIdx.x < 32 && ok) {
-        T t = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) t += red[q][ln];
-        T corr = 0;
-        if (S1 != nullptr) {                      // one-pass products: remove the mean term
+        if (S1 != nullptr) {                      // one-pass products: the mean term, columns j = w, w + 8, ...
             const int a = idx / p, c = idx % p;
             const float* x = S1 + (long)a * m;
             const float* y = S1 + (long)(R + c) * m;
             T d0 = 0, d1 = 0;
-            for (int j = 0; j < m; j += 2) {
+            int j = w;
+            for (; j + 8 < m; j += 16) {
                 d0 = fma((T)x[j], (T)y[j], d0);
-                d1 = fma((T)x[j + 1], (T)y[j + 1], d1);
+                d1 = fma((T)x[j + 8], (T)y[j + 8], d1);
             }
-            corr = (d0 + d1) / (T)N;
+            if (j < m) d0 = fma((T)x[j], (T)y[j], d0);
+            cp = d0 + d1;
         }
+    }
+    red[w][ln] = sp;
+    cred[w][ln] = cp;
+    __syncthreads();
+    if (threadIdx.x < 32 && ok) {
+        T t = 0, corr = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            t += red[q][ln];
+            corr += cred[q][ln];
+        }
+        corr /= (T)N;
         C[idx] = (double)(t - corr) * scale;
     }
 }
