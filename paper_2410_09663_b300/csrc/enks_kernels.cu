@@ -728,23 +728,37 @@ update_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float* __
     }
 }
 
-__global__ void block_means_kernel(const float* __restrict__ E, long ms, int N, int m, int row0,
-                                   int rows_per_block, int n_blocks, float* __restrict__ out)
+__global__ void __launch_bounds__(256) block_means_kernel(const float* __restrict__ E, long ms, int N, int m,
+                                                          int row0, int rows_per_block, int n_blocks,
+                                                          float* __restrict__ out)
 {
+    // 32 outputs per CTA (lane = output, coalesced); the members are split
+    // over the 8 warps (four loads in flight each), then summed in shared memory
     pdl_begin();
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_blocks * rows_per_block * m) return;
-    const long off = (long)row0 * m + idx;      // blocks are contiguous rows
+    __shared__ float red[8][33];
+    const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    const int idx = blockIdx.x * 32 + ln;
+    const bool ok = idx < n_blocks * rows_per_block * m;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int i = 0;
-    for (; i + 4 <= N; i += 4) {
-        s0 += E[(long)i * ms + off];
-        s1 += E[(long)(i + 1) * ms + off];
-        s2 += E[(long)(i + 2) * ms + off];
-        s3 += E[(long)(i + 3) * ms + off];
+    if (ok) {
+        const long off = (long)row0 * m + idx;  // blocks are contiguous rows
+        int i = w;
+        for (; i + 24 < N; i += 32) {
+            s0 += E[(long)i * ms + off];
+            s1 += E[(long)(i + 8) * ms + off];
+            s2 += E[(long)(i + 16) * ms + off];
+            s3 += E[(long)(i + 24) * ms + off];
+        }
+        for (; i < N; i += 8) s0 += E[(long)i * ms + off];
     }
-    for (; i < N; ++i) s0 += E[(long)i * ms + off];
-    out[idx] = ((s0 + s1) + (s2 + s3)) / (float)N;
+    red[w][ln] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (w == 0 && ok) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][ln];
+        out[idx] = t / (float)N;
+    }
 }
 
 }  // namespace
@@ -839,8 +853,7 @@ void launch_block_means(const float* E, long ms, int N, int m, int row0, int row
                         int n_blocks, float* out, cudaStream_t st)
 {
     const int total = n_blocks * rows_per_block * m;
-    pdl_launch(block_means_kernel, (total + 255) / 256, 256, 0, st, E, ms, N, m, row0, rows_per_block,
-                                                            n_blocks, out);
+    pdl_launch(block_means_kernel, (total + 31) / 32, 256, 0, st, E, ms, N, m, row0, rows_per_block, n_blocks, out);
 }
 
 }  // namespace oic
