@@ -702,7 +702,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                        const float* __restrict__ Bmat, int l, const __nv_bfloat16* __restrict__ w0,
                        const float* __restrict__ b0, const __nv_bfloat16* __restrict__ w1,
                        const float* __restrict__ b1, __nv_bfloat16* __restrict__ out, int Nb, int n,
-                       int* __restrict__ err, UAdvance ua)
+                       int* __restrict__ err)
 {
     pdl_begin();
     using F = FBS<C, W>;
@@ -814,14 +814,11 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
         } else if (warp >= F::PROD_WARP0) {
             // ============ first-layer input rows: [X, B U] at each position ============
             const int pt = tid - 32 * F::PROD_WARP0;            // position G + pt
-            // (the segment that starts at row 0 also advances U_t = U_{t-1} + W)
-            const bool adv = ua.next != nullptr && ys == 0;
             for (int e = pt; e < G * l * m; e += 32 * F::NPW) {
                 const int b = e / (l * m), rr = e % (l * m), c = rr / m, xx = rr % m;
                 const int mbr = g * G + b;
                 const float uv = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
                 su[(b * m + xx) * l + c] = uv;
-                if (adv && mbr < Nb) ua.next[(long)mbr * u_ms + rr] = uv + ua.w[(long)mbr * l * m + rr];
             }
             tc::named_bar(2, 32 * F::NPW);
             const int pb = pt % G, px = pt / G, pmb = g * G + pb;
@@ -915,7 +912,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
 template <int W>
 __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const float* __restrict__ U, long u_ms,
                                   const float* __restrict__ Bmat, int Nb, int n, int l,
-                                  __nv_bfloat16* __restrict__ act, UAdvance ua)
+                                  __nv_bfloat16* __restrict__ act)
 {
     pdl_begin();
     constexpr int G = BM / W, m = W, NPOS = BM + 2 * G;
@@ -931,10 +928,6 @@ __global__ void bf16_input_kernel(const float* __restrict__ X, long x_ms, const 
     if (mbr < Nb) {
         xv = X[(long)mbr * x_ms + (long)r * m + x];
         for (int c = 0; c < l; ++c) bu = fmaf(Bmat[r * l + c], U[(long)mbr * u_ms + (long)c * m + x], bu);
-        if (ua.next != nullptr && r == 0)               // U_t = U_{t-1} + W, once per member and pixel
-            for (int c = 0; c < l; ++c)
-                ua.next[(long)mbr * u_ms + (long)c * m + x] =
-                    U[(long)mbr * u_ms + (long)c * m + x] + ua.w[((long)mbr * l + c) * m + x];
     }
     const __nv_bfloat162 v = __floats2bfloat162_rn(xv, bu);
     __nv_bfloat16* row = act + ((size_t)g * n + r) * 2 * NPOS * 8;
@@ -965,7 +958,7 @@ int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const void* wpk, con
 template <int C, int W>
 int bf16_first_layers(const float* X, long x_ms, const float* U, long u_ms, const float* Bmat, int l, const void* w0,
                       const float* b0, const void* w1, const float* b1, __nv_bfloat16* out, int Nb, int n, int n_sm,
-                      int* err, cudaStream_t st, UAdvance ua)
+                      int* err, cudaStream_t st)
 {
     using F = FBS<C, W>;
     constexpr int G = F::G;
@@ -977,7 +970,7 @@ int bf16_first_layers(const float* X, long x_ms, const float* U, long u_ms, cons
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
     pdl_launch(conv_bf16_first_kernel<C, W>, grid, F::NT, smem, st, X, x_ms, U, u_ms, Bmat, l,
-               static_cast<const __nv_bfloat16*>(w0), b0, static_cast<const __nv_bfloat16*>(w1), b1, out, Nb, n, err, ua);
+               static_cast<const __nv_bfloat16*>(w0), b0, static_cast<const __nv_bfloat16*>(w1), b1, out, Nb, n, err);
     return 0;
 }
 
@@ -1005,8 +998,7 @@ int bf16_fused_layer(const __nv_bfloat16* in, const float* X, long x_ms, float* 
 
 template <int W>
 int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
-                   const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st,
-                   UAdvance ua)
+                   const float* Bmat, int Nb, int n, int l, float rs, int n_sm, int* err, cudaStream_t st)
 {
     const int C = net.C;
     __nv_bfloat16* bufs[2] = {static_cast<__nv_bfloat16*>(net.act[0]), static_cast<__nv_bfloat16*>(net.act[1])};
@@ -1016,10 +1008,10 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
         // layers 0 and 1 fused: the first layer's input and output rows stay on chip
         if (C == 64)
             rc |= bf16_first_layers<64, W>(X, x_ms, U, u_ms, Bmat, l, net.w[0], net.b[0], net.w[1], net.b[1], bufs[1],
-                                           Nb, n, n_sm, err, st, ua);
+                                           Nb, n, n_sm, err, st);
         else
             rc |= bf16_first_layers<32, W>(X, x_ms, U, u_ms, Bmat, l, net.w[0], net.b[0], net.w[1], net.b[1], bufs[1],
-                                           Nb, n, n_sm, err, st, ua);
+                                           Nb, n, n_sm, err, st);
         cur = bufs[1];
         k0 = 2;
     } else {
@@ -1027,7 +1019,7 @@ int bf16_forward_g(const Bf16Net& net, const float* X, long x_ms, const float* U
         const int groups = (Nb + G - 1) / G;
         const long total = (long)groups * n * BM;
         pdl_launch(bf16_input_kernel<W>, (unsigned)((total + 255) / 256), 256, 0, st, X, x_ms, U, u_ms, Bmat, Nb, n,
-                   l, static_cast<__nv_bfloat16*>(net.act_in), ua);
+                   l, static_cast<__nv_bfloat16*>(net.act_in));
         // first layer (input channels padded to 16)
         const __nv_bfloat16* in = static_cast<const __nv_bfloat16*>(net.act_in);
         if (C == 64) rc |= bf16_layer<16, 64, MODE_HIDDEN, W>(in, bufs[0], net.w[0], net.b[0], Nb, n, n_sm, err, st);
@@ -1106,14 +1098,14 @@ void bf16_pack_layer(const float* w, int cin, int cout, int CI, int CO, void* ds
 
 int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout,
                         long o_ms, const float* Bmat, int Nb, int n, int m, int l, float rs, int n_sm, int* err,
-                        cudaStream_t st, UAdvance ua)
+                        cudaStream_t st)
 {
     switch (m) {
-    case 128: return bf16_forward_g<128>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
-    case 96: return bf16_forward_g<96>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
-    case 64: return bf16_forward_g<64>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
-    case 32: return bf16_forward_g<32>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
-    case 16: return bf16_forward_g<16>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st, ua);
+    case 128: return bf16_forward_g<128>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 96: return bf16_forward_g<96>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 64: return bf16_forward_g<64>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 32: return bf16_forward_g<32>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
+    case 16: return bf16_forward_g<16>(net, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, rs, n_sm, err, st);
     }
     return 1;
 }

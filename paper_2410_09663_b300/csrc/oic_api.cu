@@ -265,8 +265,8 @@ oic_status last_cuda()
 // X_next[b] = CNN_theta(X[b], U[b]) for b < Nb, member strides x_ms / u_ms / o_ms.
 // ua: the control advance U_t = U_{t-1} + W, done by the fused FP32 CNN kernel
 // while it reads U (cnn_advances_u); the caller launches it otherwise.  The
-// BF16 kernels can do it too, but at 128 x 128 the separate launch measured
-// faster (13.39 against 13.17 control steps/s on one box).
+// BF16 path keeps the separate launch: the advance inside its first kernel
+// measured slower at 128 x 128 (13.17 against 13.39 control steps/s on one box).
 bool cnn_advances_u(const oic_handle* h) { return h->fused; }
 
 void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* U, long u_ms,
@@ -286,7 +286,7 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
         net.act[1] = h->at<char>(h->lay.act1);
         run_stage(h, OIC_STAGE_CNN_BF16, [&] {
             launch_bf16_forward(net, X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l,
-                                c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st, ua);
+                                c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st);
         });
         return;
     }

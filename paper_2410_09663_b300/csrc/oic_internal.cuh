@@ -179,7 +179,7 @@ size_t bf16_layer_bytes(int CI, int CO);
 void bf16_pack_layer(const float* w, int cin, int cout, int CI, int CO, void* dst_host);
 int launch_bf16_forward(const Bf16Net& net, const float* X, long x_ms, const float* U, long u_ms, float* Xout,
                         long o_ms, const float* Bmat, int Nb, int n, int m, int l, float rs, int n_sm, int* err,
-                        cudaStream_t st, UAdvance ua = UAdvance());
+                        cudaStream_t st);
 // Known-answer check of the tcgen05 path: res[0] = mismatches (-1 timeout).
 void launch_tc_selftest(int* res, cudaStream_t st);
 
