@@ -320,8 +320,15 @@ def run_oic(args, wl):
             s.oic_step(window(args.warmup + i), ur, None, u_out, x_out)
         breakdown = s.oic_profile_end()
         dominant = max(breakdown, key=lambda k: breakdown[k][0]) if breakdown else None
+        # the timed region brackets one launch of the dominant stage per step
+        # (the middle one of its per_step launches, all of the same size): an
+        # event record between two kernels keeps the second from starting
+        # early, so bracketing all of them would slow the step it measures
+        per_step_l = max(1, round(breakdown[dominant][1] / n_break)) if dominant is not None else 1
+        sample = (per_step_l, per_step_l // 2)
         if dominant is not None:                        # capture the timed variant's graph
             s.oic_profile_begin(stages=[dominant], max_launches=128)
+            s.oic_profile_sample(*sample)
             s.oic_step(window(args.warmup + n_break), ur, None, u_out, x_out)
             s.oic_profile_end()
 
@@ -333,6 +340,7 @@ def run_oic(args, wl):
         launches0 = oic.oic_launch_count()
         if dominant is not None:
             s.oic_profile_begin(stages=[dominant], max_launches=128 * args.steps)
+            s.oic_profile_sample(*sample)
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
             for i in range(args.steps):
@@ -347,6 +355,28 @@ def run_oic(args, wl):
         launches = oic.oic_launch_count() - launches0
         s.oic_sync()
         per_step = [a.elapsed_time(c) for a, c in ev]
+        # the same kind of step launched kernel by kernel instead of replayed
+        # from its graph: the launch overhead the graph removes (not part of
+        # the value above)
+        n_eager = min(args.steps, 20)
+        ev_e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(n_eager)]
+        os.environ["OIC_NO_GRAPH"] = "1"
+        try:
+            if dominant is not None:                    # the same event brackets as the timed graph
+                s.oic_profile_begin(stages=[dominant], max_launches=128 * n_eager)
+                s.oic_profile_sample(*sample)
+            for i in range(n_eager):
+                flush.fill_(float(i))
+                ev_e[i][0].record(stream)
+                s.oic_step(window(args.warmup + i), ur, None, u_out, x_out)
+                ev_e[i][1].record(stream)
+            stream.synchronize()
+            if dominant is not None:
+                s.oic_profile_end()
+        finally:
+            del os.environ["OIC_NO_GRAPH"]
+        eager_ms = sum(a.elapsed_time(c) for a, c in ev_e) / max(n_eager, 1)
     t_dev = sum(per_step) / 1e3                         # seconds of device time in steps
 
     # e2e: the host-pointer entry point, pinned host buffers, copies inside
@@ -397,6 +427,8 @@ def run_oic(args, wl):
                         "traffic": kernel_traffic(dominant),
                         "algorithmic_per_launch": amount, "launches": n_l,
                         "avg_launch_ms": avg_s * 1e3,
+                        "sampled": "launch %d of the %d %s launches of each timed step, bracketed by CUDA "
+                                   "events" % (sample[1], sample[0], dominant),
                         "fp32_ffma_equiv_frac": ach / fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2032.0)),
                         "note": ("BF16 operands, FP32 accumulation" if dominant == "cnn_bf16" else
                                  "algorithmic FP32 flops; the tensor pipe executes 3 fp16 products each")}
@@ -409,7 +441,9 @@ def run_oic(args, wl):
                                        % (peaks.get("sm_max_mhz", 2032.0), peaks["source"]),
                         "traffic": kernel_traffic(dominant),
                         "algorithmic_per_launch": amount, "launches": n_l,
-                        "avg_launch_ms": avg_s * 1e3}
+                        "avg_launch_ms": avg_s * 1e3,
+                        "sampled": "launch %d of the %d %s launches of each timed step, bracketed by CUDA "
+                                   "events" % (sample[1], sample[0], dominant)}
     share = {k: round(v / max(sum(total_ms.values()), 1e-12), 4) for k, v in total_ms.items()}
     steps_total = world * args.steps
     value = job_value(args.steps, world, t_dev)
@@ -425,11 +459,16 @@ def run_oic(args, wl):
             "cnn_tflops": value * wl.N * wl.H * cnn_flops_per_member_step(wl) / 1e12,
             "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "wall_s_timed_region": wall,
-            "launch": "one CUDA graph per control step (events only around the %s launches)" % dominant,
+            "launch": "one CUDA graph per control step (events around one %s launch per step)" % dominant,
             "stage_share": share,
             "stage_ms_per_step": {k: v / n_break for k, v in total_ms.items()},
             "stage_breakdown": "%d instrumented steps before the timed region, every stage bracketed "
-                               "by CUDA events" % n_break}),
+                               "by CUDA events" % n_break,
+            "graph_vs_eager": {"graph_ms_per_step": 1e3 * t_dev / args.steps, "eager_ms_per_step": eager_ms,
+                               "eager_steps": n_eager,
+                               "note": "eager: the same step launched kernel by kernel (OIC_NO_GRAPH), "
+                                       "with the same event brackets around the dominant stage, timed "
+                                       "after the graph run"}}),
         "roofline": roof,
         "e2e": {"value": steps_total / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

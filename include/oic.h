@@ -253,6 +253,15 @@ typedef enum {
 oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launches);
 oic_status oic_profile_end(oic_handle* h, float* ms, int* launches);
 
+/* Sampling for the profiler started by oic_profile_begin (which resets it to
+ * every launch): of the launches of a profiled stage within one solve (and
+ * the plant step that follows it in oic_step), counted from 0, only those
+ * with index % every == phase are bracketed by events; the others run
+ * without event records between them and their neighbours.  A captured step
+ * graph is re-captured when the sampling changes.  OIC_EINVAL unless
+ * every >= 1 and 0 <= phase < every; OIC_ESTATE when no profile is open. */
+oic_status oic_profile_sample(oic_handle* h, int every, int phase);
+
 /* Number of kernels this library has launched in this process. */
 unsigned long long oic_launch_count(void);
 

@@ -81,6 +81,7 @@ _SIGS = {
     "oic_last_ms": (ctypes.c_float, [_VP]),
     "oic_profile_begin": (ctypes.c_int, [_VP, ctypes.c_uint, ctypes.c_int]),
     "oic_profile_end": (ctypes.c_int, [_VP, _FP, ctypes.POINTER(ctypes.c_int)]),
+    "oic_profile_sample": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "oic_launch_count": (ctypes.c_ulonglong, []),
     "oic_selftest": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "oic_enks_update_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
@@ -349,6 +350,11 @@ class Solver:
         for st in (STAGES if stages is None else stages):
             mask |= 1 << STAGES.index(st)
         _check(self._lib.oic_profile_begin(self.h, mask, int(max_launches)), "oic_profile_begin")
+
+    def oic_profile_sample(self, every, phase=0):
+        """Bracket only launch i of a profiled stage in a solve with
+        i % every == phase (oic_profile_sample)."""
+        _check(self._lib.oic_profile_sample(self.h, int(every), int(phase)), "oic_profile_sample")
 
     def oic_profile_end(self):
         """Returns {stage: (total_ms, launches)} for the profiled stages."""

@@ -24,6 +24,7 @@ struct Profiler {
     bool on = false;
     unsigned mask = 0;
     int max = 0, used = 0;
+    int every = 1, phase = 0;              // bracket launch i of a stage in a solve when i % every == phase
     std::vector<cudaEvent_t> ev;
     std::vector<int> stage;
 };
@@ -37,6 +38,7 @@ struct StepGraph {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
     unsigned mask = 0;
+    int every = 1, phase = 0;              // the profiler's sampling at capture
     unsigned long long launches = 0;
     std::vector<cudaEvent_t> cap_ev;       // events named at capture, pairs
     std::vector<cudaGraphNode_t> node;     // their record nodes, same order
@@ -89,6 +91,7 @@ struct oic_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int> obs_host;
     Profiler prof;
+    int stage_seen[OIC_NUM_STAGES] = {};      // launches of each stage in the current solve (and its plant step)
     StepGraph sg[2];                          // [0] plain, [1] with profiling event nodes
     StepGraph* capturing = nullptr;
 
@@ -115,11 +118,12 @@ namespace {
 template <typename F>
 void run_stage(oic_handle* h, int stage, F&& launch)
 {
+    const int seen = h->stage_seen[stage]++;
     if (h->capturing != nullptr) {
         StepGraph& G = *h->capturing;
         cudaEvent_t e[2] = {nullptr, nullptr};
-        const bool rec = ((G.mask >> stage) & 1u) && cudaEventCreate(&e[0]) == cudaSuccess &&
-                         cudaEventCreate(&e[1]) == cudaSuccess;
+        const bool rec = ((G.mask >> stage) & 1u) && seen % G.every == G.phase &&
+                         cudaEventCreate(&e[0]) == cudaSuccess && cudaEventCreate(&e[1]) == cudaSuccess;
         if (rec) cudaEventRecord(e[0], h->st);
         launch();
         g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -135,7 +139,7 @@ void run_stage(oic_handle* h, int stage, F&& launch)
         return;
     }
     Profiler& P = h->prof;
-    const bool rec = P.on && ((P.mask >> stage) & 1u) && P.used < P.max;
+    const bool rec = P.on && ((P.mask >> stage) & 1u) && seen % P.every == P.phase && P.used < P.max;
     if (rec) cudaEventRecord(P.ev[2 * P.used], h->st);
     launch();
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -439,6 +443,7 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
 {
     const oic_config& c = h->cfg;
     const size_t N = c.N, n = c.n, m = c.m, l = c.l, H = c.H;
+    for (int& v : h->stage_seen) v = 0;
     if (c.noise_mode == OIC_NOISE_PHILOX) {
         const size_t e0 = N * l * m, e1 = e0 + H * N * l * m, e2 = e1 + H * N * n * m,
                      e3 = e2 + H * N * l * m, e4 = e3 + H * N * (size_t)h->nc * m;
@@ -535,6 +540,8 @@ bool capture_step(oic_handle* h, StepGraph& G, unsigned mask)
 {
     G.reset();
     G.mask = mask;
+    G.every = h->prof.every;
+    G.phase = h->prof.phase;
     const Layout& L = h->lay;
     const unsigned long long l0 = g_launches.load();
     h->capturing = &G;
@@ -585,7 +592,7 @@ bool run_step_graph(oic_handle* h)
     Profiler& P = h->prof;
     const bool prof = P.on && P.mask != 0;
     StepGraph* G = &h->sg[prof ? 1 : 0];
-    if (prof && G->x && G->mask != P.mask) G->reset();
+    if (prof && G->x && (G->mask != P.mask || G->every != P.every || G->phase != P.phase)) G->reset();
     if (!G->x && !G->failed) capture_step(h, *G, prof ? P.mask : 0);
     if (!G->x) return false;
     if (prof) {
@@ -1048,7 +1055,18 @@ oic_status oic_profile_begin(oic_handle* h, unsigned stage_mask, int max_launche
     P.max = max_launches;
     P.mask = stage_mask;
     P.used = 0;
+    P.every = 1;
+    P.phase = 0;
     P.on = true;
+    return OIC_OK;
+}
+
+oic_status oic_profile_sample(oic_handle* h, int every, int phase)
+{
+    if (!h || every < 1 || phase < 0 || phase >= every) return OIC_EINVAL;
+    if (!h->prof.on) return OIC_ESTATE;
+    h->prof.every = every;
+    h->prof.phase = phase;
     return OIC_OK;
 }
 

@@ -33,6 +33,21 @@ __device__ __forceinline__ void pdl_begin()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// The same launch without programmatic stream serialisation: the kernel
+// starts only after the previous one in the stream has completed.
+template <typename... K, typename... A>
+inline cudaError_t plain_launch(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 template <typename... K, typename... A>
 inline cudaError_t pdl_launch(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args)
 {

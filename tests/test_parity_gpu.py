@@ -161,12 +161,14 @@ def test_philox_mode_matches_oracle_fed_host_philox(cuda_ok):
         assert rel(Xn, X) <= TOL
 
 
-def _philox_steps(wl, steps, profile=None):
+def _philox_steps(wl, steps, profile=None, sample=None):
     s = solver(wl, noise_mode=oic.OIC_NOISE_PHILOX, seed=99)
     xr_all = wl.X_ref_all(steps)
     s.oic_reset_host(wl.X0(), wl.U_init())
     if profile is not None:
         s.oic_profile_begin(stages=profile, max_launches=4096)
+        if sample is not None:
+            s.oic_profile_sample(*sample)
     out = []
     for k in range(steps):
         Ua = np.zeros((wl.l, wl.m), np.float32)
@@ -176,6 +178,42 @@ def _philox_steps(wl, steps, profile=None):
     prof = s.oic_profile_end() if profile is not None else None
     s.close()
     return out, prof
+
+
+@pytest.mark.parametrize("eager", [False, True])
+def test_profile_sampling_brackets_only_the_chosen_launches(cuda_ok, monkeypatch, eager):
+    """oic_profile_sample(every, phase): of a stage's launches in one solve
+    (counted from 0), only those with index % every == phase carry events, in
+    the step graph and in eager launches alike, and the results stay
+    bit-identical to unprofiled steps.  The gain runs once per analysis, H
+    times per solve."""
+    wl = W.small_16()
+    if eager:
+        monkeypatch.setenv("OIC_NO_GRAPH", "1")
+    base, _ = _philox_steps(wl, 3)
+    one, p1 = _philox_steps(wl, 3, profile=["gain"], sample=(wl.H, wl.H // 2))
+    two, p2 = _philox_steps(wl, 3, profile=["gain"], sample=(2, 1))
+    _, pall = _philox_steps(wl, 3, profile=["gain"])
+    assert p1["gain"][1] == 3 and p1["gain"][0] > 0
+    assert p2["gain"][1] == 3 * (wl.H // 2)                # indices 1, 3, ... < H
+    assert pall["gain"][1] == 3 * wl.H
+    for (ba, bx), (oa, ox), (ta, tx) in zip(base, one, two):
+        assert np.array_equal(ba, oa) and np.array_equal(bx, ox)
+        assert np.array_equal(ba, ta) and np.array_equal(bx, tx)
+
+
+def test_profile_sampling_rejects_bad_arguments(cuda_ok):
+    wl = W.small_16()
+    s = solver(wl, noise_mode=oic.OIC_NOISE_PHILOX, seed=99)
+    with pytest.raises(RuntimeError):
+        s.oic_profile_sample(2, 0)                            # no profile open
+    s.oic_profile_begin(stages=["gain"], max_launches=16)
+    for every, phase in ((0, 0), (3, 3), (2, -1)):
+        with pytest.raises(RuntimeError):
+            s.oic_profile_sample(every, phase)
+    s.oic_profile_sample(3, 2)
+    s.oic_profile_end()
+    s.close()
 
 
 @pytest.mark.parametrize("name", ["small_16", "working_64_n32"])
