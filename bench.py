@@ -315,7 +315,7 @@ def run_oic(args, wl):
         stream.synchronize()
         # stage breakdown: a few steps with every stage bracketed by events
         # (untimed); its largest stage is the one the timed region brackets
-        s.oic_profile_begin(max_launches=128 * n_break)
+        s.oic_profile_begin(max_launches=256 * n_break)
         for i in range(n_break):
             s.oic_step(window(args.warmup + i), ur, None, u_out, x_out)
         breakdown = s.oic_profile_end()
