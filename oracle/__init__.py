@@ -16,8 +16,15 @@ Parity status per function (see the tests that pin each one):
                   in the innovation, lambda / normalisation invariance
   enks_solve      pinned: exact linear-Gaussian smoother = weighted least squares
                   (Theorem 1) for a vertical-tap linear CNN, as N*m grows
-  run             pinned: closed-loop cost under control below the uncontrolled
+  run             pinned: for a vertical-tap linear CNN and a non-zero,
+                  time-varying reference, every applied control is the first
+                  control of the Theorem-1 least-squares optimum over the
+                  window k..k+H from the current plant state and the last
+                  applied control, and the plant moves by the exact linear
+                  map; closed-loop cost under control below the uncontrolled
                   cost (qualitative, Numerical Experiments section)
+  closed_loop_cost pinned: a hand-worked S = 2 case with non-zero state,
+                  control and increment terms (tests/golden/closed_loop_cost.json)
   control_expand  pinned: a hand-worked product, T = I
   control_reduce  pinned: column means for T = [1 ... 1], reduce(expand(u)) = u,
                   T = I, rank-deficient T reported

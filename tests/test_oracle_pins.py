@@ -382,6 +382,67 @@ def test_cost_trace_form_equals_vec_kronecker_form():
     assert abs(c - np.sum(D ** 2) / s ** 2) < 1e-8 * c
 
 
+def test_golden_closed_loop_cost_hand_worked():
+    """J with non-zero state, control and increment terms over S = 2 steps:
+    an off-by-one in the reference window, the control reference or the
+    U_{-1} = U_init increment changes the value."""
+    for c in json.load(open(os.path.join(GOLDEN, "closed_loop_cost.json")))["cases"]:
+        J = oracle.closed_loop_cost(np.array(c["X_traj"]), np.array(c["U_traj"]), np.array(c["X_ref_all"]),
+                                    np.array(c["U_ref"]), np.array(c["U_init"]), c["sigma_vx"], c["sigma_vu"],
+                                    c["sigma_w"])
+        assert abs(J - c["J"]) <= 1e-12 * c["J"], (J, c["J"])
+
+
+def test_run_applies_the_theorem1_optimum_of_each_window():
+    """Algorithm 1's receding loop against Theorem 1.  With a vertical-tap
+    linear CNN (x_{t+1} = A x_t + G u_t per column) and isotropic Gaussian
+    noise, the smoother's mean at each control step k is the weighted
+    least-squares optimum of J over the window k..k+H, solved from the plant
+    state X_k and the last applied control U_{k-1}.  So, for a non-zero,
+    time-varying reference and a non-zero U^ref:
+      * every applied control U_k is within sampling error of the optimum's
+        first control u_k (not of u_{k+1}, and not of the optimum for the
+        window k+1..k+H+1 or for a stale U_{k-1});
+      * every returned plan U_hat[k] is within sampling error of the optimum;
+      * the plant advances by the exact linear map X_{k+1} = A X_k + G U_k.
+    The alternatives are checked to lie far outside the tolerance, so a wrong
+    window offset, block or warm start fails this test."""
+    rng = np.random.default_rng(71)
+    n, m, l, H, S, N = 6, 16, 2, 3, 3, 16000
+    sw, svx, svu = 0.3, 0.2, 0.5
+    net, A, G = _vertical_linear_net(n, m, l, rng)
+    x0 = rng.standard_normal((n, m))
+    u_init = 0.5 * rng.standard_normal((l, m))
+    xref_all = rng.standard_normal((S + H + 1, n, m))
+    uref = 0.3 * rng.standard_normal((l, m))
+    nr = np.random.default_rng(72)
+    noise_all = np.stack([np.concatenate([
+        (sw * nr.standard_normal((N, l, m))).ravel(), (sw * nr.standard_normal((H, N, l, m))).ravel(),
+        (svx * nr.standard_normal((H, N, n, m))).ravel(), (svu * nr.standard_normal((H, N, l, m))).ravel()])
+        for _ in range(S)])
+    Xt, Ut, Uh = oracle.run(net, N, H, S, x0, u_init, xref_all, uref, noise_all)
+
+    def optimum(xk, up, xr):
+        return np.stack([_exact_smoother_ls(A, G, xk[:, j], up[:, j], xr[:, :, j], uref[:, j], H, sw, svx, svu)
+                         for j in range(m)], axis=-1)
+
+    tol = 0.05 * sw * 3
+    np.testing.assert_array_equal(Xt[0], x0)
+    up = u_init
+    for k in range(S):
+        np.testing.assert_allclose(Xt[k + 1], A @ Xt[k] + G @ Ut[k], rtol=0, atol=1e-12)
+        opt = optimum(Xt[k], up, xref_all[k:k + H + 1])
+        assert np.abs(Ut[k] - opt[0]).max() < tol
+        assert np.abs(Uh[k] - opt).max() < tol
+        np.testing.assert_array_equal(Uh[k][0], Ut[k])
+        later_window = optimum(Xt[k], up, xref_all[k + 1:k + H + 2])[0]
+        assert np.abs(opt[1] - opt[0]).max() > 4 * tol
+        assert np.abs(later_window - opt[0]).max() > 4 * tol
+        if k > 0:
+            assert np.abs(optimum(Xt[k], u_init, xref_all[k:k + H + 1])[0] - opt[0]).max() > 4 * tol
+        up = Ut[k]
+
+
 @pytest.mark.slow
 def test_closed_loop_cost_below_uncontrolled():
     # Numerical Experiments: under Kalman-MPC the tracking error falls and the

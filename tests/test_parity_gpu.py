@@ -522,3 +522,124 @@ def test_edge_case_solve_matches_oracle(cuda_ok, name, full):
     if full:
         assert rel(X_hat, xh[:, :wl.n]) <= TOL
     s.close()
+
+
+# ------------------------------------------- mixed precision at the 128 x 128 sizes
+# The BF16 kernels hand each CTA a contiguous range of (member group, image
+# row) passes, total / (number of SMs).  The cases below give every CTA tens
+# of passes, so the 8-slot TMEM accumulator ring, the row-mod-8 barrier
+# phases and the issue-ahead window wrap many times; the FP64 cluster gain
+# sees p = 144 = 18 panels of 8 rows on 8 CTAs (block-cyclic, wrapping twice).
+C2_CNN = {
+    # first pair fused + last pair fused: 64 members x 128 rows = 8192 passes
+    "m128_c64_N64": W.large_128().with_(N=64),
+    # five layers: first pair, one per-layer 64 -> 64 kernel, last pair;
+    # two members per tile, 64 groups x 64 rows = 4096 passes
+    "m64_c64x4_N128": W.Workload("mixed_64x64_c64x4", n=64, m=64, l=8, channels=[2, 64, 64, 64, 64, 1], N=128,
+                                 H=2, S=2, ref="blobs", blob_sigma=6.0),
+    # three layers: input kernel, per-layer first layer, last pair; 8192 passes
+    "m64_c64_N256": W.Workload("mixed_64x64_c64", n=64, m=64, l=8, channels=[2, 64, 64, 1], N=256, H=2, S=2,
+                               ref="blobs", blob_sigma=6.0),
+    # 32 channels, one member per 128-position tile (96 does not divide 128)
+    "m96_c32_N64": W.Workload("mixed_96x96_c32_N64", n=96, m=96, l=12, channels=[2, 32, 32, 32, 1], N=64, H=2,
+                              S=2, ref="blobs", blob_sigma=9.0),
+}
+
+
+@pytest.mark.parametrize("name", list(C2_CNN))
+def test_mixed_precision_cnn_at_scale_every_member(cuda_ok, name):
+    """Mixed-mode CNN at sizes where every CTA runs tens of row passes,
+    checked against the FP64 oracle for every member, element by element:
+    the increment X_next - X within 4u in relative L2 and 8u in max norm,
+    u = 2^-9 (BF16 unit roundoff), per member and over the batch."""
+    wl = C2_CNN[name]
+    s = solver(wl, precision=oic.OIC_PREC_MIXED)
+    rng = np.random.default_rng(17)
+    X = (wl.X0()[None] + 0.3 * rng.standard_normal((wl.N, wl.n, wl.m))).astype(np.float32)
+    U = (0.5 * rng.standard_normal((wl.N, wl.l, wl.m))).astype(np.float32)
+    out = dev(np.zeros_like(X))
+    s.oic_cnn_forward(dev(X), dev(U), out)
+    s.oic_sync()
+    got = out.cpu().numpy().astype(np.float64)
+    want = oracle.cnn_step(onet(wl), X, U)
+    inc = want - X
+    u = 2.0 ** -9
+    assert np.linalg.norm(got - want) <= 4 * u * np.linalg.norm(inc)
+    assert np.abs(got - want).max() <= 8 * u * np.abs(inc).max()
+    per_l2 = np.linalg.norm((got - want).reshape(wl.N, -1), axis=1) / np.linalg.norm(inc.reshape(wl.N, -1), axis=1)
+    assert per_l2.max() <= 4 * u, (int(per_l2.argmax()), float(per_l2.max()))
+    s.close()
+
+
+def test_mixed_precision_fp64_gain_at_p144_matches_oracle(cuda_ok):
+    """The mixed-mode analysis alone at p = n + l = 144 observed rows (the
+    FP64 Cholesky's 18 panels wrap twice around its 8-CTA cluster) against
+    the FP64 oracle's textbook analysis: relative L2 <= 1e-4 on the increment
+    and on the ensemble mean (FP32 covariance products, FP64 gain)."""
+    wl = W.large_128().with_(N=64)
+    s = solver(wl, precision=oic.OIC_PREC_MIXED)
+    rng = np.random.default_rng(23)
+    R, p = 200, wl.p
+    assert p == 144 and R <= s.max_rows
+    E = (1.0 + 0.05 * rng.standard_normal((wl.N, R, wl.m))).astype(np.float32)
+    obs = np.sort(rng.choice(R, size=p, replace=False))
+    V = (0.02 * rng.standard_normal((wl.N, p, wl.m))).astype(np.float32)
+    Ybar = (1.2 + 0.1 * rng.standard_normal((p, wl.m))).astype(np.float32)
+    Ed = dev(E)
+    s.oic_enks_update(Ed, obs, dev(V), dev(Ybar))
+    assert s.oic_sync_status() == oic.OIC_OK
+    got = Ed.cpu().numpy()
+    want = oracle.enks_analysis(E, E[:, obs, :] + V, Ybar)
+    assert rel(got - E, want - E) <= TOL
+    assert rel(got.mean(0), want.mean(0)) <= TOL
+    s.close()
+
+
+C2_LOOP = W.large_128().with_(N=64, H=2, S=2)
+
+
+@pytest.mark.slow
+def test_mixed_precision_solve_128_matches_oracle(cuda_ok):
+    """One mixed-mode horizon solve at 128 x 128, l = 16 (p = 144), CNN
+    2-64-64-64-1, N = 64, H = 2, full history, against the FP64 oracle on the
+    same noise: smoothed controls within 4u of BF16 (u = 2^-9) in relative L2,
+    smoothed states within 1e-3."""
+    wl = C2_LOOP
+    s = solver(wl, precision=oic.OIC_PREC_MIXED, keep_full_history=True)
+    Up = (0.01 * np.random.default_rng(29).standard_normal((wl.l, wl.m))).astype(np.float32)
+    xr, ur, nz = wl.X_ref_window(1), wl.U_ref(), wl.noise(1)
+    U_hat = np.zeros((wl.H + 1, wl.l, wl.m), np.float32)
+    X_hat = np.zeros((wl.H + 1, wl.n, wl.m), np.float32)
+    s.oic_solve_host(wl.X0(), Up, xr, ur, nz, U_hat, X_hat)
+    xh = oracle.enks_solve(onet(wl), wl.N, wl.H, wl.X0(), Up, xr, ur, nz)
+    assert rel(U_hat, xh[:, wl.n:wl.n + wl.l]) <= 4 * 2.0 ** -9
+    assert rel(X_hat, xh[:, :wl.n]) <= 1e-3
+    s.close()
+
+
+@pytest.mark.slow
+def test_mixed_precision_closed_loop_128_cost_within_half_percent(cuda_ok):
+    """Two receding-horizon control steps of the mixed mode at 128 x 128
+    (CNN 2-64-64-64-1, l = 16, N = 64, H = 2) against the FP64 oracle fed the
+    same noise: cost J within 0.5%, applied controls within 4u, states within
+    1e-3."""
+    wl = C2_LOOP
+    S = wl.S
+    s = solver(wl, precision=oic.OIC_PREC_MIXED)
+    xr_all = wl.X_ref_all(S)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    Ut = np.zeros((S, wl.l, wl.m), np.float32)
+    Xt = np.zeros((S + 1, wl.n, wl.m), np.float32)
+    Xt[0] = wl.X0()
+    for k in range(S):
+        s.oic_step_host(xr_all[k:k + wl.H + 1], wl.U_ref(), wl.noise(k), Ut[k], Xt[k + 1])
+    Xo, Uo, _ = oracle.run(onet(wl), wl.N, wl.H, S, wl.X0(), wl.U_init(), xr_all, wl.U_ref(),
+                           wl.noise_all(S))
+    jg = oracle.closed_loop_cost(Xt, Ut, xr_all, wl.U_ref(), wl.U_init(), wl.sigma_vx, wl.sigma_vu,
+                                 wl.sigma_w)
+    jo = oracle.closed_loop_cost(Xo, Uo, xr_all, wl.U_ref(), wl.U_init(), wl.sigma_vx, wl.sigma_vu,
+                                 wl.sigma_w)
+    assert abs(jg - jo) <= 5e-3 * abs(jo)
+    assert rel(Ut, Uo) <= 4 * 2.0 ** -9
+    assert rel(Xt, Xo) <= 1e-3
+    s.close()
