@@ -280,10 +280,11 @@ oic_status oic_selftest(oic_handle* h, int* result);
  * paper has no counterpart: this is a deployment variant of the same
  * ensemble Kalman analysis.
  *
- * Who needs it: code that may not call cudaMalloc at all -- work issued
- * inside a CUDA graph capture, a real-time loop that must never reach the
- * allocator after start-up, a plug-in whose host application owns all GPU
- * memory, or an embedding with a fixed memory map.  Such a caller cannot
+ * Who needs it: code that may not call cudaMalloc at all -- a real-time
+ * loop that must never reach the allocator after start-up (an allocation can
+ * block or fail at any moment), a plug-in whose host application owns all
+ * GPU memory and forbids allocations of its own, or an embedding with a
+ * fixed memory map.  Such a caller cannot
  * provide the workspace oic_bind needs, so this entry point takes no handle
  * and keeps every intermediate (split-K partials, innovations, covariances,
  * gain, row tables, status) in one device array of OIC_STATIC_SCRATCH_BYTES
@@ -300,11 +301,14 @@ oic_status oic_selftest(oic_handle* h, int* result);
  *   Ybar         [p][m] pseudo-observation
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream)
  * Returns OIC_OK, OIC_ENOTSPD (the update was skipped; E unchanged),
- * OIC_EINVAL on bad arguments, or OIC_ENOMEM when these sizes need more than
+ * OIC_EINVAL on bad arguments (including E, V or Ybar not in the current
+ * device's memory), OIC_ECUDA when the CUDA runtime fails (no device), or
+ * OIC_ENOMEM when these sizes need more than
  * OIC_STATIC_SCRATCH_BYTES, which is about
  *   4 (N p m + s (R + p)(m + p) + (R + p) m + p R) + 8 (R + p) p bytes,
- * s = split count (<= 148 / ceil((R + p) / 64)).  It allocates nothing and
- * synchronises the stream before returning (it reads the status word).
+ * s = split count (<= 148 / ceil((R + p) / 64)).  It allocates nothing; it
+ * copies the row table from host memory and reads the status word back,
+ * synchronising the stream before it returns.
  *
  * The first call on each device looks up the scratch's device address with
  * that device current; make that first call before any stream capture.

@@ -588,13 +588,12 @@ int fused_launch(const float* X, long x_ms, const float* U, long u_ms, float* Xo
 {
     const size_t smem = fused_smem<C, G>(n, l);
     if (smem > 227 * 1024) return 1;
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(cnn_fused_kernel<C, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024) != cudaSuccess)
-            return 1;
-        configured = true;
-    }
+    static DeviceOnce configured;
+    if (!configured.run([] {
+            return cudaFuncSetAttribute(cnn_fused_kernel<C, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024) == cudaSuccess;
+        }))
+        return 1;
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
     pdl_launch(cnn_fused_kernel<C, G>, grid, FT, smem, st, X, x_ms, U, u_ms, Xout, o_ms, Bmat, Nb, n, l, b1, b2, b3,

@@ -105,12 +105,12 @@ extern "C" oic_status oic_control_reduce(const float* U, int l, int m, const flo
     if (!U || !T || !u || mu < 1 || mu > 64 || mu > m || m > 1024 || l < 1 || l > 256) return OIC_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t smem = sizeof(double) * ((size_t)mu * mu + (size_t)l * mu);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(control_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * (64 * 64 + 256 * 64)));
-        attr_set = true;
-    }
+    static DeviceOnce attr_set;
+    if (!attr_set.run([] {
+            return cudaFuncSetAttribute(control_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * (64 * 64 + 256 * 64))) == cudaSuccess;
+        }))
+        return OIC_ECUDA;
     pdl_launch(control_reduce_kernel, 1, CT_T, smem, st, U, l, m, T, mu, u);
     int status = 0;
     if (cudaMemcpyFromSymbolAsync(&status, g_ctl_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

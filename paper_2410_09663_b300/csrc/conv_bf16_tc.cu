@@ -941,13 +941,12 @@ int bf16_layer(const __nv_bfloat16* in, __nv_bfloat16* out, const void* wpk, con
 {
     using S = BS<CI, CO, MODE, W>;
     constexpr int G = S::G;
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(conv_bf16_kernel<CI, CO, MODE, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 S::SMEM) != cudaSuccess)
-            return 1;
-        configured = true;
-    }
+    static DeviceOnce configured;
+    if (!configured.run([] {
+            return cudaFuncSetAttribute(conv_bf16_kernel<CI, CO, MODE, W>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) == cudaSuccess;
+        }))
+        return 1;
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
     pdl_launch(conv_bf16_kernel<CI, CO, MODE, W>, grid, S::NT, S::SMEM, st, 
@@ -985,13 +984,12 @@ int bf16_fused_layer(const __nv_bfloat16* in, const float* X, long x_ms, float* 
 {
     using S = BS<C, C, MODE_FUSED, W>;
     constexpr int G = S::G;
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(conv_bf16_fused_kernel<C, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
-            cudaSuccess)
-            return 1;
-        configured = true;
-    }
+    static DeviceOnce configured;
+    if (!configured.run([] {
+            return cudaFuncSetAttribute(conv_bf16_fused_kernel<C, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        S::SMEM) == cudaSuccess;
+        }))
+        return 1;
     const long tiles = (long)((Nb + G - 1) / G) * n;
     const int grid = (int)(tiles < n_sm ? tiles : n_sm);
     pdl_launch(conv_bf16_fused_kernel<C, W>, grid, S::NT, S::SMEM, st, in, X, x_ms, Xout, o_ms,

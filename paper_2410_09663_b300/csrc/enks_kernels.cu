@@ -649,12 +649,11 @@ template <int SL>
 void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st, float* Aop)
 {
     const size_t smem = gain_chol_smem(p);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(gain_chol_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)gain_chol_smem(32 * SL));
-        attr_set = true;
-    }
+    static DeviceOnce attr_set;
+    attr_set.run([] {
+        return cudaFuncSetAttribute(gain_chol_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)gain_chol_smem(32 * SL)) == cudaSuccess;
+    });
     const int grid = R > 0 ? (R + GC_W - 1) / GC_W : 1;
     pdl_launch(gain_chol_kernel<SL>, grid, GC_T, smem, st, C, R, p, Kt, status, Aop);
 }
@@ -794,12 +793,13 @@ void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs,
     const int M = act.count + obs.count, p = obs.count;
     dim3 grid((M + SBM - 1) / SBM, (p + SBN - 1) / SBN, splits);
     const size_t smem = stats_smem_bytes(m);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(stats_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(stats_kernel<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static DeviceOnce attr_set;
+    attr_set.run([] {
+        return cudaFuncSetAttribute(stats_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                   cudaSuccess &&
+               cudaFuncSetAttribute(stats_kernel<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                   cudaSuccess;
+    });
     // loader chunks: SBM m / 4 and SBN m / 4 pieces over S_NT threads
     if (m <= 64)
         pdl_launch(stats_kernel<4, 4>, grid, S_NT, smem, st, E, ms, N, m, act, obs, V, Yx, Yu, n_yx, part1, part2, Dbuf,
@@ -845,11 +845,11 @@ void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt,
                    cudaStream_t st)
 {
     const size_t smem = sizeof(float) * 2 * (size_t)p * (UBM + SPAD);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static DeviceOnce attr_set;
+    attr_set.run([] {
+        return cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+               cudaSuccess;
+    });
     dim3 grid((act.count + UBM - 1) / UBM, N * ((m + UBN - 1) / UBN));
     pdl_launch(update_kernel, grid, UT, smem, st, E, ms, m, act, Kt, p, Dbuf);
 }

@@ -310,12 +310,12 @@ void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt
 {
     pdl_launch(chol64c_kernel, CL, C64_T, 0, st, C, R, p, L, status, bad);
     const size_t smem = sizeof(double) * ((size_t)p * (p | 1) + p);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(solve64s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * ((size_t)C64_PMAX * (C64_PMAX | 1) + C64_PMAX)));
-        attr_set = true;
-    }
+    static DeviceOnce attr_set;
+    attr_set.run([] {
+        return cudaFuncSetAttribute(solve64s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(double) * ((size_t)C64_PMAX * (C64_PMAX | 1) + C64_PMAX))) ==
+               cudaSuccess;
+    });
     pdl_launch(solve64s_kernel, (R + S64_W - 1) / S64_W, 32 * S64_W, smem, st, C, R, p, L, bad, Kt);
 }
 

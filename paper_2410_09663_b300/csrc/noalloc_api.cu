@@ -1,10 +1,11 @@
 // noalloc_api.cu -- oic_enks_update_static: the ensemble Kalman analysis
 // for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs inside a CUDA
-// graph being captured, a real-time control loop that must never reach the
-// allocator after start-up, a plug-in whose host process owns the GPU memory
-// pool, or firmware-like embeddings with a fixed memory map.  For them this
+// Some callers cannot call cudaMalloc at all: a real-time control loop that
+// must never reach the allocator after start-up (an allocation can block or
+// fail at any time), a plug-in whose host process owns the GPU memory pool
+// and forbids allocations of its own, or an embedding with a fixed memory
+// map.  For them this
 // entry point runs the same kernels as oic_enks_update but keeps every
 // intermediate (split-K partial sums, innovations, covariances, gain, row
 // tables, status word) in one file-scope device array of fixed size,
@@ -46,6 +47,20 @@ oic_status scratch_for_current_device(unsigned char** out)
     return OIC_OK;
 }
 
+// True when p is device memory of the current device (or managed memory,
+// which the current device can reach).  A pointer into another GPU's memory
+// or into pageable host memory is refused before anything is launched.
+bool on_current_device(const void* p, int dev)
+{
+    cudaPointerAttributes a = {};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" oic_status oic_enks_update_static(int N, int R, int m, int p, const int* obs_rows, float* E,
@@ -76,6 +91,10 @@ extern "C" oic_status oic_enks_update_static(int N, int R, int m, int p, const i
     unsigned char* base = nullptr;
     const oic_status st = scratch_for_current_device(&base);
     if (st != OIC_OK) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return OIC_ECUDA;
+    if (!on_current_device(E, dev) || !on_current_device(V, dev) || !on_current_device(Ybar, dev))
+        return OIC_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
     // row tables: active rows 0 .. R-1, then the observed rows (copied from

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <utility>
 
 #include "oic.h"
@@ -21,6 +22,28 @@ namespace oic {
 
 // Values of the device status word.
 enum : int { DEV_OK = 0, DEV_NOTSPD = 1, DEV_TIMEOUT = 2 };
+
+// cudaFuncSetAttribute acts on the context of the current device only, so a
+// kernel's raised shared-memory limit must be set once per device.  Each call
+// site keeps one DeviceOnce; run(f) calls f (returning true on success) the
+// first time it is reached with each device current, from any host thread.
+class DeviceOnce {
+  public:
+    template <class F>
+    bool run(F&& f)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return f();
+        std::lock_guard<std::mutex> lock(mu_);
+        if (!done_[dev]) done_[dev] = f();
+        return done_[dev];
+    }
+
+  private:
+    static constexpr int kMaxDevices = 64;
+    std::mutex mu_;
+    bool done_[kMaxDevices] = {};
+};
 
 // Programmatic dependent launch: every kernel is launched with programmatic
 // stream serialisation, and its first statements let the next kernel in the

@@ -233,11 +233,11 @@ void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* 
     const int items = (int)((NM + UT_N - 1) / UT_N) * rtiles;
     const int grid = items < 148 ? items : 148;
     const size_t smem = update_tc_smem();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    static DeviceOnce attr_set;
+    attr_set.run([smem] {
+        return cudaFuncSetAttribute(update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+               cudaSuccess;
+    });
     pdl_launch(update_tc_kernel, grid, UT_NT, smem, st, E, ms, m, act, Aop, Bd, NM, KCH, rtiles, items, err);
 }
 

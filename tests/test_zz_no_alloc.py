@@ -1,9 +1,10 @@
 """oic_enks_update_static: the ensemble Kalman analysis for callers that
-cannot allocate device memory (graph capture, allocator-free real-time
-loops, hosts that own the GPU memory pool).  It keeps all of its scratch in a
-fixed device array inside the library, so its results must equal those of
-the workspace-based oic_enks_update, call after call, even though every call
-reuses (and leaves behind) the same scratch.
+cannot allocate device memory (real-time loops that must never reach the
+allocator after start-up, plug-ins whose host application owns the GPU
+memory pool).  It keeps all of its scratch in a fixed device array inside the
+library, so its results must equal those of the workspace-based
+oic_enks_update -- and the FP64 oracle's analysis -- call after call, even
+though every call reuses (and leaves behind) the same scratch.
 
 This file is collected last so a failure here never hides the other tests.
 """
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import paper_2410_09663_b300 as oic
 from paper_2410_09663_b300 import workloads as W
 
@@ -66,3 +68,27 @@ def test_static_scratch_update_matches_workspace_update_twice(cuda_ok):
         ref, got = E_ref.cpu().numpy(), E_st.cpu().numpy()
         assert _rel(got - E, ref - E) <= TOL
         assert _rel(got.mean(0), ref.mean(0)) <= TOL
+        want = oracle.enks_analysis(E, E[:, obs, :] + V, Ybar)
+        assert _rel(got - E, want - E) <= TOL
+        assert _rel(got.mean(0), want.mean(0)) <= TOL
+
+
+@pytest.mark.gpu
+def test_static_refuses_host_pointers(cuda_ok):
+    """E, V and Ybar must be memory of the current device: pageable host
+    arrays are refused on the host, before anything is launched."""
+    import torch
+    lib = oic.load()
+    N, R, m, p = 4, 8, 16, 4
+    rows = np.arange(p, dtype=np.int32)
+    E = np.ones((N, R, m), np.float32)
+    V = np.zeros((N, p, m), np.float32)
+    Y = np.zeros((p, m), np.float32)
+    st = lib.oic_enks_update_static(N, R, m, p, rows.ctypes.data, E.ctypes.data, V.ctypes.data, Y.ctypes.data,
+                                    None)
+    assert st == oic.OIC_EINVAL
+    Ed = torch.from_numpy(E).cuda()
+    st = lib.oic_enks_update_static(N, R, m, p, rows.ctypes.data, ctypes.c_void_p(Ed.data_ptr()), V.ctypes.data,
+                                    Y.ctypes.data, None)
+    assert st == oic.OIC_EINVAL
+    np.testing.assert_array_equal(Ed.cpu().numpy(), E)
