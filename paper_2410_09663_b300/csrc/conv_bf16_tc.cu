@@ -101,14 +101,17 @@ __host__ __device__ constexpr uint32_t desc_lo(uint32_t saddr, uint32_t lbo)
 {
     return ((saddr & 0x3FFFFu) >> 4) | (((lbo >> 4) & 0x3FFFu) << 16);
 }
+// One MMA, called by the whole issuing warp with warp-uniform operands; the
+// elected lane issues it (the operands stay in uniform registers).
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
-        "{\n\t.reg .b64 da, db;\n\t.reg .pred p;\n\t"
+        "{\n\t.reg .b64 da, db;\n\t.reg .pred p, e;\n\t"
         "mov.b64 da, {%1, %5};\n\t"
         "mov.b64 db, {%2, %5};\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n\t}\n" ::"r"(d_tmem),
         "r"(a_lo), "r"(b_lo), "r"(idesc), "r"(acc), "r"(DESC_HI)
         : "memory");
 }
@@ -322,22 +325,22 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
             __syncwarp();
         } else if (warp == S::ISSUE_WARP) {
             // ============ MMAs: input row j ============
-            if (lane == 0) {
+            {  // the whole warp: an elected lane issues
                 const uint32_t dIn = desc_lo(s0 + S::OFF_IN, S::PLANE);
                 const uint32_t dB = desc_lo(s0 + S::OFF_B, S::NB * 16);
                 // output row j+1 takes the ring slot of row j+1-NS, drained in pass
                 // j+2-NS
                 constexpr int LAG = S::NS - 2;
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
-                    if (j - LAG >= f_lo) wait(BB_PASS + ((j - LAG) & (S::NS - 1)));
-                    wait(BB_FULL + j % S::NIN);
+                    if (j - LAG >= f_lo) wait_w(BB_PASS + ((j - LAG) & (S::NS - 1)));
+                    wait_w(BB_FULL + j % S::NIN);
                     issue_row<S, CO>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
-                    tc::mma_commit(mb + BB_FREE + j % S::NIN);
-                    tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
+                    tc::mma_commit_elect(mb + BB_FREE + j % S::NIN);
+                    tc::mma_commit_elect(mb + BB_HDONE + (j & (S::NS - 1)));
                 }
                 // the remaining drain passes
                 for (int k = f_hi + 1 - LAG; k <= f_hi + 1 && !failed; ++k)
-                    if (k >= f_lo && k <= (ye < n ? ye : n)) wait(BB_PASS + (k & (S::NS - 1)));
+                    if (k >= f_lo && k <= (ye < n ? ye : n)) wait_w(BB_PASS + (k & (S::NS - 1)));
             }
             __syncwarp();
         } else {
@@ -504,7 +507,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
             __syncwarp();
         } else if (warp == S::ISSUE_WARP) {
             // ============ MMAs of both layers ============
-            if (lane == 0) {
+            {  // the whole warp: an elected lane issues
                 const uint32_t dIn = desc_lo(s0 + S::OFF_IN, S::PLANE);
                 const uint32_t dB = desc_lo(s0 + S::OFF_B, S::NB * 16);
                 const uint32_t dH2 = desc_lo(s0 + S::OFF_H2, S::PLANE);
@@ -512,35 +515,35 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
                 // last layer of hidden row h (in its shared-memory slot h mod 2)
                 auto issue_last = [&](int h) {
                     if (!Hv(h) || failed) return;
-                    if (h - 2 >= r_lo) wait(BB_LPASS + (h & 1));      // its TMEM slot, read for row h-2
+                    if (h - 2 >= r_lo) wait_w(BB_LPASS + (h & 1));      // its TMEM slot, read for row h-2
                     constexpr uint32_t id = tc::idesc_f16(BM, 16, true);
                     const uint32_t a = dH2 + (h & 1) * (S::OUTROW / 16);
 #pragma unroll
                     for (int ks = 0; ks < C / 16; ++ks)
                         mma_bf16(tmem + T_L + (h & 1) * 16, a + (2 * ks * S::PLANE) / 16 + G,
                                  dBL + (ks * 2 * 16 * 16) / 16, id, ks > 0 ? 1u : 0u);
-                    tc::mma_commit(mb + BB_LDONE + (h & 1));
+                    tc::mma_commit_elect(mb + BB_LDONE + (h & 1));
                 };
                 for (int j = f_lo; j <= f_hi && !failed; ++j) {
                     // hidden output row j+1 takes the ring slot of row j-3, drained
                     // in pass j-2, which also put hidden row j-3 in shared memory
                     if (j - 2 >= f_lo) {
-                        wait(BB_PASS + ((j - 2) & (S::NS - 1)));
+                        wait_w(BB_PASS + ((j - 2) & (S::NS - 1)));
                         issue_last(j - 3);
                     }
-                    wait(BB_FULL + j % S::NIN);
+                    wait_w(BB_FULL + j % S::NIN);
                     issue_row<S, C>(tmem, j, j == f_lo, dIn + (j % S::NIN) * (S::INROW / 16), dB);
-                    tc::mma_commit(mb + BB_FREE + j % S::NIN);
-                    tc::mma_commit(mb + BB_HDONE + (j & (S::NS - 1)));
+                    tc::mma_commit_elect(mb + BB_FREE + j % S::NIN);
+                    tc::mma_commit_elect(mb + BB_HDONE + (j & (S::NS - 1)));
                 }
                 for (int k = f_hi - 1; k <= hlast && !failed; ++k)
                     if (k >= f_lo) {
-                        wait(BB_PASS + (k & (S::NS - 1)));
+                        wait_w(BB_PASS + (k & (S::NS - 1)));
                         issue_last(k - 1);
                     }
                 // the last layer's drains of the final two hidden rows
                 for (int h = r_hi - 1; h <= r_hi && !failed; ++h)
-                    if (Hv(h)) wait(BB_LPASS + (h & 1));
+                    if (Hv(h)) wait_w(BB_LPASS + (h & 1));
             }
             __syncwarp();
         } else if (warp >= S::NDW) {
@@ -781,7 +784,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
         auto Ov = [&](int h) { return h >= ys && h < ye; };
 
         if (warp == F::ISSUE_WARP) {
-            if (lane == 0) {
+            {  // the whole warp: an elected lane issues
                 const uint32_t dA0 = desc_lo(s0 + F::OFF_A0, F::PLANE);
                 const uint32_t dW0 = desc_lo(s0 + F::OFF_W0, S0::NB * 16);
                 const uint32_t dA1 = desc_lo(s0 + F::OFF_A1, F::PLANE);
@@ -790,23 +793,23 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                 auto issue_second = [&](int j) {
                     if (!Rv(j) || failed) return;
                     issue_row<S1, C>(tmem + F::T_B, j, j == r_lo, dA1 + (j & 1) * (F::IN1 / 16), dW1);
-                    tc::mma_commit(mb + FB_L1 + (j & 1));
+                    tc::mma_commit_elect(mb + FB_L1 + (j & 1));
                 };
                 for (int f = f_lo; f <= f_hi && !failed; ++f) {
                     // pass f-2 drained first-layer output row f-3 (its ring A slot is
                     // the one row f+1 starts in) and second-layer output row f-5
                     if (f - 2 >= f_lo) {
-                        wait(FB_PASS + ((f - 2) & 3));
+                        wait_w(FB_PASS + ((f - 2) & 3));
                         issue_second(f - 3);
                     }
-                    wait(FB_A0FULL + (f & 3));
+                    wait_w(FB_A0FULL + (f & 3));
                     issue_row<S0, C>(tmem, f, f == f_lo, dA0 + (f & 3) * (F::IN0 / 16), dW0);
-                    tc::mma_commit(mb + FB_A0FREE + (f & 3));
-                    tc::mma_commit(mb + FB_HDA + (f & 1));
+                    tc::mma_commit_elect(mb + FB_A0FREE + (f & 3));
+                    tc::mma_commit_elect(mb + FB_HDA + (f & 1));
                 }
                 for (int k = f_hi - 1; k <= last && !failed; ++k)
                     if (k >= f_lo) {
-                        wait(FB_PASS + (k & 3));
+                        wait_w(FB_PASS + (k & 3));
                         issue_second(k - 1);
                     }
             }

@@ -52,6 +52,19 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
         : "memory");
 }
 
+// The same commit from a whole warp whose lanes agree on `mbar`: the elected
+// lane (the lowest active one, so the lane that issued the warp's MMAs
+// through an elected predicate as well) commits.
+__device__ __forceinline__ void mma_commit_elect(uint64_t* mbar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(
+            smem_u32(mbar))
+        : "memory");
+}
+
 // Arrive once on `mbar` when every tcgen05 operation issued so far by this
 // thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* mbar)
