@@ -547,6 +547,7 @@ def run_mix(args, name):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wls = workloads.BATCHES[name](seed=2024 + 1000 * rank)
+    P_ = len(wls)
     stream = torch.cuda.Stream(device=dev)
     solvers, refs = [], []
     S_ref = args.steps + args.warmup + 8
@@ -567,26 +568,45 @@ def run_mix(args, name):
                 xr.copy_(r[k:k + w.H + 1])
                 ur.zero_()
 
-        for k in range(args.warmup):
-            fill(k)
-            batch.step()
-        batch.sync()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        launches0 = oic.oic_launch_count()
-        with ClockSampler(local) as clk:
-            for i in range(args.steps):
-                flush.fill_(float(i))
-                ev[i][0].record(stream)
-                fill(args.warmup + i)
-                batch.step()
-                ev[i][1].record(stream)
-            batch.sync()
-        launches = oic.oic_launch_count() - launches0
-        per_step = [a.elapsed_time(c) for a, c in ev]
+        def time_batch(bt):
+            for k in range(args.warmup):
+                fill(k)
+                bt.step()
+            bt.sync()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            l0 = oic.oic_launch_count()
+            with ClockSampler(local) as ck:
+                for i in range(args.steps):
+                    flush.fill_(float(i))
+                    ev[i][0].record(stream)
+                    fill(args.warmup + i)
+                    bt.step()
+                    ev[i][1].record(stream)
+                bt.sync()
+            return [a.elapsed_time(c) for a, c in ev], oic.oic_launch_count() - l0, ck
+
+        per_step, launches, clk = time_batch(batch)
+        t_rule = sum(per_step) / 1e3
+        tuned = None
+        if args.tune:
+            # every problem's plan chosen by the autotuner (timed alone, cached
+            # by shape), then the batch graph captured again with those plans
+            t0 = time.perf_counter()
+            ms_r, ms_t = batch.autotune(reps=2)
+            t_tune = time.perf_counter() - t0
+            plans = [sv.oic_get_plan()[0] for sv in solvers]
+            per_step, launches, clk = time_batch(batch)
+            tuned = {"tuner": "oic_batch_autotune: one choice for all problems, timed as whole batch steps",
+                     "tuner_ms_rule": ms_r, "tuner_ms_tuned": ms_t,
+                     "plans_distinct": len({tuple(sorted(p.items())) for p in plans}),
+                     "plan_of_first_problem": plans[0],
+                     "tuning_s": t_tune,
+                     "rule_value": job_value(P_ * args.steps, world, t_rule),
+                     "note": "value is with the tuned plans; rule_value the same batch with the built-in rules"}
         t_batch = sum(per_step) / 1e3
         # the same problems one after another, each through its own step graph
         k_seq = min(args.steps, 3)
@@ -620,7 +640,9 @@ def run_mix(args, name):
         t_e2e = time.perf_counter() - t0
     h2d = sum((w.H + 1) * w.n * w.m * 4 for w in wls)
     d2h = sum((w.l + w.n) * w.m * 4 for w in wls)
-    t_batch, t_seq, t_e2e = max_over_ranks([t_batch, t_seq, t_e2e], world, dev)
+    t_batch, t_seq, t_e2e, t_rule = max_over_ranks([t_batch, t_seq, t_e2e, t_rule], world, dev)
+    if tuned is not None:
+        tuned["rule_value"] = job_value(P_ * args.steps, world, t_rule)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -643,7 +665,8 @@ def run_mix(args, name):
                    "parallelism": "replicas" if world > 1 else "single",
                    "sequential_value": job_value(P * k_seq, world, t_seq),
                    "sequential": "the same problems one after another, each through its own step graph",
-                   "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+                   "p50_step_ms": lat[len(lat) // 2], "p99_step_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                   "plans": tuned if tuned is not None else "built-in rules (no --tune)"},
         "roofline": None,
         "e2e": {"value": job_value(P * args.steps, world, t_e2e), "unit": "control steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -730,7 +753,7 @@ def run_cov(args, wl):
 SERVE_METRIC = "served control requests/s (Poisson arrivals, continuous batching)"
 
 
-def run_serve(args, rate=200.0, budget_gb=150.0):
+def run_serve(args, rate=200.0):
     """Serving loop: Poisson arrivals of control requests (one control step
     of one problem each) over the mix64 problem population, served with
     continuous batching and admission by HBM footprint.  Reports the achieved
@@ -744,6 +767,7 @@ def run_serve(args, rate=200.0, budget_gb=150.0):
         return 0                                        # one server per node
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    budget_gb = args.budget_gb
     count = args.steps if args.steps != 200 else 10000
     wls = workloads.mix64(seed=2024)
     arrivals = serving.poisson_arrivals(rate, count, len(wls), seed=77)
@@ -766,6 +790,7 @@ def run_serve(args, rate=200.0, budget_gb=150.0):
     with ClockSampler(0) as clk:
         rec, _, wall = srv2.run(arrivals)
     launches = oic.oic_launch_count() - launches0
+    overlap = serving.max_overlap(srv2.device_intervals)
     lat = sorted(1e3 * (r[4] - r[2]) for r in rec)
     svc = sorted(1e3 * (r[4] - r[3]) for r in rec)
     span = max(r[4] for r in rec) - min(r[2] for r in rec)
@@ -798,6 +823,7 @@ def run_serve(args, rate=200.0, budget_gb=150.0):
                    "problems": len(wls), "sizes": "mix64 (grids {32,64,96,128}^2, N {64..512}, H 5..20)",
                    "hbm_budget_bytes": int(budget_gb * 1e9), "footprint_all_problems_bytes": int(footprint),
                    "evictions": int(sum(p.evictions for p in srv2.problems.values())),
+                   "max_steps_in_flight_on_device": int(overlap),
                    "latency_ms_p50": pick(lat, 0.5), "latency_ms_p99": pick(lat, 0.99),
                    "latency_ms_max": lat[-1], "service_ms_p50": pick(svc, 0.5), "service_ms_p99": pick(svc, 0.99),
                    "wall_s": wall,
@@ -825,6 +851,10 @@ def main(argv=None):
     ap.add_argument("--workload", default="working_64")
     ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", action="store_true",
+                    help="batch mode: autotune every problem's plan and time the batch with the tuned plans")
+    ap.add_argument("--budget-gb", type=float, default=150.0,
+                    help="serving mode: HBM budget for admission (GB)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--members", type=int, default=0,
                     help="ensemble size N other than the workload's (smaller cases for profiling)")

@@ -273,6 +273,60 @@ unsigned long long oic_launch_count(void);
  * completed.  Synchronous. */
 oic_status oic_selftest(oic_handle* h, int* result);
 
+/* ------------------------------------------------------ scheduling plans
+ * How a handle's kernels are laid out on the GPU; the paper has no
+ * counterpart (these choices schedule the same arithmetic).  A field of 0
+ * means the built-in rule.
+ *   stats_splits  member splits of the covariance products of Eq.
+ *                 (Ybar-sample-mean-cov): the sums over the N m samples are
+ *                 cut into this many partial sums (1 .. limits.stats_splits).
+ *                 The partial sums are added in another grouping, so results
+ *                 move at the level of FP32 rounding.
+ *   update_ctas   CTAs of the persistent tensor-core member update of Eq.
+ *                 (ensemble-based-Kalman-update-samplewise), 1 ..
+ *                 limits.update_ctas.  Every value gives bit-identical
+ *                 results (each output tile is computed the same way).
+ *   cnn_ctas      CTAs of the persistent CNN kernels (the fused FP32 kernel,
+ *                 the BF16 and the per-layer tensor-core convolutions), 1 ..
+ *                 limits.cnn_ctas (the SM count).  Bit-identical results for
+ *                 every value. */
+typedef struct {
+    int stats_splits;
+    int update_ctas;
+    int cnn_ctas;
+} oic_plan;
+
+/* The plan in use with every rule resolved to its value (stats_splits: at
+ * the last assimilation time, whose row count is the largest) and, if
+ * limits is not NULL, the largest value each field accepts.  OIC_EINVAL on
+ * NULL h or plan. */
+oic_status oic_get_plan(const oic_handle* h, oic_plan* plan, oic_plan* limits);
+
+/* Sets the plan (0 fields: the rule).  The captured step graphs are dropped
+ * and captured again at the next step.  OIC_EINVAL when a field is negative
+ * or above its limit. */
+oic_status oic_set_plan(oic_handle* h, const oic_plan* plan);
+
+/* Chooses the plan by timing: one field at a time (cnn_ctas, then
+ * stats_splits, then update_ctas), each candidate value runs one untimed
+ * control step and then `reps` control steps between CUDA events on the
+ * bound stream (replays of the step graph in the device-noise mode, launches
+ * one by one otherwise), and a value replaces the current one only if it is
+ * at least 1% faster.  The inputs of these steps are zero references and
+ * device-drawn noise; the plant state, the Philox solve index and the bound
+ * stream's ordering are restored afterwards, so the next oic_step continues
+ * exactly where the caller left off.  The winner is stored in a process-wide
+ * cache keyed by the problem's shape (sizes, channels, precision, history
+ * mode, constraint rows, SM count); a later call for the same shape takes it
+ * from there without timing unless flags has OIC_TUNE_FORCE.  chosen gets the
+ * plan; ms_rule / ms_tuned (may be NULL) the milliseconds per control step
+ * with the rule plan and with the chosen plan (both -1 when the plan came from
+ * the cache).  Synchronous.  OIC_ESTATE unless h is bound with a plant
+ * (oic_reset) and the stage profiler is off; OIC_EINVAL unless 1 <= reps <=
+ * 1000. */
+#define OIC_TUNE_FORCE 1
+oic_status oic_autotune(oic_handle* h, int reps, int flags, oic_plan* chosen, float* ms_rule, float* ms_tuned);
+
 /* Size of the fixed device scratch behind oic_enks_update_static. */
 #define OIC_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 
@@ -396,6 +450,22 @@ oic_status oic_batch_create(oic_handle* const* handles, int count, void* cuda_st
  * asynchronously on the batch's stream.  Inputs must be in place, in stream
  * order, before the call. */
 oic_status oic_batch_step(oic_batch* b);
+
+/* Chooses one plan for every problem of the batch by timing whole batch
+ * steps (the problems share the GPU, so the best choice for a problem alone
+ * need not be the best in the mix): CNN CTAs as a fraction of the SMs, the
+ * member update's CTAs, and the covariance splits as a fraction of each
+ * problem's rule, one field at a time, each candidate a captured batch graph
+ * run once untimed and `reps` times between CUDA events on the batch's
+ * stream; a value replaces the current one only if at least 1% faster.  The
+ * batch graph is captured again with the chosen plans (each handle's plan is
+ * set; oic_get_plan reads it).  Every handle's state is restored afterwards;
+ * the input slots (oic_io_slots: X_ref, U_ref) hold zeros after the call, so
+ * fill them before the next oic_batch_step.  ms_rule / ms_tuned (may be
+ * NULL): ms per batch step with the built-in rules and with the chosen
+ * plans.  Synchronous.  OIC_EINVAL unless
+ * 1 <= reps <= 1000; OIC_ESTATE if a handle's profiler is on. */
+oic_status oic_batch_autotune(oic_batch* b, int reps, float* ms_rule, float* ms_tuned);
 
 /* Waits for the batch's stream; returns the first non-OK device status of
  * the handles, in handle order (and clears every handle's status). */

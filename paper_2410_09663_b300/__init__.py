@@ -52,6 +52,15 @@ class oic_constraints(ctypes.Structure):
     ]
 
 
+class oic_plan(ctypes.Structure):
+    _fields_ = [("stats_splits", ctypes.c_int), ("update_ctas", ctypes.c_int), ("cnn_ctas", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+OIC_TUNE_FORCE = 1
+
 _lib = None
 _VP = ctypes.c_void_p
 _FP = ctypes.POINTER(ctypes.c_float)
@@ -83,6 +92,10 @@ _SIGS = {
     "oic_profile_end": (ctypes.c_int, [_VP, _FP, ctypes.POINTER(ctypes.c_int)]),
     "oic_profile_sample": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "oic_launch_count": (ctypes.c_ulonglong, []),
+    "oic_get_plan": (ctypes.c_int, [_VP, ctypes.POINTER(oic_plan), ctypes.POINTER(oic_plan)]),
+    "oic_set_plan": (ctypes.c_int, [_VP, ctypes.POINTER(oic_plan)]),
+    "oic_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(oic_plan),
+                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "oic_selftest": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "oic_enks_update_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                               _VP, _VP, _VP]),
@@ -94,6 +107,8 @@ _SIGS = {
     "oic_io_slots": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "oic_batch_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "oic_batch_step": (ctypes.c_int, [_VP]),
+    "oic_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float)]),
     "oic_batch_sync": (ctypes.c_int, [_VP]),
     "oic_batch_destroy": (None, [_VP]),
     "oic_destroy": (None, [_VP]),
@@ -153,6 +168,14 @@ class Batch:
 
     def step(self):
         _check(self._lib.oic_batch_step(self.b), "oic_batch_step")
+
+    def autotune(self, reps=3):
+        """One plan for all problems chosen by timing batch steps; returns
+        (ms per batch step with the rules, with the chosen plans)."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(self._lib.oic_batch_autotune(self.b, int(reps), ctypes.byref(a), ctypes.byref(b)),
+               "oic_batch_autotune")
+        return float(a.value), float(b.value)
 
     def sync(self):
         _check(self._lib.oic_batch_sync(self.b), "oic_batch_sync")
@@ -335,6 +358,25 @@ class Solver:
         res = (ctypes.c_int * 5)()
         st = self._lib.oic_selftest(self.h, res)
         return int(st), list(res)
+
+    def oic_get_plan(self):
+        """(plan in use with rules resolved, limits) as dicts."""
+        pl, lim = oic_plan(), oic_plan()
+        _check(self._lib.oic_get_plan(self.h, ctypes.byref(pl), ctypes.byref(lim)), "oic_get_plan")
+        return pl.as_dict(), lim.as_dict()
+
+    def oic_set_plan(self, stats_splits=0, update_ctas=0, cnn_ctas=0):
+        pl = oic_plan(stats_splits, update_ctas, cnn_ctas)
+        _check(self._lib.oic_set_plan(self.h, ctypes.byref(pl)), "oic_set_plan")
+
+    def oic_autotune(self, reps=3, force=False):
+        """Returns (chosen plan dict, ms per step with the rule plan, with the
+        chosen plan); both times are -1 when the plan came from the cache."""
+        pl = oic_plan()
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(self._lib.oic_autotune(self.h, int(reps), OIC_TUNE_FORCE if force else 0, ctypes.byref(pl),
+                                      ctypes.byref(a), ctypes.byref(b)), "oic_autotune")
+        return pl.as_dict(), float(a.value), float(b.value)
 
     def oic_sync(self):
         _check(self._lib.oic_sync(self.h), "oic_sync")

@@ -468,7 +468,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                 const int mbr = g * G + b;
                 const float uv = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
                 su[(b * m + xx) * l + c] = uv;
-                if (adv && mbr < Nb) ua.next[(long)mbr * u_ms + rr] = uv + ua.w[(long)mbr * l * m + rr];
+                if (adv && mbr < Nb) ua.next[(long)mbr * u_ms + rr] = uv + noise1(ua.w, (long)mbr * l * m + rr);
             }
             tc::named_bar(BAR_DRAIN, ND);
 

@@ -30,7 +30,7 @@ __device__ __forceinline__ float softplus_barrier(float x, float alpha, float be
 __global__ void __launch_bounds__(256)
 constraint_obs_kernel(float* __restrict__ E, long ms, int N, int m, int n, int xrow, int urow, int zrow, int c,
                       const float* __restrict__ G, const int* __restrict__ cols, int nk,
-                      const float* __restrict__ h, float alpha, float beta, const float* __restrict__ eps)
+                      const float* __restrict__ h, float alpha, float beta, NoiseSrc eps)
 {
     pdl_begin();
     const int m4 = m / 4;
@@ -55,8 +55,8 @@ constraint_obs_kernel(float* __restrict__ E, long ms, int N, int m, int n, int x
     }
     float4 z = make_float4(softplus_barrier(g.x, alpha, beta), softplus_barrier(g.y, alpha, beta),
                            softplus_barrier(g.z, alpha, beta), softplus_barrier(g.w, alpha, beta));
-    if (eps != nullptr) {
-        const float4 v = *reinterpret_cast<const float4*>(eps + ((long)i * c + r) * m + j);
+    if (eps.live()) {
+        const float4 v = noise4(eps, ((long)i * c + r) * m + j);
         z.x += v.x;
         z.y += v.y;
         z.z += v.z;
@@ -69,7 +69,7 @@ constraint_obs_kernel(float* __restrict__ E, long ms, int N, int m, int n, int x
 
 void launch_constraint_obs(float* E, long ms, int N, int m, int n, int xrow, int urow, int zrow, int c,
                            const float* G, const int* cols, int nk, const float* h, float alpha, float beta,
-                           const float* eps, cudaStream_t st)
+                           NoiseSrc eps, cudaStream_t st)
 {
     const long units = (long)N * c * (m / 4);
     const unsigned blocks = (unsigned)((units + 255) / 256);

@@ -20,31 +20,38 @@ namespace oic {
 namespace {
 
 // ------------------------------------------------------------------ init
+// Four consecutive elements per thread (m % 4 == 0, so rows and members
+// start on 16-byte boundaries); the noise of a quad is one Philox block when
+// it is drawn in place.
 __global__ void init_kernel(float* __restrict__ E, long ms, int n, int m, int l, int x_row0, int u_row0,
-                            const float* __restrict__ X_k, const float* __restrict__ U_prev,
-                            const float* __restrict__ W0)
+                            const float* __restrict__ X_k, const float* __restrict__ U_prev, NoiseSrc W0)
 {
     pdl_begin();
     const int i = blockIdx.y;
     float* Ei = E + (long)i * ms;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (n + l) * m; e += gridDim.x * blockDim.x) {
+    for (int e = 4 * (blockIdx.x * blockDim.x + threadIdx.x); e < (n + l) * m; e += 4 * gridDim.x * blockDim.x) {
         if (e < n * m) {
-            Ei[(long)x_row0 * m + e] = X_k[e];
+            *reinterpret_cast<float4*>(Ei + (long)x_row0 * m + e) = *reinterpret_cast<const float4*>(X_k + e);
         } else {
             const int r = e - n * m;
-            Ei[(long)u_row0 * m + r] = U_prev[r] + W0[(long)i * l * m + r];
+            const float4 u = *reinterpret_cast<const float4*>(U_prev + r);
+            const float4 w = noise4(W0, (long)i * l * m + r);
+            *reinterpret_cast<float4*>(Ei + (long)u_row0 * m + r) =
+                make_float4(u.x + w.x, u.y + w.y, u.z + w.z, u.w + w.w);
         }
     }
 }
 
-__global__ void u_advance_kernel(float* __restrict__ E, long ms, int m, int l, int u_from, int u_to,
-                                 const float* __restrict__ W)
+__global__ void u_advance_kernel(float* __restrict__ E, long ms, int m, int l, int u_from, int u_to, NoiseSrc W)
 {
     pdl_begin();
     const int i = blockIdx.y;
     float* Ei = E + (long)i * ms;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * m; e += gridDim.x * blockDim.x)
-        Ei[(long)u_to * m + e] = Ei[(long)u_from * m + e] + W[(long)i * l * m + e];
+    for (int e = 4 * (blockIdx.x * blockDim.x + threadIdx.x); e < l * m; e += 4 * gridDim.x * blockDim.x) {
+        const float4 u = *reinterpret_cast<const float4*>(Ei + (long)u_from * m + e);
+        const float4 w = noise4(W, (long)i * l * m + e);
+        *reinterpret_cast<float4*>(Ei + (long)u_to * m + e) = make_float4(u.x + w.x, u.y + w.y, u.z + w.z, u.w + w.w);
+    }
 }
 
 // ----------------------------------------------------------------- stats
@@ -106,7 +113,7 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
         if (a < R) { off = (long)act.rows[a] * m; return; }
         const int c = a - R;
         off = (long)obs.rows[c] * m;
-        if (V.Va == nullptr || c >= p - obs.nc) return;   // constraint rows carry their noise in E
+        if (!V.a.live() || c >= p - obs.nc) return;   // constraint rows carry their noise in E
         if (c < V.pa) { vs = 1; vo = (long)c * m; }
         else { vs = 2; vo = (long)(c - V.pa) * m; }
     };
@@ -133,8 +140,8 @@ stats_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, Row
     }
     auto value = [&](int i, long off, int vs, long vo, int j) {
         float4 x = *reinterpret_cast<const float4*>(E + (long)i * ms + off + j);
-        if (vs == 1) x = f4add(x, *reinterpret_cast<const float4*>(V.Va + (long)i * V.pa * m + vo + j));
-        else if (vs == 2) x = f4add(x, *reinterpret_cast<const float4*>(V.Vb + (long)i * pb_rows * m + vo + j));
+        if (vs == 1) x = f4add(x, noise4(V.a, (long)i * V.pa * m + vo + j));
+        else if (vs == 2) x = f4add(x, noise4(V.b, (long)i * pb_rows * m + vo + j));
         return x;
     };
     // member 0 (the shift) into shared memory
@@ -267,13 +274,13 @@ __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict_
 // mixed-precision mode's FP64 anomaly step); else FP32 with an FP64 result.
 template <bool F64>
 __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restrict__ part2,
-                                                           const float* __restrict__ S1, int splits, int R, int p,
-                                                           int m, int N, double* __restrict__ C, double scale)
+                                                           const float* __restrict__ S1, const float* __restrict__ S1o,
+                                                           int splits, int M, int p, int m, int N,
+                                                           double* __restrict__ C, double scale)
 {
     pdl_begin();
     using T = typename std::conditional<F64, double, float>::type;
     __shared__ T red[8][33], cred[8][33];
-    const int M = R + p;
     const int idx = blockIdx.x * 32 + threadIdx.x % 32;
     const bool ok = idx < M * p;
     const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
         if (S1 != nullptr) {                      // one-pass products: the mean term, columns j = w, w + 8, ...
             const int a = idx / p, c = idx % p;
             const float* x = S1 + (long)a * m;
-            const float* y = S1 + (long)(R + c) * m;
+            const float* y = S1o + (long)c * m;
             T d0 = 0, d1 = 0;
             int j = w;
             for (; j + 8 < m; j += 16) {
@@ -763,16 +770,15 @@ __global__ void __launch_bounds__(256) block_means_kernel(const float* __restric
 }  // namespace
 
 void launch_ensemble_init(float* E, long ms, int N, int n, int m, int l, int x_row0, int u_row0, const float* X_k, const float* U_prev,
-                          const float* W0, cudaStream_t st)
+                          NoiseSrc W0, cudaStream_t st)
 {
-    dim3 grid(((n + l) * m + 255) / 256, N);
+    dim3 grid(((n + l) * m / 4 + 255) / 256, N);
     pdl_launch(init_kernel, grid, 256, 0, st, E, ms, n, m, l, x_row0, u_row0, X_k, U_prev, W0);
 }
 
-void launch_u_advance(float* E, long ms, int N, int m, int l, int u_from, int u_to, const float* W,
-                      cudaStream_t st)
+void launch_u_advance(float* E, long ms, int N, int m, int l, int u_from, int u_to, NoiseSrc W, cudaStream_t st)
 {
-    dim3 grid((l * m + 255) / 256, N);
+    dim3 grid((l * m / 4 + 255) / 256, N);
     pdl_launch(u_advance_kernel, grid, 256, 0, st, E, ms, m, l, u_from, u_to, W);
 }
 
@@ -819,14 +825,23 @@ void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, c
     plain_launch(s1_reduce_kernel, (M * m + 31) / 32, 256, 0, st, part1, splits, M, m, S1);
 }
 
+void launch_cov_finalize_rows(const float* part2, const float* S1_left, const float* S1_obs, int splits, int M, int p,
+                              int m, int N, double* C, cudaStream_t st, bool f64, double scale)
+{
+    const int total = M * p;
+    if (f64)
+        plain_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2, S1_left, S1_obs, splits, M, p, m,
+                     N, C, scale);
+    else
+        plain_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1_left, S1_obs, splits, M, p, m,
+                     N, C, scale);
+}
+
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
                          cudaStream_t st, bool f64, double scale)
 {
-    const int total = (R + p) * p;
-    if (f64)
-        plain_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C, scale);
-    else
-        plain_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1, splits, R, p, m, N, C, scale);
+    launch_cov_finalize_rows(part2, S1, S1 != nullptr ? S1 + (size_t)R * m : nullptr, splits, R + p, p, m, N, C, st,
+                             f64, scale);
 }
 
 

@@ -306,9 +306,13 @@ solve64s_kernel(const double* __restrict__ C, int R, int p, const double* __rest
 
 int gain64_max_p() { return C64_PMAX; }
 
-void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st)
+void launch_chol64(const double* C, int R, int p, double* L, int* bad, int* status, cudaStream_t st)
 {
     pdl_launch(chol64c_kernel, CL, C64_T, 0, st, C, R, p, L, status, bad);
+}
+
+void launch_solve64(const double* C, int R, int p, const double* L, const int* bad, float* Kt, cudaStream_t st)
+{
     const size_t smem = sizeof(double) * ((size_t)p * (p | 1) + p);
     static DeviceOnce attr_set;
     attr_set.run([] {
@@ -317,6 +321,12 @@ void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt
                cudaSuccess;
     });
     pdl_launch(solve64s_kernel, (R + S64_W - 1) / S64_W, 32 * S64_W, smem, st, C, R, p, L, bad, Kt);
+}
+
+void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st)
+{
+    launch_chol64(C, R, p, L, bad, status, st);
+    launch_solve64(C, R, p, L, bad, Kt, st);
 }
 
 }  // namespace oic

@@ -125,7 +125,7 @@ extern "C" oic_status oic_enks_update_static(int N, int R, int m, int p, const i
     float* Kt = reinterpret_cast<float*>(base + off_K);
     RowSet act{rows, R};
     RowSet obs{rows + R, p};
-    ObsNoise Vn{V, V, p};
+    const ObsNoise Vn = obs_noise_buf(V, V, p);
     const long ms = (long)R * m;
     launch_stats(E, ms, N, m, act, obs, Vn, Ybar, Ybar, p, part1, part2, D, splits, s);
     launch_s1_reduce(part1, splits, M, m, S1, s);

@@ -7,7 +7,10 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "oic_internal.cuh"
@@ -91,6 +94,7 @@ struct oic_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<int> obs_host;
     Profiler prof;
+    oic_plan plan{};                          // scheduling choices (0 = the built-in rule)
     int stage_seen[OIC_NUM_STAGES] = {};      // launches of each stage in the current solve (and its plant step)
     StepGraph sg[2];                          // [0] plain, [1] with profiling event nodes
     StepGraph* capturing = nullptr;
@@ -110,6 +114,15 @@ struct oic_handle {
 };
 
 namespace {
+
+// The plan's values, rules resolved.
+int cnn_ctas(const oic_handle* h) { return h->plan.cnn_ctas > 0 ? h->plan.cnn_ctas : h->n_sm; }
+int update_ctas(const oic_handle* h) { return h->plan.update_ctas > 0 ? h->plan.update_ctas : 148; }
+int plan_splits(const oic_handle* h, int rule)
+{
+    const int s = h->plan.stats_splits > 0 ? h->plan.stats_splits : rule;
+    return s < h->splits_max ? s : h->splits_max;
+}
 
 // Runs one kernel launch of stage `stage`, counting it and, when the stage is
 // being profiled, bracketing it with CUDA events on the bound stream (while a
@@ -290,7 +303,7 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
         net.act[1] = h->at<char>(h->lay.act1);
         run_stage(h, OIC_STAGE_CNN_BF16, [&] {
             launch_bf16_forward(net, X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l,
-                                c.residual_scale, h->n_sm, h->at<int>(h->lay.status), h->st);
+                                c.residual_scale, cnn_ctas(h), h->at<int>(h->lay.status), h->st);
         });
         return;
     }
@@ -299,7 +312,7 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
         const int C = c.channels[1];
         run_stage(h, OIC_STAGE_CNN_FUSED, [&] {
             launch_cnn_fused(X, x_ms, U, u_ms, Xout, o_ms, h->at<float>(h->lay.B), Nb, c.n, c.m, c.l, b,
-                             b + C, b + 2 * C, h->at<char>(h->lay.wfused), c.residual_scale, h->n_sm,
+                             b + C, b + 2 * C, h->at<char>(h->lay.wfused), c.residual_scale, cnn_ctas(h),
                              h->at<int>(h->lay.status), h->st, ua);
         });
         return;
@@ -316,7 +329,7 @@ void cnn_forward(oic_handle* h, int Nb, const float* X, long x_ms, const float* 
         const size_t toff = h->wtc_off[k];
         run_stage(h, k == 0 ? OIC_STAGE_CONV_FIRST : OIC_STAGE_CONV_HIDDEN, [&] {
             if (toff != SIZE_MAX)
-                launch_conv_tc(a, z, h->at<char>(h->lay.wtc) + toff, b, cout, Nb, c.n, c.m, h->n_sm,
+                launch_conv_tc(a, z, h->at<char>(h->lay.wtc) + toff, b, cout, Nb, c.n, c.m, cnn_ctas(h),
                                h->at<int>(h->lay.status), h->st);
             else
                 launch_conv_hidden(a, cin, z, cout, Nb, c.n, c.m, w, b, h->st);
@@ -348,7 +361,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
     const bool utc = tcs && update_tc_supported(c.m, p);
     float* Bd = utc ? h->at<float>(h->lay.tBd) : nullptr;
     if (tcs) {
-        const int splits = stats_tc_splits(M, c.N);
+        const int splits = plan_splits(h, stats_tc_splits(M, c.N));
         run_stage(h, OIC_STAGE_COV, [&] {
             launch_stats_tc(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, h->at<float>(h->lay.tB), part1, part2,
                             utc ? nullptr : D, Bd, splits, h->at<int>(h->lay.status), h->st);
@@ -358,7 +371,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
             launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed);
         });
     } else {
-        const int splits = stats_splits(R, p, c.N);
+        const int splits = plan_splits(h, stats_splits(R, p, c.N));
         run_stage(h, OIC_STAGE_COV, [&] {
             launch_stats(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, part1, part2, D, splits, h->st);
         });
@@ -377,7 +390,8 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
     });
     if (utc)
         run_stage(h, OIC_STAGE_UPDATE, [&] {
-            launch_update_tc(E, ms, c.N, c.m, act, Kt, p, h->at<float>(h->lay.tAop), Bd, h->at<int>(h->lay.status),
+            launch_update_tc(E, ms, c.N, c.m, act, Kt, p, h->at<float>(h->lay.tAop), update_ctas(h), Bd,
+                             h->at<int>(h->lay.status),
                              h->st, mixed);                // the FP32 gain writes the tiles itself
         });
     else
@@ -429,7 +443,7 @@ void ensemble_cov(oic_handle* h, const float* E, long ms, RowSet rows, const Cov
     const int splits = stats_splits(0, R, c.N);
     RowSet none{rows.rows, 0};
     run_stage(h, OIC_STAGE_COV_OUT, [&] {
-        launch_stats(E, ms, c.N, c.m, none, rows, ObsNoise{nullptr, nullptr, 0}, nullptr, nullptr, 0, part1, part2,
+        launch_stats(E, ms, c.N, c.m, none, rows, ObsNoise(), nullptr, nullptr, 0, part1, part2,
                      nullptr, splits, h->st);
     });
     run_stage(h, OIC_STAGE_COV_OUT, [&] { launch_s1_reduce(part1, splits, R, c.m, S1, h->st); });
@@ -444,33 +458,48 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
     const oic_config& c = h->cfg;
     const size_t N = c.N, n = c.n, m = c.m, l = c.l, H = c.H;
     for (int& v : h->stage_seen) v = 0;
-    if (c.noise_mode == OIC_NOISE_PHILOX) {
-        const size_t e0 = N * l * m, e1 = e0 + H * N * l * m, e2 = e1 + H * N * n * m,
-                     e3 = e2 + H * N * l * m, e4 = e3 + H * N * (size_t)h->nc * m;
+    // The solve's random numbers, segments W0 | W | V_X | V_U | eps of the
+    // noise layout.  Device mode: each consumer draws its elements in place
+    // from the Philox stream (the numbers the noise kernel would write, bit for
+    // bit); with OIC_NOISE_BUFFER set the noise kernel writes the whole stream
+    // to the buffer first and the consumers read it.  The solve index
+    // advances after the solve's last draw.
+    const size_t e0 = N * l * m, e1 = e0 + H * N * l * m, e2 = e1 + H * N * n * m,
+                 e3 = e2 + H * N * l * m, e4 = e3 + H * N * (size_t)h->nc * m;
+    const bool philox = c.noise_mode == OIC_NOISE_PHILOX;
+    const bool in_place = philox && getenv("OIC_NOISE_BUFFER") == nullptr;
+    unsigned long long* ctr = h->at<unsigned long long>(h->lay.ctr);
+    if (philox && !in_place) {
         const size_t ends[5] = {e0, e1, e2, e3, e4};
         const float sig[5] = {(float)c.sigma_w, (float)c.sigma_w, (float)c.sigma_vx, (float)c.sigma_vu, h->c_sigma};
         float* buf = h->at<float>(h->lay.noise);
         run_stage(h, OIC_STAGE_NOISE, [&] {
-            launch_philox_noise(buf, h->noise_n, c.seed, h->at<unsigned long long>(h->lay.ctr), ends, sig,
-                                h->nc > 0 ? 5 : 4, h->st);
+            launch_philox_noise(buf, h->noise_n, c.seed, ctr, ends, sig, h->nc > 0 ? 5 : 4, h->st, false);
         });
-        g_launches.fetch_add(1, std::memory_order_relaxed);   // the counter tick
         noise = buf;
     }
-    const float* W0 = noise;
-    const float* W = W0 + N * l * m;
-    const float* VX = W + H * N * l * m;
-    const float* VU = VX + H * N * n * m;
-    const float* VZ = VU + H * N * l * m;
+    auto segment = [&](size_t start, float sigma) {
+        NoiseSrc s;
+        if (in_place) {
+            s.ctr = ctr;
+            s.seed = c.seed;
+            s.base = start;
+            s.sigma = sigma;
+        } else {
+            s.buf = noise + start;
+        }
+        return s;
+    };
     float* E = h->at<float>(h->lay.E);
     const long ms = h->ms();
 
     run_stage(h, OIC_STAGE_INIT, [&] {
-        launch_ensemble_init(E, ms, c.N, c.n, c.m, c.l, h->xrow(0), h->urow(0), X_k, U_prev, W0, h->st);
+        launch_ensemble_init(E, ms, c.N, c.n, c.m, c.l, h->xrow(0), h->urow(0), X_k, U_prev,
+                             segment(0, (float)c.sigma_w), h->st);
     });
     for (int s = 1; s <= c.H; ++s) {
         // prediction, Eq. (prediction-samplewise): X̄_t = f_CNN(X̄_{t-1}) + W̄_{t-1}
-        const float* Ws = W + (s - 1) * N * l * m;
+        const NoiseSrc Ws = segment(e0 + (s - 1) * N * l * m, (float)c.sigma_w);
         UAdvance ua;
         if (cnn_advances_u(h)) {
             ua.next = E + (size_t)h->urow(s) * m;
@@ -488,16 +517,22 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
                 launch_constraint_obs(E, ms, c.N, c.m, c.n, h->xrow(s), h->urow(s), h->zrow, h->nc,
                                       h->at<float>(h->lay.cG), h->at<int>(h->lay.ccols), h->nk,
                                       h->at<float>(h->lay.ch), h->c_alpha, h->c_beta,
-                                      VZ + (s - 1) * N * (size_t)h->nc * m, h->st);
+                                      segment(e3 + (s - 1) * N * (size_t)h->nc * m, h->c_sigma), h->st);
             });
         // analysis at t = k + s with Ybar_t = [X_ref[s]; U_ref; 0]
         RowSet act{h->act_rows(s), h->R_of(s)};
         RowSet obs{h->obs_rows(s), h->p, h->nc};
-        ObsNoise V{VX + (s - 1) * N * n * m, VU + (s - 1) * N * l * m, c.n};
+        ObsNoise V;
+        V.a = segment(e1 + (s - 1) * N * n * m, (float)c.sigma_vx);
+        V.b = segment(e2 + (s - 1) * N * l * m, (float)c.sigma_vu);
+        V.pa = c.n;
         const size_t slot = (size_t)(s - 1) * h->R_act_max * h->R_act_max;
         if (cov && cov->pred) ensemble_cov(h, E, ms, act, *cov, cov->pred + slot);     // Sigma^X_{t|t-1}
         analysis(h, E, ms, act, obs, V, X_ref + (size_t)s * n * m, U_ref, c.n);
         if (cov && cov->post) ensemble_cov(h, E, ms, act, *cov, cov->post + slot);     // Sigma^X_{t|t}
+    }
+    if (philox) {
+        run_stage(h, OIC_STAGE_NOISE, [&] { launch_counter_tick(ctr, h->st); });
     }
     run_stage(h, OIC_STAGE_BLOCK_MEANS, [&] {
         launch_block_means(E, ms, c.N, c.m, h->urow(0), c.l, c.H + 1, U_hat, h->st);
@@ -554,7 +589,8 @@ bool capture_step(oic_handle* h, StepGraph& G, unsigned mask)
     h->capturing = nullptr;
     G.launches = g_launches.load() - l0;
     g_launches.fetch_sub(G.launches);                     // captured, not run
-    if (s != OIC_OK || G.g == nullptr || cudaGraphInstantiate(&G.x, G.g, 0) != cudaSuccess) {
+    if (s != OIC_OK || G.g == nullptr ||
+        cudaGraphInstantiate(&G.x, G.g, 0) != cudaSuccess) {
         cudaGetLastError();
         G.reset();
         G.failed = true;
@@ -610,6 +646,54 @@ bool run_step_graph(oic_handle* h)
     if (cudaGraphLaunch(G->x, h->st) != cudaSuccess) return false;
     g_launches.fetch_add(G->launches, std::memory_order_relaxed);
     return true;
+}
+
+// ---------------------------------------------------------------- plans
+// Plans chosen by oic_autotune, by problem shape (process-wide).
+std::mutex g_plan_mu;
+std::map<std::string, oic_plan> g_plan_cache;
+
+std::string plan_key(const oic_handle* h)
+{
+    const oic_config& c = h->cfg;
+    std::string k = std::to_string(c.n) + "x" + std::to_string(c.m) + "/l" + std::to_string(c.l) + "/N" +
+                    std::to_string(c.N) + "/H" + std::to_string(c.H) + "/c";
+    for (int i = 0; i <= c.n_layers; ++i) k += std::to_string(c.channels[i]) + ",";
+    k += "/pr" + std::to_string(c.precision) + "/fh" + std::to_string(c.keep_full_history) + "/nm" +
+         std::to_string(c.noise_mode) + "/nc" + std::to_string(h->nc) + "/sm" + std::to_string(h->n_sm);
+    return k;
+}
+
+// The covariance products' rule at the last assimilation time (the largest
+// row count).
+int rule_splits(const oic_handle* h)
+{
+    const int R = h->R_of(h->cfg.H), p = h->p;
+    return stats_tc_supported(h->cfg.m, p) ? stats_tc_splits(R + p, h->cfg.N) : stats_splits(R, p, h->cfg.N);
+}
+
+oic_plan effective_plan(const oic_handle* h)
+{
+    oic_plan e;
+    e.stats_splits = plan_splits(h, rule_splits(h));
+    e.update_ctas = update_ctas(h);
+    e.cnn_ctas = cnn_ctas(h);
+    return e;
+}
+
+oic_plan plan_limits(const oic_handle* h)
+{
+    oic_plan l;
+    l.stats_splits = h->splits_max;
+    l.update_ctas = 148;
+    l.cnn_ctas = h->n_sm;
+    return l;
+}
+
+void drop_step_graphs(oic_handle* h)
+{
+    h->sg[0].reset();
+    h->sg[1].reset();
 }
 
 oic_status read_status(oic_handle* h)
@@ -1021,7 +1105,7 @@ oic_status oic_enks_update(oic_handle* h, int R, const int* obs_rows, float* E, 
     OIC_CUDA_OK(cudaMemcpyAsync(gobs, obs_rows, sizeof(int) * p, cudaMemcpyHostToDevice, h->st));
     RowSet act{gen, R};
     RowSet obs{gobs, p};
-    ObsNoise Vn{V, V, p};
+    const ObsNoise Vn = obs_noise_buf(V, V, p);
     analysis(h, E, (long)R * h->cfg.m, act, obs, Vn, Ybar, Ybar, p);
     return last_cuda();
 }
@@ -1088,6 +1172,140 @@ oic_status oic_profile_end(oic_handle* h, float* ms, int* launches)
 }
 
 unsigned long long oic_launch_count(void) { return g_launches.load(); }
+
+oic_status oic_get_plan(const oic_handle* h, oic_plan* plan, oic_plan* limits)
+{
+    if (!h || !plan) return OIC_EINVAL;
+    *plan = effective_plan(h);
+    if (limits) *limits = plan_limits(h);
+    return OIC_OK;
+}
+
+oic_status oic_set_plan(oic_handle* h, const oic_plan* plan)
+{
+    if (!h || !plan) return OIC_EINVAL;
+    const oic_plan l = plan_limits(h);
+    if (plan->stats_splits < 0 || plan->stats_splits > l.stats_splits || plan->update_ctas < 0 ||
+        plan->update_ctas > l.update_ctas || plan->cnn_ctas < 0 || plan->cnn_ctas > l.cnn_ctas)
+        return OIC_EINVAL;
+    h->plan = *plan;
+    drop_step_graphs(h);
+    return OIC_OK;
+}
+
+oic_status oic_autotune(oic_handle* h, int reps, int flags, oic_plan* chosen, float* ms_rule, float* ms_tuned)
+{
+    if (!h || reps < 1 || reps > 1000) return OIC_EINVAL;
+    if (!h->bound || !h->plant_ready || h->prof.on) return OIC_ESTATE;
+    if (ms_rule) *ms_rule = -1.f;
+    if (ms_tuned) *ms_tuned = -1.f;
+    const std::string key = plan_key(h);
+    if (!(flags & OIC_TUNE_FORCE)) {
+        std::lock_guard<std::mutex> lock(g_plan_mu);
+        const auto it = g_plan_cache.find(key);
+        if (it != g_plan_cache.end()) {
+            h->plan = it->second;
+            drop_step_graphs(h);
+            if (chosen) *chosen = effective_plan(h);
+            return OIC_OK;
+        }
+    }
+    // the state the tuning steps disturb, restored at the end
+    std::vector<unsigned char> saved(oic_state_bytes(h));
+    oic_status s = oic_save_state(h, saved.data());
+    if (s != OIC_OK) return s;
+    const oic_plan entry = h->plan;
+    const oic_config& c = h->cfg;
+    const Layout& L = h->lay;
+    const size_t n = c.n, m = c.m, l = c.l, H = c.H;
+    // inputs: zero references; device-drawn noise where the caller supplies it
+    OIC_CUDA_OK(cudaMemsetAsync(h->at<float>(L.xref), 0, sizeof(float) * (H + 1) * n * m, h->st));
+    OIC_CUDA_OK(cudaMemsetAsync(h->at<float>(L.uref), 0, sizeof(float) * l * m, h->st));
+    if (c.noise_mode == OIC_NOISE_HOST) {
+        const size_t N = c.N, e0 = N * l * m, e1 = e0 + H * N * l * m, e2 = e1 + H * N * n * m,
+                     e3 = e2 + H * N * l * m, e4 = e3 + H * N * (size_t)h->nc * m;
+        const size_t ends[5] = {e0, e1, e2, e3, e4};
+        const float sig[5] = {(float)c.sigma_w, (float)c.sigma_w, (float)c.sigma_vx, (float)c.sigma_vu, h->c_sigma};
+        launch_philox_noise(h->at<float>(L.noise), h->noise_n, c.seed, h->at<unsigned long long>(L.ctr), ends, sig,
+                            h->nc > 0 ? 5 : 4, h->st);
+    }
+    auto one_step = [&]() -> oic_status {
+        if (run_step_graph(h)) return last_cuda();
+        return step_impl(h, h->at<float>(L.xref), h->at<float>(L.uref), h->at<float>(L.noise), h->at<float>(L.uapp),
+                         h->at<float>(L.xnext));
+    };
+    auto time_plan = [&](const oic_plan& p, float* ms) -> oic_status {
+        h->plan = p;
+        drop_step_graphs(h);
+        oic_status r = one_step();                  // untimed: captures the step graph
+        for (int i = 0; i < reps && r == OIC_OK; ++i) {
+            if (i == 0) OIC_CUDA_OK(cudaEventRecord(h->ev0, h->st));
+            r = one_step();
+        }
+        if (r != OIC_OK) return r;
+        OIC_CUDA_OK(cudaEventRecord(h->ev1, h->st));
+        OIC_CUDA_OK(cudaEventSynchronize(h->ev1));
+        float t = 0.f;
+        OIC_CUDA_OK(cudaEventElapsedTime(&t, h->ev0, h->ev1));
+        *ms = t / reps;
+        return read_status(h);
+    };
+    oic_plan cur{};                                 // start from the rules
+    float best = 0.f;
+    s = time_plan(cur, &best);
+    const float rule_ms = best;
+    const oic_plan base = effective_plan(h);
+    // candidates per field, one field at a time
+    for (int field = 0; field < 3 && s == OIC_OK; ++field) {
+        std::vector<int> cand;
+        if (field == 0) {
+            for (int d : {8, 7, 6, 4}) cand.push_back(h->n_sm * d / 8);
+        } else if (field == 1) {
+            const int r = base.stats_splits;
+            for (int v : {r, r / 2, 2 * r / 3, 3 * r / 2, 2 * r, c.N / 8}) cand.push_back(v);
+        } else {
+            for (int v : {148, 111, 74, 37}) cand.push_back(v);
+        }
+        const oic_plan lim = plan_limits(h);
+        const int lim_f = field == 0 ? lim.cnn_ctas : field == 1 ? lim.stats_splits : lim.update_ctas;
+        const oic_plan eff = [&] { h->plan = cur; return effective_plan(h); }();
+        const int cur_v = field == 0 ? eff.cnn_ctas : field == 1 ? eff.stats_splits : eff.update_ctas;
+        std::vector<int> tried{cur_v};
+        for (int v : cand) {
+            if (v < 1 || v > lim_f || std::find(tried.begin(), tried.end(), v) != tried.end()) continue;
+            tried.push_back(v);
+            oic_plan trial = cur;
+            (field == 0 ? trial.cnn_ctas : field == 1 ? trial.stats_splits : trial.update_ctas) = v;
+            float t = 0.f;
+            s = time_plan(trial, &t);
+            if (s != OIC_OK) break;
+            if (t < 0.99f * best) {
+                best = t;
+                cur = trial;
+            }
+        }
+    }
+    if (s != OIC_OK) {
+        h->plan = entry;
+        drop_step_graphs(h);
+        oic_load_state(h, saved.data());
+        cudaStreamSynchronize(h->st);
+        return s;
+    }
+    h->plan = cur;
+    drop_step_graphs(h);
+    s = oic_load_state(h, saved.data());
+    if (s != OIC_OK) return s;
+    OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    {
+        std::lock_guard<std::mutex> lock(g_plan_mu);
+        g_plan_cache[key] = cur;
+    }
+    if (chosen) *chosen = effective_plan(h);
+    if (ms_rule) *ms_rule = rule_ms;
+    if (ms_tuned) *ms_tuned = best;
+    return OIC_OK;
+}
 
 oic_status oic_selftest(oic_handle* h, int* result)
 {
@@ -1175,31 +1393,22 @@ oic_status oic_io_slots(const oic_handle* h, float** X_ref, float** U_ref, float
     return OIC_OK;
 }
 
-oic_status oic_batch_create(oic_handle* const* handles, int count, void* cuda_stream, oic_batch** out)
+// (Re)captures one control step of every problem of b as one graph.
+oic_status capture_batch(oic_batch* b)
 {
-    if (!handles || !out || count < 1 || count > 4096) return OIC_EINVAL;
-    *out = nullptr;
-    for (int i = 0; i < count; ++i) {
-        oic_handle* h = handles[i];
-        if (!h) return OIC_EINVAL;
-        if (h->cfg.noise_mode != OIC_NOISE_PHILOX) return OIC_EINVAL;
-        if (!h->bound || !h->plant_ready) return OIC_ESTATE;
-        for (int k = 0; k < i; ++k)
-            if (handles[k] == h) return OIC_EINVAL;
-    }
-    oic_batch* b = new (std::nothrow) oic_batch;
-    if (!b) return OIC_ENOMEM;
+    if (b->x) cudaGraphExecDestroy(b->x);
+    if (b->g) cudaGraphDestroy(b->g);
+    b->x = nullptr;
+    b->g = nullptr;
+    const int count = (int)b->hs.size();
     std::vector<cudaStream_t> br;
     std::vector<cudaEvent_t> join;
     try {
-        b->hs.assign(handles, handles + count);
         br.assign(count, nullptr);
         join.assign(count, nullptr);
     } catch (...) {
-        delete b;
         return OIC_ENOMEM;
     }
-    b->st = static_cast<cudaStream_t>(cuda_stream);
     // One capture: an origin stream forks to one stream per problem, each
     // problem's step is captured on its own stream (its kernels keep their
     // programmatic-dependency edges inside the branch), and the branches
@@ -1215,7 +1424,7 @@ oic_status oic_batch_create(oic_handle* const* handles, int count, void* cuda_st
     if (ok && cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
         bool cap = cudaEventRecord(fork, origin) == cudaSuccess;
         for (int i = 0; cap && i < count; ++i) {
-            oic_handle* h = handles[i];
+            oic_handle* h = b->hs[i];
             cap = cudaStreamWaitEvent(br[i], fork, 0) == cudaSuccess;
             StepGraph none;                       // capture mode, no profiling events
             const cudaStream_t own = h->st;
@@ -1247,10 +1456,134 @@ oic_status oic_batch_create(oic_handle* const* handles, int count, void* cuda_st
     if (origin) cudaStreamDestroy(origin);
     if (!ok) {
         cudaGetLastError();
-        oic_batch_destroy(b);
         return OIC_ECUDA;
     }
+    return OIC_OK;
+}
+
+oic_status oic_batch_create(oic_handle* const* handles, int count, void* cuda_stream, oic_batch** out)
+{
+    if (!handles || !out || count < 1 || count > 4096) return OIC_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        oic_handle* h = handles[i];
+        if (!h) return OIC_EINVAL;
+        if (h->cfg.noise_mode != OIC_NOISE_PHILOX) return OIC_EINVAL;
+        if (!h->bound || !h->plant_ready) return OIC_ESTATE;
+        for (int k = 0; k < i; ++k)
+            if (handles[k] == h) return OIC_EINVAL;
+    }
+    oic_batch* b = new (std::nothrow) oic_batch;
+    if (!b) return OIC_ENOMEM;
+    try {
+        b->hs.assign(handles, handles + count);
+    } catch (...) {
+        delete b;
+        return OIC_ENOMEM;
+    }
+    b->st = static_cast<cudaStream_t>(cuda_stream);
+    const oic_status s = capture_batch(b);
+    if (s != OIC_OK) {
+        oic_batch_destroy(b);
+        return s;
+    }
     *out = b;
+    return OIC_OK;
+}
+
+oic_status oic_batch_autotune(oic_batch* b, int reps, float* ms_rule, float* ms_tuned)
+{
+    if (!b || reps < 1 || reps > 1000) return OIC_EINVAL;
+    if (ms_rule) *ms_rule = -1.f;
+    if (ms_tuned) *ms_tuned = -1.f;
+    const int count = (int)b->hs.size();
+    std::vector<std::vector<unsigned char>> saved(count);
+    std::vector<oic_plan> entry(count);
+    for (int i = 0; i < count; ++i) {
+        oic_handle* h = b->hs[i];
+        if (h->prof.on) return OIC_ESTATE;
+        saved[i].resize(oic_state_bytes(h));
+        const oic_status s = oic_save_state(h, saved[i].data());
+        if (s != OIC_OK) return s;
+        entry[i] = h->plan;
+        const Layout& L = h->lay;
+        OIC_CUDA_OK(cudaMemsetAsync(h->at<float>(L.xref), 0, sizeof(float) * (h->cfg.H + 1) * h->cfg.n * h->cfg.m,
+                                    h->st));
+        OIC_CUDA_OK(cudaMemsetAsync(h->at<float>(L.uref), 0, sizeof(float) * h->cfg.l * h->cfg.m, h->st));
+        OIC_CUDA_OK(cudaStreamSynchronize(h->st));
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    OIC_CUDA_OK(cudaEventCreate(&e0));
+    OIC_CUDA_OK(cudaEventCreate(&e1));
+    // a choice applied to every problem: CNN CTAs as a fraction (eighths) of
+    // the SMs, member-update CTAs, covariance splits as a fraction (eighths)
+    // of each problem's rule
+    struct Choice { int cnn8 = 8, upd = 0, split8 = 8; };
+    auto apply = [&](const Choice& ch) {
+        for (oic_handle* h : b->hs) {
+            oic_plan p{};
+            p.cnn_ctas = ch.cnn8 == 8 ? 0 : std::max(1, h->n_sm * ch.cnn8 / 8);
+            p.update_ctas = ch.upd;
+            p.stats_splits = ch.split8 == 8 ? 0 : std::max(1, rule_splits(h) * ch.split8 / 8);
+            h->plan = p;
+            drop_step_graphs(h);
+        }
+        return capture_batch(b);
+    };
+    auto time_choice = [&](const Choice& ch, float* ms) -> oic_status {
+        oic_status s = apply(ch);
+        if (s != OIC_OK) return s;
+        OIC_CUDA_OK(cudaGraphLaunch(b->x, b->st));       // untimed
+        OIC_CUDA_OK(cudaEventRecord(e0, b->st));
+        for (int r = 0; r < reps; ++r) OIC_CUDA_OK(cudaGraphLaunch(b->x, b->st));
+        OIC_CUDA_OK(cudaEventRecord(e1, b->st));
+        OIC_CUDA_OK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        OIC_CUDA_OK(cudaEventElapsedTime(&t, e0, e1));
+        *ms = t / reps;
+        for (oic_handle* h : b->hs) {
+            s = read_status(h);
+            if (s != OIC_OK) return s;
+        }
+        return OIC_OK;
+    };
+    Choice cur;
+    float best = 0.f;
+    oic_status s = time_choice(cur, &best);
+    const float rule_ms = best;
+    const int cnn_c[] = {6, 4, 2, 1}, upd_c[] = {74, 37, 18}, split_c[] = {4, 2};
+    for (int field = 0; field < 3 && s == OIC_OK; ++field) {
+        const int* cv = field == 0 ? cnn_c : field == 1 ? upd_c : split_c;
+        const int nc = field == 0 ? 4 : field == 1 ? 3 : 2;
+        for (int k = 0; k < nc && s == OIC_OK; ++k) {
+            Choice trial = cur;
+            (field == 0 ? trial.cnn8 : field == 1 ? trial.upd : trial.split8) = cv[k];
+            float t = 0.f;
+            s = time_choice(trial, &t);
+            if (s == OIC_OK && t < 0.99f * best) {
+                best = t;
+                cur = trial;
+            }
+        }
+    }
+    if (s == OIC_OK) s = apply(cur);
+    if (s != OIC_OK) {
+        for (int i = 0; i < count; ++i) {
+            b->hs[i]->plan = entry[i];
+            drop_step_graphs(b->hs[i]);
+        }
+        capture_batch(b);
+    }
+    for (int i = 0; i < count; ++i) {
+        const oic_status r = oic_load_state(b->hs[i], saved[i].data());
+        if (s == OIC_OK) s = r;
+        cudaStreamSynchronize(b->hs[i]->st);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != OIC_OK) return s;
+    if (ms_rule) *ms_rule = rule_ms;
+    if (ms_tuned) *ms_tuned = best;
     return OIC_OK;
 }
 

@@ -17,6 +17,7 @@
 #include <utility>
 
 #include "oic.h"
+#include "philox.cuh"
 
 namespace oic {
 
@@ -97,13 +98,27 @@ struct RowSet {
 };
 
 // Observation perturbation V^i of the p - nc rows before the constraint rows:
-// rows c < pa come from Va (member stride pa*m), rows pa <= c < p - nc from
-// Vb (member stride (p-nc-pa)*m).  Va == nullptr means V = 0.
+// rows c < pa come from a (member stride pa*m), rows pa <= c < p - nc from
+// b (member stride (p-nc-pa)*m), each a buffer or drawn in place (NoiseSrc).
+// !a.live() means V = 0.
 struct ObsNoise {
-    const float* Va;
-    const float* Vb;
-    int pa;
+    NoiseSrc a, b;
+    int pa = 0;
 };
+inline NoiseSrc noise_buf(const float* p)
+{
+    NoiseSrc s;
+    s.buf = p;
+    return s;
+}
+inline ObsNoise obs_noise_buf(const float* Va, const float* Vb, int pa)
+{
+    ObsNoise o;
+    o.a = noise_buf(Va);
+    o.b = noise_buf(Vb);
+    o.pa = pa;
+    return o;
+}
 
 // ---------------------------------------------------------------- CNN
 // act0[b] = [X^b ; B U^b]  (two planes of n x m), b < Nb.
@@ -121,10 +136,10 @@ void launch_conv_out_residual(const float* in, int Cin, const float* Xin, long x
 // ---------------------------------------------------------------- EnKS
 // Algorithm 1 line 4: E[i][x_row0 ..] = X_k, E[i][u_row0 ..] = U_prev + W0^i.
 void launch_ensemble_init(float* E, long ms, int N, int n, int m, int l, int x_row0, int u_row0,
-                          const float* X_k, const float* U_prev, const float* W0, cudaStream_t st);
+                          const float* X_k, const float* U_prev, NoiseSrc W0, cudaStream_t st);
 // E[i][u_to rows] = E[i][u_from rows] + W^i (l x m per member).
 void launch_u_advance(float* E, long ms, int N, int m, int l, int u_from, int u_to,
-                      const float* W, cudaStream_t st);
+                      NoiseSrc W, cudaStream_t st);
 // Shifted anomaly sums (split-K over members): part1[s][a][j] (first column
 // tile only) and part2[s][a][c]; the first row tile also writes the
 // innovations Dbuf[i][c][j] = Ybar[c][j] - Y^i[c][j].  Rows a < R are active
@@ -138,17 +153,30 @@ void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, c
 // C = scale (sum_s part2 - S1 S1_Y^T / N)  ([(R + p) x p], Cxy on top, Cyy below).
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
                          cudaStream_t st, bool f64 = false, double scale = 1.0);
+// The same for M left rows whose split sums part2 [splits][M][p] hold alone:
+// C[a][c] = scale (sum_s part2[s][a][c] - S1_left[a] . S1_obs[c] / N).
+void launch_cov_finalize_rows(const float* part2, const float* S1_left, const float* S1_obs, int splits, int M, int p,
+                              int m, int N, double* C, cudaStream_t st, bool f64 = false, double scale = 1.0);
 // Anomaly products on the tensor cores (TF32 hi / lo split, one pass over
 // the ensemble): part1 / part2 as launch_stats writes them, so the same
 // s1 reduction and finalisation follow.  Bop: stats_tc_bbytes of scratch.
 bool stats_tc_supported(int m, int p);
 int stats_tc_splits(int M, int N);
+int stats_tc_rtiles(int M);
 size_t stats_tc_bbytes(int N, int p, int m);
 // The innovations go to Dbuf (plain [i][c][m]) or, when Bd is given, to
 // the tensor-core update's operand (launch_update_tc).
 void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
                      const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, float* Bd,
                      int splits, int* err, cudaStream_t st);
+// The two halves of launch_stats_tc: the observation tiles (and innovations),
+// then the products of M left rows, which are the act rows followed by the
+// obs rows, cut at M (M = p with act.count = 0: the observed rows alone, for
+// Sigma^Y; M = act.count: the state rows alone, for Sigma^XY).
+void launch_yprep_tc(const float* E, long ms, int N, int m, RowSet obs, ObsNoise V, const float* Yx, const float* Yu,
+                     int n_yx, float* Bop, float* Dbuf, float* Bd, cudaStream_t st);
+void launch_stats_tc_rows(const float* E, long ms, int N, int m, RowSet act, RowSet obs, int M, const float* Bop,
+                          float* part1, float* part2, int splits, int* err, cudaStream_t st);
 
 // Member update on the tensor cores: E[act rows] += K D from Kt [p][R] and
 // the operand tiles yprep wrote (Bd); Aop: update_tc_abytes of scratch.
@@ -157,12 +185,16 @@ size_t update_tc_abytes(int Rmax, int p);
 size_t update_tc_bbytes(int N, int m, int p);
 // Kt is turned into the gain tiles Aop first unless the gain kernel already
 // wrote them (prep_gain = false).
-void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop,
+void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop, int max_ctas,
                       const float* Bd, int* err, cudaStream_t st, bool prep_gain = true);
 // Mixed-precision gain: FP64 Cholesky of Cyy on a cluster of 8 CTAs into
 // L [p][p] (p <= 160), then FP64 triangular solves per row of Cxy; bad:
 // device flag (not SPD).
 void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st);
+// Its two halves: the factorisation (reads only the Cyy rows R .. R+p-1 of
+// C) and the substitutions for the R gain rows.
+void launch_chol64(const double* C, int R, int p, double* L, int* bad, int* status, cudaStream_t st);
+void launch_solve64(const double* C, int R, int p, const double* L, const int* bad, float* Kt, cudaStream_t st);
 // Kt = (Cxy Cyy^{-1})^T, [p][R] (FP32 Cholesky, p <= 160); with Aop also the
 // member update's TF32 operand tiles of the gain.
 void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop = nullptr);
@@ -192,7 +224,7 @@ void cnn_fused_pack_weights(const float* w1, const float* w2, const float* w3, v
 // once per member.  next == nullptr: no advance.
 struct UAdvance {
     float* next = nullptr;
-    const float* w = nullptr;
+    NoiseSrc w;
 };
 int launch_cnn_fused(const float* X, long x_ms, const float* U, long u_ms, float* Xout, long o_ms,
                      const float* Bmat, int Nb, int n, int m, int l, const float* b1, const float* b2,
@@ -229,14 +261,16 @@ void launch_tc_selftest(int* res, cudaStream_t st);
 // eps == nullptr: no perturbation.
 void launch_constraint_obs(float* E, long ms, int N, int m, int n, int xrow, int urow, int zrow, int c,
                            const float* G, const int* cols, int nk, const float* h, float alpha, float beta,
-                           const float* eps, cudaStream_t st);
+                           NoiseSrc eps, cudaStream_t st);
 
 // Philox-4x32-10 normal noise (Salmon et al., SC'11) for one solve.
 // Philox normals for one solve; the solve index is read from *solve_ctr
 // and then incremented on the device (two launches).
 void launch_philox_noise(float* out, size_t count_total, unsigned long long seed,
                          unsigned long long* solve_ctr, const size_t* seg_end, const float* seg_sigma,
-                         int n_seg, cudaStream_t st);
+                         int n_seg, cudaStream_t st, bool tick = true);
+// Advances the device solve index by one (the end of a solve's draws).
+void launch_counter_tick(unsigned long long* solve_ctr, cudaStream_t st);
 
 }  // namespace oic
 

@@ -22,7 +22,7 @@
 // stage) into a raw shared-memory ring with cp.async, RD - 1 stages ahead,
 // then shift, split, accumulate the S1 sums and store hi / lo into
 // 128-byte-swizzled K-major tiles; a loader bulk-copies the member's
-// pre-split observation tile; one thread issues the MMAs.  yprep_kernel
+// pre-split observation tile; one warp (an elected lane) issues the MMAs.  yprep_kernel
 // runs first, once per analysis: it writes the observation tiles, the
 // shifted observation rows e_i (the producers' source for left rows >= R,
 // so every left row is one plain row of some buffer) and the innovations
@@ -54,9 +54,10 @@ __device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, in
                                         const ObsNoise& V, int p, int i, int c, int j)
 {
     float4 v = __ldg(reinterpret_cast<const float4*>(E + (long)i * ms + (long)obs.rows[c] * m + j));
-    if (V.Va != nullptr && c < p - obs.nc) {         // constraint rows carry their noise in E
-        const float* vr = c < V.pa ? V.Va + ((long)i * V.pa + c) * m : V.Vb + ((long)i * (p - obs.nc - V.pa) + (c - V.pa)) * m;
-        v = f4add(v, __ldg(reinterpret_cast<const float4*>(vr + j)));
+    if (V.a.live() && c < p - obs.nc) {              // constraint rows carry their noise in E
+        const float4 w = c < V.pa ? noise4(V.a, ((long)i * V.pa + c) * m + j)
+                                  : noise4(V.b, ((long)i * (p - obs.nc - V.pa) + (c - V.pa)) * m + j);
+        v = f4add(v, w);
     }
     return v;
 }
@@ -160,14 +161,14 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 __global__ void __launch_bounds__(ST_NT, 1)
 stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, RowSet obs,
                 const float* __restrict__ Ysh, const float* __restrict__ Bop, int pp, int KH, int S, int splits,
-                int tmem_cols, float* __restrict__ part1, float* __restrict__ part2, int* __restrict__ err)
+                int tmem_cols, int M, float* __restrict__ part1, float* __restrict__ part2, int* __restrict__ err)
 {
     pdl_begin();
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t s0 = (raw + 1023u) & ~1023u;                     // swizzle atoms need 1024-byte alignment
     unsigned char* smem = smem_raw + (s0 - raw);
-    const int R = act.count, p = obs.count, M = R + p;
+    const int R = act.count, p = obs.count;             // left rows: act rows, then obs rows, cut at M <= R + p
     const int STAGE = 2 * ATILE + 2 * pp * 128;
     const uint32_t rawring = s0 + S * STAGE;
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem + S * STAGE + RD * RTILE);   // full bful free done
@@ -347,14 +348,17 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
         // the copies in flight land before the CTA leaves
         for (int r = q - S < 0 ? 0 : q - S; r < q; ++r)
             tc::mbar_wait_bounded(bful + r % S, (uint32_t)((r / S) & 1), ST_WAIT);
-    } else if (warp == ST_ISSUER && lane == 0) {
-        // ---- issuer: per stage 4 K steps of 8, three MMAs each
+    } else if (warp == ST_ISSUER) {
+        // ---- issuer: per stage 4 K steps of 8, three MMAs each; the whole
+        // warp runs the loop (warp-uniform operands, outcomes agreed by
+        // vote) and the elected lane issues
         const uint32_t id = idesc_tf32(TM, pp);
         for (int q = 0; q < nst; ++q) {
             const int s = q % S;
             const uint32_t par = (uint32_t)((q / S) & 1);
-            if (!tc::mbar_wait_bounded(full + s, par, ST_WAIT) || !tc::mbar_wait_bounded(bful + s, par, ST_WAIT)) {
-                atomicExch(err, DEV_TIMEOUT);
+            const bool got = tc::mbar_wait_bounded(full + s, par, ST_WAIT) && tc::mbar_wait_bounded(bful + s, par, ST_WAIT);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) atomicExch(err, DEV_TIMEOUT);
                 break;
             }
             tc::fence_after_sync();
@@ -365,13 +369,13 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
                 const uint32_t al = sw_desc(base + ATILE + ks * 32);
                 const uint32_t bh = sw_desc(base + 2 * ATILE + ks * 32);
                 const uint32_t bl = sw_desc(base + 2 * ATILE + pp * 128 + ks * 32);
-                st_mma(tmem, ah, bh, id, (q | ks) != 0 ? 1u : 0u);
-                st_mma(tmem, ah, bl, id, 1u);
-                st_mma(tmem, al, bh, id, 1u);
+                st_mma_el(tmem, ah, bh, id, (q | ks) != 0 ? 1u : 0u);
+                st_mma_el(tmem, ah, bl, id, 1u);
+                st_mma_el(tmem, al, bh, id, 1u);
             }
-            tc::mma_commit(freeb + s);
+            tc::mma_commit_elect(freeb + s);
         }
-        tc::mma_commit(done);
+        tc::mma_commit_elect(done);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -412,21 +416,35 @@ bool stats_tc_supported(int m, int p)
     return p >= 1 && m >= 4 && m % 4 == 0 && stats_tc_pp(p) <= 256 && stats_tc_smem(p) <= 232448;
 }
 
-void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
-                     const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, float* Bd,
-                     int splits, int* err, cudaStream_t st)
+void launch_yprep_tc(const float* E, long ms, int N, int m, RowSet obs, ObsNoise V, const float* Yx, const float* Yu,
+                     int n_yx, float* Bop, float* Dbuf, float* Bd, cudaStream_t st)
 {
-    const int p = obs.count, M = act.count + p, pp = stats_tc_pp(p), KH = stats_tc_kh(m);
+    const int p = obs.count, pp = stats_tc_pp(p), KH = stats_tc_kh(m);
     const int KCD = (p + 31) / 32;
     float* Ysh = Bop + (size_t)N * KH * 2 * pp * 32;      // after the observation tiles
     const size_t ysm = Bd != nullptr ? sizeof(float) * 32 * (32 * KCD + 1) : 0;
     pdl_launch(yprep_kernel, N * KH, 256, ysm, st, E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop, Ysh, Dbuf, Bd, KCD);
+}
+
+void launch_stats_tc_rows(const float* E, long ms, int N, int m, RowSet act, RowSet obs, int M, const float* Bop,
+                          float* part1, float* part2, int splits, int* err, cudaStream_t st)
+{
+    const int p = obs.count, pp = stats_tc_pp(p), KH = stats_tc_kh(m);
+    const float* Ysh = Bop + (size_t)N * KH * 2 * pp * 32;
     const int S = st_stages(pp);
     const int cols = pp <= 32 ? 32 : pp <= 64 ? 64 : pp <= 128 ? 128 : 256;
     const size_t smem = stats_tc_smem(p);
     cudaFuncSetAttribute(stats_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    pdl_launch(stats_tc_kernel, dim3(stats_tc_rtiles(M), splits), ST_NT, smem, st, E, ms, N, m, act, obs, Ysh, Bop, pp, KH,
-                                                                           S, splits, cols, part1, part2, err);
+    pdl_launch(stats_tc_kernel, dim3(stats_tc_rtiles(M), splits), ST_NT, smem, st, E, ms, N, m, act, obs, Ysh, Bop, pp,
+               KH, S, splits, cols, M, part1, part2, err);
+}
+
+void launch_stats_tc(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
+                     const float* Yu, int n_yx, float* Bop, float* part1, float* part2, float* Dbuf, float* Bd,
+                     int splits, int* err, cudaStream_t st)
+{
+    launch_yprep_tc(E, ms, N, m, obs, V, Yx, Yu, n_yx, Bop, Dbuf, Bd, st);
+    launch_stats_tc_rows(E, ms, N, m, act, obs, act.count + obs.count, Bop, part1, part2, splits, err, st);
 }
 
 }  // namespace oic

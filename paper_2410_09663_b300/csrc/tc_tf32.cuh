@@ -56,6 +56,20 @@ __device__ __forceinline__ void st_mma(uint32_t d, uint32_t a, uint32_t b, uint3
         "r"(a), "r"(b), "r"(idesc), "r"(acc), "r"(SW_DESC_HI)
         : "memory");
 }
+// The same MMA called by a whole warp with warp-uniform operands: the
+// elected lane issues it, and the operands stay in uniform registers.
+__device__ __forceinline__ void st_mma_el(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .b64 da, db;\n\t.reg .pred p, e;\n\t"
+        "mov.b64 da, {%1, %5};\n\t"
+        "mov.b64 db, {%2, %5};\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], da, db, %3, p;\n\t}\n" ::"r"(d),
+        "r"(a), "r"(b), "r"(idesc), "r"(acc), "r"(SW_DESC_HI)
+        : "memory");
+}
 // instruction descriptor: TF32 A and B (format 2), FP32 D, K-major, N, M
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
 {

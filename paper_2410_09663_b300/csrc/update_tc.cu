@@ -14,7 +14,7 @@
 // A persistent grid walks work items (column group, row tile), row tile
 // fastest so that consecutive items of a CTA reuse the same Bd rows from L2.
 // Per item a loader bulk-copies one stage per K chunk (A hi / lo and
-// B hi / lo, 64 KB) into a 3-stage ring, one thread issues the MMAs into
+// B hi / lo, 64 KB) into a 3-stage ring, one warp (an elected lane) issues the MMAs into
 // one of two tensor-memory accumulators, and four drain warps add the
 // finished accumulator into the ensemble (one lane per row, 16 columns at a
 // time) while the next item accumulates into the other one.
@@ -121,21 +121,24 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
         }
         for (int r = q - UT_S < 0 ? 0 : q - UT_S; r < q; ++r)
             tc::mbar_wait_bounded(full + r % UT_S, (uint32_t)((r / UT_S) & 1), UT_WAIT);
-    } else if (warp == UT_ISSUER && lane == 0) {
+    } else if (warp == UT_ISSUER) {
+        // the whole warp runs the issue loop (warp-uniform operands, outcomes
+        // agreed by vote); the elected lane issues each MMA and commit
         const uint32_t id = idesc_tf32(UT_M, UT_N);
         bool ok = true;
         for (int u = 0; u < t1 - t0 && ok; ++u) {
             const int buf = u & 1;
             const uint32_t acc = tmem + buf * UT_N;
-            if (u >= 2 && !tc::mbar_wait_bounded(accd + buf, (uint32_t)((u / 2 - 1) & 1), UT_WAIT)) {
-                atomicExch(err, DEV_TIMEOUT);
+            if (u >= 2 &&
+                !__all_sync(0xffffffffu, tc::mbar_wait_bounded(accd + buf, (uint32_t)((u / 2 - 1) & 1), UT_WAIT))) {
+                if (lane == 0) atomicExch(err, DEV_TIMEOUT);
                 break;
             }
             tc::fence_after_sync();
             for (int kc = 0; kc < KCH; ++kc) {
                 const int q = u * KCH + kc, s = q % UT_S;
-                if (!tc::mbar_wait_bounded(full + s, (uint32_t)((q / UT_S) & 1), UT_WAIT)) {
-                    atomicExch(err, DEV_TIMEOUT);
+                if (!__all_sync(0xffffffffu, tc::mbar_wait_bounded(full + s, (uint32_t)((q / UT_S) & 1), UT_WAIT))) {
+                    if (lane == 0) atomicExch(err, DEV_TIMEOUT);
                     ok = false;
                     break;
                 }
@@ -147,13 +150,13 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
                     const uint32_t al = sw_desc(base + UT_PART + ks * 32);
                     const uint32_t bh = sw_desc(base + 2 * UT_PART + ks * 32);
                     const uint32_t bl = sw_desc(base + 3 * UT_PART + ks * 32);
-                    st_mma(acc, ah, bh, id, (kc | ks) != 0 ? 1u : 0u);
-                    st_mma(acc, ah, bl, id, 1u);
-                    st_mma(acc, al, bh, id, 1u);
+                    st_mma_el(acc, ah, bh, id, (kc | ks) != 0 ? 1u : 0u);
+                    st_mma_el(acc, ah, bl, id, 1u);
+                    st_mma_el(acc, al, bh, id, 1u);
                 }
-                tc::mma_commit(freeb + s);
+                tc::mma_commit_elect(freeb + s);
             }
-            tc::mma_commit(accf + buf);
+            tc::mma_commit_elect(accf + buf);
         }
     } else if (warp < 4) {
         // drain: lane = row a of the tile; the item's ensemble values are
@@ -223,7 +226,7 @@ int update_tc_kch(int p) { return (p + UT_KC - 1) / UT_KC; }
 size_t update_tc_abytes(int Rmax, int p) { return (size_t)((Rmax + UT_M - 1) / UT_M) * update_tc_kch(p) * 2 * UT_PART; }
 size_t update_tc_bbytes(int N, int m, int p) { return (size_t)update_tc_kch(p) * 2 * N * m * 128; }
 
-void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop,
+void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop, int max_ctas,
                       const float* Bd, int* err, cudaStream_t st, bool prep_gain)
 {
     const int R = act.count, rtiles = (R + UT_M - 1) / UT_M, KCH = update_tc_kch(p);
@@ -231,7 +234,8 @@ void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* 
     if (prep_gain) pdl_launch(kprep_kernel, (unsigned)((prep + 255) / 256), 256, 0, st, Kt, R, p, rtiles, KCH, Aop);
     const long NM = (long)N * m;
     const int items = (int)((NM + UT_N - 1) / UT_N) * rtiles;
-    const int grid = items < 148 ? items : 148;
+    const int cap = max_ctas > 0 ? max_ctas : 148;
+    const int grid = items < cap ? items : cap;
     const size_t smem = update_tc_smem();
     static DeviceOnce attr_set;
     attr_set.run([smem] {

@@ -128,13 +128,20 @@ class Server:
     def run(self, arrivals):
         """Serve `arrivals` = [(arrival time in s, problem id)] in real time.
         Returns one record per request: (pid, step, arrival, start, done) in
-        seconds from the start, plus U_applied if keep_outputs."""
+        seconds from the start, plus U_applied if keep_outputs.  Afterwards
+        `device_intervals[i]` holds (start, end) in ms of request i's work on
+        the GPU (CUDA events on the problem's stream, relative to an event
+        recorded when the run began), from which overlap on the device is
+        measured."""
         torch = self.torch
         order = sorted(range(len(arrivals)), key=lambda i: arrivals[i][0])
         rec = [None] * len(arrivals)
         outs = [None] * len(arrivals)
+        evs = [None] * len(arrivals)
         running = []
         nxt, left = 0, len(arrivals)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev0.record(torch.cuda.current_stream(self.device))
         t0 = time.perf_counter()
         while left:
             now = time.perf_counter() - t0
@@ -169,9 +176,12 @@ class Server:
                 i = p.queue.popleft()
                 k = p.k
                 with torch.cuda.stream(p.stream):
+                    ev_start = torch.cuda.Event(enable_timing=True)
+                    ev_start.record(p.stream)
                     p.solver.oic_step(p.refs[k:k + p.wl.H + 1], p.uref, None, p.u_out, p.x_out)
-                    ev = torch.cuda.Event()
+                    ev = torch.cuda.Event(enable_timing=True)
                     ev.record(p.stream)
+                evs[i] = (ev_start, ev)
                 p.running = (i, ev, time.perf_counter() - t0)
                 running.append(p)
             if not running and nxt < len(order):
@@ -179,7 +189,19 @@ class Server:
                 if wait > 0:
                     time.sleep(min(wait, 0.002))
         wall = time.perf_counter() - t0
+        torch.cuda.synchronize(self.device)
+        self.device_intervals = [(ev0.elapsed_time(a), ev0.elapsed_time(b)) for a, b in evs]
         return rec, outs, wall
+
+
+def max_overlap(intervals):
+    """Largest number of intervals (start, end) open at one instant."""
+    pts = sorted([(s, 1) for s, _ in intervals] + [(e, -1) for _, e in intervals], key=lambda x: (x[0], x[1]))
+    cur = best = 0
+    for _, d in pts:
+        cur += d
+        best = max(best, cur)
+    return best
 
 
 def poisson_arrivals(rate, count, n_problems, seed):

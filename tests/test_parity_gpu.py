@@ -236,6 +236,47 @@ def test_step_graph_replays_match_eager_launches(cuda_ok, name, monkeypatch):
     assert set(prof) == {"cov", "gain"}
 
 
+def _device_noise_steps(wl, steps, precision, cons=None):
+    w, b = wl.flat_weights()
+    s = oic.Solver(oic.config_from_workload(wl, noise_mode=oic.OIC_NOISE_PHILOX, seed=31, precision=precision),
+                   w, b, wl.B(), constraints=cons)
+    s.oic_reset_host(wl.X0(), wl.U_init())
+    xr_all = wl.X_ref_all(steps)
+    out = []
+    for k in range(steps):
+        Ua = np.zeros((wl.l, wl.m), np.float32)
+        Xn = np.zeros((wl.n, wl.m), np.float32)
+        s.oic_step_host(xr_all[k:k + wl.H + 1], wl.U_ref(), None, Ua, Xn)
+        out.append((Ua, Xn))
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("case", ["fused", "mixed", "per_layer", "constrained"])
+def test_noise_drawn_in_place_equals_the_noise_buffer(cuda_ok, case, monkeypatch):
+    """Device-noise mode: the kernels that consume the random numbers draw
+    them in place from the Philox stream; with OIC_NOISE_BUFFER the noise
+    kernel writes the stream to the buffer first and they read it.  The two
+    give bit-identical controls and states, step after step."""
+    cons = None
+    prec = oic.OIC_PREC_FP32
+    if case == "fused":
+        wl = W.working_64().with_(N=32, H=3)
+    elif case == "mixed":
+        wl, prec = MIXED_CASES["m32_c64"].with_(N=24, H=3, S=3), oic.OIC_PREC_MIXED
+    elif case == "per_layer":
+        wl = MID
+    else:
+        wl = W.small_16()
+        cons = W.u_box(wl.n, wl.l, 0.05)
+    drawn = _device_noise_steps(wl, 3, prec, cons)
+    monkeypatch.setenv("OIC_NOISE_BUFFER", "1")
+    buffered = _device_noise_steps(wl, 3, prec, cons)
+    for (a0, x0), (a1, x1) in zip(drawn, buffered):
+        assert np.array_equal(a0, a1) and np.array_equal(x0, x1)
+    assert not np.array_equal(drawn[0][0], drawn[1][0])
+
+
 @pytest.mark.parametrize("precision", [oic.OIC_PREC_FP32, oic.OIC_PREC_MIXED])
 def test_enks_update_matches_oracle(cuda_ok, precision):
     """FP32 mode: FP32 gain by elimination; mixed mode: FP64 mean correction,
@@ -460,6 +501,36 @@ def test_served_results_equal_each_problem_alone_with_evictions(cuda_ok):
         assert k == i // 3
         assert np.array_equal(outs[i], alone[pid][k][0])
     assert sum(p.evictions for p in srv.problems.values()) >= 2
+
+
+def test_served_results_in_the_mix_equal_each_problem_alone(cuda_ok):
+    """Continuous batching with every problem resident: requests of four
+    problems of different grid, ensemble and horizon sizes arrive within a
+    millisecond of each other, so steps of different problems are on
+    the GPU at the same time (their CUDA-event intervals on the device
+    overlap); every applied control equals, bit for bit, the same problem
+    stepped alone, and nothing is evicted."""
+    from paper_2410_09663_b300 import serving
+    wls = [W.small_16(), W.small_16().with_(N=48, H=3, seed=7), W.working_64().with_(N=32, H=3, seed=11),
+           W.small_16().with_(N=24, H=4, seed=9)]
+    steps = 3
+    alone = [_steps_alone(w, steps, oic.OIC_PREC_FP32) for w in wls]
+    srv = serving.Server("cuda", budget_bytes=1, precision=oic.OIC_PREC_FP32, keep_outputs=True)
+    for pid, w in enumerate(wls):
+        srv.add(pid, w, steps_max=steps)
+    srv.budget = sum(p.bytes for p in srv.problems.values())
+    arrivals = [(0.0001 * i, i % len(wls)) for i in range(len(wls) * steps)]
+    rec, outs, _ = srv.run(arrivals)
+    for i, (t, pid) in enumerate(arrivals):
+        k = rec[i][1]
+        assert k == i // len(wls)
+        assert np.array_equal(outs[i], alone[pid][k][0])
+    assert sum(p.evictions for p in srv.problems.values()) == 0
+    iv = srv.device_intervals
+    overlapping = [(i, j) for i in range(len(iv)) for j in range(i + 1, len(iv))
+                   if arrivals[i][1] != arrivals[j][1] and iv[i][0] < iv[j][1] and iv[j][0] < iv[i][1]]
+    assert overlapping, iv
+    assert serving.max_overlap(iv) >= 2
 
 
 @pytest.mark.parametrize("l,mu,m", [(4, 1, 16), (8, 3, 64), (16, 8, 128), (5, 7, 24)])
