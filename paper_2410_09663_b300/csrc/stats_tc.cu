@@ -7,9 +7,11 @@
 //
 // with d_i = l_i - l_0 the left rows (the R active state rows, then the p
 // perturbed observation rows Y^i = H X^i + V^i) shifted by member 0 and
-// e_i = Y^i - Y^0 the observation rows shifted the same way; the
-// finalisation removes the mean exactly, C = sum part2 - (1/N) S1_a S1_c^T.
-// The member-0 shift keeps every operand at the scale of the anomalies.
+// e_i = Y^i - H X^0 the observation rows shifted by member 0's unperturbed
+// value (any shift constant over the members gives the same moments; this
+// one needs no draw of member 0's perturbation); the finalisation removes
+// the mean exactly, C = sum part2 - (1/N) S1_a S1_c^T.  The shift keeps
+// every operand at the scale of the anomalies and the perturbations.
 //
 // FP32 accuracy from TF32 operands: x = hi + lo with hi = tf32(x) and
 // lo = tf32(x - hi), so x is carried to ~2^-22; per K step the products
@@ -63,7 +65,7 @@ __device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, in
 }
 
 // One block per (member i, K chunk kh of 32 columns j); thread units
-// (observation row c < pp, 16-byte chunk): e = Y^i - Y^0 split into the B
+// (observation row c < pp, 16-byte chunk): e = Y^i - H X^0 split into the B
 // tile [i][kh][hi rows pp | lo rows pp][128 B] (swizzled; zero beyond p and
 // beyond m); for c < p also e itself into Ysh [i][c][m].  The innovations
 // D^i = Ybar - Y^i (Ybar = 0 on the obs.nc trailing constraint rows, whose
@@ -94,7 +96,7 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
         float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi, d = hi;
         if (c < p && j < m) {
             const float4 y = yrow4(E, ms, m, obs, V, p, i, c, j);
-            const float4 y0 = yrow4(E, ms, m, obs, V, p, 0, c, j);
+            const float4 y0 = __ldg(reinterpret_cast<const float4*>(E + (long)obs.rows[c] * m + j));
             const float4 ev = f4sub(y, y0);
             split_tf32(ev, hi, lo);
             *reinterpret_cast<float4*>(Ysh + ((long)i * p + c) * m + j) = ev;
@@ -133,12 +135,15 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
     }
 }
 
-// a left row's source: member 0's row and the stride between members
-// (E rows, or the shifted observation rows, whose member-0 row is zero)
+// a left row's source: member 0's row and the stride between members (E
+// rows, shifted by member 0's value; or the observation rows e_i yprep
+// wrote, already shifted by the same constant as the right-hand side, so
+// that S1 of these rows is the right-hand side's sum)
 struct RowSrc {
     const float* e;
     long stride;
     bool live;
+    bool shift;
 };
 
 __device__ __forceinline__ float4 load_unit(const RowSrc& s, int i, int j, int m)
@@ -212,9 +217,11 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
             if (a < R) {
                 src[u].e = E + (long)act.rows[a] * m;
                 src[u].stride = ms;
+                src[u].shift = true;
             } else {
                 src[u].e = Ysh + (long)(a < M ? a - R : 0) * m;
                 src[u].stride = (long)p * m;
+                src[u].shift = false;
             }
         }
         // raw ring: thread's unit u of stage q at raw(q % RD) + row * 128 + k * 16
@@ -248,7 +255,7 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
                 if (kh > 0) flush(kh - 1);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    v0[u] = load_unit(src[u], 0, j, m);
+                    v0[u] = src[u].shift ? load_unit(src[u], 0, j, m) : make_float4(0.f, 0.f, 0.f, 0.f);
                     s1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
