@@ -339,12 +339,17 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
 // panel (its 8 x 8 diagonal block read into every lane and factored there
 // redundantly, so the pivot chain has no shuffles in it; each lane then forms
 // the panel's U rows for its own columns; a pivot <= 0 means "not positive
-// definite") while the workers update the remaining rows and run their
-// forward substitutions.  Worker w solves gain row a = 9 b + w: lane t holds
-// elements t + 32 s (s < SL); its forward substitution takes one block of
-// eight per panel inside the loop, the backward one follows, eight elements
-// per block from the bottom.  Only U's upper rows are stored: U[i][c] with
-// lane = i (ld odd) reads conflict-free for the backward updates.
+// definite") while the workers update the remaining rows (two at a time,
+// their loads in flight together) and run their forward substitutions.
+// Workers 0-2 (warps 1-3, one per sub-partition) solve gain rows
+// a = 3 b + w: lane t holds elements t + 32 s (s < SL); the forward
+// substitution takes one block of eight per panel inside the loop, the
+// backward one follows, eight elements per block from the bottom.  Only U's
+// upper rows are stored: U[i][c] with lane = i (ld odd) reads conflict-free
+// for the backward updates.  Three rows per CTA rather than nine: the
+// backward substitutions, which issue-bound the kernel's tail, then run one
+// warp per scheduler (the factorisation is repeated in 3x as many CTAs,
+// which the GPU has to spare).
 //
 // Warp roles: warp 0 factors; warps 4 and 8, which share its scheduler
 // (warp w issues from sub-partition w mod 4), stay idle; the other nine are
@@ -360,7 +365,8 @@ __device__ __forceinline__ float gsel(const float (&v)[N], int q)
 
 constexpr int GC_NW = 12;                         // warps per CTA
 constexpr int GC_T = 32 * GC_NW;
-constexpr int GC_W = 9;                           // worker warps = gain rows per CTA
+constexpr int GC_W = 9;                           // worker warps (the trailing updates)
+constexpr int GC_R = 3;                           // gain rows per CTA: workers 0-2, one per sub-partition
 constexpr int GC_B = 8;                           // panel height = substitution block
 constexpr int GC_BAR_PANEL = 1;                   // named barrier: next panel's rows updated
 constexpr int GC_TILE = 128 * 128;                // one operand part of the update's gain tile, bytes
@@ -478,6 +484,48 @@ __device__ __forceinline__ void panel_update_row(float* __restrict__ A, int ld, 
     }
 }
 
+// The same for rows i and i2 (i2 >= p: none) at once, their loads in flight
+// together.
+template <int SL>
+__device__ __forceinline__ void panel_update_rows2(float* __restrict__ A, int ld, int p, int j0, int i, int i2,
+                                                   int lane, const float (&pu)[GC_B][SL])
+{
+    if (i2 >= p) {
+        panel_update_row<SL>(A, ld, p, j0, i, lane, pu);
+        return;
+    }
+    float q[GC_B], q2[GC_B];
+#pragma unroll
+    for (int d = 0; d < GC_B; ++d) {
+        q[d] = A[(j0 + d) * ld + i];
+        q2[d] = A[(j0 + d) * ld + i2];
+    }
+    float* ai = A + i * ld;
+    float* ai2 = A + i2 * ld;
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int c = lane + 32 * s;
+        if (c >= i && c < p) {
+            float y = 0.f, z = 0.f;
+#pragma unroll
+            for (int d = 0; d < GC_B; d += 2) {
+                y = fmaf(q[d], pu[d][s], y);
+                z = fmaf(q[d + 1], pu[d + 1][s], z);
+            }
+            ai[c] -= y + z;
+        }
+        if (c >= i2 && c < p) {
+            float y = 0.f, z = 0.f;
+#pragma unroll
+            for (int d = 0; d < GC_B; d += 2) {
+                y = fmaf(q2[d], pu[d][s], y);
+                z = fmaf(q2[d + 1], pu[d + 1][s], z);
+            }
+            ai2[c] -= y + z;
+        }
+    }
+}
+
 template <int SL>
 __global__ void __launch_bounds__(GC_T, 1)
 gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status,
@@ -494,37 +542,40 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
     const bool factor = w == 0;
     const int wk = gc_worker(w);                  // worker index, -1: not a worker
     const double* Cyy = C + (long)R * p;
-    // staging: zero the padding, then Cyy row by row (each warp a row, the
-    // lanes its columns), every load of a thread in flight at once
+    // staging: zero the padding, then the worker's gain row and Cyy (each
+    // warp rows w, w + 12, ..., the lanes their columns) in rounds of two rows
+    // per warp (measured faster than one round of every row)
     if (pp > p)
         for (int e = tid; e < pp * ld; e += GC_T) {
             const int i = e / ld, c = e % ld;
             if (i >= p || c >= p) A[e] = 0.f;
         }
+    const int a = blockIdx.x * GC_R + wk;
+    const bool mine = wk >= 0 && wk < GC_R && a < R;
+    float b[SL];
     {
-        constexpr int U = 2 * SL;                 // (row, column) pairs per lane: rows w, w + 12, ...
-        for (int i0 = w; i0 < p; i0 += GC_NW * U / SL) {
-            double v[U];
+        constexpr int RW = 2;                                       // rows per warp and round
+        double g[SL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+        for (int s = 0; s < SL; ++s) {
+            const int i = lane + 32 * s;
+            g[s] = mine && i < p ? __ldg(C + (long)a * p + i) : 0.0;
+        }
+        for (int i0 = w; i0 < p; i0 += GC_NW * RW) {
+            double v[RW * SL];
+#pragma unroll
+            for (int u = 0; u < RW * SL; ++u) {
                 const int i = i0 + GC_NW * (u / SL), c = lane + 32 * (u % SL);
                 v[u] = i < p && c < p ? __ldg(Cyy + (long)i * p + c) : 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < RW * SL; ++u) {
                 const int i = i0 + GC_NW * (u / SL), c = lane + 32 * (u % SL);
                 if (i < p && c < p) A[i * ld + c] = (float)v[u];
             }
         }
-    }
-    // the worker's gain row, loaded while panel 0 is factored
-    const int a = blockIdx.x * GC_W + wk;
-    const bool mine = wk >= 0 && a < R;
-    float b[SL];
 #pragma unroll
-    for (int s = 0; s < SL; ++s) {
-        const int i = lane + 32 * s;
-        b[s] = mine && i < p ? (float)__ldg(C + (long)a * p + i) : 0.f;
+        for (int s = 0; s < SL; ++s) b[s] = (float)g[s];
     }
     __syncthreads();
     bool fbad = false;                            // the factor warp: a panel failed
@@ -555,7 +606,8 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
                 asm volatile("bar.arrive %0, %1;" ::"n"(GC_BAR_PANEL), "n"(32 * (GC_W + 1)) : "memory");
             }
             // the rows from panel j+2 on
-            for (int i = n0 + GC_B + wk; i < p; i += GC_W) panel_update_row<SL>(A, ld, p, j0, i, lane, pu);
+            for (int i = n0 + GC_B + wk; i < p; i += 2 * GC_W)
+                panel_update_rows2<SL>(A, ld, p, j0, i, i + GC_W, lane, pu);
             // forward substitution, block j of the own gain row: U^T z = b
             if (mine) {
                 const int slot = j0 >> 5, l0 = j0 & 31;
@@ -661,7 +713,7 @@ void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cud
         return cudaFuncSetAttribute(gain_chol_kernel<SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)gain_chol_smem(32 * SL)) == cudaSuccess;
     });
-    const int grid = R > 0 ? (R + GC_W - 1) / GC_W : 1;
+    const int grid = R > 0 ? (R + GC_R - 1) / GC_R : 1;
     pdl_launch(gain_chol_kernel<SL>, grid, GC_T, smem, st, C, R, p, Kt, status, Aop);
 }
 
