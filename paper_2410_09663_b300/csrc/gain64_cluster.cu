@@ -108,7 +108,7 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
     pdl_begin();
     __shared__ __align__(16) double own[C64_OWN][PB][C64_PMAX];    // this CTA's panels (rows of A, then of U)
     __shared__ __align__(16) double pan[PB][C64_PMAX];             // the current panel (U rows)
-    __shared__ double rsv[PB];
+    __shared__ double rsv[PB], ips[PB];                          // 1 / U[g][g], 1 / pivot
     __shared__ __align__(8) uint64_t rdy[C64_NB];
     __shared__ int bad_here, bad_seen, timeout;
     const int tid = threadIdx.x, w = tid / 32, lane = tid % 32;
@@ -133,23 +133,38 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
     __syncthreads();
     cl_sync();                                          // every barrier initialised before any remote arrive
 
+    // 1 / sqrt and 1 / pivot d of the panel at column c0, by warp 0 alone (the
+    // pivot chain is a series of dependent FP64 operations of ~64 cycles each,
+    // whatever the number of active lanes; computed by every warp, they also
+    // queued behind each other on the FP64 pipe)
+    auto pivot = [&](double (*A)[C64_PMAX], int c0, int d) {
+        const int g = c0 + d;
+        const double piv = A[d][g];
+        const double r = (g < p && piv > 0.0) ? rsqrt64(piv) : 0.0;
+        if (lane == 0) {
+            if (g < p && !(piv > 0.0)) bad_here = 1;
+            rsv[d] = r;
+            ips[d] = r * r;
+        }
+    };
     // the owner eliminates panel B's pivots (right-looking, rows in own[B / CL]),
     // scales the rows to U and releases the panel to every CTA
     auto eliminate = [&](int B) {
         double (*A)[C64_PMAX] = own[B / CL];
         const int c0 = PB * B;
+        if (w == 0) pivot(A, c0, 0);
+        __syncthreads();
         for (int d = 0; d < PB; ++d) {
-            const int g = c0 + d;
-            const double piv = A[d][g];
-            const double r = (g < p && piv > 0.0) ? rsqrt64(piv) : 0.0;
-            const double ip = r * r;
-            if (g < p && !(piv > 0.0) && tid == 0) bad_here = 1;
-            if (tid == 0) rsv[d] = r;
-            // rows e > d of the panel, columns c >= c0 + e: warp w takes row d + 1 + w
+            // rows e > d of the panel, columns c >= c0 + e: warp w takes row d + 1 + w;
+            // warp 0, whose row holds the next pivot, then computes its reciprocals
             const int e = d + 1 + w;
             if (e < PB) {
-                const double f = A[d][c0 + e] * ip;
+                const double f = A[d][c0 + e] * ips[d];
                 for (int c = c0 + e + lane; c < pp; c += 32) A[e][c] = fma(-f, A[d][c], A[e][c]);
+                if (w == 0) {
+                    __syncwarp();
+                    pivot(A, c0, d + 1);
+                }
             }
             __syncthreads();
         }
