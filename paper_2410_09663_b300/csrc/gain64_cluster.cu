@@ -173,8 +173,9 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
             if (c >= c0 + d) A[d][c] *= rsv[d];
         }
         __syncthreads();
-        if (tid == 0)
-            for (uint32_t t = 0; t < CL; ++t) cl_arrive(cl_map(rdy + B, t));
+        // one remote arrive per CTA of the cluster, each from its own lane (issued
+        // one after another by one thread they took ~1.7 us)
+        if (tid < CL) cl_arrive(cl_map(rdy + B, (uint32_t)tid));
     };
     // rank-8 update of panel B2's rows (this CTA's), columns c >= row, by the panel in pan
     auto update = [&](int B2) {
