@@ -295,7 +295,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
                  const float* __restrict__ b1, const float* __restrict__ b2, const float* __restrict__ b3,
                  const __half* __restrict__ wpk, float rs, int* __restrict__ err, UAdvance ua)
 {
-    pdl_begin();
+    pdl_trigger();
     using S = FS<C, G>;
     static_assert(C == 32, "16 drain warps = 4 lane quarters x 4 groups of 8 channels");
     static_assert(MB_COUNT * 8 + 4 <= 128, "MISC region");
@@ -335,6 +335,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    pdl_wait();                                         // the set-up above reads no kernel's output
 
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n;

@@ -244,7 +244,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
                  const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias, int Nb, int n,
                  int* __restrict__ err)
 {
-    pdl_begin();
+    pdl_trigger();
     using S = BS<CI, CO, MODE, W>;
     static_assert(MODE == MODE_HIDDEN, "hidden layers");
     constexpr int G = S::G;
@@ -272,6 +272,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    pdl_wait();                                         // the set-up above reads no kernel's output
 
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n;
@@ -413,7 +414,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
                        const float* __restrict__ bias, const __nv_bfloat16* __restrict__ wlast,
                        const float* __restrict__ blast, int Nb, int n, float rs, int* __restrict__ err)
 {
-    pdl_begin();
+    pdl_trigger();
     using S = BS<C, C, MODE_FUSED, W>;
     constexpr int G = S::G, m = W;
     constexpr int LIVE = G * W;
@@ -453,6 +454,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    pdl_wait();                                         // the set-up above reads no kernel's output
 
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n;
@@ -707,7 +709,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                        const float* __restrict__ b1, __nv_bfloat16* __restrict__ out, int Nb, int n,
                        int* __restrict__ err)
 {
-    pdl_begin();
+    pdl_trigger();
     using F = FBS<C, W>;
     using S0 = typename F::S0;
     using S1 = typename F::S1;
@@ -751,6 +753,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    pdl_wait();                                         // the set-up above reads no kernel's output
 
     const int groups = (Nb + G - 1) / G;
     const long total = (long)groups * n;

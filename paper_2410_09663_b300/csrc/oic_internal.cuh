@@ -47,14 +47,19 @@ class DeviceOnce {
 };
 
 // Programmatic dependent launch: every kernel is launched with programmatic
-// stream serialisation, and its first statements let the next kernel in the
-// stream start launching and then wait until the previous one has finished
-// and its writes are visible.  No kernel reads anything before that wait, so
-// the only overlap is launch latency and CTA rasterisation.
+// stream serialisation, and its first statement lets the next kernel in the
+// stream start launching; it then waits until the previous one has finished
+// and its writes are visible (pdl_begin: both at once).  The tensor-core
+// kernels put their set-up between the two (barrier initialisation, tensor
+// memory allocation, copies of the constant weights into shared memory), so
+// that it overlaps the previous kernel's last CTAs; nothing before the wait
+// reads memory that any kernel writes, or writes memory that any kernel reads.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_begin()
 {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_trigger();
+    pdl_wait();
 }
 
 // The same launch without programmatic stream serialisation: the kernel

@@ -168,7 +168,7 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
                 const float* __restrict__ Ysh, const float* __restrict__ Bop, int pp, int KH, int S, int splits,
                 int tmem_cols, int M, float* __restrict__ part1, float* __restrict__ part2, int* __restrict__ err)
 {
-    pdl_begin();
+    pdl_trigger();
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t s0 = (raw + 1023u) & ~1023u;                     // swizzle atoms need 1024-byte alignment
@@ -204,6 +204,7 @@ stats_tc_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet act, 
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    pdl_wait();                                         // the set-up above reads no kernel's output
     bool failed = false;
 
     if (warp < ST_PW) {

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(UT_NT, 1)
 update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float* __restrict__ Aop,
                  const float* __restrict__ Bd, long NM, int KCH, int rtiles, int items, int* __restrict__ err)
 {
-    pdl_begin();
+    pdl_trigger();
     extern __shared__ unsigned char usm_raw[];
     const uint32_t raw = tc::smem_u32(usm_raw);
     const uint32_t s0 = (raw + 1023u) & ~1023u;
@@ -97,6 +97,7 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
+    pdl_wait();                                         // the set-up above reads no kernel's output
     const int nst = (t1 - t0) * KCH;
 
     if (warp == UT_LOADER && lane == 0) {
