@@ -145,6 +145,7 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
             if (g < p && !(piv > 0.0)) bad_here = 1;
             rsv[d] = r;
             ips[d] = r * r;
+            if (g < p) Lg[(long)p * p + g] = r;                 // 1 / L_gg, for the substitutions
         }
     };
     // the owner eliminates panel B's pivots (right-looking, rows in own[B / CL]),
@@ -246,6 +247,11 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
     }
 }
 
+__device__ __forceinline__ void cp_async8(double* dst, const double* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+
 // One warp per gain row a; L staged in shared memory with an odd leading
 // dimension (column reads of the forward pass and row reads of the backward
 // pass are both conflict-free); lane t holds z_i for i = t + 32 q.
@@ -267,12 +273,12 @@ solve64s_kernel(const double* __restrict__ C, int R, int p, const double* __rest
             for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
         return;
     }
-    for (int e = threadIdx.x; e < p * p; e += 32 * S64_W) {
-        const int i = e / p, k = e % p;
-        if (k <= i) Ls[i * ld + k] = __ldg(Lg + e);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < p; i += 32 * S64_W) rinv[i] = 1.0 / Ls[i * ld + i];
+    // the lower triangle of L and 1 / L_ii (written by the factorisation) by
+    // asynchronous 8-byte copies, all in flight at once (one round trip)
+    for (int i = w; i < p; i += S64_W)
+        for (int k = lane; k <= i; k += 32) cp_async8(Ls + i * ld + k, Lg + (long)i * p + k);
+    for (int i = threadIdx.x; i < p; i += 32 * S64_W) cp_async8(rinv + i, Lg + (long)p * p + i);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (a >= R) return;
     double z[S64_Q];

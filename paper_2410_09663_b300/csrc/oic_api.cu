@@ -243,7 +243,7 @@ void compute_layout(oic_handle* h)
     L.D = take(sizeof(float) * N * p * m);
     L.C = take(sizeof(double) * (Ra + p) * p);
     L.K = take(sizeof(float) * Ra * p);
-    L.L64 = take(c.precision == OIC_PREC_MIXED ? sizeof(double) * p * p : 0);
+    L.L64 = take(c.precision == OIC_PREC_MIXED ? sizeof(double) * (p * p + p) : 0);
     // tensor-core anomaly products: the pre-split observation tiles
     L.tB = take(stats_tc_supported(c.m, (int)p) ? stats_tc_bbytes(c.N, (int)p, c.m) : 0);
     // tensor-core update: gain tiles and the transposed innovations

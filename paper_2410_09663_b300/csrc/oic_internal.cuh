@@ -193,8 +193,8 @@ size_t update_tc_bbytes(int N, int m, int p);
 void launch_update_tc(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, float* Aop, int max_ctas,
                       const float* Bd, int* err, cudaStream_t st, bool prep_gain = true);
 // Mixed-precision gain: FP64 Cholesky of Cyy on a cluster of 8 CTAs into
-// L [p][p] (p <= 160), then FP64 triangular solves per row of Cxy; bad:
-// device flag (not SPD).
+// L [p][p] (p <= 160) followed by 1 / L_ii [p], then FP64 triangular solves
+// per row of Cxy; bad: device flag (not SPD).
 void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt, int* status, cudaStream_t st);
 // Its two halves: the factorisation (reads only the Cyy rows R .. R+p-1 of
 // C) and the substitutions for the R gain rows.
