@@ -654,19 +654,23 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
 // the image).
 //
 // Drain pass k: (A) first-layer output row k-1 -> shared slot (k-1) mod 2 once
-// the first layer's MMAs of input row k are done; (B) second-layer output row
-// k-3 -> HBM once the second layer's MMAs of its input row k-2 are done.  The
-// issuer waits pass k before the second layer's MMAs of row k-1 (the slot
-// they read was filled in pass k) and, for both TMEM rings, before reusing the
-// slot drained in pass k.  One drain group runs the passes in order, so a
-// pass barrier also covers every earlier pass, and the second layer's wait in
-// pass k+1 covers reuse of shared slot (k-1) mod 2 in pass k+2.
+// the first layer's MMAs of input row k are done, then an arrival on
+// FB_SLOT(k); (B) second-layer output row k-3 -> HBM once the second layer's
+// MMAs of its input row k-2 are done.  The issuer waits FB_SLOT(k) before the
+// second layer's MMAs of row k-1 (the slot they read was filled in part A)
+// and, for both TMEM rings, before reusing a slot drained in pass k-1 (ring
+// B, part B) or in pass k (ring A, part A).  One drain group runs the passes
+// in order, so an arrival also covers every earlier part, and the second
+// layer's wait in pass k+1 covers reuse of shared slot (k-1) mod 2 in pass
+// k+2.  Arriving after part A, not after the whole pass, lets the second
+// layer's MMAs of row k-1 run while the drains do part B of pass k: two
+// rows of the second layer in flight instead of one.
 enum : int {
     FB_A0FULL = 0,     // [4] first-layer input row f built (f mod 4), 4 producer warps
     FB_A0FREE = 4,     // [4] first-layer MMAs of input row f done (f mod 4)
     FB_HDA = 8,        // [2] first-layer MMAs of input row f done (f mod 2), for the drain
     FB_L1 = 10,        // [2] second-layer MMAs of input row j done (j mod 2)
-    FB_PASS = 12,      // [4] drain pass k done (k mod 4), 16 drain warps
+    FB_SLOT = 12,      // [4] part A of drain pass k done (k mod 4), 16 drain warps
     FB_FIN = 16,
     FB_COUNT = 17
 };
@@ -739,7 +743,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
     for (int e = tid; e < n * l; e += F::NT) sB[e] = Bmat[e];
     if (tid == 0) {
         for (int i = 0; i < FB_COUNT; ++i) {
-            const int cnt = (i >= FB_A0FULL && i < FB_A0FULL + 4) ? F::NPW : (i >= FB_PASS && i < FB_PASS + 4) ? F::NDW : 1;
+            const int cnt = (i >= FB_A0FULL && i < FB_A0FULL + 4) ? F::NPW : (i >= FB_SLOT && i < FB_SLOT + 4) ? F::NDW : 1;
             tc::mbar_init(mb + i, cnt);
         }
         tc::fence_mbar_init();
@@ -800,9 +804,9 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                 };
                 for (int f = f_lo; f <= f_hi && !failed; ++f) {
                     // pass f-2 drained first-layer output row f-3 (its ring A slot is
-                    // the one row f+1 starts in) and second-layer output row f-5
+                    // the one row f+1 starts in), pass f-3 second-layer output row f-6
                     if (f - 2 >= f_lo) {
-                        wait_w(FB_PASS + ((f - 2) & 3));
+                        wait_w(FB_SLOT + ((f - 2) & 3));
                         issue_second(f - 3);
                     }
                     wait_w(FB_A0FULL + (f & 3));
@@ -812,7 +816,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                 }
                 for (int k = f_hi - 1; k <= last && !failed; ++k)
                     if (k >= f_lo) {
-                        wait_w(FB_PASS + (k & 3));
+                        wait_w(FB_SLOT + (k & 3));
                         issue_second(k - 1);
                     }
             }
@@ -881,6 +885,9 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                     }
                     tc::fence_proxy_async_smem();
                 }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mb + FB_SLOT + (k & 3));
                 // (B) second-layer output row k-3 -> HBM
                 if (Rv(k - 2)) wait_w(FB_L1 + ((k - 2) & 1));
                 const int h = k - 3;
@@ -895,9 +902,6 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                                 make_uint4(pk[4 * pl], pk[4 * pl + 1], pk[4 * pl + 2], pk[4 * pl + 3]);
                     }
                 }
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(mb + FB_PASS + (k & 3));
             }
         }
         tc::fence_before_sync();
