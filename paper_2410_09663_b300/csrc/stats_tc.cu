@@ -51,17 +51,13 @@ constexpr long long ST_WAIT = 4000000000LL;             // ~2 s at 2 GHz
 constexpr int RD = 4;                                   // raw ring depth (stages)
 constexpr int RTILE = TM * 128;                         // one raw stage, bytes
 
-// Observation row c of member i, columns j .. j+3 (E row plus noise).
-__device__ __forceinline__ float4 yrow4(const float* __restrict__ E, long ms, int m, const RowSet& obs,
-                                        const ObsNoise& V, int p, int i, int c, int j)
+// V^i of observation row c, columns j .. j+3 (zero on the constraint rows,
+// whose perturbation is already in E, and without a live noise source).
+__device__ __forceinline__ float4 obs_noise4(const ObsNoise& V, const RowSet& obs, int p, int i, int c, int j, int m)
 {
-    float4 v = __ldg(reinterpret_cast<const float4*>(E + (long)i * ms + (long)obs.rows[c] * m + j));
-    if (V.a.live() && c < p - obs.nc) {              // constraint rows carry their noise in E
-        const float4 w = c < V.pa ? noise4(V.a, ((long)i * V.pa + c) * m + j)
-                                  : noise4(V.b, ((long)i * (p - obs.nc - V.pa) + (c - V.pa)) * m + j);
-        v = f4add(v, w);
-    }
-    return v;
+    if (!V.a.live() || c >= p - obs.nc) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return c < V.pa ? noise4(V.a, ((long)i * V.pa + c) * m + j)
+                    : noise4(V.b, ((long)i * (p - obs.nc - V.pa) + (c - V.pa)) * m + j);
 }
 
 // One block per (member i, K chunk kh of 32 columns j); thread units
@@ -90,32 +86,51 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
             Ds[jj * ldd + c] = 0.f;
         }
     char* tile = reinterpret_cast<char*>(Bop) + ((size_t)i * KH + kh) * (size_t)(2 * pp) * 128;
-    for (int e = threadIdx.x; e < pp * 8; e += 256) {
-        const int c = e / 8, k = e % 8;
-        const int j = kh * KC + k * 4;
-        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi, d = hi;
-        if (c < p && j < m) {
-            const float4 y = yrow4(E, ms, m, obs, V, p, i, c, j);
-            const float4 y0 = __ldg(reinterpret_cast<const float4*>(E + (long)obs.rows[c] * m + j));
-            const float4 ev = f4sub(y, y0);
-            split_tf32(ev, hi, lo);
-            *reinterpret_cast<float4*>(Ysh + ((long)i * p + c) * m + j) = ev;
-            if (c < p - obs.nc) {
-                const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
-                d = f4sub(*reinterpret_cast<const float4*>(yb + j), y);
-            } else {
-                d = f4sub(make_float4(0.f, 0.f, 0.f, 0.f), y);     // constraint rows: reference 0
+    // YU units of a thread per round: every load of the round issued before the
+    // first is used (one round trip to memory; one round up to pp = 160)
+    constexpr int YU = 5;
+    const int units = pp * 8;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int base = 0; base < units; base += 256 * YU) {
+        float4 yv[YU], y0v[YU], ybv[YU];
+#pragma unroll
+        for (int u = 0; u < YU; ++u) {
+            const int e = base + threadIdx.x + 256 * u;
+            const int c = e / 8, j = kh * KC + (e % 8) * 4;
+            yv[u] = y0v[u] = ybv[u] = zero;
+            if (e < units && c < p && j < m) {
+                yv[u] = __ldg(reinterpret_cast<const float4*>(E + (long)i * ms + (long)obs.rows[c] * m + j));
+                y0v[u] = __ldg(reinterpret_cast<const float4*>(E + (long)obs.rows[c] * m + j));
+                if (c < p - obs.nc) {
+                    const float* yb = c < n_yx ? Yx + (long)c * m : Yu + (long)(c - n_yx) * m;
+                    ybv[u] = *reinterpret_cast<const float4*>(yb + j);
+                }
             }
-            if (Dbuf != nullptr) *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + j) = d;
         }
-        if (Bd != nullptr) {
-            Ds[(k * 4 + 0) * ldd + c] = d.x;
-            Ds[(k * 4 + 1) * ldd + c] = d.y;
-            Ds[(k * 4 + 2) * ldd + c] = d.z;
-            Ds[(k * 4 + 3) * ldd + c] = d.w;
+#pragma unroll
+        for (int u = 0; u < YU; ++u) {
+            const int e = base + threadIdx.x + 256 * u;
+            if (e >= units) break;
+            const int c = e / 8, k = e % 8;
+            const int j = kh * KC + k * 4;
+            float4 hi = zero, lo = zero, d = zero;
+            if (c < p && j < m) {
+                const float4 y = f4add(yv[u], obs_noise4(V, obs, p, i, c, j, m));
+                const float4 ev = f4sub(y, y0v[u]);
+                split_tf32(ev, hi, lo);
+                *reinterpret_cast<float4*>(Ysh + ((long)i * p + c) * m + j) = ev;
+                d = f4sub(ybv[u], y);                       // constraint rows: reference 0
+                if (Dbuf != nullptr) *reinterpret_cast<float4*>(Dbuf + ((long)i * p + c) * m + j) = d;
+            }
+            if (Bd != nullptr) {
+                Ds[(k * 4 + 0) * ldd + c] = d.x;
+                Ds[(k * 4 + 1) * ldd + c] = d.y;
+                Ds[(k * 4 + 2) * ldd + c] = d.z;
+                Ds[(k * 4 + 3) * ldd + c] = d.w;
+            }
+            *reinterpret_cast<float4*>(tile + swz(c, k)) = hi;
+            *reinterpret_cast<float4*>(tile + swz(pp + c, k)) = lo;
         }
-        *reinterpret_cast<float4*>(tile + swz(c, k)) = hi;
-        *reinterpret_cast<float4*>(tile + swz(pp + c, k)) = lo;
     }
     if (Bd == nullptr) return;
     __syncthreads();
