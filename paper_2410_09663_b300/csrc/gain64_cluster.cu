@@ -258,6 +258,43 @@ __device__ __forceinline__ void cp_async8(double* dst, const double* src)
 constexpr int S64_W = 4;                                // warps (gain rows) per CTA
 constexpr int S64_Q = 5;                                // p <= 160
 
+// The forward substitution's pivots j in slot QJ (j = 32 QJ + lj): lane i
+// of slot q holds z_{32 q + i}.
+template <int QJ>
+__device__ __forceinline__ void fwd_slot(double (&z)[S64_Q], const double* __restrict__ Ls,
+                                         const double* __restrict__ rinv, int ld, int p, int lane)
+{
+    static_assert(QJ < S64_Q, "slot");
+    const int j0 = 32 * QJ, j1 = p < j0 + 32 ? p : j0 + 32;
+    for (int j = j0; j < j1; ++j) {
+        const int lj = j - j0;
+        const double zj = __shfl_sync(0xffffffffu, z[QJ], lj) * rinv[j];
+        if (lane == lj) z[QJ] = zj;
+        else if (lane > lj && j0 + lane < p) z[QJ] = fma(-Ls[(j0 + lane) * ld + j], zj, z[QJ]);
+#pragma unroll
+        for (int q = QJ + 1; q < S64_Q; ++q) {
+            const int i = lane + 32 * q;
+            if (32 * q < p && i < p) z[q] = fma(-Ls[i * ld + j], zj, z[q]);
+        }
+    }
+}
+// The backward substitution's pivots j in slot QJ, from the top of the slot down.
+template <int QJ>
+__device__ __forceinline__ void bwd_slot(double (&z)[S64_Q], const double* __restrict__ Ls,
+                                         const double* __restrict__ rinv, int ld, int p, int lane)
+{
+    static_assert(QJ < S64_Q, "slot");
+    const int j0 = 32 * QJ, j1 = p < j0 + 32 ? p : j0 + 32;
+    for (int j = j1 - 1; j >= j0; --j) {
+        const int lj = j - j0;
+        const double kj = __shfl_sync(0xffffffffu, z[QJ], lj) * rinv[j];
+        if (lane == lj) z[QJ] = kj;
+        else if (lane < lj) z[QJ] = fma(-Ls[j * ld + j0 + lane], kj, z[QJ]);
+#pragma unroll
+        for (int q = 0; q < QJ; ++q) z[q] = fma(-Ls[j * ld + lane + 32 * q], kj, z[q]);
+    }
+}
+
 __global__ void __launch_bounds__(32 * S64_W)
 solve64s_kernel(const double* __restrict__ C, int R, int p, const double* __restrict__ Lg,
                 const int* __restrict__ bad_in, float* __restrict__ Kt)
@@ -287,36 +324,22 @@ solve64s_kernel(const double* __restrict__ C, int R, int p, const double* __rest
         const int i = lane + 32 * q;
         z[q] = i < p ? C[(long)a * p + i] : 0.0;
     }
-    // forward: z_j /= L_jj, then z_i -= L_ij z_j for i > j (column j of L)
-    for (int j = 0; j < p; ++j) {
-        const int qj = j / 32, lj = j % 32;
-        double zj = z[0];
-#pragma unroll
-        for (int q = 1; q < S64_Q; ++q) zj = q == qj ? z[q] : zj;
-        zj = __shfl_sync(0xffffffffu, zj, lj) * rinv[j];
-#pragma unroll
-        for (int q = 0; q < S64_Q; ++q) {
-            if (32 * q + 31 < j || 32 * q >= p) continue;      // slot wholly above the pivot: untouched
-            const int i = lane + 32 * q;
-            if (i == j) z[q] = zj;
-            else if (i > j && i < p) z[q] = fma(-Ls[i * ld + j], zj, z[q]);
-        }
-    }
-    // back: k_j = z_j / L_jj, then z_i -= L_ji k_j for i < j (row j of L)
-    for (int j = p - 1; j >= 0; --j) {
-        const int qj = j / 32, lj = j % 32;
-        double kj = z[0];
-#pragma unroll
-        for (int q = 1; q < S64_Q; ++q) kj = q == qj ? z[q] : kj;
-        kj = __shfl_sync(0xffffffffu, kj, lj) * rinv[j];
-#pragma unroll
-        for (int q = 0; q < S64_Q; ++q) {
-            if (32 * q > j) continue;                           // slot wholly below the pivot: done
-            const int i = lane + 32 * q;
-            if (i == j) z[q] = kj;
-            else if (i < j) z[q] = fma(-Ls[j * ld + i], kj, z[q]);
-        }
-    }
+    // forward: z_j /= L_jj, then z_i -= L_ij z_j for i > j (column j of L);
+    // back: k_j = z_j / L_jj, then z_i -= L_ji k_j for i < j (row j of L).
+    // The pivots of slot QJ (j = 32 QJ .. 32 QJ + 31) are taken together, QJ a
+    // compile-time constant: z_j comes straight from slot QJ and the slots
+    // wholly past the pivot are known, so each step issues only its FP64
+    // multiply and the FMAs of the live slots (B300's FP64 pipe is the limit).
+    fwd_slot<0>(z, Ls, rinv, ld, p, lane);
+    fwd_slot<1>(z, Ls, rinv, ld, p, lane);
+    fwd_slot<2>(z, Ls, rinv, ld, p, lane);
+    fwd_slot<3>(z, Ls, rinv, ld, p, lane);
+    fwd_slot<4>(z, Ls, rinv, ld, p, lane);
+    bwd_slot<4>(z, Ls, rinv, ld, p, lane);
+    bwd_slot<3>(z, Ls, rinv, ld, p, lane);
+    bwd_slot<2>(z, Ls, rinv, ld, p, lane);
+    bwd_slot<1>(z, Ls, rinv, ld, p, lane);
+    bwd_slot<0>(z, Ls, rinv, ld, p, lane);
 #pragma unroll
     for (int q = 0; q < S64_Q; ++q) {
         const int i = lane + 32 * q;
