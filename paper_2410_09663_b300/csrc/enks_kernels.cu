@@ -256,16 +256,22 @@ __device__ __forceinline__ float split_sum(const float* __restrict__ part, long 
     return t;
 }
 
-// S1[a][j] = sum over splits of part1.
+// S1[a][j] = sum over splits of part1; with S1oT also the rows a >= R
+// transposed, S1oT[j][a - R] (p = M - R columns), for coalesced reads in the
+// finalisation.
 __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict__ part1, int splits, int M, int m,
-                                                        float* __restrict__ S1)
+                                                        float* __restrict__ S1, float* __restrict__ S1oT, int R)
 {
     pdl_begin();
     __shared__ float red[8][33];
     const int idx = blockIdx.x * 32 + threadIdx.x % 32;
     const bool ok = idx < M * m;
     const float t = split_sum(part1, (long)M * m, splits, idx, ok, red);
-    if (threadIdx.x < 32 && ok) S1[idx] = t;
+    if (threadIdx.x < 32 && ok) {
+        S1[idx] = t;
+        const int a = idx / m;
+        if (S1oT != nullptr && a >= R) S1oT[(long)(idx - a * m) * (M - R) + (a - R)] = t;
+    }
 }
 
 // C[a][c] = scale (sum over splits of part2 - (1/N) sum_j S1[a][j] S1[R + c][j])
@@ -276,7 +282,7 @@ template <bool F64>
 __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restrict__ part2,
                                                            const float* __restrict__ S1, const float* __restrict__ S1o,
                                                            int splits, int M, int p, int m, int N,
-                                                           double* __restrict__ C, double scale)
+                                                           double* __restrict__ C, double scale, int so_c, int so_j)
 {
     pdl_begin();
     using T = typename std::conditional<F64, double, float>::type;
@@ -301,14 +307,14 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
         if (S1 != nullptr) {                      // one-pass products: the mean term, columns j = w, w + 8, ...
             const int a = idx / p, c = idx % p;
             const float* x = S1 + (long)a * m;
-            const float* y = S1o + (long)c * m;
+            const float* y = S1o + (long)c * so_c;     // so_j = 1: row-major; so_c = 1: transposed
             T d0 = 0, d1 = 0;
             int j = w;
             for (; j + 8 < m; j += 16) {
-                d0 = fma((T)x[j], (T)y[j], d0);
-                d1 = fma((T)x[j + 8], (T)y[j + 8], d1);
+                d0 = fma((T)x[j], (T)y[(long)j * so_j], d0);
+                d1 = fma((T)x[j + 8], (T)y[(long)(j + 8) * so_j], d1);
             }
-            if (j < m) d0 = fma((T)x[j], (T)y[j], d0);
+            if (j < m) d0 = fma((T)x[j], (T)y[(long)j * so_j], d0);
             cp = d0 + d1;
         }
     }
@@ -872,28 +878,32 @@ void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs,
 // the SMs around the products' persistent grid while it still runs, and the
 // 64 x 64 step measured slower (528 against 532 control steps/s device-timed,
 // 530 against 545 end to end, on one box).
-void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st)
+void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st, float* S1oT, int R)
 {
-    plain_launch(s1_reduce_kernel, (M * m + 31) / 32, 256, 0, st, part1, splits, M, m, S1);
+    plain_launch(s1_reduce_kernel, (M * m + 31) / 32, 256, 0, st, part1, splits, M, m, S1, S1oT, R);
 }
 
 void launch_cov_finalize_rows(const float* part2, const float* S1_left, const float* S1_obs, int splits, int M, int p,
-                              int m, int N, double* C, cudaStream_t st, bool f64, double scale)
+                              int m, int N, double* C, cudaStream_t st, bool f64, double scale, bool obs_t)
 {
+    const int so_c = obs_t ? 1 : m, so_j = obs_t ? p : 1;
     const int total = M * p;
     if (f64)
         plain_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2, S1_left, S1_obs, splits, M, p, m,
-                     N, C, scale);
+                     N, C, scale, so_c, so_j);
     else
         plain_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1_left, S1_obs, splits, M, p, m,
-                     N, C, scale);
+                     N, C, scale, so_c, so_j);
 }
 
 void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st, bool f64, double scale)
+                         cudaStream_t st, bool f64, double scale, const float* S1oT)
 {
-    launch_cov_finalize_rows(part2, S1, S1 != nullptr ? S1 + (size_t)R * m : nullptr, splits, R + p, p, m, N, C, st,
-                             f64, scale);
+    if (S1 != nullptr && S1oT != nullptr)
+        launch_cov_finalize_rows(part2, S1, S1oT, splits, R + p, p, m, N, C, st, f64, scale, true);
+    else
+        launch_cov_finalize_rows(part2, S1, S1 != nullptr ? S1 + (size_t)R * m : nullptr, splits, R + p, p, m, N, C,
+                                 st, f64, scale);
 }
 
 

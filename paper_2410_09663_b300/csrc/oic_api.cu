@@ -64,7 +64,7 @@ struct StepGraph {
 };
 
 struct Layout {
-    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, D, C, K, L64, tB, tAop, tBd, ctr, rowtab, status, selftest;
+    size_t w, b, B, wtc, wfused, w16, b16, act16_in, E, act0, act1, part1, part2, S1, S1T, D, C, K, L64, tB, tAop, tBd, ctr, rowtab, status, selftest;
     size_t cG, ccols, ch;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
@@ -240,6 +240,7 @@ void compute_layout(oic_handle* h)
     L.part1 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * m);
     L.part2 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * p);
     L.S1 = take(sizeof(float) * (Ra + p) * m);
+    L.S1T = take(sizeof(float) * p * m);                  // the observed rows' sums, transposed
     L.D = take(sizeof(float) * N * p * m);
     L.C = take(sizeof(double) * (Ra + p) * p);
     L.K = take(sizeof(float) * Ra * p);
@@ -352,6 +353,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
     float* part1 = h->at<float>(h->lay.part1);
     float* part2 = h->at<float>(h->lay.part2);
     float* S1 = h->at<float>(h->lay.S1);
+    float* S1T = h->at<float>(h->lay.S1T);
     float* D = h->at<float>(h->lay.D);
     double* C = h->at<double>(h->lay.C);
     float* Kt = h->at<float>(h->lay.K);
@@ -366,18 +368,18 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
             launch_stats_tc(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, h->at<float>(h->lay.tB), part1, part2,
                             utc ? nullptr : D, Bd, splits, h->at<int>(h->lay.status), h->st);
         });
-        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
+        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R); });
         run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
-            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed);
+            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T);
         });
     } else {
         const int splits = plan_splits(h, stats_splits(R, p, c.N));
         run_stage(h, OIC_STAGE_COV, [&] {
             launch_stats(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, part1, part2, D, splits, h->st);
         });
-        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st); });
+        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R); });
         run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
-            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed);
+            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T);
         });
     }
     run_stage(h, OIC_STAGE_GAIN, [&] {
