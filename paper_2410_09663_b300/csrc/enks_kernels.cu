@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(256) block_means_kernel(const float* __restric
                                                           float* __restrict__ out)
 {
     // 32 outputs per CTA (lane = output, coalesced); the members are split
-    // over the 8 warps (four loads in flight each), then summed in shared memory
+    // over the 8 warps (eight loads in flight each), then summed in shared memory
     pdl_begin();
     __shared__ float red[8][33];
     const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
@@ -807,11 +807,18 @@ __global__ void __launch_bounds__(256) block_means_kernel(const float* __restric
     if (ok) {
         const long off = (long)row0 * m + idx;  // blocks are contiguous rows
         int i = w;
-        for (; i + 24 < N; i += 32) {
-            s0 += E[(long)i * ms + off];
-            s1 += E[(long)(i + 8) * ms + off];
-            s2 += E[(long)(i + 16) * ms + off];
-            s3 += E[(long)(i + 24) * ms + off];
+        for (; i + 56 < N; i += 64) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = E[(long)(i + 8 * q) * ms + off];
+            s0 += v[0];
+            s1 += v[1];
+            s2 += v[2];
+            s3 += v[3];
+            s0 += v[4];
+            s1 += v[5];
+            s2 += v[6];
+            s3 += v[7];
         }
         for (; i < N; i += 8) s0 += E[(long)i * ms + off];
     }

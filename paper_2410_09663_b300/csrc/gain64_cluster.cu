@@ -236,12 +236,13 @@ chol64c_kernel(const double* __restrict__ C, int R, int p, double* __restrict__ 
         return;
     }
     if (rank == 0 && tid == 0) *bad_out = 0;
-    // L[i][g] = U[g][i] for i >= g, zero above the diagonal
+    // L[i][g] = U[g][i] for i >= g, zero above the diagonal (a panel's 8
+    // columns of a row next to each other: 64-byte segments)
     for (int sl = 0; sl < C64_OWN; ++sl) {
         const int B = (int)rank + CL * sl;
         if (B >= NB) break;
         for (int x = tid; x < PB * p; x += C64_T) {
-            const int d = x / p, i = x % p, g = PB * B + d;
+            const int d = x % PB, i = x / PB, g = PB * B + d;
             if (g < p) Lg[(long)i * p + g] = i >= g ? own[sl][d][i] : 0.0;
         }
     }
