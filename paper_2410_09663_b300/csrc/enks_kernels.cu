@@ -258,9 +258,11 @@ __device__ __forceinline__ float split_sum(const float* __restrict__ part, long 
 
 // S1[a][j] = sum over splits of part1; with S1oT also the rows a >= R
 // transposed, S1oT[j][a - R] (p = M - R columns), for coalesced reads in the
-// finalisation.
+// finalisation.  OT = double for the FP64 finalisation (converted once here,
+// not once per use on the FP64 pipe).
+template <typename OT>
 __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict__ part1, int splits, int M, int m,
-                                                        float* __restrict__ S1, float* __restrict__ S1oT, int R)
+                                                        OT* __restrict__ S1, OT* __restrict__ S1oT, int R)
 {
     pdl_begin();
     __shared__ float red[8][33];
@@ -268,9 +270,9 @@ __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict_
     const bool ok = idx < M * m;
     const float t = split_sum(part1, (long)M * m, splits, idx, ok, red);
     if (threadIdx.x < 32 && ok) {
-        S1[idx] = t;
+        S1[idx] = (OT)t;
         const int a = idx / m;
-        if (S1oT != nullptr && a >= R) S1oT[(long)(idx - a * m) * (M - R) + (a - R)] = t;
+        if (S1oT != nullptr && a >= R) S1oT[(long)(idx - a * m) * (M - R) + (a - R)] = (OT)t;
     }
 }
 
@@ -280,7 +282,8 @@ __global__ void __launch_bounds__(256) s1_reduce_kernel(const float* __restrict_
 // mixed-precision mode's FP64 anomaly step); else FP32 with an FP64 result.
 template <bool F64>
 __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restrict__ part2,
-                                                           const float* __restrict__ S1, const float* __restrict__ S1o,
+                                                           const typename std::conditional<F64, double, float>::type* __restrict__ S1,
+                                                           const typename std::conditional<F64, double, float>::type* __restrict__ S1o,
                                                            int splits, int M, int p, int m, int N,
                                                            double* __restrict__ C, double scale, int so_c, int so_j)
 {
@@ -306,8 +309,8 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
         for (; k < splits; k += 8) sp += (T)part2[k * st + idx];
         if (S1 != nullptr) {                      // one-pass products: the mean term, columns j = w, w + 8, ...
             const int a = idx / p, c = idx % p;
-            const float* x = S1 + (long)a * m;
-            const float* y = S1o + (long)c * so_c;     // so_j = 1: row-major; so_c = 1: transposed
+            const T* x = S1 + (long)a * m;
+            const T* y = S1o + (long)c * so_c;         // so_j = 1: row-major; so_c = 1: transposed
             T d0 = 0, d1 = 0;
             int j = w;
             for (; j + 8 < m; j += 16) {
@@ -885,32 +888,43 @@ void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs,
 // the SMs around the products' persistent grid while it still runs, and the
 // 64 x 64 step measured slower (528 against 532 control steps/s device-timed,
 // 530 against 545 end to end, on one box).
-void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st, float* S1oT, int R)
+void launch_s1_reduce(const float* part1, int splits, int M, int m, void* S1, cudaStream_t st, void* S1oT, int R,
+                      bool f64)
 {
-    plain_launch(s1_reduce_kernel, (M * m + 31) / 32, 256, 0, st, part1, splits, M, m, S1, S1oT, R);
+    if (f64)
+        plain_launch(s1_reduce_kernel<double>, (M * m + 31) / 32, 256, 0, st, part1, splits, M, m,
+                     static_cast<double*>(S1), static_cast<double*>(S1oT), R);
+    else
+        plain_launch(s1_reduce_kernel<float>, (M * m + 31) / 32, 256, 0, st, part1, splits, M, m,
+                     static_cast<float*>(S1), static_cast<float*>(S1oT), R);
 }
 
-void launch_cov_finalize_rows(const float* part2, const float* S1_left, const float* S1_obs, int splits, int M, int p,
+void launch_cov_finalize_rows(const float* part2, const void* S1_left, const void* S1_obs, int splits, int M, int p,
                               int m, int N, double* C, cudaStream_t st, bool f64, double scale, bool obs_t)
 {
     const int so_c = obs_t ? 1 : m, so_j = obs_t ? p : 1;
     const int total = M * p;
     if (f64)
-        plain_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2, S1_left, S1_obs, splits, M, p, m,
-                     N, C, scale, so_c, so_j);
+        plain_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2,
+                     static_cast<const double*>(S1_left), static_cast<const double*>(S1_obs), splits, M, p, m, N, C,
+                     scale, so_c, so_j);
     else
-        plain_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2, S1_left, S1_obs, splits, M, p, m,
-                     N, C, scale, so_c, so_j);
+        plain_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2,
+                     static_cast<const float*>(S1_left), static_cast<const float*>(S1_obs), splits, M, p, m, N, C,
+                     scale, so_c, so_j);
 }
 
-void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st, bool f64, double scale, const float* S1oT)
+void launch_cov_finalize(const float* part2, const void* S1, int splits, int R, int p, int m, int N, double* C,
+                         cudaStream_t st, bool f64, double scale, const void* S1oT)
 {
-    if (S1 != nullptr && S1oT != nullptr)
+    if (S1 != nullptr && S1oT != nullptr) {
         launch_cov_finalize_rows(part2, S1, S1oT, splits, R + p, p, m, N, C, st, f64, scale, true);
-    else
-        launch_cov_finalize_rows(part2, S1, S1 != nullptr ? S1 + (size_t)R * m : nullptr, splits, R + p, p, m, N, C,
-                                 st, f64, scale);
+        return;
+    }
+    const void* S1o = S1 == nullptr ? nullptr
+                      : f64 ? static_cast<const void*>(static_cast<const double*>(S1) + (size_t)R * m)
+                            : static_cast<const void*>(static_cast<const float*>(S1) + (size_t)R * m);
+    launch_cov_finalize_rows(part2, S1, S1o, splits, R + p, p, m, N, C, st, f64, scale);
 }
 
 

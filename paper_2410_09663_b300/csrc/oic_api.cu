@@ -239,8 +239,8 @@ void compute_layout(oic_handle* h)
     L.act1 = take(act_bytes);
     L.part1 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * m);
     L.part2 = take(sizeof(float) * (size_t)h->splits_max * (Ra + p) * p);
-    L.S1 = take(sizeof(float) * (Ra + p) * m);
-    L.S1T = take(sizeof(float) * p * m);                  // the observed rows' sums, transposed
+    L.S1 = take(sizeof(double) * (Ra + p) * m);           // FP64 in the mixed mode
+    L.S1T = take(sizeof(double) * p * m);                 // the observed rows' sums, transposed
     L.D = take(sizeof(float) * N * p * m);
     L.C = take(sizeof(double) * (Ra + p) * p);
     L.K = take(sizeof(float) * Ra * p);
@@ -368,7 +368,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
             launch_stats_tc(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, h->at<float>(h->lay.tB), part1, part2,
                             utc ? nullptr : D, Bd, splits, h->at<int>(h->lay.status), h->st);
         });
-        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R); });
+        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R, mixed); });
         run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
             launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T);
         });
@@ -377,7 +377,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
         run_stage(h, OIC_STAGE_COV, [&] {
             launch_stats(E, ms, c.N, c.m, act, obs, V, Yx, Yu, n_yx, part1, part2, D, splits, h->st);
         });
-        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R); });
+        run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R, mixed); });
         run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
             launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T);
         });
@@ -427,7 +427,7 @@ CovScratch cov_scratch(const oic_handle* h)
     c.part1 = 0;
     c.part2 = align_up(sizeof(float) * p1, 256);
     c.S1 = c.part2 + align_up(sizeof(float) * p2, 256);
-    c.total = c.S1 + align_up(sizeof(float) * s1, 256);
+    c.total = c.S1 + align_up(sizeof(double) * s1, 256);
     return c;
 }
 
@@ -440,7 +440,7 @@ void ensemble_cov(oic_handle* h, const float* E, long ms, RowSet rows, const Cov
     const CovScratch cs = cov_scratch(h);
     float* part1 = reinterpret_cast<float*>(co.scratch + cs.part1);
     float* part2 = reinterpret_cast<float*>(co.scratch + cs.part2);
-    float* S1 = reinterpret_cast<float*>(co.scratch + cs.S1);
+    double* S1 = reinterpret_cast<double*>(co.scratch + cs.S1);
     const int R = rows.count;
     const int splits = stats_splits(0, R, c.N);
     RowSet none{rows.rows, 0};
@@ -448,7 +448,7 @@ void ensemble_cov(oic_handle* h, const float* E, long ms, RowSet rows, const Cov
         launch_stats(E, ms, c.N, c.m, none, rows, ObsNoise(), nullptr, nullptr, 0, part1, part2,
                      nullptr, splits, h->st);
     });
-    run_stage(h, OIC_STAGE_COV_OUT, [&] { launch_s1_reduce(part1, splits, R, c.m, S1, h->st); });
+    run_stage(h, OIC_STAGE_COV_OUT, [&] { launch_s1_reduce(part1, splits, R, c.m, S1, h->st, nullptr, 0, true); });
     run_stage(h, OIC_STAGE_COV_OUT, [&] {
         launch_cov_finalize(part2, S1, splits, 0, R, c.m, c.N, out, h->st, true, co.lambda / c.N);
     });

@@ -154,15 +154,17 @@ int stats_splits(int R, int p, int N);
 size_t stats_smem_bytes(int m);
 void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs, ObsNoise V, const float* Yx,
                   const float* Yu, int n_yx, float* part1, float* part2, float* Dbuf, int splits, cudaStream_t st);
-void launch_s1_reduce(const float* part1, int splits, int M, int m, float* S1, cudaStream_t st,
-                      float* S1oT = nullptr, int R = 0);
+// f64: S1 (and S1oT) as FP64, for the FP64 finalisation.
+void launch_s1_reduce(const float* part1, int splits, int M, int m, void* S1, cudaStream_t st,
+                      void* S1oT = nullptr, int R = 0, bool f64 = false);
 // C = scale (sum_s part2 - S1 S1_Y^T / N)  ([(R + p) x p], Cxy on top, Cyy below).
-void launch_cov_finalize(const float* part2, const float* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st, bool f64 = false, double scale = 1.0, const float* S1oT = nullptr);
+// (S1 and S1oT in FP64 when f64)
+void launch_cov_finalize(const float* part2, const void* S1, int splits, int R, int p, int m, int N, double* C,
+                         cudaStream_t st, bool f64 = false, double scale = 1.0, const void* S1oT = nullptr);
 // The same for M left rows whose split sums part2 [splits][M][p] hold alone:
 // C[a][c] = scale (sum_s part2[s][a][c] - S1_left[a] . S1_obs[c] / N); obs_t:
 // S1_obs is transposed, [m][p] (coalesced reads; launch_s1_reduce's S1oT).
-void launch_cov_finalize_rows(const float* part2, const float* S1_left, const float* S1_obs, int splits, int M, int p,
+void launch_cov_finalize_rows(const float* part2, const void* S1_left, const void* S1_obs, int splits, int M, int p,
                               int m, int N, double* C, cudaStream_t st, bool f64 = false, double scale = 1.0,
                               bool obs_t = false);
 // Anomaly products on the tensor cores (TF32 hi / lo split, one pass over
