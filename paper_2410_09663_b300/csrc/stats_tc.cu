@@ -69,7 +69,8 @@ __device__ __forceinline__ float4 obs_noise4(const ObsNoise& V, const RowSet& ob
 // transpose in shared memory, to the member update's operand Bd: rows
 // n = i m + j, K = c in chunks of 32, [kc][hi | lo][N m rows][128 B]
 // (swizzled, zero beyond p).
-__global__ void __launch_bounds__(256)
+constexpr int YP_NT = 384;                              // yprep threads: 24 warps per SM at two blocks
+__global__ void __launch_bounds__(YP_NT, 2)
 yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, ObsNoise V,
              const float* __restrict__ Yx, const float* __restrict__ Yu, int n_yx, int KH, int pp,
              float* __restrict__ Bop, float* __restrict__ Ysh, float* __restrict__ Dbuf, float* __restrict__ Bd,
@@ -81,21 +82,21 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
     const int i = blockIdx.x / KH, kh = blockIdx.x % KH;
     const int ldd = 32 * KCD + 1;
     if (Bd != nullptr)
-        for (int e = threadIdx.x; e < 32 * (32 * KCD - pp); e += 256) {
+        for (int e = threadIdx.x; e < 32 * (32 * KCD - pp); e += YP_NT) {
             const int jj = e / (32 * KCD - pp), c = pp + e % (32 * KCD - pp);
             Ds[jj * ldd + c] = 0.f;
         }
     char* tile = reinterpret_cast<char*>(Bop) + ((size_t)i * KH + kh) * (size_t)(2 * pp) * 128;
     // YU units of a thread per round: every load of the round issued before the
-    // first is used (one round trip to memory; one round up to pp = 160)
-    constexpr int YU = 5;
+    // first is used (one round trip to memory; one round up to pp = 144)
+    constexpr int YU = 3;
     const int units = pp * 8;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int base = 0; base < units; base += 256 * YU) {
+    for (int base = 0; base < units; base += YP_NT * YU) {
         float4 yv[YU], y0v[YU], ybv[YU];
 #pragma unroll
         for (int u = 0; u < YU; ++u) {
-            const int e = base + threadIdx.x + 256 * u;
+            const int e = base + threadIdx.x + YP_NT * u;
             const int c = e / 8, j = kh * KC + (e % 8) * 4;
             yv[u] = y0v[u] = ybv[u] = zero;
             if (e < units && c < p && j < m) {
@@ -109,7 +110,7 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
         }
 #pragma unroll
         for (int u = 0; u < YU; ++u) {
-            const int e = base + threadIdx.x + 256 * u;
+            const int e = base + threadIdx.x + YP_NT * u;
             if (e >= units) break;
             const int c = e / 8, k = e % 8;
             const int j = kh * KC + k * 4;
@@ -136,7 +137,7 @@ yprep_kernel(const float* __restrict__ E, long ms, int N, int m, RowSet obs, Obs
     __syncthreads();
     const long NM = (long)N * m;
     char* bd = reinterpret_cast<char*>(Bd);
-    for (int e = threadIdx.x; e < 32 * KCD * 8; e += 256) {
+    for (int e = threadIdx.x; e < 32 * KCD * 8; e += YP_NT) {
         const int jj = e / (KCD * 8), kc = (e / 8) % KCD, q = e % 8;
         const int j = kh * KC + jj;
         if (j >= m) continue;
@@ -446,7 +447,7 @@ void launch_yprep_tc(const float* E, long ms, int N, int m, RowSet obs, ObsNoise
     const int KCD = (p + 31) / 32;
     float* Ysh = Bop + (size_t)N * KH * 2 * pp * 32;      // after the observation tiles
     const size_t ysm = Bd != nullptr ? sizeof(float) * 32 * (32 * KCD + 1) : 0;
-    pdl_launch(yprep_kernel, N * KH, 256, ysm, st, E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop, Ysh, Dbuf, Bd, KCD);
+    pdl_launch(yprep_kernel, N * KH, YP_NT, ysm, st, E, ms, N, m, obs, V, Yx, Yu, n_yx, KH, pp, Bop, Ysh, Dbuf, Bd, KCD);
 }
 
 void launch_stats_tc_rows(const float* E, long ms, int N, int m, RowSet act, RowSet obs, int M, const float* Bop,
