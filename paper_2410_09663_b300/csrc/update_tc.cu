@@ -4,10 +4,13 @@
 //
 //   E[rows a][columns n = (i, j)] += sum_c K[a][c] Bd[n][c]
 //
-// with M = the R active rows (tiles of 128), N = N m ensemble columns
-// (groups of 128) and K = p (chunks of 32).  FP32 accuracy from TF32
-// operands split x = hi + lo, three products per K step
-// (K_hi D_hi + K_hi D_lo + K_lo D_hi) into one FP32 tensor-memory
+// computed transposed, acc[n][a] = sum_c Bd[n][c] K[a][c]: M = a group of
+// 128 ensemble columns, N = a tile of 128 of the R active rows, K = p
+// (chunks of 32).  A tensor-memory lane is then one ensemble column, so for
+// each active row the 32 lanes of a drain warp add into 32 consecutive
+// values of the ensemble row: one 128-byte run per warp access.  FP32
+// accuracy from TF32 operands split x = hi + lo, three products per K step
+// (D_hi K_hi + D_lo K_hi + D_hi K_lo) into one FP32 tensor-memory
 // accumulator.  Operands, both 128-byte-swizzled K-major tiles:
 //   Aop [row tile][kc][hi | lo][128 rows][32 values]   from the gain (kprep)
 //   Bd  [kc][hi | lo][N m rows][32 values]             from yprep_kernel
@@ -15,9 +18,9 @@
 // fastest so that consecutive items of a CTA reuse the same Bd rows from L2.
 // Per item a loader bulk-copies one stage per K chunk (A hi / lo and
 // B hi / lo, 64 KB) into a 3-stage ring, one warp (an elected lane) issues the MMAs into
-// one of two tensor-memory accumulators, and four drain warps add the
-// finished accumulator into the ensemble (one lane per row, 16 columns at a
-// time) while the next item accumulates into the other one.
+// one of two tensor-memory accumulators, and sixteen drain warps add the
+// finished accumulator into the ensemble (one lane per column, 16 rows per
+// tensor-memory load) while the next item accumulates into the other one.
 #include "oic_internal.cuh"
 #include "tc_sm103.cuh"
 #include "tc_tf32.cuh"
@@ -33,8 +36,10 @@ constexpr int UT_KC = 32;                               // K values per stage
 constexpr int UT_PART = UT_M * 128;                     // one operand part (hi or lo), bytes
 constexpr int UT_STAGE = 4 * UT_PART;                   // A hi, A lo, B hi, B lo
 constexpr int UT_S = 3;                                 // ring stages
-constexpr int UT_NT = 192;                              // 4 drain warps, loader, issuer
-constexpr int UT_LOADER = 4, UT_ISSUER = 5;
+constexpr int UT_DW = 16;                               // drain warps: four per tensor-memory lane quarter
+constexpr int UT_NT = (UT_DW + 2) * 32;                 // drain warps, loader, issuer
+constexpr int UT_LOADER = UT_DW, UT_ISSUER = UT_DW + 1;
+constexpr int UT_DR = UT_M * 4 / UT_DW;                 // active rows a drain warp adds
 constexpr long long UT_WAIT = 4000000000LL;
 
 // Kt [p][R] (K transposed) -> Aop tiles; one thread per (row tile, kc, row,
@@ -74,6 +79,7 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
     uint64_t* accf = freeb + UT_S;                          // [2] accumulator ready
     uint64_t* accd = accf + 2;                              // [2] accumulator drained (4 warps)
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accd + 2);
+    int* row_off = reinterpret_cast<int*>(smem + UT_S * UT_STAGE + 128);   // [drain warp][UT_DR]
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int R = act.count;
     const int t0 = (int)((long)blockIdx.x * items / gridDim.x);
@@ -85,7 +91,7 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(accf + b, 1);
-            tc::mbar_init(accd + b, 4);
+            tc::mbar_init(accd + b, UT_DW);
         }
         tc::fence_mbar_init();
     }
@@ -147,41 +153,45 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
                 const uint32_t base = s0 + s * UT_STAGE;
 #pragma unroll
                 for (int ks = 0; ks < UT_KC / 8; ++ks) {
-                    const uint32_t ah = sw_desc(base + ks * 32);
-                    const uint32_t al = sw_desc(base + UT_PART + ks * 32);
-                    const uint32_t bh = sw_desc(base + 2 * UT_PART + ks * 32);
-                    const uint32_t bl = sw_desc(base + 3 * UT_PART + ks * 32);
-                    st_mma_el(acc, ah, bh, id, (kc | ks) != 0 ? 1u : 0u);
-                    st_mma_el(acc, ah, bl, id, 1u);
-                    st_mma_el(acc, al, bh, id, 1u);
+                    const uint32_t kh = sw_desc(base + ks * 32);                  // gain rows (N)
+                    const uint32_t kl = sw_desc(base + UT_PART + ks * 32);
+                    const uint32_t dh = sw_desc(base + 2 * UT_PART + ks * 32);    // ensemble columns (M)
+                    const uint32_t dl = sw_desc(base + 3 * UT_PART + ks * 32);
+                    st_mma_el(acc, dh, kh, id, (kc | ks) != 0 ? 1u : 0u);
+                    st_mma_el(acc, dl, kh, id, 1u);
+                    st_mma_el(acc, dh, kl, id, 1u);
                 }
                 tc::mma_commit_elect(freeb + s);
             }
             tc::mma_commit_elect(accf + buf);
         }
-    } else if (warp < 4) {
-        // drain: lane = row a of the tile; the item's ensemble values are
-        // loaded before the accumulator is waited for (they overlap the
-        // MMAs), then added 16 columns per TMEM load
+    } else if (warp < UT_DW) {
+        // drain: lane = ensemble column n (tensor-memory lane 32 (warp % 4) +
+        // lane), accumulator column = active row a of the tile; the warps of
+        // one lane quarter take consecutive runs of UT_DR of the tile's rows.
+        // The item's ensemble values are loaded before the accumulator is
+        // waited for (they overlap the MMAs), then added 16 rows per
+        // tensor-memory load; for each row the warp's loads and stores are one
+        // run of 32 consecutive columns (two runs where it crosses a member's
+        // last column).  Sixteen warps keep a whole item's loads in flight.
         for (int u = 0; u < t1 - t0; ++u) {
             const int buf = u & 1;
             const int t = t0 + u, g = t / rtiles, rt = t % rtiles;
-            const long n0 = (long)g * UT_N;
-            const int a = rt * UT_M + 32 * warp + lane;
-            float* erow = a < R ? E + (long)act.rows[a] * m : nullptr;
-            float4 ev[UT_N / 4];
-            float4* dst[UT_N / 16];
+            const int quarter = warp & 3, a0 = (warp >> 2) * UT_DR;
+            const long n = (long)g * UT_N + 32 * quarter + lane;
+            const bool live = n < NM;
+            const long i = live ? n / m : 0;
+            float* const col = E + i * ms + (live ? n - i * m : 0);
+            const int nt = R - rt * UT_M < UT_M ? R - rt * UT_M : UT_M;       // rows of this tile, >= 1
+            const int na = nt - a0;                                          // of this warp (may be <= 0)
+            // the warp's row offsets, its own copy (read back as broadcasts)
+            int* const off = row_off + warp * UT_DR;
+            __syncwarp();                                   // the previous item's reads are done
+            for (int k = lane; k < UT_DR; k += 32) off[k] = k < na ? act.rows[rt * UT_M + a0 + k] * m : 0;
+            __syncwarp();
+            float ev[UT_DR];
 #pragma unroll
-            for (int c = 0; c < UT_N / 16; ++c) {
-                const long n = n0 + 16 * c;
-                dst[c] = nullptr;
-                if (erow != nullptr && n < NM) {
-                    const long i = n / m;                   // 16 columns of one member (m % 16 == 0)
-                    dst[c] = reinterpret_cast<float4*>(erow + i * ms + (n - i * m));
-#pragma unroll
-                    for (int w4 = 0; w4 < 4; ++w4) ev[4 * c + w4] = dst[c][w4];
-                }
-            }
+            for (int a = 0; a < UT_DR; ++a) ev[a] = (a < na && live) ? col[off[a]] : 0.f;
             bool ok = true;
             if (lane == 0) ok = tc::mbar_wait_bounded(accf + buf, (uint32_t)((u / 2) & 1), UT_WAIT);
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -190,22 +200,17 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
                 break;
             }
             tc::fence_after_sync();
-            const uint32_t tl = tmem + buf * UT_N + ((uint32_t)(32 * warp) << 16);
+            const uint32_t tl = tmem + buf * UT_N + a0 + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll
-            for (int c = 0; c < UT_N / 16; ++c) {
+            for (int c = 0; c < UT_DR / 16; ++c) {
+                if (16 * c >= na) break;                                     // warp-uniform
                 float v[16];
                 tc::tmem_ld16(tl + 16 * c, v);
                 tc::tmem_ld_wait();
-                if (dst[c] != nullptr) {
 #pragma unroll
-                    for (int w4 = 0; w4 < 4; ++w4) {
-                        float4 x = ev[4 * c + w4];
-                        x.x += v[4 * w4 + 0];
-                        x.y += v[4 * w4 + 1];
-                        x.z += v[4 * w4 + 2];
-                        x.w += v[4 * w4 + 3];
-                        dst[c][w4] = x;
-                    }
+                for (int r = 0; r < 16; ++r) {
+                    const int a = 16 * c + r;
+                    if (a < na && live) col[off[a]] = ev[a] + v[r];
                 }
             }
             tc::fence_before_sync();
@@ -218,7 +223,7 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
     if (warp == UT_LOADER) tc::tmem_dealloc(tmem, 2 * UT_N);
 }
 
-size_t update_tc_smem() { return 1024 + (size_t)UT_S * UT_STAGE + 128; }
+size_t update_tc_smem() { return 1024 + (size_t)UT_S * UT_STAGE + 128 + UT_DW * UT_DR * sizeof(int); }
 
 }  // namespace
 
