@@ -10,8 +10,12 @@
 // each active row the 32 lanes of a drain warp add into 32 consecutive
 // values of the ensemble row: one 128-byte run per warp access.  FP32
 // accuracy from TF32 operands split x = hi + lo, three products per K step
-// (D_hi K_hi + D_lo K_hi + D_hi K_lo) into one FP32 tensor-memory
-// accumulator.  Operands, both 128-byte-swizzled K-major tiles:
+// in two MMAs: D_hi [K_hi; K_lo] (N = 256: the gain tile's hi and lo rows
+// are contiguous) into accumulator columns [0, 256), then D_lo K_hi into
+// columns [128, 256); the result is columns a + (128 + a).  Two MMA issues
+// per K step instead of three, with the same tensor-pipe cycles (a single
+// issuing thread needs about as long to issue an N = 128 MMA as the tensor
+// core to run it).  Operands, both 128-byte-swizzled K-major tiles:
 //   Aop [row tile][kc][hi | lo][128 rows][32 values]   from the gain (kprep)
 //   Bd  [kc][hi | lo][N m rows][32 values]             from yprep_kernel
 // A persistent grid walks work items (column group, row tile), row tile
@@ -34,6 +38,7 @@ constexpr int UT_M = 128;                               // rows per tile
 constexpr int UT_N = 128;                               // columns per item
 constexpr int UT_KC = 32;                               // K values per stage
 constexpr int UT_PART = UT_M * 128;                     // one operand part (hi or lo), bytes
+constexpr int UT_ACC = 2 * UT_N;                        // accumulator columns: [hi hi | hi lo + lo hi]
 constexpr int UT_STAGE = 4 * UT_PART;                   // A hi, A lo, B hi, B lo
 constexpr int UT_S = 3;                                 // ring stages
 constexpr int UT_DW = 16;                               // drain warps: four per tensor-memory lane quarter
@@ -96,7 +101,7 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
         tc::fence_mbar_init();
     }
     if (warp == UT_LOADER) {
-        tc::tmem_alloc(tmem_holder, 2 * UT_N);
+        tc::tmem_alloc(tmem_holder, 2 * UT_ACC);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -131,11 +136,11 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
     } else if (warp == UT_ISSUER) {
         // the whole warp runs the issue loop (warp-uniform operands, outcomes
         // agreed by vote); the elected lane issues each MMA and commit
-        const uint32_t id = idesc_tf32(UT_M, UT_N);
+        const uint32_t id2 = idesc_tf32(UT_M, 2 * UT_N), id1 = idesc_tf32(UT_M, UT_N);
         bool ok = true;
         for (int u = 0; u < t1 - t0 && ok; ++u) {
             const int buf = u & 1;
-            const uint32_t acc = tmem + buf * UT_N;
+            const uint32_t acc = tmem + buf * UT_ACC;
             if (u >= 2 &&
                 !__all_sync(0xffffffffu, tc::mbar_wait_bounded(accd + buf, (uint32_t)((u / 2 - 1) & 1), UT_WAIT))) {
                 if (lane == 0) atomicExch(err, DEV_TIMEOUT);
@@ -153,13 +158,11 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
                 const uint32_t base = s0 + s * UT_STAGE;
 #pragma unroll
                 for (int ks = 0; ks < UT_KC / 8; ++ks) {
-                    const uint32_t kh = sw_desc(base + ks * 32);                  // gain rows (N)
-                    const uint32_t kl = sw_desc(base + UT_PART + ks * 32);
+                    const uint32_t k2 = sw_desc(base + ks * 32);                  // gain rows hi | lo (N = 256)
                     const uint32_t dh = sw_desc(base + 2 * UT_PART + ks * 32);    // ensemble columns (M)
                     const uint32_t dl = sw_desc(base + 3 * UT_PART + ks * 32);
-                    st_mma_el(acc, dh, kh, id, (kc | ks) != 0 ? 1u : 0u);
-                    st_mma_el(acc, dl, kh, id, 1u);
-                    st_mma_el(acc, dh, kl, id, 1u);
+                    st_mma_el(acc, dh, k2, id2, (kc | ks) != 0 ? 1u : 0u);
+                    st_mma_el(acc + UT_N, dl, k2, id1, 1u);
                 }
                 tc::mma_commit_elect(freeb + s);
             }
@@ -200,17 +203,18 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
                 break;
             }
             tc::fence_after_sync();
-            const uint32_t tl = tmem + buf * UT_N + a0 + ((uint32_t)(32 * quarter) << 16);
+            const uint32_t tl = tmem + buf * UT_ACC + a0 + ((uint32_t)(32 * quarter) << 16);
 #pragma unroll
             for (int c = 0; c < UT_DR / 16; ++c) {
                 if (16 * c >= na) break;                                     // warp-uniform
-                float v[16];
+                float v[16], w[16];
                 tc::tmem_ld16(tl + 16 * c, v);
+                tc::tmem_ld16(tl + UT_N + 16 * c, w);
                 tc::tmem_ld_wait();
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int a = 16 * c + r;
-                    if (a < na && live) col[off[a]] = ev[a] + v[r];
+                    if (a < na && live) col[off[a]] = ev[a] + (v[r] + w[r]);
                 }
             }
             tc::fence_before_sync();
@@ -220,7 +224,7 @@ update_tc_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float*
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == UT_LOADER) tc::tmem_dealloc(tmem, 2 * UT_N);
+    if (warp == UT_LOADER) tc::tmem_dealloc(tmem, 2 * UT_ACC);
 }
 
 size_t update_tc_smem() { return 1024 + (size_t)UT_S * UT_STAGE + 128 + UT_DW * UT_DR * sizeof(int); }
