@@ -797,11 +797,13 @@ update_kernel(float* __restrict__ E, long ms, int m, RowSet act, const float* __
 
 __global__ void __launch_bounds__(256) block_means_kernel(const float* __restrict__ E, long ms, int N, int m,
                                                           int row0, int rows_per_block, int n_blocks,
-                                                          float* __restrict__ out)
+                                                          float* __restrict__ out, unsigned long long* tick,
+                                                          float* __restrict__ c0, float* __restrict__ c1)
 {
     // 32 outputs per CTA (lane = output, coalesced); the members are split
     // over the 8 warps (eight loads in flight each), then summed in shared memory
     pdl_begin();
+    if (tick && blockIdx.x == 0 && threadIdx.x == 0) *tick += 1ull;   // after every draw of the solve
     __shared__ float red[8][33];
     const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
     const int idx = blockIdx.x * 32 + ln;
@@ -831,7 +833,24 @@ __global__ void __launch_bounds__(256) block_means_kernel(const float* __restric
         float t = 0.f;
 #pragma unroll
         for (int q = 0; q < 8; ++q) t += red[q][ln];
-        out[idx] = t / (float)N;
+        const float v = t / (float)N;
+        out[idx] = v;
+        if (idx < rows_per_block * m) {             // block 0 also to the copies
+            if (c0) c0[idx] = v;
+            if (c1) c1[idx] = v;
+        }
+    }
+}
+
+// d0 = d1 = src (count floats; d1 may be null)
+__global__ void __launch_bounds__(256) copy2_kernel(const float* __restrict__ src, float* __restrict__ d0,
+                                                    float* __restrict__ d1, int count)
+{
+    pdl_begin();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const float v = src[i];
+        d0[i] = v;
+        if (d1) d1[i] = v;
     }
 }
 
@@ -953,10 +972,17 @@ void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt,
 }
 
 void launch_block_means(const float* E, long ms, int N, int m, int row0, int rows_per_block,
-                        int n_blocks, float* out, cudaStream_t st)
+                        int n_blocks, float* out, cudaStream_t st, unsigned long long* tick, float* c0, float* c1)
 {
     const int total = n_blocks * rows_per_block * m;
-    pdl_launch(block_means_kernel, (total + 31) / 32, 256, 0, st, E, ms, N, m, row0, rows_per_block, n_blocks, out);
+    pdl_launch(block_means_kernel, (total + 31) / 32, 256, 0, st, E, ms, N, m, row0, rows_per_block, n_blocks, out,
+               tick, c0, c1);
+}
+
+void launch_copy2(const float* src, float* d0, float* d1, int count, cudaStream_t st)
+{
+    const int blocks = (count + 1023) / 1024;
+    pdl_launch(copy2_kernel, blocks < 1 ? 1 : blocks, 256, 0, st, src, d0, d1, count);
 }
 
 }  // namespace oic

@@ -83,9 +83,4 @@ void launch_philox_noise(float* out, size_t count_total, unsigned long long seed
     if (tick) pdl_launch(counter_tick_kernel, 1, 1, 0, st, solve_ctr);
 }
 
-void launch_counter_tick(unsigned long long* solve_ctr, cudaStream_t st)
-{
-    pdl_launch(counter_tick_kernel, 1, 1, 0, st, solve_ctr);
-}
-
 }  // namespace oic

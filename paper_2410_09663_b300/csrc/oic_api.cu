@@ -455,7 +455,8 @@ void ensemble_cov(oic_handle* h, const float* E, long ms, RowSet rows, const Cov
 }
 
 oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
-                      const float* U_ref, const float* noise, float* U_hat, float* X_hat, const CovOut* cov = nullptr)
+                      const float* U_ref, const float* noise, float* U_hat, float* X_hat, const CovOut* cov = nullptr,
+                      float* u0a = nullptr, float* u0b = nullptr)
 {
     const oic_config& c = h->cfg;
     const size_t N = c.N, n = c.n, m = c.m, l = c.l, H = c.H;
@@ -533,11 +534,11 @@ oic_status solve_impl(oic_handle* h, const float* X_k, const float* U_prev, cons
         analysis(h, E, ms, act, obs, V, X_ref + (size_t)s * n * m, U_ref, c.n);
         if (cov && cov->post) ensemble_cov(h, E, ms, act, *cov, cov->post + slot);     // Sigma^X_{t|t}
     }
-    if (philox) {
-        run_stage(h, OIC_STAGE_NOISE, [&] { launch_counter_tick(ctr, h->st); });
-    }
+    // the smoothed means (Û_k also to u0a / u0b where given); the first launch
+    // also advances the solve index, every draw of the solve being done
     run_stage(h, OIC_STAGE_BLOCK_MEANS, [&] {
-        launch_block_means(E, ms, c.N, c.m, h->urow(0), c.l, c.H + 1, U_hat, h->st);
+        launch_block_means(E, ms, c.N, c.m, h->urow(0), c.l, c.H + 1, U_hat, h->st, philox ? ctr : nullptr, u0a,
+                           u0b);
     });
     if (X_hat)
         run_stage(h, OIC_STAGE_BLOCK_MEANS, [&] {
@@ -550,23 +551,20 @@ oic_status step_impl(oic_handle* h, const float* X_ref, const float* U_ref, cons
                      float* U_applied, float* X_next)
 {
     const oic_config& c = h->cfg;
-    const size_t n = c.n, m = c.m, l = c.l;
+    const size_t n = c.n, m = c.m;
     float* uhat = h->at<float>(h->lay.uhat);
     float* pX = h->at<float>(h->lay.plantX);
     float* pU = h->at<float>(h->lay.plantU);
     float* tmp = h->at<float>(h->lay.plantTmp);
+    // the solve's block means also write Û_k to the plant's control and to
+    // U_applied (the solve read U_prev = pU at its start)
     oic_status s = solve_impl(h, pX, pU, X_ref, U_ref, noise, uhat,
-                              h->full() ? h->at<float>(h->lay.xhat) : nullptr);
+                              h->full() ? h->at<float>(h->lay.xhat) : nullptr, nullptr, pU, U_applied);
     if (s != OIC_OK) return s;
-    // Algorithm 1, lines 15-17: apply U_k = Û_{k|k:k+H} to the plant
+    // Algorithm 1, lines 15-17: apply U_k = Û_{k|k:k+H} to the plant, then
+    // X_k <- X_{k+1} (and X_next) in one launch
     cnn_forward(h, 1, pX, 0, uhat, 0, tmp, 0);
-    OIC_CUDA_OK(cudaMemcpyAsync(pX, tmp, sizeof(float) * n * m, cudaMemcpyDeviceToDevice, h->st));
-    OIC_CUDA_OK(cudaMemcpyAsync(pU, uhat, sizeof(float) * l * m, cudaMemcpyDeviceToDevice, h->st));
-    if (U_applied)
-        OIC_CUDA_OK(cudaMemcpyAsync(U_applied, uhat, sizeof(float) * l * m, cudaMemcpyDeviceToDevice,
-                                    h->st));
-    if (X_next)
-        OIC_CUDA_OK(cudaMemcpyAsync(X_next, pX, sizeof(float) * n * m, cudaMemcpyDeviceToDevice, h->st));
+    launch_copy2(tmp, pX, X_next, (int)(n * m), h->st);
     return last_cuda();
 }
 

@@ -211,9 +211,13 @@ void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStrea
 // E^i[act rows] += K D^i for every member.
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
                    cudaStream_t st);
-// out[b][r][j] = mean_i E[i][row0 + b*rows_per_block + r][j] for blocks b.
+// out[b][r][j] = mean_i E[i][row0 + b*rows_per_block + r][j] for blocks b;
+// block 0 also to c0 and c1 where given; with tick, *tick += 1 (once).
 void launch_block_means(const float* E, long ms, int N, int m, int row0, int rows_per_block,
-                        int n_blocks, float* out, cudaStream_t st);
+                        int n_blocks, float* out, cudaStream_t st, unsigned long long* tick = nullptr,
+                        float* c0 = nullptr, float* c1 = nullptr);
+// d0 = src and, where d1 is given, d1 = src (count floats, one launch).
+void launch_copy2(const float* src, float* d0, float* d1, int count, cudaStream_t st);
 
 // Hidden C -> C conv layer on the tensor cores (FP32-accurate fp16 split).
 bool conv_tc_supported(int cin, int cout, int m);
@@ -279,8 +283,6 @@ void launch_constraint_obs(float* E, long ms, int N, int m, int n, int xrow, int
 void launch_philox_noise(float* out, size_t count_total, unsigned long long seed,
                          unsigned long long* solve_ctr, const size_t* seg_end, const float* seg_sigma,
                          int n_seg, cudaStream_t st, bool tick = true);
-// Advances the device solve index by one (the end of a solve's draws).
-void launch_counter_tick(unsigned long long* solve_ctr, cudaStream_t st);
 
 }  // namespace oic
 
