@@ -89,12 +89,33 @@ def stage_work(wl, stage):
     return None
 
 
-def kernel_traffic(stage):
+def kernel_traffic(stage, wl=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of the kernel (else None)."""
+    on the current source of the kernel and on this workload (else None).  A
+    line captured on fewer members (`members=`) is scaled by N / members: the
+    kernels stream every member's rows once, so their traffic grows in
+    proportion to the members."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
+    src_files = {"conv_hidden": "conv_tc.cu", "conv_first": "cnn_kernels.cu",
+                 "conv_out": "cnn_kernels.cu", "cnn_fused": "cnn_fused_tc.cu", "cnn_bf16": "conv_bf16_tc.cu"}
+    f = src_files.get(stage)
+    if f is None:
+        return None
+    src = os.path.join(ROOT, "paper_2410_09663_b300", "csrc", f)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if parts.get("stage") != stage or parts.get("src_sha") != sha:
+            continue
+        if wl is not None and "workload" in parts and parts["workload"] != wl.name:
+            continue
+        scale = wl.N / float(parts["members"]) if (wl is not None and "members" in parts) else 1.0
+        return float(parts["dram_bytes_per_launch"]) * scale
+    return None
     src_files = {"conv_hidden": "conv_tc.cu", "conv_first": "cnn_kernels.cu",
                  "conv_out": "cnn_kernels.cu", "cnn_fused": "cnn_fused_tc.cu"}
     f = src_files.get(stage)
@@ -464,7 +485,7 @@ def run_oic(args, wl):
                         "peak_kind": "sustained" if sustained else "burst",
                         "peak_source": "%s bf16 dense %s (%s; timed region %.3f s; fp16 runs at the bf16 rate)"
                                        % (peaks["source"], "sustained" if sustained else "burst", key, wall),
-                        "traffic": kernel_traffic(dominant),
+                        "traffic": kernel_traffic(dominant, wl),
                         "algorithmic_per_launch": amount, "launches": n_l,
                         "avg_launch_ms": avg_s * 1e3,
                         "sampled": "launch %d of the %d %s launches of each timed step, bracketed by CUDA "
@@ -479,7 +500,7 @@ def run_oic(args, wl):
                         "frac": amount / avg_s / 1e12 / peak,
                         "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)"
                                        % (peaks.get("sm_max_mhz", 2032.0), peaks["source"]),
-                        "traffic": kernel_traffic(dominant),
+                        "traffic": kernel_traffic(dominant, wl),
                         "algorithmic_per_launch": amount, "launches": n_l,
                         "avg_launch_ms": avg_s * 1e3,
                         "sampled": "launch %d of the %d %s launches of each timed step, bracketed by CUDA "
