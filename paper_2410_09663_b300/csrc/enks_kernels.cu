@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
                                                            const typename std::conditional<F64, double, float>::type* __restrict__ S1,
                                                            const typename std::conditional<F64, double, float>::type* __restrict__ S1o,
                                                            int splits, int M, int p, int m, int N,
-                                                           double* __restrict__ C, double scale, int so_c, int so_j)
+                                                           double* __restrict__ C, double scale, int so_c, int so_j,
+                                                           float* __restrict__ cyy32, int R, int ld32)
 {
     pdl_begin();
     using T = typename std::conditional<F64, double, float>::type;
@@ -332,7 +333,11 @@ __global__ void __launch_bounds__(256) cov_finalize_kernel(const float* __restri
             corr += cred[q][ln];
         }
         corr /= (T)N;
-        C[idx] = (double)(t - corr) * scale;
+        const double v = (double)(t - corr) * scale;
+        C[idx] = v;
+        // rows R.. (Sigma^Y) also as FP32 rows of ld32, the FP32 gain's
+        // shared-memory layout (one bulk copy there)
+        if (cyy32 != nullptr && idx >= R * p) cyy32[(idx / p - R) * ld32 + idx % p] = (float)v;
     }
 }
 
@@ -379,6 +384,7 @@ constexpr int GC_R = 3;                           // gain rows per CTA: workers 
 constexpr int GC_B = 8;                           // panel height = substitution block
 constexpr int GC_BAR_PANEL = 1;                   // named barrier: next panel's rows updated
 constexpr int GC_TILE = 128 * 128;                // one operand part of the update's gain tile, bytes
+constexpr long long GC_WAIT = 4000000000LL;       // bounded wait for the staging copy (~2 s)
 
 __device__ __forceinline__ int gc_worker(int w) { return w & 3 ? w - 1 - (w >> 2) : -1; }
 
@@ -538,10 +544,11 @@ __device__ __forceinline__ void panel_update_rows2(float* __restrict__ A, int ld
 template <int SL>
 __global__ void __launch_bounds__(GC_T, 1)
 gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__ Kt, int* __restrict__ status,
-                 float* __restrict__ Aop)
+                 float* __restrict__ Aop, const float* __restrict__ cyy32)
 {
     pdl_begin();
     extern __shared__ __align__(16) float gsm[];
+    __shared__ __align__(8) uint64_t cmb;          // the bulk copy of Cyy (with cyy32)
     const int pp = (p + GC_B - 1) & ~(GC_B - 1);  // whole panels (zero rows, rinv 0)
     const int ld = pp | 1;
     const int nb = pp / GC_B;
@@ -551,14 +558,25 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
     const bool factor = w == 0;
     const int wk = gc_worker(w);                  // worker index, -1: not a worker
     const double* Cyy = C + (long)R * p;
-    // staging: zero the padding, then the worker's gain row and Cyy (each
-    // warp rows w, w + 12, ..., the lanes their columns) in rounds of two rows
-    // per warp (measured faster than one round of every row)
-    if (pp > p)
+    // staging.  With cyy32 (Cyy already in FP32 rows of ld, written by the
+    // finalisation) one bulk copy brings the whole [pp][ld] block; otherwise
+    // zero the padding, then the worker's gain row and Cyy (each warp rows w,
+    // w + 12, ..., the lanes their columns) in rounds of two rows per warp
+    // (measured faster than one round of every row)
+    const uint32_t cbytes = (uint32_t)(sizeof(float) * pp * ld);   // a multiple of 32 (pp of 8)
+    if (cyy32 != nullptr) {
+        if (tid == 0) {
+            tc::mbar_init(&cmb, 1);
+            tc::fence_mbar_init();
+            tf32::st_expect_tx(&cmb, cbytes);
+            tf32::st_bulk(tc::smem_u32(A), cyy32, cbytes, &cmb);
+        }
+    } else if (pp > p) {
         for (int e = tid; e < pp * ld; e += GC_T) {
             const int i = e / ld, c = e % ld;
             if (i >= p || c >= p) A[e] = 0.f;
         }
+    }
     const int a = blockIdx.x * GC_R + wk;
     const bool mine = wk >= 0 && wk < GC_R && a < R;
     float b[SL];
@@ -570,7 +588,7 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
             const int i = lane + 32 * s;
             g[s] = mine && i < p ? __ldg(C + (long)a * p + i) : 0.0;
         }
-        for (int i0 = w; i0 < p; i0 += GC_NW * RW) {
+        for (int i0 = w; cyy32 == nullptr && i0 < p; i0 += GC_NW * RW) {
             double v[RW * SL];
 #pragma unroll
             for (int u = 0; u < RW * SL; ++u) {
@@ -586,7 +604,37 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
 #pragma unroll
         for (int s = 0; s < SL; ++s) b[s] = (float)g[s];
     }
+    // the gain rows that read K = 0: the update leaves the ensemble as it is
+    auto zero_gain = [&]() {
+        if (mine) {
+            for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
+            if (Aop != nullptr) {
+                char* t0 = reinterpret_cast<char*>(Aop) + (size_t)(a >> 7) * SL * 2 * GC_TILE;
+                const int off = tf32::swz(a & 127, lane >> 2) + (lane & 3) * 4;
+                for (int s = 0; s < 2 * SL; ++s) *reinterpret_cast<float*>(t0 + (size_t)s * GC_TILE + off) = 0.f;
+            }
+        }
+    };
     __syncthreads();
+    if (cyy32 != nullptr) {
+        // every thread waits for the copy (bounded); on a timeout thread 0
+        // waits once more for the copy in flight before the CTA leaves
+        if (__syncthreads_or(!tc::mbar_wait_bounded(&cmb, 0u, GC_WAIT))) {
+            if (tid == 0) {
+                atomicExch(status, DEV_TIMEOUT);
+                tc::mbar_wait_bounded(&cmb, 0u, GC_WAIT);
+            }
+            zero_gain();
+            return;
+        }
+        if (pp > p) {                             // the padding rows and columns read zero
+            for (int e = tid; e < pp * ld; e += GC_T) {
+                const int i = e / ld, c = e % ld;
+                if (i >= p || c >= p) A[e] = 0.f;
+            }
+            __syncthreads();
+        }
+    }
     bool fbad = false;                            // the factor warp: a panel failed
     if (factor) fbad = factor_panel<SL>(0, p, pp, ld, lane, A, rinv);
     // one CTA barrier per panel; it also tells every thread whether a panel failed
@@ -649,14 +697,7 @@ gain_chol_kernel(const double* __restrict__ C, int R, int p, float* __restrict__
     }
     if (failed) {                                 // K = 0: the update leaves the ensemble as it is
         if (tid == 0) atomicExch(status, DEV_NOTSPD);
-        if (mine) {
-            for (int i = lane; i < p; i += 32) Kt[(long)i * R + a] = 0.f;
-            if (Aop != nullptr) {
-                char* t0 = reinterpret_cast<char*>(Aop) + (size_t)(a >> 7) * SL * 2 * GC_TILE;
-                const int off = tf32::swz(a & 127, lane >> 2) + (lane & 3) * 4;
-                for (int s = 0; s < 2 * SL; ++s) *reinterpret_cast<float*>(t0 + (size_t)s * GC_TILE + off) = 0.f;
-            }
-        }
+        zero_gain();
         return;
     }
     if (!mine) return;
@@ -714,7 +755,8 @@ size_t gain_chol_smem(int p)
 }
 
 template <int SL>
-void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st, float* Aop)
+void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cudaStream_t st, float* Aop,
+                      const float* cyy32)
 {
     const size_t smem = gain_chol_smem(p);
     static DeviceOnce attr_set;
@@ -723,7 +765,7 @@ void gain_chol_launch(const double* C, int R, int p, float* Kt, int* status, cud
                                     (int)gain_chol_smem(32 * SL)) == cudaSuccess;
     });
     const int grid = R > 0 ? (R + GC_R - 1) / GC_R : 1;
-    pdl_launch(gain_chol_kernel<SL>, grid, GC_T, smem, st, C, R, p, Kt, status, Aop);
+    pdl_launch(gain_chol_kernel<SL>, grid, GC_T, smem, st, C, R, p, Kt, status, Aop, cyy32);
 }
 
 // ---------------------------------------------------------------- update
@@ -919,43 +961,53 @@ void launch_s1_reduce(const float* part1, int splits, int M, int m, void* S1, cu
 }
 
 void launch_cov_finalize_rows(const float* part2, const void* S1_left, const void* S1_obs, int splits, int M, int p,
-                              int m, int N, double* C, cudaStream_t st, bool f64, double scale, bool obs_t)
+                              int m, int N, double* C, cudaStream_t st, bool f64, double scale, bool obs_t,
+                              float* cyy32, int R)
 {
     const int so_c = obs_t ? 1 : m, so_j = obs_t ? p : 1;
     const int total = M * p;
+    const int ld32 = gain_chol_ld(p);
     if (f64)
         plain_launch(cov_finalize_kernel<true>, (total + 31) / 32, 256, 0, st, part2,
                      static_cast<const double*>(S1_left), static_cast<const double*>(S1_obs), splits, M, p, m, N, C,
-                     scale, so_c, so_j);
+                     scale, so_c, so_j, cyy32, R, ld32);
     else
         plain_launch(cov_finalize_kernel<false>, (total + 31) / 32, 256, 0, st, part2,
                      static_cast<const float*>(S1_left), static_cast<const float*>(S1_obs), splits, M, p, m, N, C,
-                     scale, so_c, so_j);
+                     scale, so_c, so_j, cyy32, R, ld32);
 }
 
 void launch_cov_finalize(const float* part2, const void* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st, bool f64, double scale, const void* S1oT)
+                         cudaStream_t st, bool f64, double scale, const void* S1oT, float* cyy32)
 {
     if (S1 != nullptr && S1oT != nullptr) {
-        launch_cov_finalize_rows(part2, S1, S1oT, splits, R + p, p, m, N, C, st, f64, scale, true);
+        launch_cov_finalize_rows(part2, S1, S1oT, splits, R + p, p, m, N, C, st, f64, scale, true, cyy32, R);
         return;
     }
     const void* S1o = S1 == nullptr ? nullptr
                       : f64 ? static_cast<const void*>(static_cast<const double*>(S1) + (size_t)R * m)
                             : static_cast<const void*>(static_cast<const float*>(S1) + (size_t)R * m);
-    launch_cov_finalize_rows(part2, S1, S1o, splits, R + p, p, m, N, C, st, f64, scale);
+    launch_cov_finalize_rows(part2, S1, S1o, splits, R + p, p, m, N, C, st, f64, scale, false, cyy32, R);
 }
 
 
-void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop)
+void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop,
+                 const float* cyy32)
 {
     switch ((p + 31) / 32) {
-    case 1: gain_chol_launch<1>(C, R, p, K, status, st, Aop); break;
-    case 2: gain_chol_launch<2>(C, R, p, K, status, st, Aop); break;
-    case 3: gain_chol_launch<3>(C, R, p, K, status, st, Aop); break;
-    case 4: gain_chol_launch<4>(C, R, p, K, status, st, Aop); break;
-    default: gain_chol_launch<5>(C, R, p, K, status, st, Aop); break;
+    case 1: gain_chol_launch<1>(C, R, p, K, status, st, Aop, cyy32); break;
+    case 2: gain_chol_launch<2>(C, R, p, K, status, st, Aop, cyy32); break;
+    case 3: gain_chol_launch<3>(C, R, p, K, status, st, Aop, cyy32); break;
+    case 4: gain_chol_launch<4>(C, R, p, K, status, st, Aop, cyy32); break;
+    default: gain_chol_launch<5>(C, R, p, K, status, st, Aop, cyy32); break;
     }
+}
+
+int gain_chol_ld(int p) { return ((p + GC_B - 1) & ~(GC_B - 1)) | 1; }
+size_t gain_cyy32_bytes(int p)
+{
+    const int pp = (p + GC_B - 1) & ~(GC_B - 1);
+    return sizeof(float) * (size_t)pp * (pp | 1);
 }
 
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,

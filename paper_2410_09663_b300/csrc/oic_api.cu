@@ -68,6 +68,7 @@ struct Layout {
     size_t cG, ccols, ch;
     size_t plantX, plantU, plantTmp;
     size_t xk, uprev, xref, uref, noise, uhat, xhat, uapp, xnext;
+    size_t cyy32;                     // the FP32 gain's copy of Sigma^Y (FP32 mode)
     size_t total;
 };
 
@@ -244,6 +245,7 @@ void compute_layout(oic_handle* h)
     L.D = take(sizeof(float) * N * p * m);
     L.C = take(sizeof(double) * (Ra + p) * p);
     L.K = take(sizeof(float) * Ra * p);
+    L.cyy32 = take(c.precision == OIC_PREC_MIXED ? 0 : gain_cyy32_bytes((int)p));
     L.L64 = take(c.precision == OIC_PREC_MIXED ? sizeof(double) * (p * p + p) : 0);
     // tensor-core anomaly products: the pre-split observation tiles
     L.tB = take(stats_tc_supported(c.m, (int)p) ? stats_tc_bbytes(c.N, (int)p, c.m) : 0);
@@ -362,6 +364,8 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
     const bool tcs = stats_tc_supported(c.m, p);
     const bool utc = tcs && update_tc_supported(c.m, p);
     float* Bd = utc ? h->at<float>(h->lay.tBd) : nullptr;
+    // the FP32 gain stages Sigma^Y from an FP32 copy in its own layout
+    float* cyy32 = !mixed && gain_cyy32_bytes(p) <= gain_cyy32_bytes(h->p) ? h->at<float>(h->lay.cyy32) : nullptr;
     if (tcs) {
         const int splits = plan_splits(h, stats_tc_splits(M, c.N));
         run_stage(h, OIC_STAGE_COV, [&] {
@@ -370,7 +374,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
         });
         run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R, mixed); });
         run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
-            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T);
+            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T, cyy32);
         });
     } else {
         const int splits = plan_splits(h, stats_splits(R, p, c.N));
@@ -379,7 +383,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
         });
         run_stage(h, OIC_STAGE_MEANS, [&] { launch_s1_reduce(part1, splits, M, c.m, S1, h->st, S1T, R, mixed); });
         run_stage(h, OIC_STAGE_COV_REDUCE, [&] {
-            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T);
+            launch_cov_finalize(part2, S1, splits, R, p, c.m, c.N, C, h->st, mixed, 1.0, S1T, cyy32);
         });
     }
     run_stage(h, OIC_STAGE_GAIN, [&] {
@@ -388,7 +392,7 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
                           h->at<int>(h->lay.status), h->st);
         else
             launch_gain(C, R, p, Kt, h->at<int>(h->lay.status), h->st,
-                        utc ? h->at<float>(h->lay.tAop) : nullptr);
+                        utc ? h->at<float>(h->lay.tAop) : nullptr, cyy32);
     });
     if (utc)
         run_stage(h, OIC_STAGE_UPDATE, [&] {

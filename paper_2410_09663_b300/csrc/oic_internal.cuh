@@ -158,15 +158,23 @@ void launch_stats(const float* E, long ms, int N, int m, RowSet act, RowSet obs,
 void launch_s1_reduce(const float* part1, int splits, int M, int m, void* S1, cudaStream_t st,
                       void* S1oT = nullptr, int R = 0, bool f64 = false);
 // C = scale (sum_s part2 - S1 S1_Y^T / N)  ([(R + p) x p], Cxy on top, Cyy below).
-// (S1 and S1oT in FP64 when f64)
+// (S1 and S1oT in FP64 when f64).  With cyy32, Cyy is also written as FP32
+// rows of gain_chol_ld(p) floats (cyy32 holds gain_cyy32_bytes(p); entries
+// beyond p are left as they are).
 void launch_cov_finalize(const float* part2, const void* S1, int splits, int R, int p, int m, int N, double* C,
-                         cudaStream_t st, bool f64 = false, double scale = 1.0, const void* S1oT = nullptr);
+                         cudaStream_t st, bool f64 = false, double scale = 1.0, const void* S1oT = nullptr,
+                         float* cyy32 = nullptr);
 // The same for M left rows whose split sums part2 [splits][M][p] hold alone:
 // C[a][c] = scale (sum_s part2[s][a][c] - S1_left[a] . S1_obs[c] / N); obs_t:
-// S1_obs is transposed, [m][p] (coalesced reads; launch_s1_reduce's S1oT).
+// S1_obs is transposed, [m][p] (coalesced reads; launch_s1_reduce's S1oT);
+// cyy32: the FP32 copy of rows R.. as above.
 void launch_cov_finalize_rows(const float* part2, const void* S1_left, const void* S1_obs, int splits, int M, int p,
                               int m, int N, double* C, cudaStream_t st, bool f64 = false, double scale = 1.0,
-                              bool obs_t = false);
+                              bool obs_t = false, float* cyy32 = nullptr, int R = 0);
+// The FP32 gain's shared-memory layout of Cyy: rows of gain_chol_ld(p)
+// floats, gain_cyy32_bytes(p) in all (p rounded up to whole panels).
+int gain_chol_ld(int p);
+size_t gain_cyy32_bytes(int p);
 // Anomaly products on the tensor cores (TF32 hi / lo split, one pass over
 // the ensemble): part1 / part2 as launch_stats writes them, so the same
 // s1 reduction and finalisation follow.  Bop: stats_tc_bbytes of scratch.
@@ -206,8 +214,10 @@ void launch_gain64(const double* C, int R, int p, double* L, int* bad, float* Kt
 void launch_chol64(const double* C, int R, int p, double* L, int* bad, int* status, cudaStream_t st);
 void launch_solve64(const double* C, int R, int p, const double* L, const int* bad, float* Kt, cudaStream_t st);
 // Kt = (Cxy Cyy^{-1})^T, [p][R] (FP32 Cholesky, p <= 160); with Aop also the
-// member update's TF32 operand tiles of the gain.
-void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop = nullptr);
+// member update's TF32 operand tiles of the gain; with cyy32 (the
+// finalisation's FP32 copy of Cyy) Cyy is staged by one bulk copy.
+void launch_gain(const double* C, int R, int p, float* K, int* status, cudaStream_t st, float* Aop = nullptr,
+                 const float* cyy32 = nullptr);
 // E^i[act rows] += K D^i for every member.
 void launch_update(float* E, long ms, int N, int m, RowSet act, const float* Kt, int p, const float* Dbuf,
                    cudaStream_t st);
