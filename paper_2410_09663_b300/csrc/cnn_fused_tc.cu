@@ -270,23 +270,6 @@ __device__ __forceinline__ void issue_last(uint32_t acc, uint32_t a, uint32_t b)
     }
 }
 
-// Bounded wait with back-off: a warp whose phase is not complete yet sleeps
-// between polls (8 ns doubling up to 64 ns) instead of polling the barrier
-// back to back, leaving issue slots and the barrier's shared-memory word to
-// the warps that are working.
-__device__ __forceinline__ bool wait_backoff(uint64_t* mbar, uint32_t parity, long long max_cycles)
-{
-    if (tc::mbar_try_wait(mbar, parity)) return true;
-    const long long t0 = clock64();
-    unsigned ns = 8;
-    do {
-        __nanosleep(ns);
-        if (ns < 64) ns += ns;
-        if (tc::mbar_try_wait(mbar, parity)) return true;
-    } while (clock64() - t0 <= max_cycles);
-    return false;
-}
-
 // mbarriers in the MISC region (8 bytes each); [2] = by row parity
 enum : int {
     MB_F = 0,          // [2] first layer of row f done (tensor core -> drain warps)
@@ -360,7 +343,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
     uint32_t ph = 0;                                    // this thread's phase bit per mbarrier
     bool failed = false;
     auto wait = [&](int i) {
-        if (!wait_backoff(mb + i, (ph >> i) & 1u, F_WAIT)) {
+        if (!tc::mbar_wait_backoff(mb + i, (ph >> i) & 1u, F_WAIT)) {
             failed = true;
             atomicExch(err, DEV_TIMEOUT);
         }

@@ -281,7 +281,7 @@ conv_bf16_kernel(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict
     uint64_t ph = 0;                                    // this thread's phase bit per mbarrier
     bool failed = false;
     auto wait = [&](int i) {
-        if (!tc::mbar_wait_bounded(mb + i, (uint32_t)((ph >> i) & 1ull), B_WAIT)) {
+        if (!tc::mbar_wait_backoff(mb + i, (uint32_t)((ph >> i) & 1ull), B_WAIT)) {
             failed = true;
             atomicExch(err, DEV_TIMEOUT);
         }
@@ -463,7 +463,7 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
     uint64_t ph = 0;
     bool failed = false;
     auto wait = [&](int i) {
-        if (!tc::mbar_wait_bounded(mb + i, (uint32_t)((ph >> i) & 1ull), B_WAIT)) {
+        if (!tc::mbar_wait_backoff(mb + i, (uint32_t)((ph >> i) & 1ull), B_WAIT)) {
             failed = true;
             atomicExch(err, DEV_TIMEOUT);
         }
@@ -765,7 +765,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
     uint32_t ph = 0;
     bool failed = false;
     auto wait = [&](int i) {
-        if (!tc::mbar_wait_bounded(mb + i, (ph >> i) & 1u, B_WAIT)) {
+        if (!tc::mbar_wait_backoff(mb + i, (ph >> i) & 1u, B_WAIT)) {
             failed = true;
             atomicExch(err, DEV_TIMEOUT);
         }

@@ -134,6 +134,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parit
     return true;
 }
 
+// The same wait with back-off: while the phase is not complete the thread
+// sleeps between polls (NS0 ns doubling up to NS1 ns) instead of polling the
+// barrier back to back, which leaves issue slots and the barrier's shared-
+// memory word to the warps that are working.  Still bounded by max_cycles.
+template <unsigned NS0 = 8, unsigned NS1 = 64>
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* mbar, uint32_t parity, long long max_cycles)
+{
+    if (mbar_try_wait(mbar, parity)) return true;
+    const long long t0 = clock64();
+    unsigned ns = NS0;
+    do {
+        __nanosleep(ns);
+        if (ns < NS1) ns += ns;
+        if (mbar_try_wait(mbar, parity)) return true;
+    } while (clock64() - t0 <= max_cycles);
+    return false;
+}
+
 // Tensor memory: allocation by one full warp; the base address is written to
 // shared memory.  ncols is a power of two >= 32.
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
