@@ -70,7 +70,10 @@ __device__ __forceinline__ void cl_arrive(uint32_t mbar_cluster_addr)
 __device__ __forceinline__ bool cl_wait(uint64_t* mbar, uint32_t parity, long long max_cycles)
 {
     const long long t0 = clock64();
+    unsigned ns = 0;                                    // sleep between polls, 8 ns doubling to 64 ns
     for (;;) {
+        if (ns) __nanosleep(ns);
+        ns = ns == 0 ? 8 : ns < 64 ? 2 * ns : 64;
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
