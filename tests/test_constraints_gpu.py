@@ -145,3 +145,47 @@ def test_constrained_working_size_tensor_path(cuda_ok):
     xh = oracle.enks_solve(onet(wl), wl.N, wl.H, wl.X0(), Up, xr, ur, nz, ocons(wc.cons))
     assert rel(U_hat, xh[:, wl.n:wl.n + wl.l]) <= TOL
     s.close()
+
+
+def test_analyses_of_different_observation_counts_on_one_handle(cuda_ok):
+    """One constrained handle alternates constrained solves (p = n + l + c
+    observed rows: 42 here, Sigma^Y staged for the FP32 gain as 48 rows of 49)
+    with a plain analysis through oic_enks_update (p = n + l = 36: 40 rows of
+    41), so the staged copy of Sigma^Y changes layout from call to call over
+    the same buffer.  Each result must match the oracle: a call may read only
+    its own rows, whatever the previous call left behind."""
+    import torch
+
+    wl = MID
+    wc = wl.with_(cons=affine(wl, 6, 3))
+    s = solver(wc)
+    Up = np.zeros((wl.l, wl.m), np.float32)
+    ur = np.full((wl.l, wl.m), 0.2, np.float32)
+    net, cons = onet(wl), ocons(wc.cons)
+
+    def constrained(k):
+        xr, nz = wl.X_ref_window(k), wc.noise(k)
+        U_hat = np.zeros((wl.H + 1, wl.l, wl.m), np.float32)
+        s.oic_solve_host(wl.X0(), Up, xr, ur, nz, U_hat)
+        xh = oracle.enks_solve(net, wl.N, wl.H, wl.X0(), Up, xr, ur, nz, cons)
+        assert rel(U_hat, xh[:, wl.n:wl.n + wl.l]) <= TOL
+
+    def plain(seed):
+        rng = np.random.default_rng(seed)
+        R, p = 45, wl.n + wl.l
+        E = (1.0 + 0.05 * rng.standard_normal((wl.N, R, wl.m))).astype(np.float32)
+        obs = np.sort(rng.choice(R, size=p, replace=False))
+        V = (0.02 * rng.standard_normal((wl.N, p, wl.m))).astype(np.float32)
+        Ybar = (1.2 + 0.1 * rng.standard_normal((p, wl.m))).astype(np.float32)
+        Ed = torch.from_numpy(E).cuda()
+        s.oic_enks_update(Ed, obs, torch.from_numpy(V).cuda(), torch.from_numpy(Ybar).cuda())
+        s.oic_sync()
+        got = Ed.cpu().numpy()
+        want = oracle.enks_analysis(E, E[:, obs, :] + V, Ybar)
+        assert rel(got - E, want - E) <= TOL
+
+    constrained(1)
+    plain(11)
+    constrained(2)
+    plain(12)
+    s.close()
