@@ -696,7 +696,7 @@ struct FBS {
     static constexpr int OFF_W1 = OFF_A1 + NA1 * IN1;
     static constexpr int OFF_BIAS = OFF_W1 + S1::BBYTES;    // b0[C], b1[C]
     static constexpr int OFF_MISC = OFF_BIAS + 2 * C * 4;
-    static constexpr int OFF_DYN = OFF_MISC + 256;          // U of the group [G][m][l], then B [n][l]
+    static constexpr int OFF_DYN = OFF_MISC + 256;          // U of the group [l][m G], then B [n][l]
     static constexpr int NDW = 16, NPW = 4;
     static constexpr int PROD_WARP0 = NDW, ISSUE_WARP = NDW + NPW;
     static constexpr int NT = 32 * (ISSUE_WARP + 1);
@@ -724,7 +724,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem + F::OFF_MISC);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + F::OFF_MISC + FB_COUNT * 8);
     float* sbias = reinterpret_cast<float*>(smem + F::OFF_BIAS);
-    float* su = reinterpret_cast<float*>(smem + F::OFF_DYN);                 // [G][m][l]
+    float* su = reinterpret_cast<float*>(smem + F::OFF_DYN);                 // [l][m G]
     float* sB = su + G * l * m;                                             // [n][l]
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const uint32_t s0 = tc::smem_u32(smem);
@@ -823,12 +823,15 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
             __syncwarp();
         } else if (warp >= F::PROD_WARP0) {
             // ============ first-layer input rows: [X, B U] at each position ============
+            // U of the group staged control-major, [l][position] (position xx G + b
+            // for member b, pixel xx): for one control the 128 positions' values are
+            // consecutive words, so the B U loop's loads are free of bank conflicts
             const int pt = tid - 32 * F::PROD_WARP0;            // position G + pt
             for (int e = pt; e < G * l * m; e += 32 * F::NPW) {
                 const int b = e / (l * m), rr = e % (l * m), c = rr / m, xx = rr % m;
                 const int mbr = g * G + b;
                 const float uv = mbr < Nb ? U[(long)mbr * u_ms + rr] : 0.f;
-                su[(b * m + xx) * l + c] = uv;
+                su[c * (G * m) + xx * G + b] = uv;
             }
             tc::named_bar(2, 32 * F::NPW);
             const int pb = pt % G, px = pt / G, pmb = g * G + pb;
@@ -838,9 +841,9 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                 float xv = 0.f, bu = 0.f;
                 if (live) {
                     xv = X[(long)pmb * x_ms + (long)f * m + px];
-                    const float* ub = su + (pb * m + px) * l;
+                    const float* ub = su + pt;                   // px G + pb = pt
                     const float* bb = sB + f * l;
-                    for (int c = 0; c < l; ++c) bu = fmaf(bb[c], ub[c], bu);
+                    for (int c = 0; c < l; ++c) bu = fmaf(bb[c], ub[c * (G * m)], bu);
                 }
                 const __nv_bfloat162 v = __floats2bfloat162_rn(xv, bu);
                 *reinterpret_cast<uint4*>(smem + F::OFF_A0 + (f & 3) * F::IN0 + (G + pt) * 16) =
