@@ -144,7 +144,7 @@ oic_status oic_bind(oic_handle* h, void* dev_workspace, size_t bytes, void* cuda
  * previously applied control U_prev (l x m).  Device pointers. */
 oic_status oic_reset(oic_handle* h, const float* X0, const float* U_prev);
 
-/* One receding-horizon solve (Algorithm 1, lines 4-15) from X_k with the
+/* One receding-horizon solve (Algorithm 1 for one control step) from X_k with the
  * previously applied control U_prev.
  *   X_ref  [(H+1)][n][m] references for times k .. k+H (index 0 unused by the
  *          updates, kept so callers pass a whole window)
@@ -159,9 +159,9 @@ oic_status oic_reset(oic_handle* h, const float* X0, const float* U_prev);
 oic_status oic_solve(oic_handle* h, const float* X_k, const float* U_prev, const float* X_ref,
                      const float* U_ref, const float* noise, float* U_hat, float* X_hat);
 
-/* oic_solve with Algorithm 1's optional covariance steps executed (lines 8
- * and 11, which the paper lets be skipped because the update does not use
- * them): for s = 1 .. H (t = k + s)
+/* oic_solve with Algorithm 1's optional covariance steps executed (the
+ * predicted and the updated state covariance, which the paper lets be skipped
+ * because the update does not use them): for s = 1 .. H (t = k + s)
  *   Sigma_pred slot s-1: Sigma^X_{t|t-1} after the prediction to t, whose last
  *                        block row / column are Sigma^{X̄}_{t|t-1} and
  *                        Sigma^{X X̄}_{t|t-1} (Eq. (prediction-cov) ..
@@ -187,7 +187,7 @@ size_t oic_cov_scratch_bytes(const oic_handle* h);
 /* Rows kept at s (1 .. H; 0 otherwise). */
 int oic_cov_rows(const oic_handle* h, int s);
 
-/* One control step (Algorithm 1, lines 4-17) on the device-resident plant:
+/* One control step (Algorithm 1: a solve, then U_k applied) on the device-resident plant:
  * solve from the plant state, apply U_k = Û_{k|k:k+H} to the plant
  * X_{k+1} = CNN_theta(X_k, U_k) (the plant is the surrogate itself), and
  * keep U_k as the next step's U_prev.  U_applied [l][m] and X_next [n][m]
@@ -232,7 +232,7 @@ int oic_max_rows(const oic_handle* h);
  * events themselves. */
 typedef enum {
     OIC_STAGE_NOISE = 0,       /* Philox noise for one solve                    */
-    OIC_STAGE_INIT,            /* Algorithm 1 line 4                            */
+    OIC_STAGE_INIT,            /* Algorithm 1, ensemble initialisation          */
     OIC_STAGE_CNN_INPUT,       /* [X; B U] assembly, Eq. (1)                    */
     OIC_STAGE_CONV_FIRST,      /* first conv layer (2 input channels), tanh     */
     OIC_STAGE_CONV_HIDDEN,     /* hidden -> hidden conv layers, tanh            */

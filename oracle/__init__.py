@@ -285,7 +285,7 @@ def noise_floats(n, m, l, N, H, c=0):
 
 
 def enks_solve(net: Net, N, H, X_k, U_prev, X_ref, U_ref, noise, cons: Cons | None = None):
-    """One receding-horizon solve (Algorithm 1 lines 4-15) with full history,
+    """One receding-horizon solve (Algorithm 1, one control step) with full history,
     with the constraint rows of `cons` appended to the pseudo-observation.
 
     Returns Xbar_hat [(H+1)][q][m]: smoothed means of blocks k..k+H."""

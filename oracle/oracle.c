@@ -363,7 +363,8 @@ void oracle_constraint_obs(const oracle_cons *cs, int n, int l, int m, const dou
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1, lines 4-15, for one control step k.
+/* Algorithm 1 for one control step k (initialise, predict and update over the
+   horizon, smoothed means).
  *
  * Augmented state X̄ = [X; U; dU] has q = n + 2l rows; the pseudo-observation
  * Ȳ = [X^ref; U^ref] has p = n + l rows and H = [I 0 0; 0 I 0].
@@ -409,7 +410,7 @@ int oracle_enks_solve_cov(const oracle_net *net, int N, int H, const double *X_k
     double *Ybar = malloc(sizeof(double) * (size_t)p * m);
     if (!hist || !Y || !Ybar) { free(hist); free(Y); free(Ybar); return -1; }
 
-    /* line 4: initialise X̄^i_{k|k} */
+    /* Algorithm 1's initialisation of X̄^i_{k|k} */
     for (int i = 0; i < N; ++i) {
         double *blk = hist + i * xs;
         const double *w0 = W0 + (size_t)i * l * m;
@@ -422,7 +423,7 @@ int oracle_enks_solve_cov(const oracle_net *net, int N, int H, const double *X_k
 
     int status = 0;
     for (int s = 1; s <= H; ++s) {                    /* t = k + s        */
-        /* line 6, Eq. (prediction-samplewise):
+        /* prediction, Eq. (prediction-samplewise):
          * X̄^i_{t|t-1} = f_CNN(X̄^i_{t-1|t-1}) + W̄^i_{t-1}               */
         const double *Ws = W + (size_t)(s - 1) * N * l * m;
         int err = 0;
@@ -438,10 +439,10 @@ int oracle_enks_solve_cov(const oracle_net *net, int N, int H, const double *X_k
             }
         }
         if (err) { status = -1; break; }
-        /* line 7, Eq. (prediction-concatenate): script-X^i = blocks 0..s,
+        /* Eq. (prediction-concatenate): script-X^i = blocks 0..s,
          * which is the contiguous prefix of hist for member i.              */
 
-        /* line 9, Eq. (Ybar-samples): Y^i = H X̄^i_t + V̄^i_t               */
+        /* Eq. (Ybar-samples): Y^i = H X̄^i_t + V̄^i_t                       */
         const double *VXs = VX + (size_t)(s - 1) * N * n * m;
         const double *VUs = VU + (size_t)(s - 1) * N * l * m;
         for (int i = 0; i < N; ++i) {
@@ -461,7 +462,7 @@ int oracle_enks_solve_cov(const oracle_net *net, int N, int H, const double *X_k
         memcpy(Ybar + (size_t)n * m, U_ref, sizeof(double) * (size_t)l * m);
         memset(Ybar + (size_t)(n + l) * m, 0, sizeof(double) * (size_t)nc * m);
 
-        /* lines 9-10, Eq. (Ybar-sample-mean-cov), Eq. (ensemble-based-
+        /* Eq. (Ybar-sample-mean-cov), Eq. (ensemble-based-
          * Kalman-update): update every block 0..s of every member.          */
         const int Rs = (s + 1) * q;
         const size_t slot = (size_t)(H + 1) * q * (size_t)(H + 1) * q;
@@ -477,7 +478,7 @@ int oracle_enks_solve_cov(const oracle_net *net, int N, int H, const double *X_k
         }
     }
 
-    /* line 15: smoothed means of all blocks */
+    /* Algorithm 1's output: smoothed means of all blocks */
     if (status == 0) {
         memset(Xbar_hat, 0, sizeof(double) * (size_t)(H + 1) * bq);
         for (int i = 0; i < N; ++i)
@@ -503,7 +504,7 @@ int oracle_enks_solve(const oracle_net *net, int N, int H, const double *X_k,
     return oracle_enks_solve_c(net, N, H, X_k, U_prev, X_ref, U_ref, noise, NULL, Xbar_hat);
 }
 
-/* Algorithm 1, lines 3-19, for S control steps with the plant taken to be
+/* Algorithm 1's receding-horizon loop for S control steps with the plant taken to be
  * CNN_theta itself (no model mismatch, no plant noise):
  *   solve at k -> U_k = smoothed U block at time k -> X_{k+1} = CNN(X_k, U_k).
  * Inputs: X_0 (n x m), U_init (U_{-1}, l x m), X_ref_all ((S+H) + 1 blocks of

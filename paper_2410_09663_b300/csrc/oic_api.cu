@@ -404,7 +404,8 @@ void analysis(oic_handle* h, float* E, long ms, RowSet act, RowSet obs, ObsNoise
         run_stage(h, OIC_STAGE_UPDATE, [&] { launch_update(E, ms, c.N, c.m, act, Kt, p, D, h->st); });
 }
 
-// Algorithm 1's optional covariance steps (lines 8 and 11): where to write
+// Algorithm 1's optional covariance steps (the predicted and the updated state
+// covariance): where to write
 // them and the scratch the products use.
 struct CovOut {
     double lambda = 1.0;
@@ -565,7 +566,7 @@ oic_status step_impl(oic_handle* h, const float* X_ref, const float* U_ref, cons
     oic_status s = solve_impl(h, pX, pU, X_ref, U_ref, noise, uhat,
                               h->full() ? h->at<float>(h->lay.xhat) : nullptr, nullptr, pU, U_applied);
     if (s != OIC_OK) return s;
-    // Algorithm 1, lines 15-17: apply U_k = Û_{k|k:k+H} to the plant, then
+    // Algorithm 1, end of the control step: apply U_k = Û_{k|k:k+H} to the plant, then
     // X_k <- X_{k+1} (and X_next) in one launch
     cnn_forward(h, 1, pX, 0, uhat, 0, tmp, 0);
     launch_copy2(tmp, pX, X_next, (int)(n * m), h->st);

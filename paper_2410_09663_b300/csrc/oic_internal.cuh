@@ -139,7 +139,7 @@ void launch_conv_out_residual(const float* in, int Cin, const float* Xin, long x
                               const float* bias, float rs, cudaStream_t st);
 
 // ---------------------------------------------------------------- EnKS
-// Algorithm 1 line 4: E[i][x_row0 ..] = X_k, E[i][u_row0 ..] = U_prev + W0^i.
+// Algorithm 1's ensemble initialisation: E[i][x_row0 ..] = X_k, E[i][u_row0 ..] = U_prev + W0^i.
 void launch_ensemble_init(float* E, long ms, int N, int n, int m, int l, int x_row0, int u_row0,
                           const float* X_k, const float* U_prev, NoiseSrc W0, cudaStream_t st);
 // E[i][u_to rows] = E[i][u_from rows] + W^i (l x m per member).
