@@ -50,6 +50,8 @@ constexpr int FM = 128;                                 // tile rows (pixels)
 constexpr int BAR_DRAIN = 1;                            // named barrier of the drain warps (segment start)
 constexpr int BAR_E3 = 2;                               // named barrier of the last-layer warps
 constexpr int E3_WARP0 = 16;                            // warps 16-19 finish the last layer
+constexpr int E3_ISSUE = E3_WARP0 + 1;                  // the one of them that issues its MMAs (warp 17:
+                                                        // not on the main issuing warp's scheduler)
 constexpr int ISSUE_WARP = 20;
 constexpr long long F_WAIT = 4000000000LL;
 
@@ -407,7 +409,7 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
             const uint32_t dH2 = desc_lo(s0 + S::OFF_H2 + G * 16, S::PLANE);      // hidden rows, centre (A)
             const uint32_t dB3 = desc_lo(s0 + S::OFF_B3, 32 * 16);                // last-layer tiles (B)
             for (int h = r_lo; h <= r_hi; ++h) {
-                if (warp == E3_WARP0) {
+                if (warp == E3_ISSUE) {
                     // hidden row h in its buffer; its accumulator buffer was read
                     // out for row h-2 by all four warps before the last barrier
                     wait_w(MB_W2 + (h & 1));
