@@ -475,11 +475,13 @@ cnn_fused_kernel(const float* __restrict__ X, long x_ms, const float* __restrict
             }
             tc::named_bar(BAR_DRAIN, ND);
 
-            // warps 4-7 build the first-layer operands: thread p owns position
+            // four drain warps build the first-layer operands: thread p owns position
             // G + p (member p % G, pixel p / G) and keeps [X, B U] of the three
             // rows it needs in registers
-            const bool f_role = tid >= FM && tid < 2 * FM;
-            const int fp = f_role ? tid - FM : 0;
+            // (drain warps 2, 3, 6 and 7: on schedulers 2 and 3, away from the two
+            // MMA-issuing warps on schedulers 0 and 1)
+            const bool f_role = (warp & 2) != 0 && warp < 8;
+            const int fp = f_role ? tid - (warp < 4 ? 64 : 128) : 0;
             const int f_b = fp % G, f_x = fp / G, f_mb = g * G + f_b;
             auto fetch_x = [&](int r) -> float {
                 return (f_role && r >= 0 && r < n && f_mb < Nb) ? X[(long)f_mb * x_ms + (long)r * m + f_x] : 0.f;
