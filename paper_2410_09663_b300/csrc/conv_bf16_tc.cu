@@ -698,8 +698,11 @@ struct FBS {
     static constexpr int OFF_MISC = OFF_BIAS + 2 * C * 4;
     static constexpr int OFF_DYN = OFF_MISC + 256;          // U of the group [l][m G], then B [n][l]
     static constexpr int NDW = 16, NPW = 4;
-    static constexpr int PROD_WARP0 = NDW, ISSUE_WARP = NDW + NPW;
-    static constexpr int NT = 32 * (ISSUE_WARP + 1);
+    // warp 20 issues the MMAs; the producers are warps 17, 18, 19 and 21, so that none
+    // shares the issuing warp's scheduler (20 mod 4 = 0); warp 16 has no role
+    static constexpr int ISSUE_WARP = 20;
+    static constexpr int NT = 32 * 22;
+    static_assert(NDW == 16 && NPW == 4, "warp roles");
     static constexpr int T_B = 4 * C;                   // ring B after ring A
     static_assert(8 * C <= 512, "tensor memory");
     static_assert(FB_COUNT * 8 + 4 <= 256, "barrier region");
@@ -821,12 +824,12 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
                     }
             }
             __syncwarp();
-        } else if (warp >= F::PROD_WARP0) {
+        } else if (warp >= 17) {
             // ============ first-layer input rows: [X, B U] at each position ============
             // U of the group staged control-major, [l][position] (position xx G + b
             // for member b, pixel xx): for one control the 128 positions' values are
             // consecutive words, so the B U loop's loads are free of bank conflicts
-            const int pt = tid - 32 * F::PROD_WARP0;            // position G + pt
+            const int pt = 32 * (warp == 21 ? 3 : warp - 17) + lane;    // position G + pt
             for (int e = pt; e < G * l * m; e += 32 * F::NPW) {
                 const int b = e / (l * m), rr = e % (l * m), c = rr / m, xx = rr % m;
                 const int mbr = g * G + b;
@@ -856,7 +859,7 @@ conv_bf16_first_kernel(const float* __restrict__ X, long x_ms, const float* __re
             // next segment starts with every slot free
             for (int f = f_hi - 3; f <= f_hi && !failed; ++f)
                 if (f >= f_lo) wait_w(FB_A0FREE + (f & 3));
-        } else {
+        } else if (warp < F::NDW) {
             // ============ drains (warps 0-15) ============
             const int q4 = warp & 3, cg = warp >> 2;
             const int ep = 32 * q4 + lane;
