@@ -28,11 +28,13 @@
 //                          through shared memory) and keep rolling sums over
 //                          output rows h+1, h, h-1
 //
-// Roles: one warp issues the MMAs (an elected lane each, operands warp-
+// Roles: one warp (20) issues the MMAs (an elected lane each, operands warp-
 // uniform) and waits only on "operand ready" /
 // "accumulator drained" mbarriers; 16 drain warps turn accumulators into the
-// next layer's operands (tanh, split, stores); 4 warps finish the last layer
-// (neighbour sums, residual, X_next).  Both wait on the MMA commit barriers.
+// next layer's operands (tanh, split, stores), four of them (2, 3, 6, 7) also
+// building the first layer's operand rows; 4 warps (16-19) finish the last
+// layer (neighbour sums, residual, X_next), warp 17 issuing its MMAs.  Both
+// wait on the MMA commit barriers.
 // Only X, U and the weights are read and X_next written (X_next must not
 // overlap X: neighbouring CTAs read halo rows of X).  The grid is persistent
 // over contiguous (group, row) ranges.

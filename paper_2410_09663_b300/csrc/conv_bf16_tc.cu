@@ -646,8 +646,9 @@ conv_bf16_fused_kernel(const __nv_bfloat16* __restrict__ in, const float* __rest
 
 // The first layer ([X, B U] -> C, tanh) fused with the second (C -> C, tanh):
 // the first layer's input rows are built in shared memory from X and U, and
-// its output rows never leave shared memory.  Warps 0-15 drain, warps 16-19
-// build input rows, one thread issues both layers' MMAs.  A segment owns the
+// its output rows never leave shared memory.  Warps 0-15 drain, warps 17, 18,
+// 19 and 21 build input rows, warp 20 issues both layers' MMAs (an elected
+// lane), warp 16 has no role: no builder shares the issuing warp's scheduler.  A segment owns the
 // second layer's output rows [ys, ye) of one member group; they need its
 // input rows (the first layer's outputs) [r_lo, r_hi] = [ys-1, ye] and those
 // need first-layer input rows [f_lo, f_hi] one further on each side (within
